@@ -1,0 +1,7 @@
+"""FP64 CPU oracle of the TV-deblurring PCG path (test infrastructure only).
+
+Only the tests, the package smoke check and the benchmark's CPU-baseline leg
+import this package. The CUDA library never does.
+"""
+from .tvd_oracle import *  # noqa: F401,F403
+from .tvd_oracle import AR, R, PC_NONE, PC_DIAG, PC_FAST, PC_DFAST  # noqa: F401

@@ -1,0 +1,495 @@
+"""Plain FP64 CPU oracle for the PCG inner step of lagged-diffusivity TV deblurring.
+
+TEST INFRASTRUCTURE ONLY. This module is the slow, obviously correct reference
+that the CUDA path is checked against. Only the test suite, the package smoke
+check and the benchmark's CPU-baseline leg may import it; the library itself
+never calls it and has no CPU fallback.
+
+Everything is float64 numpy/scipy, written from the paper's definitions
+(Bai, Donatelli, Serra-Capizzano, "Fast preconditioners for total variation
+deblurring with anti-reflective boundary conditions"):
+
+* boundary extension and blur: Sec. 2, eq. (blurred1d:matrixform), eq. (anti1d),
+  the reflective rule of Sec. 2 and the 2D corner formulas of Sec. 2;
+* lagged-diffusivity operator L(u) and the fixed-point step: Sec. 1, eqs. (el), (fp);
+* optimal preconditioners R, D_R (cosine algebra, eqs. (R), (D), (R2), (DR2)) and
+  M, D_M (sine algebra with hat-S, eqs. (M), (hats), the Proposition and the
+  2D section 3.2), with eigenvalues from eqs. (symb), (lambda), (gridy);
+* PCG: Golub & Van Loan, Algorithm 10.3.1, as cited in Sec. 1, with the stopping
+  rule ||r_k|| / ||r_0|| < tol of Sec. 5.
+
+Readings where the paper is silent or garbled (each also listed in the design doc):
+
+* L(u) is discretised as D_r^T W D_r + D_c^T W D_c with forward differences that
+  vanish on the last row / column (zero Neumann, eq. (el)), W = diag(psi^-1),
+  psi = sqrt(|D u|^2 + beta^2) per pixel, unit grid spacing.
+* The data term is read as 1/2 ||H u - v||^2; then eq. (fp) is exactly the
+  lagged-diffusivity stationarity condition of the functional below.
+* The AR transform T_n is sampled on y_i = (i-1) pi / (n-1), i = 1..n; the
+  eigenvalue for the last basis vector (y/pi) is h_hat(0) as eq. (gridy) orders it.
+* The cosine transform C is used as the frequency-by-space orthonormal DCT-II
+  (scipy's ``dct(type=2, norm='ortho')``), with the algebra {C^T Lambda C}.
+* Level-2 projections are computed as U^T diag(U A U^T) U with U the 2D
+  transform (equal to the Q-permuted level-2 construction of Sec. 3.2).
+* The diagonal ("D") preconditioner of the tables is D = I + alpha diag(L), eq. (D).
+* PCG uses the Fletcher-Reeves beta of Algorithm 10.3.1, the recursive
+  residual, and a strict ``<`` test after each residual update; ||r_0|| = 0
+  means zero iterations. The iteration count is the number of products with A.
+
+Index conventions: images are (n_rows, n_cols) float64 arrays, element (i, j)
+row-major. A PSF is a (2 m_r + 1, 2 m_c + 1) array with h[m_r + a, m_c + b] =
+h_{a,b}; it must be quadrantally symmetric for the fast preconditioners.
+"""
+from __future__ import annotations
+
+import numpy as np
+import scipy.fft as sfft
+
+AR = "ar"   # anti-reflective boundary conditions
+R = "r"     # reflective (Neumann) boundary conditions
+
+PC_NONE = "none"     # I: no preconditioner
+PC_DIAG = "diag"     # D = I + alpha diag(L(u)), eq. (D)
+PC_FAST = "fast"     # R (reflective) or M (anti-reflective), eqs. (R2), (M)
+PC_DFAST = "dfast"   # D_R = D^1/2 R D^1/2 or D_M = D^1/2 M D^1/2
+
+
+# --------------------------------------------------------------------------
+# Boundary extension, Sec. 2
+# --------------------------------------------------------------------------
+
+def _ext_index_1d(t: int, n: int, bc: str):
+    """Return [(index, coefficient), ...] giving x~_t as a combination of x_0..x_{n-1}.
+
+    0-based form of eq. (anti1d): x~_{-j} = 2 x_0 - x_j and
+    x~_{n-1+j} = 2 x_{n-1} - x_{n-1-j}; reflective rule of Sec. 2:
+    x~_{-j} = x_{j-1} and x~_{n-1+j} = x_{n-j}.
+    """
+    if 0 <= t < n:
+        return [(t, 1.0)]
+    if bc == AR:
+        if t < 0:
+            return [(0, 2.0), (-t, -1.0)]
+        return [(n - 1, 2.0), (2 * (n - 1) - t, -1.0)]
+    if bc == R:
+        if t < 0:
+            return [(-t - 1, 1.0)]
+        return [(2 * n - 1 - t, 1.0)]
+    raise ValueError(bc)
+
+
+def extend(x: np.ndarray, mr: int, mc: int, bc: str) -> np.ndarray:
+    """Extended image x~ of shape (n_r + 2 m_r, n_c + 2 m_c); x~[i+m_r, j+m_c] = x~_{i,j}.
+
+    Edges follow the 1D rules of Sec. 2 along the crossing direction. For AR,
+    the four corner blocks follow the explicit corner formulas of Sec. 2, e.g.
+    x~_{-i,-j} = 4 x_{0,0} - 2 x_{0,j} - 2 x_{i,0} + x_{i,j} (0-based). For R the
+    corner blocks are the reflection in both directions.
+    """
+    x = np.asarray(x, dtype=np.float64)
+    nr, nc = x.shape
+    out = np.zeros((nr + 2 * mr, nc + 2 * mc))
+    out[mr:mr + nr, mc:mc + nc] = x
+    if bc == R:
+        # reflection: x~_{-j} = x_{j-1}, x~_{n-1+j} = x_{n-j}, in each direction
+        ir = np.concatenate([np.arange(mr - 1, -1, -1), np.arange(nr), np.arange(nr - 1, nr - 1 - mr, -1)])
+        ic = np.concatenate([np.arange(mc - 1, -1, -1), np.arange(nc), np.arange(nc - 1, nc - 1 - mc, -1)])
+        return x[np.ix_(ir, ic)].copy()
+    if bc != AR:
+        raise ValueError(bc)
+    i = np.arange(1, mr + 1)          # distance outside, rows
+    j = np.arange(1, mc + 1)          # distance outside, columns
+    # edge strips, eq. (anti1d) along the crossing direction
+    out[mr - i, mc:mc + nc] = 2.0 * x[0, :][None, :] - x[i, :]
+    out[mr + nr - 1 + i, mc:mc + nc] = 2.0 * x[nr - 1, :][None, :] - x[nr - 1 - i, :]
+    out[mr:mr + nr, mc - j] = 2.0 * x[:, 0][:, None] - x[:, j]
+    out[mr:mr + nr, mc + nc - 1 + j] = 2.0 * x[:, nc - 1][:, None] - x[:, nc - 1 - j]
+    # the four corner formulas of Sec. 2, with I, J the outside distances
+    I, J = np.meshgrid(i, j, indexing="ij")
+    for (bi, mi, oi) in ((0, I, mr - I), (nr - 1, nr - 1 - I, mr + nr - 1 + I)):
+        for (bj, mj, oj) in ((0, J, mc - J), (nc - 1, nc - 1 - J, mc + nc - 1 + J)):
+            out[oi, oj] = 4.0 * x[bi, bj] - 2.0 * x[bi, mj] - 2.0 * x[mi, bj] + x[mi, mj]
+    return out
+
+
+def extend_adjoint(z: np.ndarray, mr: int, mc: int, bc: str) -> np.ndarray:
+    """Transpose of ``extend``: folds an extended array back onto the n_r x n_c grid.
+
+    The extension acts separately on rows and columns (the AR corner formulas
+    are the composition of the two 1D rules), so its transpose applies the
+    transposed 1D rule along each axis in turn.
+    """
+    z = np.asarray(z, dtype=np.float64)
+    nr = z.shape[0] - 2 * mr
+    nc = z.shape[1] - 2 * mc
+    # fold the row direction: (n_r + 2 m_r, n_c + 2 m_c) -> (n_r, n_c + 2 m_c)
+    t = np.zeros((nr, z.shape[1]))
+    for I in range(-mr, nr + mr):
+        for (ii, ci) in _ext_index_1d(I, nr, bc):
+            t[ii, :] += ci * z[I + mr, :]
+    out = np.zeros((nr, nc))
+    for J in range(-mc, nc + mc):
+        for (jj, cj) in _ext_index_1d(J, nc, bc):
+            out[:, jj] += cj * t[:, J + mc]
+    return out
+
+
+# --------------------------------------------------------------------------
+# Blur operator H and its adjoint, Sec. 2, eq. (blurred1d:matrixform)
+# --------------------------------------------------------------------------
+
+def _psf_halfwidths(h: np.ndarray):
+    pr, pc = h.shape
+    if pr % 2 == 0 or pc % 2 == 0:
+        raise ValueError("PSF sides must be odd")
+    return pr // 2, pc // 2
+
+
+def blur(x: np.ndarray, h: np.ndarray, bc: str) -> np.ndarray:
+    """y = H x: extend x by the BC, then v_{ij} = sum_{a,b} h_{a,b} x~_{i-a, j-b}."""
+    x = np.asarray(x, dtype=np.float64)
+    mr, mc = _psf_halfwidths(h)
+    nr, nc = x.shape
+    xe = extend(x, mr, mc, bc)
+    y = np.zeros((nr, nc))
+    for a in range(-mr, mr + 1):
+        for b in range(-mc, mc + 1):
+            hab = h[mr + a, mc + b]
+            if hab != 0.0:
+                y += hab * xe[mr - a:mr - a + nr, mc - b:mc - b + nc]
+    return y
+
+
+def blur_adjoint(y: np.ndarray, h: np.ndarray, bc: str) -> np.ndarray:
+    """x = H^T y = E^T C^T y, with C the convolution on the extended grid."""
+    y = np.asarray(y, dtype=np.float64)
+    mr, mc = _psf_halfwidths(h)
+    nr, nc = y.shape
+    z = np.zeros((nr + 2 * mr, nc + 2 * mc))
+    for a in range(-mr, mr + 1):
+        for b in range(-mc, mc + 1):
+            hab = h[mr + a, mc + b]
+            if hab != 0.0:
+                z[mr - a:mr - a + nr, mc - b:mc - b + nc] += hab * y
+    return extend_adjoint(z, mr, mc, bc)
+
+
+def blur_at(x: np.ndarray, h: np.ndarray, bc: str, i: int, j: int) -> float:
+    """(H x)_{i,j} for a single output pixel, evaluated directly from the definition.
+
+    Used to check full-size results on sampled pixels without forming H x.
+    """
+    x = np.asarray(x, dtype=np.float64)
+    mr, mc = _psf_halfwidths(h)
+    nr, nc = x.shape
+    acc = 0.0
+    for a in range(-mr, mr + 1):
+        for b in range(-mc, mc + 1):
+            hab = h[mr + a, mc + b]
+            if hab == 0.0:
+                continue
+            I, J = i - a, j - b
+            r_in, c_in = 0 <= I < nr, 0 <= J < nc
+            if bc == AR and not r_in and not c_in:
+                bi, mi = (0, -I) if I < 0 else (nr - 1, 2 * (nr - 1) - I)
+                bj, mj = (0, -J) if J < 0 else (nc - 1, 2 * (nc - 1) - J)
+                val = 4.0 * x[bi, bj] - 2.0 * x[bi, mj] - 2.0 * x[mi, bj] + x[mi, mj]
+            else:
+                val = 0.0
+                for (ii, ci) in _ext_index_1d(I, nr, bc):
+                    for (jj, cj) in _ext_index_1d(J, nc, bc):
+                        val += ci * cj * x[ii, jj]
+            acc += hab * val
+    return acc
+
+
+# --------------------------------------------------------------------------
+# Lagged-diffusivity TV operator, Sec. 1, eqs. (el), (fp)
+# --------------------------------------------------------------------------
+
+def grad_r(u: np.ndarray) -> np.ndarray:
+    """Forward difference along rows, zero on the last row (zero Neumann)."""
+    d = np.zeros_like(u, dtype=np.float64)
+    d[:-1, :] = u[1:, :] - u[:-1, :]
+    return d
+
+
+def grad_c(u: np.ndarray) -> np.ndarray:
+    """Forward difference along columns, zero on the last column (zero Neumann)."""
+    d = np.zeros_like(u, dtype=np.float64)
+    d[:, :-1] = u[:, 1:] - u[:, :-1]
+    return d
+
+
+def grad_r_T(g: np.ndarray) -> np.ndarray:
+    """Transpose of ``grad_r``."""
+    out = np.zeros_like(g, dtype=np.float64)
+    out[:-1, :] -= g[:-1, :]
+    out[1:, :] += g[:-1, :]
+    return out
+
+
+def grad_c_T(g: np.ndarray) -> np.ndarray:
+    """Transpose of ``grad_c``."""
+    out = np.zeros_like(g, dtype=np.float64)
+    out[:, :-1] -= g[:, :-1]
+    out[:, 1:] += g[:, :-1]
+    return out
+
+
+def diffusivity(u: np.ndarray, beta: float) -> np.ndarray:
+    """w = psi^-1 = (|D u|^2 + beta^2)^(-1/2) per pixel (the lagged coefficient of L(u))."""
+    u = np.asarray(u, dtype=np.float64)
+    return 1.0 / np.sqrt(grad_r(u) ** 2 + grad_c(u) ** 2 + beta * beta)
+
+
+def tv_apply(w: np.ndarray, y: np.ndarray) -> np.ndarray:
+    """L y = D_r^T W D_r y + D_c^T W D_c y for the diffusivity field w."""
+    y = np.asarray(y, dtype=np.float64)
+    return grad_r_T(w * grad_r(y)) + grad_c_T(w * grad_c(y))
+
+
+def tv_diag(w: np.ndarray) -> np.ndarray:
+    """diag(L) for the diffusivity w: the sum of the coefficients of the 5-point stencil."""
+    w = np.asarray(w, dtype=np.float64)
+    d = np.zeros_like(w)
+    d[:-1, :] += w[:-1, :]
+    d[1:, :] += w[:-1, :]
+    d[:, :-1] += w[:, :-1]
+    d[:, 1:] += w[:, :-1]
+    return d
+
+
+def tv_functional(u, v, h, bc, alpha, beta) -> float:
+    """1/2 ||H u - v||^2 + alpha sum_pq sqrt(|D u|_pq^2 + beta^2), eq. (mp) discretised."""
+    res = blur(u, h, bc) - v
+    tv = np.sqrt(grad_r(u) ** 2 + grad_c(u) ** 2 + beta * beta).sum()
+    return 0.5 * float((res * res).sum()) + alpha * float(tv)
+
+
+def euler_lagrange(u, v, h, bc, alpha, beta) -> np.ndarray:
+    """g(u) = H^T (H u - v) + alpha L(u) u, eq. (el) (the gradient of ``tv_functional``)."""
+    w = diffusivity(u, beta)
+    return blur_adjoint(blur(u, h, bc) - v, h, bc) + alpha * tv_apply(w, u)
+
+
+# --------------------------------------------------------------------------
+# Fast transforms, Secs. 2 and 3
+# --------------------------------------------------------------------------
+
+def transform_matrix(n: int, bc: str) -> np.ndarray:
+    """Rows are the orthonormal basis vectors b_k of the 1D transform U.
+
+    AR: hat-S_n = diag(1, S_{n-2}, 1) with S_m the DST-I of eq. (lambda).
+    R: the DCT-II matrix C (frequency-by-space), so that C x = dct(x, 2, 'ortho').
+    """
+    eye = np.eye(n)
+    if bc == AR:
+        B = np.zeros((n, n))
+        B[0, 0] = 1.0
+        B[n - 1, n - 1] = 1.0
+        if n > 2:
+            B[1:n - 1, 1:n - 1] = sfft.dst(np.eye(n - 2), type=1, norm="ortho", axis=0)
+        return B
+    if bc == R:
+        return sfft.dct(eye, type=2, norm="ortho", axis=0)
+    raise ValueError(bc)
+
+
+def transform_fwd(x: np.ndarray, bc: str, axis: int) -> np.ndarray:
+    """Apply U along ``axis``: hat-S (AR, DST-I on the interior) or the DCT-II (R)."""
+    x = np.asarray(x, dtype=np.float64)
+    if bc == AR:
+        out = x.copy()
+        n = x.shape[axis]
+        if n > 2:
+            sl = [slice(None)] * x.ndim
+            sl[axis] = slice(1, n - 1)
+            out[tuple(sl)] = sfft.dst(x[tuple(sl)], type=1, norm="ortho", axis=axis)
+        return out
+    return sfft.dct(x, type=2, norm="ortho", axis=axis)
+
+
+def transform_inv(x: np.ndarray, bc: str, axis: int) -> np.ndarray:
+    """Apply U^{-1} along ``axis``: hat-S again (it is an involution) or the DCT-III (R)."""
+    if bc == AR:
+        return transform_fwd(x, bc, axis)
+    return sfft.idct(np.asarray(x, dtype=np.float64), type=2, norm="ortho", axis=axis)
+
+
+def symbol_grid(n: int, bc: str) -> np.ndarray:
+    """Frequencies at which the PSF symbol gives the eigenvalues of H.
+
+    AR, eq. (gridy): basis vector 0 (the 1 - y/pi column) and n-1 (the y/pi
+    column) take y = 0; interior basis vector k (DST-I frequency k) takes
+    y = k pi / (n-1). R: DCT-II frequency k takes y = k pi / n.
+    """
+    k = np.arange(n, dtype=np.float64)
+    if bc == AR:
+        y = k * np.pi / (n - 1)
+        y[0] = 0.0
+        y[n - 1] = 0.0
+        return y
+    return k * np.pi / n
+
+
+def psf_symbol(h: np.ndarray, yr: np.ndarray, yc: np.ndarray) -> np.ndarray:
+    """h_hat(y_i, y_j) = sum_{a,b} h_{a,b} exp(i (a y_i + b y_j)), eq. (symb), real part.
+
+    For a quadrantally symmetric h the imaginary part vanishes.
+    """
+    mr, mc = _psf_halfwidths(h)
+    ar = np.arange(-mr, mr + 1)
+    ac = np.arange(-mc, mc + 1)
+    Er = np.exp(1j * np.outer(yr, ar))
+    Ec = np.exp(1j * np.outer(yc, ac))
+    return np.real(Er @ h @ Ec.T)
+
+
+def spectrum_H(h: np.ndarray, nr: int, nc: int, bc: str) -> np.ndarray:
+    """Eigenvalues Lambda_H[i, j] of H in the 2D transform basis (n_r x n_c)."""
+    return psf_symbol(h, symbol_grid(nr, bc), symbol_grid(nc, bc))
+
+
+def _E_G(n: int, bc: str):
+    """E[k,p] = b_k(p)^2 and G[k,p] = ((D_1 b_k)_p)^2, with D_1 the Neumann forward difference."""
+    B = transform_matrix(n, bc)
+    E = B * B
+    D = np.zeros_like(B)
+    D[:, :-1] = B[:, 1:] - B[:, :-1]
+    return E, D * D
+
+
+def spectrum_L(w: np.ndarray, bc: str) -> np.ndarray:
+    """Lambda_L = diag(U L U^T) for L = D_r^T W D_r + D_c^T W D_c and U = B_r (x) B_c.
+
+    (b_i (x) b_j)^T L (b_i (x) b_j) = sum_pq w_pq [G_r(i,p) E_c(j,q) + E_r(i,p) G_c(j,q)],
+    i.e. Lambda_L = G_r W E_c^T + E_r W G_c^T. These are the eigenvalues of the
+    level-2 projection c_2(L) (R) or hat-s_2(L) (AR) of Sec. 3.2.
+    """
+    w = np.asarray(w, dtype=np.float64)
+    nr, nc = w.shape
+    Er, Gr = _E_G(nr, bc)
+    Ec, Gc = _E_G(nc, bc)
+    return Gr @ w @ Ec.T + Er @ w @ Gc.T
+
+
+# --------------------------------------------------------------------------
+# Preconditioners, Sec. 3
+# --------------------------------------------------------------------------
+
+def precond_setup(u_lag, h, bc, alpha, beta, kind):
+    """Everything the preconditioner solve needs for the FP step at u_lag.
+
+    Returns a dict with the diffusivity ``w``, ``D`` = 1 + alpha diag(L) (eq. (D)),
+    and ``spec`` = Lambda_H^2 + alpha Lambda_L, the eigenvalues of R (eq. (R2)) or
+    M (2D form of eq. (M)); D_R / D_M scale these by D^1/2 on both sides.
+    """
+    w = diffusivity(u_lag, beta)
+    nr, nc = w.shape
+    D = 1.0 + alpha * tv_diag(w)
+    P = {"kind": kind, "bc": bc, "w": w, "D": D, "alpha": alpha}
+    if kind in (PC_FAST, PC_DFAST):
+        lam_h = spectrum_H(h, nr, nc, bc)
+        spec = lam_h * lam_h + alpha * spectrum_L(w, bc)
+        if np.min(spec) <= 1e-300:
+            raise ValueError("preconditioner spectrum is not positive")
+        P["spec"] = spec
+    return P
+
+
+def precond_apply(r: np.ndarray, P) -> np.ndarray:
+    """z = X^{-1} r for X in {I, D, R|M, D_R|D_M}.
+
+    X^{-1} r = D^{-1/2} U^{-1} diag(spec)^{-1} U D^{-1/2} r for the scaled
+    variants, with U = B_r (x) B_c applied as the 1D transform along each axis.
+    """
+    kind, bc = P["kind"], P["bc"]
+    r = np.asarray(r, dtype=np.float64)
+    if kind == PC_NONE:
+        return r.copy()
+    if kind == PC_DIAG:
+        return r / P["D"]
+    t = r / np.sqrt(P["D"]) if kind == PC_DFAST else r.copy()
+    t = transform_fwd(transform_fwd(t, bc, 1), bc, 0)
+    t = t / P["spec"]
+    t = transform_inv(transform_inv(t, bc, 0), bc, 1)
+    if kind == PC_DFAST:
+        t = t / np.sqrt(P["D"])
+    return t
+
+
+def normal_apply(x, h, bc, w, alpha) -> np.ndarray:
+    """A x = H^T H x + alpha L(w) x, the matrix of the FP step, eq. (fp)."""
+    return blur_adjoint(blur(x, h, bc), h, bc) + alpha * tv_apply(w, x)
+
+
+# --------------------------------------------------------------------------
+# PCG (Golub & Van Loan, Algorithm 10.3.1) and the FP loop, Secs. 1 and 5
+# --------------------------------------------------------------------------
+
+def pcg(apply_A, apply_M, b, x0, tol, maxit):
+    """Preconditioned CG on A x = b from x0.
+
+    Stops when ||r_k||_2 / ||r_0||_2 < tol (Sec. 5) or after ``maxit`` products
+    with A. Returns (x, iterations, relres, converged).
+    """
+    x = np.array(x0, dtype=np.float64, copy=True)
+    r = b - apply_A(x)
+    r0 = float(np.sqrt((r * r).sum()))
+    if r0 == 0.0:
+        return x, 0, 0.0, True
+    k = 0
+    rho_old = None
+    p = None
+    relres = 1.0
+    while k < maxit:
+        z = apply_M(r)
+        rho = float((r * z).sum())
+        k += 1
+        if k == 1:
+            p = z.copy()
+        else:
+            p = z + (rho / rho_old) * p
+        q = apply_A(p)
+        a = rho / float((p * q).sum())
+        x = x + a * p
+        r = r - a * q
+        rho_old = rho
+        relres = float(np.sqrt((r * r).sum())) / r0
+        if relres < tol:
+            return x, k, relres, True
+    return x, k, relres, False
+
+
+def fp_step(u, b, h, bc, alpha, beta, kind, tol, maxit):
+    """One lagged-diffusivity step: solve (H^T H + alpha L(u)) x = H^T v from x0 = u."""
+    P = precond_setup(u, h, bc, alpha, beta, kind)
+    w = P["w"]
+    return pcg(lambda y: normal_apply(y, h, bc, w, alpha),
+               lambda r: precond_apply(r, P), b, u, tol, maxit)
+
+
+def tv_deblur(v, h, bc, alpha, beta, outer=10, tol=1e-6, maxit=1000,
+              kind=PC_DFAST, outer_tol=0.0):
+    """Lagged-diffusivity FP iteration with PCG inner solves, u^0 = v (Sec. 5).
+
+    Runs ``outer`` FP steps, or stops earlier when ||u^k - u^{k-1}|| / ||u^k||
+    < outer_tol (if outer_tol > 0). Returns (u, stats) where stats holds the
+    per-step inner iteration counts, residuals and relative changes.
+    """
+    v = np.asarray(v, dtype=np.float64)
+    b = blur_adjoint(v, h, bc)
+    u = v.copy()
+    stats = {"inner_iters": [], "relres": [], "rel_change": [], "converged": []}
+    for _ in range(outer):
+        x, k, rr, ok = fp_step(u, b, h, bc, alpha, beta, kind, tol, maxit)
+        change = float(np.linalg.norm(x - u) / max(np.linalg.norm(x), 1e-300))
+        stats["inner_iters"].append(k)
+        stats["relres"].append(rr)
+        stats["rel_change"].append(change)
+        stats["converged"].append(ok)
+        u = x
+        if outer_tol > 0.0 and change < outer_tol:
+            break
+    return u, stats
