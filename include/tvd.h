@@ -1,0 +1,192 @@
+/*
+ * tvd.h -- C ABI of the GB300 TV-deblurring PCG library (libtvd.so).
+ *
+ * The library implements the inner step of the lagged-diffusivity fixed-point
+ * (FP) method for total-variation deblurring of Bai, Donatelli and
+ * Serra-Capizzano, "Fast preconditioners for total variation deblurring with
+ * anti-reflective boundary conditions": for the FP step at u^k it solves
+ *
+ *     A x = b,   A = H^T H + alpha L(u^k)                       (eq. (fp))
+ *
+ * by preconditioned CG (Golub & Van Loan, Alg. 10.3.1, cited in Sec. 1), where
+ *   H       is the blur with reflective or anti-reflective boundary conditions
+ *           (Sec. 2, eqs. (blurred1d:matrixform), (anti1d) and the 2D corner rules),
+ *   L(u)    is the lagged-diffusivity operator -div(psi^-1 grad .),
+ *           psi = sqrt(|grad u|^2 + beta^2) (Sec. 1, eq. (el)),
+ *   and the preconditioner is one of I, D = I + alpha diag(L) (eq. (D)),
+ *   R / M (eqs. (R2), (M), Sec. 3.2) or D_R / D_M = D^1/2 {R|M} D^1/2,
+ *   applied with fast trigonometric transforms: the DCT for reflective BCs and
+ *   DST-I (hat-S = diag(1, S_{n-2}, 1), eqs. (lambda), (hats)) for
+ *   anti-reflective BCs.
+ *
+ * Conventions shared by every entry point:
+ *   - Images are n_rows x n_cols, row-major and contiguous, element (i, j) at
+ *     i * n_cols + j. All image pointers are DEVICE pointers owned by the
+ *     caller; the library never frees them and never keeps them after a call
+ *     returns.
+ *   - Element type: the operator calls (ar_blur_apply, tv_operator_apply,
+ *     tau_precond_setup, tau_precond_solve) use the plan's operator type:
+ *     double for TVD_MODE_FP64 plans, float for TVD_MODE_MIXED plans. The
+ *     solver calls (pcg_solve, tv_deblur) always take double buffers: in MIXED
+ *     mode the inner CG runs in float with double scalars and the solution is
+ *     accumulated in double by iterative refinement.
+ *   - stream: a cudaStream_t passed as void* (NULL = legacy default stream).
+ *     Operator calls are asynchronous on that stream. Calls that return host
+ *     scalars (pcg_solve, tv_deblur, tvd_plan_create) synchronise it.
+ *   - The plan owns all workspace, spectra and tables and frees them in
+ *     tvd_plan_destroy. A plan must not be used from two host threads at once.
+ *   - Every call returns a tvd_status and never aborts or throws; on error,
+ *     tvd_last_error() returns a message for the calling thread.
+ */
+#ifndef TVD_H
+#define TVD_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct tvd_plan_s* tvd_plan;
+
+/* Boundary conditions of the blur, Sec. 2. */
+typedef enum {
+    TVD_BC_REFLECTIVE = 0,      /* u_{1-j} = u_j, u_{n+j} = u_{n+1-j} */
+    TVD_BC_ANTIREFLECTIVE = 1   /* u_{1-j} = 2u_1 - u_{j+1}, u_{n+j} = 2u_n - u_{n-j}, eq. (anti1d) */
+} tvd_bc;
+
+/* Preconditioner X of the inner CG (column names of Tables 1-1 and 2-1). */
+typedef enum {
+    TVD_PC_NONE = 0,   /* I */
+    TVD_PC_DIAG = 1,   /* D = I + alpha diag(L(u)), eq. (D) */
+    TVD_PC_FAST = 2,   /* R (reflective, eq. (R2)) or M (anti-reflective, Sec. 3.2) */
+    TVD_PC_DFAST = 3   /* D_R = D^1/2 R D^1/2 or D_M = D^1/2 M D^1/2 (default) */
+} tvd_precond;
+
+/* Arithmetic of the plan. */
+typedef enum {
+    TVD_MODE_FP64 = 0,  /* every kernel in double: the plain method */
+    TVD_MODE_MIXED = 1  /* float kernels, double CG scalars, double iterative refinement */
+} tvd_mode;
+
+typedef enum {
+    TVD_OK = 0,
+    TVD_EINVAL = 1,       /* bad argument: size, pointer, parameter */
+    TVD_EPSF_ASYM = 2,    /* PSF not quadrantally symmetric (fast preconditioners need it, Sec. 2) */
+    TVD_EPSF_SIZE = 3,    /* PSF side even, or half-width m > n - 2 along an axis */
+    TVD_ENOMEM = 4,       /* device allocation failed */
+    TVD_ECUDA = 5,        /* a CUDA runtime call failed */
+    TVD_ENOCONV = 6,      /* CG hit maxit before ||r_k|| / ||r_0|| < tol */
+    TVD_EBREAKDOWN = 7,   /* p^T A p <= 0, r^T z <= 0 with r != 0, or a non-finite scalar */
+    TVD_ETIMEOUT = 8      /* reserved: a bounded device-side wait gave up */
+} tvd_status;
+
+/* Per-call statistics of tv_deblur. inner_iters is caller-owned host memory
+ * with room for `cap` entries (may be NULL with cap = 0). */
+typedef struct {
+    int outer_iters;         /* FP steps taken */
+    int* inner_iters;        /* inner CG iterations of each FP step (first min(outer, cap)) */
+    int cap;
+    int total_inner_iters;   /* sum over all FP steps */
+    int refinement_sweeps;   /* MIXED: float CG solves run in total; FP64: equals outer_iters */
+    double last_relres;      /* ||r|| / ||r_0|| of the last FP step (double residual) */
+    double last_rel_change;  /* ||u^k - u^{k-1}|| / ||u^k|| of the last FP step */
+    tvd_status last_status;  /* status of the last inner solve */
+} tvd_stats;
+
+/*
+ * tvd_plan_create -- validate the problem and build the plan.
+ *   out         receives the plan handle.
+ *   n_rows, n_cols  image size, each in [3, 2048] for TVD_MODE_FP64 plans and
+ *               in [3, 4096] for TVD_MODE_MIXED plans (each transform line is
+ *               held in shared memory).
+ *   psf_host    HOST pointer to the (p_rows x p_cols) PSF, row-major doubles,
+ *               centred: psf[(m_r + a) * p_cols + (m_c + b)] = h_{a,b}. Copied.
+ *               p_rows, p_cols odd. All-zero outer rows/columns are trimmed (this
+ *               does not change H). After trimming, m_r <= n_rows - 2 and
+ *               m_c <= n_cols - 2 (else TVD_EPSF_SIZE), and h must be
+ *               quadrantally symmetric h_{a,b} = h_{-a,b} = h_{a,-b} to a relative
+ *               tolerance of 1e-12 (else TVD_EPSF_ASYM). Normalisation sum h = 1
+ *               (Sec. 2) is the caller's choice and is not enforced.
+ *   bc, pc, mode  see the enums above.
+ *   stream      stream for the set-up copies (synchronised before return).
+ */
+tvd_status tvd_plan_create(tvd_plan* out, int n_rows, int n_cols,
+                           const double* psf_host, int p_rows, int p_cols,
+                           tvd_bc bc, tvd_precond pc, tvd_mode mode, void* stream);
+
+/* Free every device and host resource of the plan. NULL is accepted. */
+tvd_status tvd_plan_destroy(tvd_plan plan);
+
+/*
+ * ar_blur_apply -- y = H x (transpose = 0) or y = H^T x (transpose = 1).
+ * H extends x by the plan's BC and convolves with the PSF (Sec. 2,
+ * eq. (blurred1d:matrixform)); H^T is its exact transpose (for reflective BCs
+ * and a symmetric PSF, H^T = H, Sec. 3.1). x and y: device arrays of the plan's
+ * operator type, n_rows x n_cols, not overlapping.
+ */
+tvd_status ar_blur_apply(tvd_plan plan, int transpose, const void* x, void* y, void* stream);
+
+/*
+ * tv_operator_apply -- y = L(u_lag) x with L = D_r^T W D_r + D_c^T W D_c,
+ * W = diag((|D u_lag|^2 + beta^2)^{-1/2}), D_r, D_c forward differences that
+ * vanish on the last row / column (zero Neumann, Sec. 1, eq. (el)).
+ * u_lag, x, y: device arrays of the plan's operator type; y must not overlap
+ * u_lag or x. beta > 0.
+ */
+tvd_status tv_operator_apply(tvd_plan plan, const void* u_lag, double beta,
+                             const void* x, void* y, void* stream);
+
+/*
+ * tau_precond_setup -- build the preconditioner of the plan for the FP step at
+ * u_lag (device array of the plan's operator type): the diffusivity, D = I +
+ * alpha diag(L(u_lag)) (eq. (D)) and the eigenvalues Lambda_H^2 + alpha Lambda_L
+ * of R / M in the 2D DCT / hat-S basis (Sec. 3.2). alpha >= 0, beta > 0.
+ * Returns TVD_EINVAL if some eigenvalue is not positive.
+ */
+tvd_status tau_precond_setup(tvd_plan plan, const void* u_lag, double alpha, double beta, void* stream);
+
+/*
+ * tau_precond_solve -- z = X^{-1} r with the preconditioner last set up
+ * (X = D^1/2 U^{-1} diag(Lambda_H^2 + alpha Lambda_L) U D^1/2 for D_R / D_M,
+ * U the 2D DCT-II or hat-S transform). r and z: device arrays of the plan's
+ * operator type; r == z is allowed.
+ */
+tvd_status tau_precond_solve(tvd_plan plan, const void* r, void* z, void* stream);
+
+/*
+ * pcg_solve -- solve (H^T H + alpha L(u_lag)) x = b by preconditioned CG from
+ * the initial guess in x_inout, stopping when ||r_k||_2 / ||r_0||_2 < tol
+ * (Sec. 5) or after maxit iterations. u_lag, b, x_inout: DOUBLE device arrays.
+ * *iters receives the CG iterations (products with A) and *relres the final
+ * relative residual; both may be NULL. In MIXED mode the residual used for the
+ * stopping test is recomputed in double after each float CG sweep.
+ * Returns TVD_ENOCONV if tol was not reached within maxit iterations.
+ */
+tvd_status pcg_solve(tvd_plan plan, const void* u_lag, double alpha, double beta,
+                     const void* b, void* x_inout, double tol, int maxit,
+                     int* iters, double* relres, void* stream);
+
+/*
+ * tv_deblur -- the FP iteration u^{k+1} = A(u^k)^{-1} H^T v from u^0 = v
+ * (Sec. 5), each step solved by pcg_solve warm-started at u^k. Runs max_outer
+ * steps, or stops earlier when ||u^k - u^{k-1}|| / ||u^k|| < outer_tol
+ * (outer_tol <= 0: fixed count). v and u_out: DOUBLE device arrays; u_out may
+ * equal v. stats may be NULL. Inner non-convergence of a step is recorded in
+ * stats->last_status but does not stop the FP loop; the return value is
+ * TVD_ENOCONV if any step did not converge.
+ */
+tvd_status tv_deblur(tvd_plan plan, const void* v, double alpha, double beta,
+                     int max_outer, double outer_tol, double inner_tol, int inner_maxit,
+                     void* u_out, tvd_stats* stats, void* stream);
+
+/* Message of the last failed call on the calling thread ("" if none). */
+const char* tvd_last_error(void);
+
+/* Library version string. */
+const char* tvd_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* TVD_H */

@@ -1,0 +1,230 @@
+"""GB300 TV-deblurring PCG library: thin Python binding of libtvd.so.
+
+The library (``libtvd.so``, built in-tree from ``csrc/`` by ``_build.build()``)
+implements the PCG inner step of the lagged-diffusivity fixed-point method for
+TV deblurring with reflective / anti-reflective boundary conditions (Bai,
+Donatelli, Serra-Capizzano). Its C ABI is declared in ``include/tvd.h``.
+
+This module only marshals arguments: torch CUDA tensors become device
+pointers, torch's current stream is passed as the CUDA stream, and status codes
+become exceptions. Every step of the computation runs in the CUDA kernels;
+there is no CPU fallback, and loading fails loudly if the library is missing.
+
+The function names mirror the C ABI: ``ar_blur_apply``, ``tv_operator_apply``,
+``tau_precond_setup``, ``tau_precond_solve``, ``pcg_solve``, ``tv_deblur``.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libtvd.so")
+
+BC = {"r": 0, "reflective": 0, "ar": 1, "antireflective": 1}
+PC = {"none": 0, "diag": 1, "fast": 2, "dfast": 3}
+MODE = {"fp64": 0, "mixed": 1}
+
+TVD_OK, TVD_EINVAL, TVD_EPSF_ASYM, TVD_EPSF_SIZE, TVD_ENOMEM, TVD_ECUDA, TVD_ENOCONV, TVD_EBREAKDOWN, TVD_ETIMEOUT = range(9)
+STATUS_NAMES = ["TVD_OK", "TVD_EINVAL", "TVD_EPSF_ASYM", "TVD_EPSF_SIZE", "TVD_ENOMEM", "TVD_ECUDA",
+                "TVD_ENOCONV", "TVD_EBREAKDOWN", "TVD_ETIMEOUT"]
+
+# Function names of the C ABI, in include/tvd.h order.
+ABI_FUNCTIONS = ["tvd_plan_create", "tvd_plan_destroy", "ar_blur_apply", "tv_operator_apply",
+                 "tau_precond_setup", "tau_precond_solve", "pcg_solve", "tv_deblur",
+                 "tvd_last_error", "tvd_version"]
+
+
+class TvdError(RuntimeError):
+    """A libtvd call returned an error status."""
+
+    def __init__(self, status: int, message: str):
+        self.status = status
+        name = STATUS_NAMES[status] if 0 <= status < len(STATUS_NAMES) else str(status)
+        super().__init__(f"{name}: {message}")
+
+
+class _Stats(ctypes.Structure):
+    _fields_ = [("outer_iters", ctypes.c_int), ("inner_iters", ctypes.POINTER(ctypes.c_int)),
+                ("cap", ctypes.c_int), ("total_inner_iters", ctypes.c_int),
+                ("refinement_sweeps", ctypes.c_int), ("last_relres", ctypes.c_double),
+                ("last_rel_change", ctypes.c_double), ("last_status", ctypes.c_int)]
+
+
+_lib = None
+
+
+def load_library(path: str | None = None) -> ctypes.CDLL:
+    """Load libtvd.so (once). Raises if it has not been built."""
+    global _lib
+    if _lib is not None and path is None:
+        return _lib
+    p = path or LIB_PATH
+    if not os.path.exists(p):
+        raise RuntimeError(f"libtvd.so not found at {p}; build it with paper_1011_5964_gb300._build.build()")
+    lib = ctypes.CDLL(p)
+    vp, i, d = ctypes.c_void_p, ctypes.c_int, ctypes.c_double
+    lib.tvd_plan_create.argtypes = [ctypes.POINTER(vp), i, i, ctypes.POINTER(d), i, i, i, i, i, vp]
+    lib.tvd_plan_destroy.argtypes = [vp]
+    lib.ar_blur_apply.argtypes = [vp, i, vp, vp, vp]
+    lib.tv_operator_apply.argtypes = [vp, vp, d, vp, vp, vp]
+    lib.tau_precond_setup.argtypes = [vp, vp, d, d, vp]
+    lib.tau_precond_solve.argtypes = [vp, vp, vp, vp]
+    lib.pcg_solve.argtypes = [vp, vp, d, d, vp, vp, d, i, ctypes.POINTER(i), ctypes.POINTER(d), vp]
+    lib.tv_deblur.argtypes = [vp, vp, d, d, i, d, d, i, vp, ctypes.POINTER(_Stats), vp]
+    lib.tvd_last_error.restype = ctypes.c_char_p
+    lib.tvd_version.restype = ctypes.c_char_p
+    for name in ABI_FUNCTIONS:
+        if name not in ("tvd_last_error", "tvd_version"):
+            getattr(lib, name).restype = ctypes.c_int
+    if path is None:
+        _lib = lib
+    return lib
+
+
+def _check(status: int, allow=()) -> int:
+    if status != TVD_OK and status not in allow:
+        msg = load_library().tvd_last_error().decode(errors="replace")
+        raise TvdError(status, msg)
+    return status
+
+
+def _stream():
+    import torch
+    return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+def _ptr(t, dtype, n):
+    import torch
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError("expected a CUDA tensor")
+    if t.dtype != dtype:
+        raise TypeError(f"expected dtype {dtype}, got {t.dtype}")
+    if not t.is_contiguous() or t.numel() != n:
+        raise ValueError(f"expected a contiguous tensor with {n} elements")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+class Plan:
+    """A libtvd plan: image size, PSF, boundary conditions, preconditioner and arithmetic.
+
+    ``psf`` is a (2 m_r + 1, 2 m_c + 1) float64 array, centred and quadrantally
+    symmetric. ``bc``: 'ar' (anti-reflective) or 'r' (reflective). ``pc``:
+    'none', 'diag', 'fast' (R / M) or 'dfast' (D_R / D_M). ``mode``: 'fp64' or
+    'mixed'. Operator calls take float64 tensors in fp64 mode and float32 in
+    mixed mode; solver calls always take float64 tensors.
+    """
+
+    def __init__(self, n_rows: int, n_cols: int, psf, bc: str = "ar", pc: str = "dfast", mode: str = "fp64"):
+        import torch
+        self.lib = load_library()
+        self.shape = (int(n_rows), int(n_cols))
+        self.n = self.shape[0] * self.shape[1]
+        self.mode = mode
+        self.op_dtype = torch.float64 if mode == "fp64" else torch.float32
+        h = np.ascontiguousarray(np.asarray(psf, dtype=np.float64))
+        handle = ctypes.c_void_p()
+        _check(self.lib.tvd_plan_create(ctypes.byref(handle), self.shape[0], self.shape[1],
+                                        h.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), h.shape[0], h.shape[1],
+                                        BC[bc], PC[pc], MODE[mode], _stream()))
+        self.handle = handle
+
+    def close(self):
+        if getattr(self, "handle", None):
+            self.lib.tvd_plan_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    # ---- operator calls (plan's operator dtype)
+    def blur(self, x, transpose: bool = False, out=None):
+        import torch
+        y = torch.empty_like(x) if out is None else out
+        _check(self.lib.ar_blur_apply(self.handle, int(bool(transpose)), _ptr(x, self.op_dtype, self.n),
+                                      _ptr(y, self.op_dtype, self.n), _stream()))
+        return y
+
+    def tv_operator(self, u_lag, beta: float, x, out=None):
+        import torch
+        y = torch.empty_like(x) if out is None else out
+        _check(self.lib.tv_operator_apply(self.handle, _ptr(u_lag, self.op_dtype, self.n), float(beta),
+                                          _ptr(x, self.op_dtype, self.n), _ptr(y, self.op_dtype, self.n), _stream()))
+        return y
+
+    def precond_setup(self, u_lag, alpha: float, beta: float):
+        _check(self.lib.tau_precond_setup(self.handle, _ptr(u_lag, self.op_dtype, self.n), float(alpha), float(beta),
+                                          _stream()))
+
+    def precond_solve(self, r, out=None):
+        import torch
+        z = torch.empty_like(r) if out is None else out
+        _check(self.lib.tau_precond_solve(self.handle, _ptr(r, self.op_dtype, self.n), _ptr(z, self.op_dtype, self.n),
+                                          _stream()))
+        return z
+
+    # ---- solver calls (float64)
+    def pcg_solve(self, u_lag, alpha: float, beta: float, b, x, tol: float = 1e-6, maxit: int = 1000):
+        """Solve (H^T H + alpha L(u_lag)) x = b in place. Returns (iterations, relres, status)."""
+        import torch
+        it = ctypes.c_int(0)
+        rr = ctypes.c_double(0.0)
+        st = self.lib.pcg_solve(self.handle, _ptr(u_lag, torch.float64, self.n), float(alpha), float(beta),
+                                _ptr(b, torch.float64, self.n), _ptr(x, torch.float64, self.n), float(tol), int(maxit),
+                                ctypes.byref(it), ctypes.byref(rr), _stream())
+        _check(st, allow=(TVD_ENOCONV,))
+        return it.value, rr.value, st
+
+    def deblur(self, v, alpha: float, beta: float, max_outer: int = 10, outer_tol: float = 0.0,
+               inner_tol: float = 1e-6, inner_maxit: int = 1000, out=None):
+        """Lagged-diffusivity FP iteration from u^0 = v. Returns (u, stats dict)."""
+        import torch
+        u = torch.empty_like(v) if out is None else out
+        cap = max(int(max_outer), 1)
+        arr = (ctypes.c_int * cap)()
+        stats = _Stats(0, arr, cap, 0, 0, 0.0, 0.0, 0)
+        st = self.lib.tv_deblur(self.handle, _ptr(v, torch.float64, self.n), float(alpha), float(beta), int(max_outer),
+                                float(outer_tol), float(inner_tol), int(inner_maxit), _ptr(u, torch.float64, self.n),
+                                ctypes.byref(stats), _stream())
+        _check(st, allow=(TVD_ENOCONV,))
+        k = stats.outer_iters
+        return u, {"outer_iters": k, "inner_iters": list(arr[:min(k, cap)]),
+                   "total_inner_iters": stats.total_inner_iters, "refinement_sweeps": stats.refinement_sweeps,
+                   "last_relres": stats.last_relres, "last_rel_change": stats.last_rel_change,
+                   "last_status": stats.last_status, "status": st}
+
+
+# Module-level names matching the C ABI.
+def ar_blur_apply(plan: Plan, transpose: bool, x, y=None):
+    return plan.blur(x, transpose, y)
+
+
+def tv_operator_apply(plan: Plan, u_lag, beta: float, x, y=None):
+    return plan.tv_operator(u_lag, beta, x, y)
+
+
+def tau_precond_setup(plan: Plan, u_lag, alpha: float, beta: float):
+    return plan.precond_setup(u_lag, alpha, beta)
+
+
+def tau_precond_solve(plan: Plan, r, z=None):
+    return plan.precond_solve(r, z)
+
+
+def pcg_solve(plan: Plan, u_lag, alpha, beta, b, x, tol=1e-6, maxit=1000):
+    return plan.pcg_solve(u_lag, alpha, beta, b, x, tol, maxit)
+
+
+def tv_deblur(plan: Plan, v, alpha, beta, max_outer=10, outer_tol=0.0, inner_tol=1e-6, inner_maxit=1000, u=None):
+    return plan.deblur(v, alpha, beta, max_outer, outer_tol, inner_tol, inner_maxit, u)

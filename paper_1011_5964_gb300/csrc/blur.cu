@@ -1,0 +1,316 @@
+// Blur operator H under reflective / anti-reflective boundary conditions and
+// its exact transpose (Sec. 2 of the paper).
+//
+//   (H x)_{ij} = sum_{a,b} h_{a,b} x~_{i-a, j-b}, x~ the BC extension of x:
+//     AR  (eq. (anti1d), corners of Sec. 2): x~_{-s} = 2 x_0 - x_s,
+//         x~_{n-1+s} = 2 x_{n-1} - x_{n-1-s}, separable in 2D;
+//     R:  x~_{-s} = x_{s-1}, x~_{n-1+s} = x_{n-s}.
+//
+// Forward: one CTA computes a 32x32 output tile from a shared-memory tile of
+// x~ (tile + PSF halo), built on the fly from x; the extended image is never
+// materialised.
+//
+// Transpose, AR: H = C E (convolution after extension), so H^T = E^T C^T. For a
+// quadrantally symmetric h the folds of E^T cancel the boundary lines of y at
+// interior outputs, which become a plain convolution of the odd extension
+//   y^_{s} = y_s (1 <= s <= n-2), y^_0 = y^_{n-1} = 0,
+//   y^_{-s} = -y_s, y^_{n-1+s} = -y_{n-1-s},
+// applied separately along rows and columns. The first/last row and column
+// of H^T y are tail-weighted sums of y near that border:
+//   row 0:   sum_{i=0..m_r} sum_b crow[i][b] yc^_{i, l+b},
+//            crow[i][b] = h_{i,b} + 2 sum_{s>i} h_{s,b}
+//   corner:  sum_{i,j} ccor[i][j] y_{ij},
+//            ccor[i][j] = h_ij + 2 sum_{s>i} h_sj + 2 sum_{t>j} h_it + 4 sum_{s>i,t>j} h_st
+// (yc^ = odd extension along the column index only). These weights are built
+// on the host from the PSF.
+// Transpose, R: H^T = H for a symmetric PSF (Sec. 3.1).
+#include "common.cuh"
+
+namespace tvd {
+
+enum { EXT_AR = 0, EXT_R = 1, EXT_ODD = 2 };
+
+constexpr int BT = 32;          // output tile side
+constexpr int BROWS = 8;        // thread rows; each thread computes BT / BROWS outputs
+
+template <typename T, int EXT>
+__device__ __forceinline__ T ext_value(const T* __restrict__ x, int I, int J, int nr, int nc, int mr, int mc) {
+    if (I < -mr || I >= nr + mr || J < -mc || J >= nc + mc) return T(0);
+    if (EXT == EXT_R) {
+        int ri = I < 0 ? -I - 1 : (I >= nr ? 2 * nr - 1 - I : I);
+        int ci = J < 0 ? -J - 1 : (J >= nc ? 2 * nc - 1 - J : J);
+        return x[(size_t)ri * nc + ci];
+    } else if (EXT == EXT_ODD) {
+        if (I == 0 || I == nr - 1 || J == 0 || J == nc - 1) return T(0);
+        T sg = T(1);
+        int ri = I, ci = J;
+        if (I < 0) { ri = -I; sg = -sg; } else if (I > nr - 1) { ri = 2 * (nr - 1) - I; sg = -sg; }
+        if (J < 0) { ci = -J; sg = -sg; } else if (J > nc - 1) { ci = 2 * (nc - 1) - J; sg = -sg; }
+        return sg * x[(size_t)ri * nc + ci];
+    } else {
+        int ri0, ri1; T cr0, cr1;
+        if (I < 0) { ri0 = 0; cr0 = T(2); ri1 = -I; cr1 = T(-1); }
+        else if (I >= nr) { ri0 = nr - 1; cr0 = T(2); ri1 = 2 * (nr - 1) - I; cr1 = T(-1); }
+        else { ri0 = I; cr0 = T(1); ri1 = I; cr1 = T(0); }
+        int ci0, ci1; T cc0, cc1;
+        if (J < 0) { ci0 = 0; cc0 = T(2); ci1 = -J; cc1 = T(-1); }
+        else if (J >= nc) { ci0 = nc - 1; cc0 = T(2); ci1 = 2 * (nc - 1) - J; cc1 = T(-1); }
+        else { ci0 = J; cc0 = T(1); ci1 = J; cc1 = T(0); }
+        T v = cr0 * cc0 * x[(size_t)ri0 * nc + ci0];
+        if (cc1 != T(0)) v += cr0 * cc1 * x[(size_t)ri0 * nc + ci1];
+        if (cr1 != T(0)) {
+            v += cr1 * cc0 * x[(size_t)ri1 * nc + ci0];
+            if (cc1 != T(0)) v += cr1 * cc1 * x[(size_t)ri1 * nc + ci1];
+        }
+        return v;
+    }
+}
+
+struct FuseArgs {
+    double alpha;
+    CgState* st;          // non-null: return at once when st->done
+    double* red;
+    unsigned int* ticket;
+    int reduce;           // reduce p^T q (FUSE only)
+    int total_blocks;     // blocks contributing to the reduction (tile + border)
+    int slot0;            // first reduction slot of this kernel
+    int finish_here;      // this kernel holds the last contributing blocks
+};
+
+__device__ __forceinline__ void finish_pq(CgState* st, double pq) {
+    st->pq = pq;
+    if (!finite_pos(pq)) {
+        st->status = TVD_EBREAKDOWN;
+        st->done = 1;
+        st->alpha = 0.0;
+    } else {
+        st->alpha = st->rho / pq;
+    }
+}
+
+// Output tile kernel. EXT selects the extension of the input; for EXT_ODD only
+// interior outputs (1..n-2 in both directions) are written. With FUSE, the
+// output is q = conv + alpha L(w) pv and p^T q is reduced.
+template <typename T, int EXT, bool FUSE>
+__global__ void __launch_bounds__(kThreads)
+blur_tile_kernel(const T* __restrict__ x, T* __restrict__ y, int nr, int nc, int mr, int mc,
+                 const int* __restrict__ tap_ab, const T* __restrict__ tap_h, int ntaps,
+                 const T* __restrict__ w, const T* __restrict__ pv, FuseArgs fa) {
+    if (fa.st && fa.st->done) return;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int TW = BT + 2 * mc, TH = BT + 2 * mr;
+    T* tile = reinterpret_cast<T*>(smem_raw);
+    T* sh = tile + TW * TH;
+    int* sab = reinterpret_cast<int*>(sh + ntaps);
+    for (int k = threadIdx.x; k < ntaps; k += blockDim.x) {
+        sh[k] = tap_h[k];
+        sab[2 * k] = tap_ab[k];
+        sab[2 * k + 1] = tap_ab[ntaps + k];
+    }
+    const int r0 = blockIdx.y * BT - mr, c0 = blockIdx.x * BT - mc;
+    for (int idx = threadIdx.x; idx < TW * TH; idx += blockDim.x) {
+        const int li = idx / TW, lj = idx - li * TW;
+        tile[idx] = ext_value<T, EXT>(x, r0 + li, c0 + lj, nr, nc, mr, mc);
+    }
+    __syncthreads();
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+    constexpr int PER = BT / BROWS;
+    T acc[PER];
+#pragma unroll
+    for (int q = 0; q < PER; ++q) acc[q] = T(0);
+    for (int k = 0; k < ntaps; ++k) {
+        const T hv = sh[k];
+        const int a = sab[2 * k], b = sab[2 * k + 1];
+        const T* base = tile + (ty + mr - a) * TW + (tx + mc - b);
+#pragma unroll
+        for (int q = 0; q < PER; ++q) acc[q] += hv * base[q * BROWS * TW];
+    }
+    double part = 0.0;
+    const int j = blockIdx.x * BT + tx;
+#pragma unroll
+    for (int q = 0; q < PER; ++q) {
+        const int i = blockIdx.y * BT + ty + q * BROWS;
+        if (i >= nr || j >= nc) continue;
+        if (EXT == EXT_ODD && (i == 0 || i == nr - 1 || j == 0 || j == nc - 1)) continue;
+        T out = acc[q];
+        if (FUSE) {
+            out += T(fa.alpha) * lap_at(w, pv, i, j, nr, nc);
+            part += (double)pv[(size_t)i * nc + j] * (double)out;
+        }
+        y[(size_t)i * nc + j] = out;
+    }
+    if (FUSE && fa.reduce) {
+        const int slot = fa.slot0 + blockIdx.y * gridDim.x + blockIdx.x;
+        double s;
+        if (block_reduce_last(part, fa.red, fa.ticket, slot, fa.total_blocks, &s) && threadIdx.x == 0 &&
+            fa.finish_here)
+            finish_pq(fa.st, s);
+    }
+}
+
+// odd extension along one axis: returns sign (0 on the boundary line) and index
+__device__ __forceinline__ int odd_map(int I, int n, int* idx) {
+    if (I == 0 || I == n - 1) { *idx = 0; return 0; }
+    if (I < 0) { *idx = -I; return -1; }
+    if (I > n - 1) { *idx = 2 * (n - 1) - I; return -1; }
+    *idx = I;
+    return 1;
+}
+
+// First/last rows and columns of H^T y under AR BCs (one thread per output).
+template <typename T, bool FUSE>
+__global__ void __launch_bounds__(kThreads)
+ar_adjoint_border_kernel(const T* __restrict__ y, T* __restrict__ out, int nr, int nc, int mr, int mc,
+                         const T* __restrict__ crow, const T* __restrict__ ccol, const T* __restrict__ ccor,
+                         const T* __restrict__ w, const T* __restrict__ pv, FuseArgs fa) {
+    if (fa.st && fa.st->done) return;
+    const int nrow = nc - 2, ncol = nr - 2;              // interior outputs on each row / column border
+    const int total = 2 * nrow + 2 * ncol + 4;
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    double part = 0.0;
+    if (t < total) {
+        int oi, oj;
+        T acc = T(0);
+        if (t < 2 * nrow) {                                // rows 0 / nr-1, interior columns
+            const bool top = t < nrow;
+            const int l = 1 + (top ? t : t - nrow);
+            oi = top ? 0 : nr - 1;
+            oj = l;
+            for (int i = 0; i <= mr; ++i) {
+                const int ri = top ? i : nr - 1 - i;
+                const T* crw = crow + (size_t)i * (2 * mc + 1);
+                for (int b = -mc; b <= mc; ++b) {
+                    int ci;
+                    const int sg = odd_map(l + b, nc, &ci);
+                    if (sg) acc += crw[b + mc] * T(sg) * y[(size_t)ri * nc + ci];
+                }
+            }
+        } else if (t < 2 * nrow + 2 * ncol) {              // columns 0 / nc-1, interior rows
+            const int u = t - 2 * nrow;
+            const bool left = u < ncol;
+            const int k = 1 + (left ? u : u - ncol);
+            oi = k;
+            oj = left ? 0 : nc - 1;
+            for (int a = -mr; a <= mr; ++a) {
+                int ri;
+                const int sg = odd_map(k + a, nr, &ri);
+                if (!sg) continue;
+                const T* ccl = ccol + (size_t)(a + mr) * (mc + 1);
+                for (int j = 0; j <= mc; ++j) {
+                    const int cj = left ? j : nc - 1 - j;
+                    acc += ccl[j] * T(sg) * y[(size_t)ri * nc + cj];
+                }
+            }
+        } else {                                           // the four corners
+            const int c = t - 2 * nrow - 2 * ncol;
+            const bool top = (c & 1) == 0, left = (c & 2) == 0;
+            oi = top ? 0 : nr - 1;
+            oj = left ? 0 : nc - 1;
+            for (int i = 0; i <= mr; ++i) {
+                const int ri = top ? i : nr - 1 - i;
+                for (int j = 0; j <= mc; ++j) {
+                    const int cj = left ? j : nc - 1 - j;
+                    acc += ccor[(size_t)i * (mc + 1) + j] * y[(size_t)ri * nc + cj];
+                }
+            }
+        }
+        if (FUSE) {
+            acc += T(fa.alpha) * lap_at(w, pv, oi, oj, nr, nc);
+            part = (double)pv[(size_t)oi * nc + oj] * (double)acc;
+        }
+        out[(size_t)oi * nc + oj] = acc;
+    }
+    if (FUSE && fa.reduce) {
+        double s;
+        if (block_reduce_last(part, fa.red, fa.ticket, fa.slot0 + blockIdx.x, fa.total_blocks, &s) &&
+            threadIdx.x == 0 && fa.finish_here)
+            finish_pq(fa.st, s);
+    }
+}
+
+static size_t tile_smem(int mr, int mc, int ntaps, size_t elem) {
+    return (size_t)(BT + 2 * mc) * (BT + 2 * mr) * elem + (size_t)ntaps * (elem + 2 * sizeof(int)) + 16;
+}
+
+template <typename T>
+static tvd_status launch_blur(const tvd_plan_s& p, const Ops<T>& o, bool transpose, const T* x, T* y,
+                              const T* w, const T* pv, double alpha, CgState* st, cudaStream_t s) {
+    const int nr = p.nr, nc = p.nc, mr = p.psf.mr, mc = p.psf.mc;
+    const dim3 grid((nc + BT - 1) / BT, (nr + BT - 1) / BT);
+    const size_t smem = tile_smem(mr, mc, o.ntaps, sizeof(T));
+    const bool fuse = (w != nullptr);
+    FuseArgs fa{alpha, st, p.red, p.ticket + 1, (fuse && st) ? 1 : 0, 0, 0, 0};
+    const int tile_blocks = (int)(grid.x * grid.y);
+    const int nborder = 2 * (nc - 2) + 2 * (nr - 2) + 4;
+    const int border_blocks = (nborder + kThreads - 1) / kThreads;
+    const bool ar_adj = transpose && p.bc == TVD_BC_ANTIREFLECTIVE;
+    if (fa.reduce) {
+        fa.total_blocks = tile_blocks + (ar_adj ? border_blocks : 0);
+        if (fa.total_blocks > kMaxRedBlocks) {
+            set_error("image too large for the reduction buffer");
+            return TVD_EINVAL;
+        }
+    }
+    if (!ar_adj) {
+        // forward H for both BCs, and H^T = H for reflective BCs
+        fa.finish_here = 1;
+        if (p.bc == TVD_BC_ANTIREFLECTIVE) {
+            if (fuse) {
+                cudaFuncSetAttribute(blur_tile_kernel<T, EXT_AR, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+                blur_tile_kernel<T, EXT_AR, true><<<grid, kThreads, smem, s>>>(x, y, nr, nc, mr, mc, o.tap_ab, o.tap_h, o.ntaps, w, pv, fa);
+            } else {
+                cudaFuncSetAttribute(blur_tile_kernel<T, EXT_AR, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+                blur_tile_kernel<T, EXT_AR, false><<<grid, kThreads, smem, s>>>(x, y, nr, nc, mr, mc, o.tap_ab, o.tap_h, o.ntaps, w, pv, fa);
+            }
+        } else {
+            if (fuse) {
+                cudaFuncSetAttribute(blur_tile_kernel<T, EXT_R, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+                blur_tile_kernel<T, EXT_R, true><<<grid, kThreads, smem, s>>>(x, y, nr, nc, mr, mc, o.tap_ab, o.tap_h, o.ntaps, w, pv, fa);
+            } else {
+                cudaFuncSetAttribute(blur_tile_kernel<T, EXT_R, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+                blur_tile_kernel<T, EXT_R, false><<<grid, kThreads, smem, s>>>(x, y, nr, nc, mr, mc, o.tap_ab, o.tap_h, o.ntaps, w, pv, fa);
+            }
+        }
+    } else {
+        fa.finish_here = 0;
+        fa.slot0 = 0;
+        if (fuse) {
+            cudaFuncSetAttribute(blur_tile_kernel<T, EXT_ODD, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            blur_tile_kernel<T, EXT_ODD, true><<<grid, kThreads, smem, s>>>(x, y, nr, nc, mr, mc, o.tap_ab, o.tap_h, o.ntaps, w, pv, fa);
+        } else {
+            cudaFuncSetAttribute(blur_tile_kernel<T, EXT_ODD, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            blur_tile_kernel<T, EXT_ODD, false><<<grid, kThreads, smem, s>>>(x, y, nr, nc, mr, mc, o.tap_ab, o.tap_h, o.ntaps, w, pv, fa);
+        }
+        fa.finish_here = 1;
+        fa.slot0 = tile_blocks;
+        if (fuse)
+            ar_adjoint_border_kernel<T, true><<<border_blocks, kThreads, 0, s>>>(x, y, nr, nc, mr, mc, o.crow, o.ccol, o.ccor, w, pv, fa);
+        else
+            ar_adjoint_border_kernel<T, false><<<border_blocks, kThreads, 0, s>>>(x, y, nr, nc, mr, mc, o.crow, o.ccol, o.ccor, w, pv, fa);
+    }
+    TVD_CUDA_TRY(cudaGetLastError());
+    return TVD_OK;
+}
+
+template <typename T>
+tvd_status blur_apply(const tvd_plan_s& p, const Ops<T>& o, bool transpose, const T* x, T* y, cudaStream_t s,
+                      CgState* st) {
+    return launch_blur<T>(p, o, transpose, x, y, nullptr, nullptr, 0.0, st, s);
+}
+
+template <typename T>
+tvd_status normal_finish(const tvd_plan_s& p, const Ops<T>& o, const T* t, const T* pv, double alpha, T* q,
+                         CgState* st, cudaStream_t s) {
+    return launch_blur<T>(p, o, true, t, q, o.w, pv, alpha, st, s);
+}
+
+template tvd_status blur_apply<float>(const tvd_plan_s&, const Ops<float>&, bool, const float*, float*, cudaStream_t,
+                                      CgState*);
+template tvd_status blur_apply<double>(const tvd_plan_s&, const Ops<double>&, bool, const double*, double*,
+                                       cudaStream_t, CgState*);
+template tvd_status normal_finish<float>(const tvd_plan_s&, const Ops<float>&, const float*, const float*, double,
+                                         float*, CgState*, cudaStream_t);
+template tvd_status normal_finish<double>(const tvd_plan_s&, const Ops<double>&, const double*, const double*, double,
+                                          double*, CgState*, cudaStream_t);
+
+}  // namespace tvd

@@ -1,0 +1,80 @@
+// Device helpers shared by the kernels: deterministic block reductions with a
+// last-block finisher, and the CG scalar finishers.
+#pragma once
+
+#include "tvd_internal.cuh"
+
+namespace tvd {
+
+constexpr int kThreads = 256;
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// Block-wide sum in a fixed order; result valid in thread 0.
+__device__ __forceinline__ double block_sum(double v) {
+    __shared__ double ws[32];
+    v = warp_sum(v);
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    __syncthreads();
+    if (lane == 0) ws[wid] = v;
+    __syncthreads();
+    const int nw = (blockDim.x + 31) >> 5;
+    double s = 0.0;
+    if (wid == 0) {
+        s = lane < nw ? ws[lane] : 0.0;
+        s = warp_sum(s);
+    }
+    return s;
+}
+
+// Writes this block's partial into red[slot]; the last block to arrive (over
+// `total` blocks, possibly spread over several kernels that share `ticket`)
+// sums red[0..total) in a fixed order and returns true with the sum in *out
+// (thread 0 only). The ticket is reset for the next use.
+__device__ __forceinline__ bool block_reduce_last(double v, double* red, unsigned int* ticket, int slot,
+                                                   int total, double* out) {
+    __shared__ bool s_last;
+    double b = block_sum(v);
+    if (threadIdx.x == 0) {
+        red[slot] = b;
+        __threadfence();
+        unsigned int t = atomicAdd(ticket, 1u);
+        s_last = (t == (unsigned int)(total - 1));
+    }
+    __syncthreads();
+    if (!s_last) return false;
+    __threadfence();
+    double acc = 0.0;
+    if (threadIdx.x < 32) {
+        // fixed order: lane l sums slots l, l+32, ... in increasing order
+        for (int i = threadIdx.x; i < total; i += 32) acc += ((volatile double*)red)[i];
+        acc = warp_sum(acc);
+    }
+    if (threadIdx.x == 0) {
+        *out = acc;
+        *ticket = 0u;
+    }
+    return true;
+}
+
+// (L(w) p)_{ij}, 5-point stencil of D_r^T W D_r + D_c^T W D_c (zero Neumann).
+template <typename T>
+__device__ __forceinline__ T lap_at(const T* __restrict__ w, const T* __restrict__ p, int i, int j, int nr, int nc) {
+    const size_t o = (size_t)i * nc + j;
+    const T pc = p[o];
+    const T wc = w[o];
+    T acc = T(0);
+    if (i < nr - 1) acc += wc * (pc - p[o + nc]);
+    if (j < nc - 1) acc += wc * (pc - p[o + 1]);
+    if (i > 0) acc += w[o - nc] * (pc - p[o - nc]);
+    if (j > 0) acc += w[o - 1] * (pc - p[o - 1]);
+    return acc;
+}
+
+__device__ __forceinline__ bool finite_pos(double v) { return isfinite(v) && v > 0.0; }
+
+}  // namespace tvd

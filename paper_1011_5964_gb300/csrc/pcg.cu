@@ -1,0 +1,261 @@
+// Vector kernels of the preconditioned CG of Golub & Van Loan, Alg. 10.3.1
+// (cited in Sec. 1 of the paper): residual initialisation, search-direction
+// update, iterate/residual update with the stopping test ||r_k|| / ||r_0|| < tol
+// (Sec. 5), and the plain preconditioners I and D = I + alpha diag(L) (eq. (D)).
+//
+// Scalars live in a device CgState (double in every mode); each reduction is a
+// fixed-order two-stage sum (per-block partials, then the last block), so
+// results are bit-reproducible run to run. Every kernel returns at once when
+// the state says the solve is done, so the host may enqueue iterations ahead
+// of the convergence test.
+#include "common.cuh"
+
+namespace tvd {
+
+int num_sms() {
+    static int n = 0;
+    if (n == 0) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+        if (n <= 0) n = 1;
+    }
+    return n;
+}
+
+static int red_blocks(size_t n) {
+    size_t b = (n + kThreads - 1) / kThreads;
+    size_t cap = (size_t)num_sms() * 4;
+    if (cap > (size_t)kMaxRedBlocks) cap = kMaxRedBlocks;
+    return (int)(b < cap ? (b ? b : 1) : cap);
+}
+
+#define GRID_STRIDE(o, n) for (size_t o = blockIdx.x * (size_t)blockDim.x + threadIdx.x; o < (n); o += (size_t)gridDim.x * blockDim.x)
+
+template <typename T>
+__global__ void __launch_bounds__(kThreads)
+cg_init_kernel(const T* __restrict__ b, const T* __restrict__ ax, T* __restrict__ r, size_t n, CgState* st,
+               double* red, unsigned int* ticket, double tol, int maxit) {
+    double part = 0.0;
+    GRID_STRIDE(o, n) {
+        const T v = b[o] - ax[o];
+        r[o] = v;
+        part += (double)v * (double)v;
+    }
+    double s;
+    if (block_reduce_last(part, red, ticket, blockIdx.x, gridDim.x, &s) && threadIdx.x == 0) {
+        st->rr0 = s;
+        st->rr = s;
+        st->tol2 = tol * tol * s;
+        st->iter = 0;
+        st->maxit = maxit;
+        st->rho = 0.0;
+        st->rho_old = 0.0;
+        st->beta = 0.0;
+        st->alpha = 0.0;
+        st->pq = 0.0;
+        st->status = TVD_OK;
+        st->done = 0;
+        if (!isfinite(s)) {
+            st->status = TVD_EBREAKDOWN;
+            st->done = 1;
+        } else if (s == 0.0 || maxit <= 0) {
+            st->done = 1;
+            if (s != 0.0) st->status = TVD_ENOCONV;
+        }
+    }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kThreads)
+cg_pupdate_kernel(const T* __restrict__ z, T* __restrict__ p, size_t n, const CgState* st) {
+    if (st->done) return;
+    const bool first = st->iter == 0;
+    const T beta = T(st->beta);
+    GRID_STRIDE(o, n) p[o] = first ? z[o] : z[o] + beta * p[o];
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kThreads)
+cg_xr_kernel(T* __restrict__ x, T* __restrict__ r, const T* __restrict__ p, const T* __restrict__ q, size_t n,
+             CgState* st, double* red, unsigned int* ticket) {
+    if (st->done) return;
+    const T a = T(st->alpha);
+    double part = 0.0;
+    GRID_STRIDE(o, n) {
+        x[o] += a * p[o];
+        const T rv = r[o] - a * q[o];
+        r[o] = rv;
+        part += (double)rv * (double)rv;
+    }
+    double s;
+    if (block_reduce_last(part, red, ticket, blockIdx.x, gridDim.x, &s) && threadIdx.x == 0) {
+        st->rr = s;
+        st->iter += 1;
+        if (!isfinite(s)) {
+            st->status = TVD_EBREAKDOWN;
+            st->done = 1;
+        } else if (s < st->tol2) {
+            st->done = 1;
+        } else if (st->iter >= st->maxit) {
+            st->status = TVD_ENOCONV;
+            st->done = 1;
+        }
+    }
+}
+
+// z = r (I) or z = r / D (diagonal preconditioner), with r^T z and the beta update.
+template <typename T>
+__global__ void __launch_bounds__(kThreads)
+cg_simple_precond_kernel(const T* __restrict__ r, const T* __restrict__ dinv, T* __restrict__ z, size_t n,
+                         CgState* st, double* red, unsigned int* ticket) {
+    if (st && st->done) return;
+    double part = 0.0;
+    GRID_STRIDE(o, n) {
+        const T v = dinv ? r[o] * dinv[o] : r[o];
+        if (z != r) z[o] = v;
+        part += (double)r[o] * (double)v;
+    }
+    if (!st) return;
+    double s;
+    if (block_reduce_last(part, red, ticket, blockIdx.x, gridDim.x, &s) && threadIdx.x == 0) {
+        st->rho_old = st->rho;
+        st->rho = s;
+        if (!(isfinite(s) && s > 0.0)) {
+            st->status = TVD_EBREAKDOWN;
+            st->done = 1;
+            st->beta = 0.0;
+        } else {
+            st->beta = st->iter == 0 ? 0.0 : s / st->rho_old;
+        }
+    }
+}
+
+template <typename T>
+tvd_status cg_init(const tvd_plan_s& p, const T* b, const T* ax, T* r, CgState* st, double tol, int maxit,
+                   cudaStream_t s) {
+    const size_t n = (size_t)p.nr * p.nc;
+    cg_init_kernel<T><<<red_blocks(n), kThreads, 0, s>>>(b, ax, r, n, st, p.red, p.ticket + 0, tol, maxit);
+    TVD_CUDA_TRY(cudaGetLastError());
+    return TVD_OK;
+}
+
+template <typename T>
+tvd_status cg_pupdate(const tvd_plan_s& p, const T* z, T* pv, CgState* st, cudaStream_t s) {
+    const size_t n = (size_t)p.nr * p.nc;
+    cg_pupdate_kernel<T><<<red_blocks(n), kThreads, 0, s>>>(z, pv, n, st);
+    TVD_CUDA_TRY(cudaGetLastError());
+    return TVD_OK;
+}
+
+template <typename T>
+tvd_status cg_xrupdate(const tvd_plan_s& p, T* x, T* r, const T* pv, const T* q, CgState* st, cudaStream_t s) {
+    const size_t n = (size_t)p.nr * p.nc;
+    cg_xr_kernel<T><<<red_blocks(n), kThreads, 0, s>>>(x, r, pv, q, n, st, p.red, p.ticket + 3);
+    TVD_CUDA_TRY(cudaGetLastError());
+    return TVD_OK;
+}
+
+template <typename T>
+tvd_status cg_simple_precond(const tvd_plan_s& p, const T* r, const T* dinv, T* z, CgState* st, cudaStream_t s) {
+    const size_t n = (size_t)p.nr * p.nc;
+    cg_simple_precond_kernel<T><<<red_blocks(n), kThreads, 0, s>>>(r, dinv, z, n, st, p.red, p.ticket + 4);
+    TVD_CUDA_TRY(cudaGetLastError());
+    return TVD_OK;
+}
+
+// ---------------------------------------------------------------- double helpers
+
+__global__ void __launch_bounds__(kThreads)
+residual_kernel(const double* __restrict__ b, const double* __restrict__ ax, double* __restrict__ r, size_t n,
+                double* out, double* red, unsigned int* ticket) {
+    double part = 0.0;
+    GRID_STRIDE(o, n) {
+        const double v = b[o] - ax[o];
+        r[o] = v;
+        part += v * v;
+    }
+    double s;
+    if (block_reduce_last(part, red, ticket, blockIdx.x, gridDim.x, &s) && threadIdx.x == 0) *out = s;
+}
+
+__global__ void __launch_bounds__(kThreads)
+diffnorm_kernel(const double* __restrict__ a, const double* __restrict__ b, size_t n, double* out, double* red,
+                unsigned int* ticket) {
+    double part = 0.0;
+    GRID_STRIDE(o, n) {
+        const double v = b ? a[o] - b[o] : a[o];
+        part += v * v;
+    }
+    double s;
+    if (block_reduce_last(part, red, ticket, blockIdx.x, gridDim.x, &s) && threadIdx.x == 0) *out = s;
+}
+
+__global__ void cast_d2f_kernel(const double* __restrict__ a, float* __restrict__ b, size_t n) {
+    GRID_STRIDE(o, n) b[o] = (float)a[o];
+}
+__global__ void axpy_f2d_kernel(double* __restrict__ x, const float* __restrict__ d, size_t n) {
+    GRID_STRIDE(o, n) x[o] += (double)d[o];
+}
+__global__ void copy_f_kernel(const float* __restrict__ a, float* __restrict__ b, size_t n) {
+    GRID_STRIDE(o, n) b[o] = a[o];
+}
+__global__ void fill_zero_f_kernel(float* __restrict__ a, size_t n) {
+    GRID_STRIDE(o, n) a[o] = 0.0f;
+}
+
+tvd_status residual_d(const tvd_plan_s& p, const double* b, const double* ax, double* r, double* out_norm2,
+                      cudaStream_t s) {
+    const size_t n = (size_t)p.nr * p.nc;
+    residual_kernel<<<red_blocks(n), kThreads, 0, s>>>(b, ax, r, n, out_norm2, p.red, p.ticket + 5);
+    TVD_CUDA_TRY(cudaGetLastError());
+    return TVD_OK;
+}
+
+tvd_status norm2_d(const tvd_plan_s& p, const double* a, double* out, cudaStream_t s) {
+    const size_t n = (size_t)p.nr * p.nc;
+    diffnorm_kernel<<<red_blocks(n), kThreads, 0, s>>>(a, nullptr, n, out, p.red, p.ticket + 5);
+    TVD_CUDA_TRY(cudaGetLastError());
+    return TVD_OK;
+}
+
+tvd_status diffnorm2_d(const tvd_plan_s& p, const double* a, const double* b, double* out, cudaStream_t s) {
+    const size_t n = (size_t)p.nr * p.nc;
+    diffnorm_kernel<<<red_blocks(n), kThreads, 0, s>>>(a, b, n, out, p.red, p.ticket + 5);
+    TVD_CUDA_TRY(cudaGetLastError());
+    return TVD_OK;
+}
+
+tvd_status cast_d2f(const double* a, float* b, size_t n, cudaStream_t s) {
+    cast_d2f_kernel<<<red_blocks(n), kThreads, 0, s>>>(a, b, n);
+    TVD_CUDA_TRY(cudaGetLastError());
+    return TVD_OK;
+}
+
+tvd_status axpy_f2d(double* x, const float* d, size_t n, cudaStream_t s) {
+    axpy_f2d_kernel<<<red_blocks(n), kThreads, 0, s>>>(x, d, n);
+    TVD_CUDA_TRY(cudaGetLastError());
+    return TVD_OK;
+}
+
+tvd_status copy_f(const float* a, float* b, size_t n, cudaStream_t s) {
+    copy_f_kernel<<<red_blocks(n), kThreads, 0, s>>>(a, b, n);
+    TVD_CUDA_TRY(cudaGetLastError());
+    return TVD_OK;
+}
+
+tvd_status fill_zero_f(float* a, size_t n, cudaStream_t s) {
+    fill_zero_f_kernel<<<red_blocks(n), kThreads, 0, s>>>(a, n);
+    TVD_CUDA_TRY(cudaGetLastError());
+    return TVD_OK;
+}
+
+#define INST(T)                                                                                                  \
+    template tvd_status cg_init<T>(const tvd_plan_s&, const T*, const T*, T*, CgState*, double, int, cudaStream_t); \
+    template tvd_status cg_pupdate<T>(const tvd_plan_s&, const T*, T*, CgState*, cudaStream_t);                  \
+    template tvd_status cg_xrupdate<T>(const tvd_plan_s&, T*, T*, const T*, const T*, CgState*, cudaStream_t);   \
+    template tvd_status cg_simple_precond<T>(const tvd_plan_s&, const T*, const T*, T*, CgState*, cudaStream_t);
+INST(float)
+INST(double)
+
+}  // namespace tvd

@@ -1,0 +1,732 @@
+// Fast trigonometric transforms of the preconditioners (Secs. 2-3 of the paper)
+// and the preconditioner spectrum.
+//
+// The 2D transform U = B_r (x) B_c acts on an n_r x n_c image as a pass over
+// rows (B_c on each row) and a pass over columns (B_r on each column):
+//   AR: B = hat-S_n = diag(1, S_{n-2}, 1), S_m the orthonormal DST-I of eq. (lambda);
+//   R:  B = C, the orthonormal DCT-II of Sec. 3.1; B^{-1} = C^T (DCT-III).
+// The preconditioner solve (D_R / D_M, Sec. 3.2) is
+//   z = D^{-1/2} U^{-1} [ (U D^{-1/2} r) / (Lambda_H^2 + alpha Lambda_L) ],
+// done in three kernels: row pass (scale, forward), column pass (forward,
+// divide by the spectrum, inverse, all in shared memory), row pass (inverse,
+// scale, r^T z).
+//
+// Every line transform is computed from one complex FFT of a pair of real
+// lines packed as re + i im, in shared memory (Stockham autosort, mixed radix;
+// radices up to 31 in registers, larger prime factors by direct sums):
+//   DST-I, length N = n-2, M = N+1: with y_j = sin(j pi/M)(x_j + x_{M-j})
+//     + (x_j - x_{M-j})/2 (x_0 = x_M = 0) and Y = DFT_M(y):
+//     F_{2k} = -Im Y_k, F_{2k+1} = F_{2k-1} + Re Y_k, F_1 = Re Y_0 / 2;
+//     S_N x = sqrt(2/M) F. (The auxiliary-array method for the sine
+//     transform via a real FFT of length M.)
+//   DCT-II, length n: Makhoul's even/odd reordering v, V = DFT_n(v),
+//     X_k = c_k Re(exp(-i pi k/(2n)) V_k); DCT-III inverts these steps.
+// Preconditioner spectrum: Lambda_L[i,j] = (b_i (x) b_j)^T L (b_i (x) b_j)
+// = sum_pq w_pq [G_r(i,p) E_c(j,q) + E_r(i,p) G_c(j,q)] with E = b_k(p)^2,
+// G = ((D_1 b_k)_p)^2. For the sine and cosine bases every row of E and G is
+// a constant plus a cosine series, so E f and G f for a line f come from one
+// real DFT of f; a row pass gives E_c w and G_c w, a column pass combines them.
+#include "common.cuh"
+
+#include <cmath>
+
+namespace tvd {
+
+enum { OP_ROW_FWD = 0, OP_COL_SOLVE = 1, OP_ROW_INV = 2, OP_ROW_EG = 3, OP_COL_EG = 4 };
+enum { BCK_AR = 0, BCK_R = 1 };
+
+// Auxiliary tables per transform length, 8 slots of 2n values of T each:
+//  AR: slot0 sin(j pi / M)              (real, j < M)
+//      slot1 exp(i pi k / M)            (complex)
+//      slot2 (4/M) sin^2(k pi / (2M))   (real)
+//  R:  slot0 c_k                        (real)
+//      slot1 (cos, sin)(pi k / (2n))    (complex)
+//      slot2 exp(i pi k / n)            (complex)
+//      slot3 c_k^2 / 2                  (real)
+//      slot4 2 c_k^2 sin^2(pi k / (2n)) (real)
+//      slot5 1 / (n c_k)                (real)
+constexpr int kAuxSlots = 8;
+
+template <typename T>
+struct LineArgs {
+    const T* in0;        // input lines (x / t / w / A)
+    const T* in1;        // second input (B for OP_COL_EG)
+    T* out0;             // output lines
+    T* out1;             // second output (B for OP_ROW_EG)
+    const T* scale;      // D^{-1/2} (optional), applied on load (ROW_FWD) or store (ROW_INV)
+    const T* spec;       // inv_spec (COL_SOLVE) / lamH2 (COL_EG)
+    T* inv_out;          // COL_EG: inv_spec output
+    const T* rvec;       // ROW_INV: r for r^T z
+    const cplx<T>* tw;   // twiddles, length L
+    const T* aux;        // auxiliary tables, kAuxSlots * 2n
+    int n;               // line length
+    int nlines;          // number of lines (image lines)
+    int nr, nc;          // image shape
+    int P;               // line pairs per block
+    int L;               // complex FFT length
+    FftPlan fp;
+    double alpha;
+    CgState* st;
+    double* red;
+    unsigned int* ticket;
+    int* bad;            // COL_EG: set if a spectrum entry is not positive
+};
+
+template <typename T>
+__device__ __forceinline__ cplx<T> cmul(cplx<T> a, cplx<T> b) {
+    return {a.re * b.re - a.im * b.im, a.re * b.im + a.im * b.re};
+}
+
+// ------------------------------------------------------------- FFT stages
+
+// R-point DFT of v (already multiplied by the stage twiddles), written to
+// dst[t * Ns], t = 0..R-1. Radix constants exp(-+2 pi i t / R) come from the
+// shared twiddle table (tw[t * LR], conjugated for the inverse transform).
+template <typename T, int R>
+__device__ __forceinline__ void dft_store(cplx<T> (&v)[R], cplx<T>* __restrict__ dst, int Ns,
+                                          const cplx<T>* __restrict__ tw, int LR, bool inv) {
+    if constexpr (R == 2) {
+        dst[0] = {v[0].re + v[1].re, v[0].im + v[1].im};
+        dst[Ns] = {v[0].re - v[1].re, v[0].im - v[1].im};
+    } else if constexpr (R == 4) {
+        const T sg = inv ? T(1) : T(-1);      // exp(-+ i pi / 2) = -+ i
+        const cplx<T> s02 = {v[0].re + v[2].re, v[0].im + v[2].im};
+        const cplx<T> d02 = {v[0].re - v[2].re, v[0].im - v[2].im};
+        const cplx<T> s13 = {v[1].re + v[3].re, v[1].im + v[3].im};
+        const cplx<T> d13 = {v[1].re - v[3].re, v[1].im - v[3].im};
+        const cplx<T> jd = {-sg * d13.im, sg * d13.re};
+        dst[0] = {s02.re + s13.re, s02.im + s13.im};
+        dst[2 * Ns] = {s02.re - s13.re, s02.im - s13.im};
+        dst[Ns] = {d02.re + jd.re, d02.im + jd.im};
+        dst[3 * Ns] = {d02.re - jd.re, d02.im - jd.im};
+    } else {
+        // out[k] = v0 + sum_{j=1}^{H} (s_j cos_jk + i d_j sin_jk) [+ v_{R/2} (-1)^k],
+        // s_j = v_j + v_{R-j}, d_j = v_j - v_{R-j}; out[R-k] takes the opposite sign of i.
+        constexpr int H = (R - 1) / 2;
+        constexpr bool even = (R % 2) == 0;
+        const cplx<T> v0 = v[0];
+        cplx<T> vh = {T(0), T(0)};
+        if constexpr (even) vh = v[R / 2];
+#pragma unroll
+        for (int j = 1; j <= H; ++j) {
+            const cplx<T> a = v[j], b = v[R - j];
+            v[j] = {a.re + b.re, a.im + b.im};
+            v[R - j] = {a.re - b.re, a.im - b.im};
+        }
+        cplx<T> o0 = v0;
+#pragma unroll
+        for (int j = 1; j <= H; ++j) { o0.re += v[j].re; o0.im += v[j].im; }
+        if constexpr (even) { o0.re += vh.re; o0.im += vh.im; }
+        dst[0] = o0;
+#pragma unroll
+        for (int k = 1; k <= H; ++k) {
+            cplx<T> a = v0, b = {T(0), T(0)};
+#pragma unroll
+            for (int j = 1; j <= H; ++j) {
+                const cplx<T> wk = tw[((j * k) % R) * LR];
+                const T sn = inv ? -wk.im : wk.im;
+                a.re += v[j].re * wk.re; a.im += v[j].im * wk.re;
+                b.re += v[R - j].re * sn; b.im += v[R - j].im * sn;
+            }
+            if constexpr (even) {
+                const T sg = (k & 1) ? T(-1) : T(1);
+                a.re += sg * vh.re; a.im += sg * vh.im;
+            }
+            dst[k * Ns] = {a.re - b.im, a.im + b.re};
+            dst[(R - k) * Ns] = {a.re + b.im, a.im - b.re};
+        }
+        if constexpr (even) {
+            cplx<T> m = v0;
+#pragma unroll
+            for (int j = 1; j <= H; ++j) {
+                const T sg = (j & 1) ? T(-1) : T(1);
+                m.re += sg * v[j].re; m.im += sg * v[j].im;
+            }
+            const T sh = ((R / 2) & 1) ? T(-1) : T(1);
+            m.re += sh * vh.re; m.im += sh * vh.im;
+            dst[(R / 2) * Ns] = m;
+        }
+    }
+}
+
+template <typename T, int R>
+__device__ void fft_stage(const cplx<T>* __restrict__ in, cplx<T>* __restrict__ out, int P, int L, int Ns,
+                          const cplx<T>* __restrict__ tw, bool inv) {
+    const int LR = L / R;
+    const int ts = L / (Ns * R);
+    for (int bf = threadIdx.x; bf < P * LR; bf += blockDim.x) {
+        const int pp = bf / LR, j = bf - pp * LR;
+        const cplx<T>* src = in + (size_t)pp * L;
+        const int k = j % Ns;
+        cplx<T> v[R];
+        v[0] = src[j];
+#pragma unroll
+        for (int r = 1; r < R; ++r) {
+            cplx<T> w = tw[k * r * ts];
+            if (inv) w.im = -w.im;
+            v[r] = cmul(src[j + r * LR], w);
+        }
+        dft_store<T, R>(v, out + (size_t)pp * L + (j / Ns) * Ns * R + k, Ns, tw, LR, inv);
+    }
+}
+
+// Radix without a register kernel: one thread per output, direct sum over R inputs.
+template <typename T>
+__device__ void fft_stage_generic(const cplx<T>* __restrict__ in, cplx<T>* __restrict__ out, int P, int L, int Ns,
+                                  int R, const cplx<T>* __restrict__ tw, bool inv) {
+    const int LR = L / R;
+    const int ts = L / (Ns * R);
+    for (int e = threadIdx.x; e < P * L; e += blockDim.x) {
+        const int pp = e / L, q = e - pp * L;
+        const int t = q / LR, j = q - t * LR;
+        const int k = j % Ns;
+        const cplx<T>* src = in + (size_t)pp * L;
+        cplx<T> acc = {T(0), T(0)};
+        for (int r = 0; r < R; ++r) {
+            cplx<T> w1 = tw[k * r * ts];
+            cplx<T> w2 = tw[((r * t) % R) * LR];
+            if (inv) { w1.im = -w1.im; w2.im = -w2.im; }
+            const cplx<T> x = cmul(cmul(src[j + r * LR], w1), w2);
+            acc.re += x.re;
+            acc.im += x.im;
+        }
+        out[(size_t)pp * L + (j / Ns) * Ns * R + k + t * Ns] = acc;
+    }
+}
+
+// Runs all stages; returns the buffer holding the result.
+template <typename T>
+__device__ cplx<T>* fft_pairs(cplx<T>* a, cplx<T>* b, int P, const FftPlan& fp, const cplx<T>* tw, bool inv) {
+    const int L = fp.L;
+    int Ns = 1;
+    for (int s = 0; s < fp.nstages; ++s) {
+        const int R = fp.radix[s];
+        switch (R) {
+            case 2: fft_stage<T, 2>(a, b, P, L, Ns, tw, inv); break;
+            case 3: fft_stage<T, 3>(a, b, P, L, Ns, tw, inv); break;
+            case 4: fft_stage<T, 4>(a, b, P, L, Ns, tw, inv); break;
+            case 5: fft_stage<T, 5>(a, b, P, L, Ns, tw, inv); break;
+            case 7: fft_stage<T, 7>(a, b, P, L, Ns, tw, inv); break;
+            case 8: fft_stage<T, 8>(a, b, P, L, Ns, tw, inv); break;
+            case 9: fft_stage<T, 9>(a, b, P, L, Ns, tw, inv); break;
+            case 11: fft_stage<T, 11>(a, b, P, L, Ns, tw, inv); break;
+            case 13: fft_stage<T, 13>(a, b, P, L, Ns, tw, inv); break;
+            case 17: fft_stage<T, 17>(a, b, P, L, Ns, tw, inv); break;
+            case 19: fft_stage<T, 19>(a, b, P, L, Ns, tw, inv); break;
+            case 23: fft_stage<T, 23>(a, b, P, L, Ns, tw, inv); break;
+            case 29: fft_stage<T, 29>(a, b, P, L, Ns, tw, inv); break;
+            case 31: fft_stage<T, 31>(a, b, P, L, Ns, tw, inv); break;
+            default: fft_stage_generic<T>(a, b, P, L, Ns, R, tw, inv); break;
+        }
+        __syncthreads();
+        cplx<T>* t = a;
+        a = b;
+        b = t;
+        Ns *= R;
+    }
+    return a;
+}
+
+// ------------------------------------------------------------- line transforms in shared memory
+// raw[l * n + idx]: 2P real lines of length n. bufA, bufB: P complex lines of length L.
+
+template <typename T>
+__device__ __forceinline__ void split_pair(const cplx<T>* Z, int k, int L, cplx<T>& Fa, cplx<T>& Fb) {
+    const cplx<T> z = Z[k];
+    const cplx<T> zm = Z[k == 0 ? 0 : L - k];
+    Fa = {T(0.5) * (z.re + zm.re), T(0.5) * (z.im - zm.im)};
+    Fb = {T(0.5) * (z.im + zm.im), T(-0.5) * (z.re - zm.re)};
+}
+
+// DST-I on positions 1..n-2 of each raw line (AR); positions 0, n-1 untouched.
+template <typename T>
+__device__ void dst1_lines(T* raw, cplx<T>* bufA, cplx<T>* bufB, T* scan, const LineArgs<T>& a,
+                           const cplx<T>* tw) {
+    const int n = a.n, M = n - 1, N = n - 2, P = a.P;
+    const T* sinh = a.aux;                    // slot0
+    for (int e = threadIdx.x; e < P * M; e += blockDim.x) {
+        const int pp = e / M, j = e - pp * M;
+        const T* xa = raw + (size_t)(2 * pp) * n;
+        const T* xb = xa + n;
+        const T a0 = j >= 1 ? xa[j] : T(0), a1 = j >= 1 ? xa[M - j] : T(0);
+        const T b0 = j >= 1 ? xb[j] : T(0), b1 = j >= 1 ? xb[M - j] : T(0);
+        const T sj = __ldg(sinh + j);
+        bufA[(size_t)pp * M + j] = {sj * (a0 + a1) + T(0.5) * (a0 - a1), sj * (b0 + b1) + T(0.5) * (b0 - b1)};
+    }
+    __syncthreads();
+    const cplx<T>* Z = fft_pairs<T>(bufA, bufB, P, a.fp, tw, false);
+    const T sc = sqrt(T(2) / T(M));
+    const int nodd = (N + 1) / 2;             // F_1, F_3, ...
+    const int neven = N / 2;                  // F_2, F_4, ...
+    // even outputs and the R_k terms of the odd recurrence (into scan[line][k])
+    const int K = nodd > neven + 1 ? nodd : neven + 1;
+    for (int e = threadIdx.x; e < P * K; e += blockDim.x) {
+        const int pp = e / K, k = e - pp * K;
+        cplx<T> Fa, Fb;
+        split_pair(Z + (size_t)pp * M, k, M, Fa, Fb);
+        if (k >= 1 && k <= neven) {
+            raw[(size_t)(2 * pp) * n + 2 * k] = -sc * Fa.im;
+            raw[(size_t)(2 * pp + 1) * n + 2 * k] = -sc * Fb.im;
+        }
+        if (k < nodd) {
+            scan[(size_t)(2 * pp) * K + k] = k == 0 ? T(0.5) * Fa.re : Fa.re;
+            scan[(size_t)(2 * pp + 1) * K + k] = k == 0 ? T(0.5) * Fb.re : Fb.re;
+        }
+    }
+    __syncthreads();
+    // inclusive prefix sums of scan, one warp per line
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int l = wid; l < 2 * P; l += nw) {
+        T carry = T(0);
+        for (int c0 = 0; c0 < nodd; c0 += 32) {
+            const int k = c0 + lane;
+            T v = k < nodd ? scan[(size_t)l * K + k] : T(0);
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const T u = __shfl_up_sync(0xffffffffu, v, o);
+                if (lane >= o) v += u;
+            }
+            v += carry;
+            if (k < nodd) raw[(size_t)l * n + 2 * k + 1] = sc * v;
+            carry = __shfl_sync(0xffffffffu, v, 31);
+        }
+    }
+    __syncthreads();
+}
+
+// Orthonormal DCT-II (inv = false) or DCT-III (inv = true) of each raw line (R).
+template <typename T>
+__device__ void dct_lines(T* raw, cplx<T>* bufA, cplx<T>* bufB, const LineArgs<T>& a, const cplx<T>* tw, bool inv) {
+    const int n = a.n, P = a.P, h = (n + 1) / 2;
+    const T* ck = a.aux;                                              // slot0
+    const cplx<T>* th = reinterpret_cast<const cplx<T>*>(a.aux + 2 * n);  // slot1 (cos, sin)(pi k / 2n)
+    const T* icn = a.aux + 10 * n;                                    // slot5 1/(n c_k)
+    if (!inv) {
+        for (int e = threadIdx.x; e < P * n; e += blockDim.x) {
+            const int pp = e / n, p = e - pp * n;
+            const int src = p < h ? 2 * p : 2 * (n - 1 - p) + 1;
+            bufA[(size_t)pp * n + p] = {raw[(size_t)(2 * pp) * n + src], raw[(size_t)(2 * pp + 1) * n + src]};
+        }
+        __syncthreads();
+        const cplx<T>* Z = fft_pairs<T>(bufA, bufB, P, a.fp, tw, false);
+        for (int e = threadIdx.x; e < P * n; e += blockDim.x) {
+            const int pp = e / n, k = e - pp * n;
+            cplx<T> Va, Vb;
+            split_pair(Z + (size_t)pp * n, k, n, Va, Vb);
+            const cplx<T> cs = th[k];
+            const T c = __ldg(ck + k);
+            raw[(size_t)(2 * pp) * n + k] = c * (cs.re * Va.re + cs.im * Va.im);
+            raw[(size_t)(2 * pp + 1) * n + k] = c * (cs.re * Vb.re + cs.im * Vb.im);
+        }
+        __syncthreads();
+    } else {
+        for (int e = threadIdx.x; e < P * n; e += blockDim.x) {
+            const int pp = e / n, k = e - pp * n;
+            const T* xa = raw + (size_t)(2 * pp) * n;
+            const T* xb = xa + n;
+            const T s0 = __ldg(icn + k);
+            const T ya = xa[k] * s0, yb = xb[k] * s0;
+            T yra = T(0), yrb = T(0);
+            if (k > 0) {
+                const T s1 = __ldg(icn + n - k);
+                yra = xa[n - k] * s1;
+                yrb = xb[n - k] * s1;
+            }
+            const cplx<T> cs = th[k];
+            const cplx<T> Va = {cs.re * ya + cs.im * yra, cs.im * ya - cs.re * yra};
+            const cplx<T> Vb = {cs.re * yb + cs.im * yrb, cs.im * yb - cs.re * yrb};
+            bufA[(size_t)pp * n + k] = {Va.re - Vb.im, Va.im + Vb.re};
+        }
+        __syncthreads();
+        const cplx<T>* Z = fft_pairs<T>(bufA, bufB, P, a.fp, tw, true);
+        for (int e = threadIdx.x; e < P * n; e += blockDim.x) {
+            const int pp = e / n, p = e - pp * n;
+            const int dst = p < h ? 2 * p : 2 * (n - 1 - p) + 1;
+            const cplx<T> z = Z[(size_t)pp * n + p];
+            raw[(size_t)(2 * pp) * n + dst] = z.re;
+            raw[(size_t)(2 * pp + 1) * n + dst] = z.im;
+        }
+        __syncthreads();
+    }
+}
+
+// E f and G f for each raw line pair member; writes E into eo[l*n+k], G into go.
+template <typename T, int BC>
+__device__ void eg_lines(const T* raw, cplx<T>* bufA, cplx<T>* bufB, T* eo, T* go, const LineArgs<T>& a,
+                         const cplx<T>* tw) {
+    const int n = a.n, P = a.P, L = a.L;
+    for (int e = threadIdx.x; e < P * L; e += blockDim.x) {
+        const int pp = e / L, j = e - pp * L;
+        bufA[(size_t)pp * L + j] = {raw[(size_t)(2 * pp) * n + j], raw[(size_t)(2 * pp + 1) * n + j]};
+    }
+    __syncthreads();
+    const cplx<T>* Z = fft_pairs<T>(bufA, bufB, P, a.fp, tw, false);
+    for (int e = threadIdx.x; e < P * n; e += blockDim.x) {
+        const int pp = e / n, k = e - pp * n;
+        const cplx<T>* Zp = Z + (size_t)pp * L;
+        const T* fa = raw + (size_t)(2 * pp) * n;
+        const T* fb = fa + n;
+        T ea, ga, eb, gb;
+        if (BC == BCK_AR) {
+            const int M = L;
+            if (k == 0) {
+                ea = ga = fa[0];
+                eb = gb = fb[0];
+            } else if (k == n - 1) {
+                ea = fa[n - 1]; ga = fa[n - 2];
+                eb = fb[n - 1]; gb = fb[n - 2];
+            } else {
+                cplx<T> F0a, F0b, Fa, Fb;
+                split_pair(Zp, 0, M, F0a, F0b);
+                split_pair(Zp, k, M, Fa, Fb);
+                const cplx<T> eh = reinterpret_cast<const cplx<T>*>(a.aux + 2 * n)[k];   // exp(i pi k/M)
+                const T g = a.aux[4 * n + k];
+                const T invM = T(1) / T(M);
+                ea = (F0a.re - Fa.re) * invM;
+                eb = (F0b.re - Fb.re) * invM;
+                ga = g * (F0a.re + eh.re * Fa.re + eh.im * Fa.im);
+                gb = g * (F0b.re + eh.re * Fb.re + eh.im * Fb.im);
+            }
+        } else {
+            cplx<T> F0a, F0b, Fa, Fb;
+            split_pair(Zp, 0, L, F0a, F0b);
+            split_pair(Zp, k, L, Fa, Fb);
+            const cplx<T> eh = reinterpret_cast<const cplx<T>*>(a.aux + 4 * n)[k];       // exp(i pi k/n)
+            const cplx<T> w = tw[k];                                                     // exp(-2 pi i k/n)
+            const T ce = a.aux[6 * n + k], cg = a.aux[8 * n + k];
+            ea = ce * (F0a.re + eh.re * Fa.re + eh.im * Fa.im);
+            eb = ce * (F0b.re + eh.re * Fb.re + eh.im * Fb.im);
+            ga = cg * (F0a.re - (w.re * Fa.re - w.im * Fa.im));
+            gb = cg * (F0b.re - (w.re * Fb.re - w.im * Fb.im));
+        }
+        eo[(size_t)(2 * pp) * n + k] = ea;
+        eo[(size_t)(2 * pp + 1) * n + k] = eb;
+        go[(size_t)(2 * pp) * n + k] = ga;
+        go[(size_t)(2 * pp + 1) * n + k] = gb;
+    }
+    __syncthreads();
+}
+
+// ------------------------------------------------------------- the line kernel
+
+__device__ __forceinline__ void finish_rho(CgState* st, double rho) {
+    st->rho_old = st->rho;
+    st->rho = rho;
+    if (!(isfinite(rho) && rho > 0.0)) {
+        st->status = TVD_EBREAKDOWN;
+        st->done = 1;
+        st->beta = 0.0;
+        return;
+    }
+    st->beta = st->iter == 0 ? 0.0 : rho / st->rho_old;
+}
+
+template <typename T, int BC, int OP>
+__global__ void __launch_bounds__(kThreads) line_kernel(LineArgs<T> a) {
+    if (a.st && a.st->done) return;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int n = a.n, P = a.P, L = a.L;
+    const int lines = 2 * P;
+    cplx<T>* tw = reinterpret_cast<cplx<T>*>(smem_raw);
+    cplx<T>* bufA = tw + L;
+    cplx<T>* bufB = bufA + (size_t)P * L;
+    T* raw = reinterpret_cast<T*>(bufB + (size_t)P * L);
+    T* extra = raw + (size_t)lines * n;      // scan / second output lines
+    for (int i = threadIdx.x; i < L; i += blockDim.x) tw[i] = a.tw[i];
+
+    constexpr bool cols = (OP == OP_COL_SOLVE || OP == OP_COL_EG);
+    // line index of local line l, or -1
+    auto gline = [&](int l) -> int {
+        int g;
+        if (OP == OP_COL_EG) g = blockIdx.x * P + (l >> 1);
+        else g = blockIdx.x * lines + l;
+        return g < a.nlines ? g : -1;
+    };
+    // ---- load
+    if (!cols) {
+        for (int e = threadIdx.x; e < lines * n; e += blockDim.x) {
+            const int l = e / n, idx = e - l * n;
+            const int g = gline(l);
+            T v = T(0);
+            if (g >= 0) {
+                const size_t o = (size_t)g * a.nc + idx;
+                v = a.in0[o];
+                if (OP == OP_ROW_FWD && a.scale) v *= a.scale[o];
+            }
+            raw[(size_t)l * n + idx] = v;
+        }
+    } else {
+        for (int e = threadIdx.x; e < lines * n; e += blockDim.x) {
+            const int idx = e / lines, l = e - idx * lines;
+            const int g = gline(l);
+            T v = T(0);
+            if (g >= 0) {
+                const size_t o = (size_t)idx * a.nc + g;
+                v = (OP == OP_COL_EG && (l & 1)) ? a.in1[o] : a.in0[o];
+            }
+            raw[(size_t)l * n + idx] = v;
+        }
+    }
+    __syncthreads();
+
+    // ---- transform(s)
+    if (OP == OP_ROW_EG || OP == OP_COL_EG) {
+        T* eo = extra;
+        T* go = extra + (size_t)lines * n;
+        eg_lines<T, BC>(raw, bufA, bufB, eo, go, a, tw);
+        if (OP == OP_ROW_EG) {
+            for (int e = threadIdx.x; e < lines * n; e += blockDim.x) {
+                const int l = e / n, idx = e - l * n;
+                const int g = gline(l);
+                if (g < 0) continue;
+                const size_t o = (size_t)g * a.nc + idx;
+                a.out0[o] = eo[e];
+                a.out1[o] = go[e];
+            }
+        } else {
+            // Lambda_L column = G(A col) + E(B col); spec = lamH2 + alpha Lambda_L
+            for (int e = threadIdx.x; e < P * n; e += blockDim.x) {
+                const int idx = e / P, pp = e - idx * P;
+                const int g = gline(2 * pp);
+                if (g < 0) continue;
+                const T lamL = go[(size_t)(2 * pp) * n + idx] + eo[(size_t)(2 * pp + 1) * n + idx];
+                const size_t o = (size_t)idx * a.nc + g;
+                const double sp = (double)a.spec[o] + a.alpha * (double)lamL;
+                if (!(sp > 1e-300) || !isfinite(sp)) atomicOr(a.bad, 1);
+                a.inv_out[o] = T(1.0 / sp);
+            }
+        }
+        return;
+    }
+
+    if (BC == BCK_AR) dst1_lines<T>(raw, bufA, bufB, extra, a, tw);
+    else dct_lines<T>(raw, bufA, bufB, a, tw, OP == OP_ROW_INV);
+
+    if (OP == OP_COL_SOLVE) {
+        for (int e = threadIdx.x; e < lines * n; e += blockDim.x) {
+            const int idx = e / lines, l = e - idx * lines;
+            const int g = gline(l);
+            if (g >= 0) raw[(size_t)l * n + idx] *= a.spec[(size_t)idx * a.nc + g];
+        }
+        __syncthreads();
+        if (BC == BCK_AR) dst1_lines<T>(raw, bufA, bufB, extra, a, tw);
+        else dct_lines<T>(raw, bufA, bufB, a, tw, true);
+        for (int e = threadIdx.x; e < lines * n; e += blockDim.x) {
+            const int idx = e / lines, l = e - idx * lines;
+            const int g = gline(l);
+            if (g >= 0) a.out0[(size_t)idx * a.nc + g] = raw[(size_t)l * n + idx];
+        }
+        return;
+    }
+    // ---- row store (ROW_FWD / ROW_INV)
+    double part = 0.0;
+    for (int e = threadIdx.x; e < lines * n; e += blockDim.x) {
+        const int l = e / n, idx = e - l * n;
+        const int g = gline(l);
+        if (g < 0) continue;
+        const size_t o = (size_t)g * a.nc + idx;
+        T v = raw[e];
+        if (OP == OP_ROW_INV && a.scale) v *= a.scale[o];
+        a.out0[o] = v;
+        if (OP == OP_ROW_INV && a.st) part += (double)a.rvec[o] * (double)v;
+    }
+    if (OP == OP_ROW_INV && a.st) {
+        double s;
+        if (block_reduce_last(part, a.red, a.ticket, blockIdx.x, gridDim.x, &s) && threadIdx.x == 0)
+            finish_rho(a.st, s);
+    }
+}
+
+// ------------------------------------------------------------- host side
+
+FftPlan make_fft_plan(int L) {
+    FftPlan fp;
+    fp.L = L;
+    int m = L;
+    auto push = [&](int r) { fp.radix[fp.nstages++] = r; m /= r; };
+    while (m % 4 == 0) push(4);
+    while (m % 2 == 0) push(2);
+    while (m % 9 == 0) push(9);
+    static const int odd[] = {3, 5, 7, 11, 13, 17, 19, 23, 29, 31};
+    for (int r : odd)
+        while (m % r == 0) push(r);
+    for (int r = 37; m > 1; r += 2)
+        while (m % r == 0) push(r);
+    return fp;
+}
+
+template <typename T>
+static size_t line_smem(const LineArgs<T>& a) {
+    const size_t lines = 2 * (size_t)a.P;
+    // tw + bufA + bufB + raw + extra (2 * lines * n covers the scan and the E/G outputs)
+    return sizeof(cplx<T>) * ((size_t)a.L + 2 * (size_t)a.P * a.L) + sizeof(T) * (lines * a.n * 3) + 64;
+}
+
+template <typename T>
+static void pick_pairs(LineArgs<T>& a, bool cols) {
+    // columns: 2P contiguous elements per row read, at least one 32-byte sector
+    int P = cols ? (int)((32 + 2 * sizeof(T) - 1) / (2 * sizeof(T))) : 1;
+    const size_t cap = 160 * 1024;
+    for (;;) {
+        a.P = P;
+        if (P == 1 || line_smem<T>(a) <= cap) break;
+        --P;
+    }
+}
+
+template <typename T, int BC, int OP>
+static tvd_status launch_line(LineArgs<T> a, cudaStream_t s) {
+    const bool cols = (OP == OP_COL_SOLVE || OP == OP_COL_EG);
+    pick_pairs<T>(a, cols);
+    const int per_block = (OP == OP_COL_EG) ? a.P : 2 * a.P;
+    const int blocks = (a.nlines + per_block - 1) / per_block;
+    const size_t smem = line_smem<T>(a);
+    if (smem > 227 * 1024) {
+        set_error("transform line too long for shared memory");
+        return TVD_EINVAL;
+    }
+    if (OP == OP_ROW_INV && a.st && blocks > kMaxRedBlocks) {
+        set_error("image too large for the reduction buffer");
+        return TVD_EINVAL;
+    }
+    TVD_CUDA_TRY(cudaFuncSetAttribute(line_kernel<T, BC, OP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    line_kernel<T, BC, OP><<<blocks, kThreads, smem, s>>>(a);
+    TVD_CUDA_TRY(cudaGetLastError());
+    return TVD_OK;
+}
+
+template <typename T>
+static LineArgs<T> base_args(const tvd_plan_s& p, const Ops<T>& o, bool cols) {
+    LineArgs<T> a{};
+    a.nr = p.nr;
+    a.nc = p.nc;
+    a.n = cols ? p.nr : p.nc;
+    a.nlines = cols ? p.nc : p.nr;
+    a.fp = cols ? p.fft_r : p.fft_c;
+    a.L = a.fp.L;
+    a.tw = cols ? o.tw_r : o.tw_c;
+    a.aux = cols ? o.aux_r : o.aux_c;
+    a.red = p.red;
+    a.ticket = p.ticket + 2;
+    return a;
+}
+
+template <typename T>
+tvd_status precond_solve(const tvd_plan_s& p, const Ops<T>& o, const T* r, T* z, CgState* st, cudaStream_t s) {
+    const bool scaled = (p.pc == TVD_PC_DFAST);
+    LineArgs<T> a = base_args<T>(p, o, false);
+    a.in0 = r;
+    a.out0 = o.t;
+    a.scale = scaled ? o.dmh : nullptr;
+    a.st = st;
+    LineArgs<T> c = base_args<T>(p, o, true);
+    c.in0 = o.t;
+    c.out0 = o.t;
+    c.spec = o.inv_spec;
+    c.st = st;
+    LineArgs<T> b = base_args<T>(p, o, false);
+    b.in0 = o.t;
+    b.out0 = z;
+    b.scale = scaled ? o.dmh : nullptr;
+    b.rvec = r;
+    b.st = st;
+    if (p.bc == TVD_BC_ANTIREFLECTIVE) {
+        TVD_TRY((launch_line<T, BCK_AR, OP_ROW_FWD>(a, s)));
+        TVD_TRY((launch_line<T, BCK_AR, OP_COL_SOLVE>(c, s)));
+        TVD_TRY((launch_line<T, BCK_AR, OP_ROW_INV>(b, s)));
+    } else {
+        TVD_TRY((launch_line<T, BCK_R, OP_ROW_FWD>(a, s)));
+        TVD_TRY((launch_line<T, BCK_R, OP_COL_SOLVE>(c, s)));
+        TVD_TRY((launch_line<T, BCK_R, OP_ROW_INV>(b, s)));
+    }
+    return TVD_OK;
+}
+
+template <typename T>
+tvd_status spectrum_setup(const tvd_plan_s& p, Ops<T>& o, double alpha, int* bad_flag, cudaStream_t s) {
+    LineArgs<T> a = base_args<T>(p, o, false);
+    a.in0 = o.w;
+    a.out0 = o.t;
+    a.out1 = o.t2;
+    LineArgs<T> c = base_args<T>(p, o, true);
+    c.in0 = o.t;
+    c.in1 = o.t2;
+    c.spec = o.lamH2;
+    c.inv_out = o.inv_spec;
+    c.alpha = alpha;
+    c.bad = bad_flag;
+    if (p.bc == TVD_BC_ANTIREFLECTIVE) {
+        TVD_TRY((launch_line<T, BCK_AR, OP_ROW_EG>(a, s)));
+        TVD_TRY((launch_line<T, BCK_AR, OP_COL_EG>(c, s)));
+    } else {
+        TVD_TRY((launch_line<T, BCK_R, OP_ROW_EG>(a, s)));
+        TVD_TRY((launch_line<T, BCK_R, OP_COL_EG>(c, s)));
+    }
+    return TVD_OK;
+}
+
+// Lambda_H^2[i,j] = (sum_a cos(a y_i) G[a][j])^2, G[a][j] = sum_b h_ab cos(b y_j) (eq. (symb)
+// at the grid of eq. (gridy) for AR, y_k = k pi / n for R). cr: n_r x (2 m_r + 1) table of cos(a y_i).
+template <typename T>
+__global__ void lamH2_kernel(const double* __restrict__ cr, const double* __restrict__ G, T* __restrict__ out,
+                             int nr, int nc, int pr) {
+    const size_t n = (size_t)nr * nc;
+    for (size_t o = blockIdx.x * (size_t)blockDim.x + threadIdx.x; o < n; o += (size_t)gridDim.x * blockDim.x) {
+        const int i = (int)(o / nc), j = (int)(o - (size_t)i * nc);
+        double acc = 0.0;
+        for (int a = 0; a < pr; ++a) acc += cr[(size_t)i * pr + a] * G[(size_t)a * nc + j];
+        out[o] = T(acc * acc);
+    }
+}
+
+static std::vector<double> symbol_grid(int n, tvd_bc bc) {
+    std::vector<double> y(n);
+    for (int k = 0; k < n; ++k) y[k] = (bc == TVD_BC_ANTIREFLECTIVE) ? k * M_PI / (n - 1) : k * M_PI / n;
+    if (bc == TVD_BC_ANTIREFLECTIVE) {
+        y[0] = 0.0;
+        y[n - 1] = 0.0;
+    }
+    return y;
+}
+
+template <typename T>
+tvd_status lamH2_setup(const tvd_plan_s& p, Ops<T>& o, cudaStream_t s) {
+    const int mr = p.psf.mr, mc = p.psf.mc, pr = 2 * mr + 1, pc = 2 * mc + 1;
+    const std::vector<double> yr = symbol_grid(p.nr, p.bc), yc = symbol_grid(p.nc, p.bc);
+    std::vector<double> cr((size_t)p.nr * pr), G((size_t)pr * p.nc, 0.0);
+    for (int i = 0; i < p.nr; ++i)
+        for (int a = -mr; a <= mr; ++a) cr[(size_t)i * pr + a + mr] = std::cos(a * yr[i]);
+    for (int a = 0; a < pr; ++a)
+        for (int j = 0; j < p.nc; ++j) {
+            double acc = 0.0;
+            for (int b = -mc; b <= mc; ++b) acc += p.psf.h[(size_t)a * pc + b + mc] * std::cos(b * yc[j]);
+            G[(size_t)a * p.nc + j] = acc;
+        }
+    double *dcr = nullptr, *dG = nullptr;
+    TVD_CUDA_TRY(cudaMalloc(&dcr, cr.size() * sizeof(double)));
+    if (cudaMalloc(&dG, G.size() * sizeof(double)) != cudaSuccess) {
+        cudaFree(dcr);
+        set_error("cudaMalloc failed");
+        return TVD_ENOMEM;
+    }
+    cudaMemcpyAsync(dcr, cr.data(), cr.size() * sizeof(double), cudaMemcpyHostToDevice, s);
+    cudaMemcpyAsync(dG, G.data(), G.size() * sizeof(double), cudaMemcpyHostToDevice, s);
+    lamH2_kernel<T><<<num_sms() * 4, kThreads, 0, s>>>(dcr, dG, o.lamH2, p.nr, p.nc, pr);
+    cudaError_t e = cudaStreamSynchronize(s);
+    cudaFree(dcr);
+    cudaFree(dG);
+    if (e != cudaSuccess) {
+        set_error(std::string("CUDA error: ") + cudaGetErrorString(e));
+        return TVD_ECUDA;
+    }
+    return TVD_OK;
+}
+
+template tvd_status precond_solve<float>(const tvd_plan_s&, const Ops<float>&, const float*, float*, CgState*, cudaStream_t);
+template tvd_status precond_solve<double>(const tvd_plan_s&, const Ops<double>&, const double*, double*, CgState*, cudaStream_t);
+template tvd_status spectrum_setup<float>(const tvd_plan_s&, Ops<float>&, double, int*, cudaStream_t);
+template tvd_status spectrum_setup<double>(const tvd_plan_s&, Ops<double>&, double, int*, cudaStream_t);
+template tvd_status lamH2_setup<float>(const tvd_plan_s&, Ops<float>&, cudaStream_t);
+template tvd_status lamH2_setup<double>(const tvd_plan_s&, Ops<double>&, cudaStream_t);
+
+}  // namespace tvd

@@ -1,0 +1,90 @@
+// Lagged-diffusivity TV operator L(u) (Sec. 1, eq. (el)) and the diagonal
+// scaling D = I + alpha diag(L(u)) of eq. (D).
+//
+// Discretisation: forward differences D_r u = u_{i+1,j} - u_{ij},
+// D_c u = u_{i,j+1} - u_{ij}, both zero on the last row / column (zero Neumann),
+// diffusivity w_ij = (D_r u^2 + D_c u^2 + beta^2)^{-1/2} per pixel, and
+// L = D_r^T W D_r + D_c^T W D_c, a symmetric 5-point stencil.
+#include "common.cuh"
+
+namespace tvd {
+
+template <typename T>
+__global__ void __launch_bounds__(kThreads)
+diffusivity_kernel(const T* __restrict__ u, T* __restrict__ w, int nr, int nc, T beta2) {
+    const size_t n = (size_t)nr * nc;
+    for (size_t o = blockIdx.x * (size_t)blockDim.x + threadIdx.x; o < n; o += (size_t)gridDim.x * blockDim.x) {
+        const int i = (int)(o / nc), j = (int)(o - (size_t)i * nc);
+        const T uc = u[o];
+        const T dr = i < nr - 1 ? u[o + nc] - uc : T(0);
+        const T dc = j < nc - 1 ? u[o + 1] - uc : T(0);
+        w[o] = T(1) / sqrt(dr * dr + dc * dc + beta2);
+    }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kThreads)
+diag_scale_kernel(const T* __restrict__ w, T* __restrict__ dmh, T* __restrict__ dinv, int nr, int nc, T alpha) {
+    const size_t n = (size_t)nr * nc;
+    for (size_t o = blockIdx.x * (size_t)blockDim.x + threadIdx.x; o < n; o += (size_t)gridDim.x * blockDim.x) {
+        const int i = (int)(o / nc), j = (int)(o - (size_t)i * nc);
+        const T wc = w[o];
+        T d = T(0);
+        if (i < nr - 1) d += wc;
+        if (j < nc - 1) d += wc;
+        if (i > 0) d += w[o - nc];
+        if (j > 0) d += w[o - 1];
+        const T D = T(1) + alpha * d;
+        dmh[o] = T(1) / sqrt(D);
+        dinv[o] = T(1) / D;
+    }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kThreads)
+tv_apply_kernel(const T* __restrict__ w, const T* __restrict__ x, T* __restrict__ y, int nr, int nc) {
+    const size_t n = (size_t)nr * nc;
+    for (size_t o = blockIdx.x * (size_t)blockDim.x + threadIdx.x; o < n; o += (size_t)gridDim.x * blockDim.x) {
+        const int i = (int)(o / nc), j = (int)(o - (size_t)i * nc);
+        y[o] = lap_at(w, x, i, j, nr, nc);
+    }
+}
+
+static int ew_blocks(size_t n) {
+    size_t b = (n + kThreads - 1) / kThreads;
+    const size_t cap = (size_t)num_sms() * 8;
+    return (int)(b < cap ? (b ? b : 1) : cap);
+}
+
+template <typename T>
+tvd_status diffusivity(const tvd_plan_s& p, const T* u, double beta, T* w, cudaStream_t s) {
+    const size_t n = (size_t)p.nr * p.nc;
+    diffusivity_kernel<T><<<ew_blocks(n), kThreads, 0, s>>>(u, w, p.nr, p.nc, T(beta * beta));
+    TVD_CUDA_TRY(cudaGetLastError());
+    return TVD_OK;
+}
+
+template <typename T>
+tvd_status diag_scale(const tvd_plan_s& p, const T* w, double alpha, T* dmh, T* dinv, cudaStream_t s) {
+    const size_t n = (size_t)p.nr * p.nc;
+    diag_scale_kernel<T><<<ew_blocks(n), kThreads, 0, s>>>(w, dmh, dinv, p.nr, p.nc, T(alpha));
+    TVD_CUDA_TRY(cudaGetLastError());
+    return TVD_OK;
+}
+
+template <typename T>
+tvd_status tv_apply(const tvd_plan_s& p, const T* w, const T* x, T* y, cudaStream_t s) {
+    const size_t n = (size_t)p.nr * p.nc;
+    tv_apply_kernel<T><<<ew_blocks(n), kThreads, 0, s>>>(w, x, y, p.nr, p.nc);
+    TVD_CUDA_TRY(cudaGetLastError());
+    return TVD_OK;
+}
+
+template tvd_status diffusivity<float>(const tvd_plan_s&, const float*, double, float*, cudaStream_t);
+template tvd_status diffusivity<double>(const tvd_plan_s&, const double*, double, double*, cudaStream_t);
+template tvd_status diag_scale<float>(const tvd_plan_s&, const float*, double, float*, float*, cudaStream_t);
+template tvd_status diag_scale<double>(const tvd_plan_s&, const double*, double, double*, double*, cudaStream_t);
+template tvd_status tv_apply<float>(const tvd_plan_s&, const float*, const float*, float*, cudaStream_t);
+template tvd_status tv_apply<double>(const tvd_plan_s&, const double*, const double*, double*, cudaStream_t);
+
+}  // namespace tvd

@@ -1,0 +1,626 @@
+// C ABI of libtvd: plan construction and validation, the operator entry
+// points, the PCG driver (Golub & Van Loan Alg. 10.3.1, as cited in Sec. 1),
+// mixed-precision iterative refinement and the lagged-diffusivity FP loop of
+// eq. (fp) with u^0 = v and warm starts u^k (Sec. 5).
+#include "common.cuh"
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+
+namespace tvd {
+
+static thread_local std::string g_err;
+void set_error(const std::string& msg) { g_err = msg; }
+
+template <typename T>
+static tvd_status dalloc(T** p, size_t n) {
+    if (n == 0) n = 1;
+    if (cudaMalloc((void**)p, n * sizeof(T)) != cudaSuccess) {
+        cudaGetLastError();
+        *p = nullptr;
+        set_error("cudaMalloc of " + std::to_string(n * sizeof(T)) + " bytes failed");
+        return TVD_ENOMEM;
+    }
+    return TVD_OK;
+}
+
+template <typename T>
+static void dfree(T*& p) {
+    if (p) cudaFree((void*)p);
+    p = nullptr;
+}
+
+template <typename T>
+static tvd_status upload(T** dst, const std::vector<double>& src, cudaStream_t s) {
+    TVD_TRY(dalloc(dst, src.size()));
+    std::vector<T> tmp(src.begin(), src.end());
+    TVD_CUDA_TRY(cudaMemcpyAsync(*dst, tmp.data(), tmp.size() * sizeof(T), cudaMemcpyHostToDevice, s));
+    TVD_CUDA_TRY(cudaStreamSynchronize(s));
+    return TVD_OK;
+}
+
+// Twiddles exp(-2 pi i k / L) and the auxiliary tables of transform.cu for a
+// line of length n (slot layout documented there).
+static void transform_tables(int n, tvd_bc bc, std::vector<double>& tw, std::vector<double>& aux) {
+    const int L = (bc == TVD_BC_ANTIREFLECTIVE) ? n - 1 : n;
+    tw.assign(2 * (size_t)L, 0.0);
+    for (int k = 0; k < L; ++k) {
+        const double a = 2.0 * M_PI * k / L;
+        tw[2 * k] = std::cos(a);
+        tw[2 * k + 1] = -std::sin(a);
+    }
+    aux.assign(16 * (size_t)n, 0.0);
+    double* s0 = aux.data();
+    double* s1 = aux.data() + 2 * n;
+    double* s2 = aux.data() + 4 * n;
+    double* s3 = aux.data() + 6 * n;
+    double* s4 = aux.data() + 8 * n;
+    double* s5 = aux.data() + 10 * n;
+    if (bc == TVD_BC_ANTIREFLECTIVE) {
+        const int M = n - 1;
+        for (int j = 0; j < M; ++j) s0[j] = std::sin(j * M_PI / M);
+        for (int k = 0; k < n; ++k) {
+            s1[2 * k] = std::cos(M_PI * k / M);
+            s1[2 * k + 1] = std::sin(M_PI * k / M);
+            const double sh = std::sin(k * M_PI / (2.0 * M));
+            s2[k] = 4.0 / M * sh * sh;
+        }
+    } else {
+        for (int k = 0; k < n; ++k) {
+            const double c = k == 0 ? std::sqrt(1.0 / n) : std::sqrt(2.0 / n);
+            s0[k] = c;
+            s1[2 * k] = std::cos(M_PI * k / (2.0 * n));
+            s1[2 * k + 1] = std::sin(M_PI * k / (2.0 * n));
+            s2[2 * k] = std::cos(M_PI * k / n);
+            s2[2 * k + 1] = std::sin(M_PI * k / n);
+            s3[k] = c * c / 2.0;
+            const double sh = std::sin(M_PI * k / (2.0 * n));
+            s4[k] = 2.0 * c * c * sh * sh;
+            s5[k] = 1.0 / (n * c);
+        }
+    }
+}
+
+template <typename T>
+static tvd_status ops_alloc(tvd_plan_s& p, Ops<T>& o, cudaStream_t s) {
+    const size_t n = (size_t)p.nr * p.nc;
+    T** arrays[] = {&o.lamH2, &o.inv_spec, &o.w, &o.dmh, &o.dinv, &o.x, &o.r, &o.z, &o.p, &o.q, &o.t, &o.t2};
+    for (T** a : arrays) TVD_TRY(dalloc(a, n));
+    o.allocated = true;
+    // PSF taps
+    o.ntaps = (int)p.psf.th.size();
+    std::vector<double> ab(2 * (size_t)o.ntaps);
+    for (int k = 0; k < o.ntaps; ++k) {
+        ab[k] = p.psf.ta[k];
+        ab[o.ntaps + k] = p.psf.tb[k];
+    }
+    TVD_TRY(upload<int>(&o.tap_ab, ab, s));
+    TVD_TRY(upload<T>(&o.tap_h, p.psf.th, s));
+    TVD_TRY(upload<T>(&o.crow, p.psf.crow, s));
+    TVD_TRY(upload<T>(&o.ccol, p.psf.ccol, s));
+    TVD_TRY(upload<T>(&o.ccor, p.psf.ccor, s));
+    std::vector<double> tw, aux;
+    transform_tables(p.nc, p.bc, tw, aux);
+    TVD_TRY(upload<T>((T**)&o.tw_c, tw, s));
+    TVD_TRY(upload<T>(&o.aux_c, aux, s));
+    transform_tables(p.nr, p.bc, tw, aux);
+    TVD_TRY(upload<T>((T**)&o.tw_r, tw, s));
+    TVD_TRY(upload<T>(&o.aux_r, aux, s));
+    TVD_TRY(lamH2_setup<T>(p, o, s));
+    return TVD_OK;
+}
+
+template <typename T>
+static void ops_free(Ops<T>& o) {
+    dfree(o.tap_ab); dfree(o.tap_h); dfree(o.crow); dfree(o.ccol); dfree(o.ccor);
+    dfree(o.tw_c); dfree(o.tw_r); dfree(o.aux_c); dfree(o.aux_r);
+    dfree(o.lamH2); dfree(o.inv_spec); dfree(o.w); dfree(o.dmh); dfree(o.dinv);
+    dfree(o.x); dfree(o.r); dfree(o.z); dfree(o.p); dfree(o.q); dfree(o.t); dfree(o.t2);
+    o.allocated = false;
+}
+
+static void plan_free(tvd_plan_s* p) {
+    ops_free(p->d);
+    ops_free(p->f);
+    dfree(p->state); dfree(p->red); dfree(p->ticket); dfree(p->scal);
+    dfree(p->hx); dfree(p->res); dfree(p->xd); dfree(p->tmp);
+    if (p->hstate) cudaFreeHost(p->hstate);
+    p->hstate = nullptr;
+}
+
+// Validate and trim the PSF; build the nonzero tap list and the AR border tail weights.
+static tvd_status build_psf(Psf& out, const double* h, int pr, int pc, int nr, int nc) {
+    if (!h || pr < 1 || pc < 1 || pr % 2 == 0 || pc % 2 == 0) {
+        set_error("PSF sides must be odd and positive");
+        return TVD_EPSF_SIZE;
+    }
+    int mr = pr / 2, mc = pc / 2;
+    double hmax = 0.0;
+    for (int i = 0; i < pr * pc; ++i) {
+        if (!std::isfinite(h[i])) {
+            set_error("PSF has a non-finite entry");
+            return TVD_EINVAL;
+        }
+        hmax = std::max(hmax, std::fabs(h[i]));
+    }
+    if (hmax == 0.0) {
+        set_error("PSF is zero");
+        return TVD_EINVAL;
+    }
+    auto H = [&](int a, int b) { return h[(size_t)(a + pr / 2) * pc + (b + pc / 2)]; };
+    const double tol = 1e-12 * hmax;
+    for (int a = -pr / 2; a <= pr / 2; ++a)
+        for (int b = -pc / 2; b <= pc / 2; ++b)
+            if (std::fabs(H(a, b) - H(-a, b)) > tol || std::fabs(H(a, b) - H(a, -b)) > tol) {
+                set_error("PSF is not quadrantally symmetric (h_{a,b} = h_{-a,b} = h_{a,-b} is required)");
+                return TVD_EPSF_ASYM;
+            }
+    // trim all-zero outer rows / columns (H does not change)
+    auto row_zero = [&](int a) {
+        for (int b = -mc; b <= mc; ++b) if (H(a, b) != 0.0) return false;
+        return true;
+    };
+    auto col_zero = [&](int b) {
+        for (int a = -mr; a <= mr; ++a) if (H(a, b) != 0.0) return false;
+        return true;
+    };
+    while (mr > 0 && row_zero(mr) && row_zero(-mr)) --mr;
+    while (mc > 0 && col_zero(mc) && col_zero(-mc)) --mc;
+    if (mr > nr - 2 || mc > nc - 2) {
+        set_error("PSF half-width exceeds n - 2 along an axis");
+        return TVD_EPSF_SIZE;
+    }
+    if (mr > 48 || mc > 48) {
+        set_error("PSF half-width above 48 is not supported");
+        return TVD_EPSF_SIZE;
+    }
+    out.mr = mr;
+    out.mc = mc;
+    const int qr = 2 * mr + 1, qc = 2 * mc + 1;
+    out.h.assign((size_t)qr * qc, 0.0);
+    out.ta.clear(); out.tb.clear(); out.th.clear();
+    for (int a = -mr; a <= mr; ++a)
+        for (int b = -mc; b <= mc; ++b) {
+            const double v = H(a, b);
+            out.h[(size_t)(a + mr) * qc + (b + mc)] = v;
+            if (v != 0.0) {
+                out.ta.push_back(a);
+                out.tb.push_back(b);
+                out.th.push_back(v);
+            }
+        }
+    auto Hs = [&](int a, int b) { return out.h[(size_t)(a + mr) * qc + (b + mc)]; };
+    out.crow.assign((size_t)(mr + 1) * qc, 0.0);
+    for (int i = 0; i <= mr; ++i)
+        for (int b = -mc; b <= mc; ++b) {
+            double v = Hs(i, b);
+            for (int s = i + 1; s <= mr; ++s) v += 2.0 * Hs(s, b);
+            out.crow[(size_t)i * qc + b + mc] = v;
+        }
+    out.ccol.assign((size_t)qr * (mc + 1), 0.0);
+    for (int a = -mr; a <= mr; ++a)
+        for (int j = 0; j <= mc; ++j) {
+            double v = Hs(a, j);
+            for (int t = j + 1; t <= mc; ++t) v += 2.0 * Hs(a, t);
+            out.ccol[(size_t)(a + mr) * (mc + 1) + j] = v;
+        }
+    out.ccor.assign((size_t)(mr + 1) * (mc + 1), 0.0);
+    for (int i = 0; i <= mr; ++i)
+        for (int j = 0; j <= mc; ++j) {
+            double v = Hs(i, j);
+            for (int s = i + 1; s <= mr; ++s) v += 2.0 * Hs(s, j);
+            for (int t = j + 1; t <= mc; ++t) v += 2.0 * Hs(i, t);
+            for (int s = i + 1; s <= mr; ++s)
+                for (int t = j + 1; t <= mc; ++t) v += 4.0 * Hs(s, t);
+            out.ccor[(size_t)i * (mc + 1) + j] = v;
+        }
+    return TVD_OK;
+}
+
+// ---------------------------------------------------------------- CG driver
+
+template <typename T>
+static tvd_status read_state(tvd_plan_s& p, cudaStream_t s) {
+    TVD_CUDA_TRY(cudaMemcpyAsync(p.hstate, p.state, sizeof(CgState), cudaMemcpyDeviceToHost, s));
+    TVD_CUDA_TRY(cudaStreamSynchronize(s));
+    return TVD_OK;
+}
+
+template <typename T>
+static tvd_status precond_step(tvd_plan_s& p, Ops<T>& o, CgState* st, cudaStream_t s) {
+    switch (p.pc) {
+        case TVD_PC_NONE: return cg_simple_precond<T>(p, o.r, nullptr, o.z, st, s);
+        case TVD_PC_DIAG: return cg_simple_precond<T>(p, o.r, o.dinv, o.z, st, s);
+        default: return precond_solve<T>(p, o, o.r, o.z, st, s);
+    }
+}
+
+// PCG on A x = b with A = H^T H + alpha L(o.w); x is updated in place.
+// The preconditioner must be set up in `o`. Iterations are enqueued in chunks;
+// the kernels of iterations past convergence return at once.
+template <typename T>
+static tvd_status cg_run(tvd_plan_s& p, Ops<T>& o, double alpha, const T* b, T* x, double tol, int maxit,
+                         CgState* out, cudaStream_t s) {
+    CgState* st = p.state;
+    TVD_TRY(blur_apply<T>(p, o, false, x, o.t, s));
+    TVD_TRY(normal_finish<T>(p, o, o.t, x, alpha, o.q, nullptr, s));
+    TVD_TRY(cg_init<T>(p, b, o.q, o.r, st, tol, maxit, s));
+    const int chunk = 8;
+    for (;;) {
+        for (int c = 0; c < chunk; ++c) {
+            TVD_TRY(precond_step<T>(p, o, st, s));
+            TVD_TRY(cg_pupdate<T>(p, o.z, o.p, st, s));
+            TVD_TRY(blur_apply<T>(p, o, false, o.p, o.t, s, st));
+            TVD_TRY(normal_finish<T>(p, o, o.t, o.p, alpha, o.q, st, s));
+            TVD_TRY(cg_xrupdate<T>(p, x, o.r, o.p, o.q, st, s));
+        }
+        TVD_TRY(read_state<T>(p, s));
+        if (p.hstate->done) break;
+    }
+    *out = *p.hstate;
+    return TVD_OK;
+}
+
+// Preconditioner set-up for the FP step at u_lag (type T).
+template <typename T>
+static tvd_status setup_precond(tvd_plan_s& p, Ops<T>& o, const T* u_lag, double alpha, double beta,
+                                cudaStream_t s) {
+    TVD_TRY(diffusivity<T>(p, u_lag, beta, o.w, s));
+    TVD_TRY(diag_scale<T>(p, o.w, alpha, o.dmh, o.dinv, s));
+    if (p.pc == TVD_PC_FAST || p.pc == TVD_PC_DFAST) {
+        int* bad = reinterpret_cast<int*>(p.scal + 8);
+        TVD_CUDA_TRY(cudaMemsetAsync(bad, 0, sizeof(int), s));
+        TVD_TRY(spectrum_setup<T>(p, o, alpha, bad, s));
+        int hb = 0;
+        TVD_CUDA_TRY(cudaMemcpyAsync(&hb, bad, sizeof(int), cudaMemcpyDeviceToHost, s));
+        TVD_CUDA_TRY(cudaStreamSynchronize(s));
+        if (hb) {
+            set_error("preconditioner eigenvalue Lambda_H^2 + alpha Lambda_L is not positive");
+            return TVD_EINVAL;
+        }
+    }
+    p.precond_ready = true;
+    p.alpha = alpha;
+    p.beta = beta;
+    return TVD_OK;
+}
+
+// MIXED-mode preconditioner: diffusivity and scaling from the double iterate,
+// cast to float, spectrum in float.
+static tvd_status setup_mixed(tvd_plan_s& p, const double* u_lag, double alpha, double beta, cudaStream_t s) {
+    const size_t n = (size_t)p.nr * p.nc;
+    TVD_TRY(diffusivity<double>(p, u_lag, beta, p.d.w, s));
+    TVD_TRY(diag_scale<double>(p, p.d.w, alpha, p.d.dmh, p.d.dinv, s));
+    TVD_TRY(cast_d2f(p.d.w, p.f.w, n, s));
+    TVD_TRY(cast_d2f(p.d.dmh, p.f.dmh, n, s));
+    TVD_TRY(cast_d2f(p.d.dinv, p.f.dinv, n, s));
+    if (p.pc == TVD_PC_FAST || p.pc == TVD_PC_DFAST) {
+        int* bad = reinterpret_cast<int*>(p.scal + 8);
+        TVD_CUDA_TRY(cudaMemsetAsync(bad, 0, sizeof(int), s));
+        TVD_TRY(spectrum_setup<float>(p, p.f, alpha, bad, s));
+        int hb = 0;
+        TVD_CUDA_TRY(cudaMemcpyAsync(&hb, bad, sizeof(int), cudaMemcpyDeviceToHost, s));
+        TVD_CUDA_TRY(cudaStreamSynchronize(s));
+        if (hb) {
+            set_error("preconditioner eigenvalue Lambda_H^2 + alpha Lambda_L is not positive");
+            return TVD_EINVAL;
+        }
+    }
+    p.precond_ready = true;
+    p.alpha = alpha;
+    p.beta = beta;
+    return TVD_OK;
+}
+
+static tvd_status read_scalars(tvd_plan_s& p, double* h, int count, cudaStream_t s) {
+    TVD_CUDA_TRY(cudaMemcpyAsync(h, p.scal, count * sizeof(double), cudaMemcpyDeviceToHost, s));
+    TVD_CUDA_TRY(cudaStreamSynchronize(s));
+    return TVD_OK;
+}
+
+struct SolveResult {
+    int iters = 0;
+    int sweeps = 0;
+    double relres = 0.0;
+    tvd_status status = TVD_OK;
+};
+
+// MIXED: x_{s+1} = x_s + d_s with d_s from float PCG on A d = b - A x_s (the
+// residual in double), until ||b - A x|| / ||b - A x_0|| < tol.
+static tvd_status solve_mixed(tvd_plan_s& p, double alpha, const double* b, double* x, double tol, int maxit,
+                              SolveResult* res, cudaStream_t s) {
+    const size_t n = (size_t)p.nr * p.nc;
+    double h[2];
+    auto residual = [&](double* out_rr) -> tvd_status {
+        TVD_TRY(blur_apply<double>(p, p.d, false, x, p.d.t, s));
+        TVD_TRY(normal_finish<double>(p, p.d, p.d.t, x, alpha, p.d.q, nullptr, s));
+        TVD_TRY(residual_d(p, b, p.d.q, p.res, p.scal, s));
+        TVD_TRY(read_scalars(p, h, 1, s));
+        *out_rr = h[0];
+        return TVD_OK;
+    };
+    double rr0 = 0.0;
+    TVD_TRY(residual(&rr0));
+    res->iters = 0;
+    res->sweeps = 0;
+    res->relres = 0.0;
+    res->status = TVD_OK;
+    if (!std::isfinite(rr0)) {
+        res->status = TVD_EBREAKDOWN;
+        return TVD_OK;
+    }
+    if (rr0 == 0.0) return TVD_OK;
+    double rr = rr0;
+    const double r0 = std::sqrt(rr0);
+    while (true) {
+        const double rel = std::sqrt(rr) / r0;
+        res->relres = rel;
+        if (rel < tol) break;
+        if (res->iters >= maxit) {
+            res->status = TVD_ENOCONV;
+            break;
+        }
+        // float correction solve to the remaining reduction (at most 1e-5 per sweep)
+        const double want = std::max(0.5 * tol / rel, 1e-5);
+        TVD_TRY(cast_d2f(p.res, p.f.t2, n, s));
+        TVD_TRY(fill_zero_f(p.f.x, n, s));
+        CgState cs;
+        TVD_TRY(cg_run<float>(p, p.f, alpha, p.f.t2, p.f.x, std::min(want, 0.5), maxit - res->iters, &cs, s));
+        res->iters += cs.iter;
+        res->sweeps += 1;
+        if (cs.status == TVD_EBREAKDOWN && cs.iter == 0) {
+            res->status = TVD_EBREAKDOWN;
+            break;
+        }
+        TVD_TRY(axpy_f2d(x, p.f.x, n, s));
+        TVD_TRY(residual(&rr));
+        if (!std::isfinite(rr)) {
+            res->status = TVD_EBREAKDOWN;
+            break;
+        }
+        if (res->sweeps > 64) {
+            res->status = TVD_ENOCONV;
+            break;
+        }
+    }
+    return TVD_OK;
+}
+
+static tvd_status solve(tvd_plan_s& p, const double* u_lag, double alpha, double beta, const double* b, double* x,
+                        double tol, int maxit, SolveResult* res, cudaStream_t s) {
+    if (p.mode == TVD_MODE_FP64) {
+        TVD_TRY(setup_precond<double>(p, p.d, u_lag, alpha, beta, s));
+        CgState cs;
+        TVD_TRY(cg_run<double>(p, p.d, alpha, b, x, tol, maxit, &cs, s));
+        res->iters = cs.iter;
+        res->sweeps = 1;
+        res->relres = cs.rr0 > 0.0 ? std::sqrt(cs.rr / cs.rr0) : 0.0;
+        res->status = (tvd_status)cs.status;
+        return TVD_OK;
+    }
+    TVD_TRY(setup_mixed(p, u_lag, alpha, beta, s));
+    return solve_mixed(p, alpha, b, x, tol, maxit, res, s);
+}
+
+}  // namespace tvd
+
+using namespace tvd;
+
+// ---------------------------------------------------------------- C ABI
+
+extern "C" {
+
+const char* tvd_last_error(void) { return g_err.c_str(); }
+
+const char* tvd_version(void) { return "tvd-gb300 0.1"; }
+
+tvd_status tvd_plan_create(tvd_plan* out, int n_rows, int n_cols, const double* psf_host, int p_rows, int p_cols,
+                           tvd_bc bc, tvd_precond pc, tvd_mode mode, void* stream) {
+    g_err.clear();
+    if (!out) {
+        set_error("out is NULL");
+        return TVD_EINVAL;
+    }
+    *out = nullptr;
+    // line transforms keep two lines (float: up to 4096) or one line pair in shared memory
+    const int max_side = (mode == TVD_MODE_FP64) ? 2048 : 4096;
+    if (n_rows < 3 || n_cols < 3 || n_rows > max_side || n_cols > max_side) {
+        set_error("image sides must be in [3, 2048] (FP64 plans) or [3, 4096] (MIXED plans)");
+        return TVD_EINVAL;
+    }
+    if ((bc != TVD_BC_REFLECTIVE && bc != TVD_BC_ANTIREFLECTIVE) || pc < TVD_PC_NONE || pc > TVD_PC_DFAST ||
+        (mode != TVD_MODE_FP64 && mode != TVD_MODE_MIXED)) {
+        set_error("invalid bc / preconditioner / mode");
+        return TVD_EINVAL;
+    }
+    tvd_plan_s* p = new tvd_plan_s();
+    p->nr = n_rows;
+    p->nc = n_cols;
+    p->bc = bc;
+    p->pc = pc;
+    p->mode = mode;
+    cudaStream_t s = (cudaStream_t)stream;
+    tvd_status st = build_psf(p->psf, psf_host, p_rows, p_cols, n_rows, n_cols);
+    if (st != TVD_OK) {
+        delete p;
+        return st;
+    }
+    const int Lr = bc == TVD_BC_ANTIREFLECTIVE ? n_rows - 1 : n_rows;
+    const int Lc = bc == TVD_BC_ANTIREFLECTIVE ? n_cols - 1 : n_cols;
+    p->fft_r = make_fft_plan(Lr);
+    p->fft_c = make_fft_plan(Lc);
+    const size_t n = (size_t)n_rows * n_cols;
+    auto fail = [&](tvd_status e) {
+        plan_free(p);
+        delete p;
+        return e;
+    };
+    if ((st = dalloc(&p->state, 1)) != TVD_OK) return fail(st);
+    if ((st = dalloc(&p->red, kMaxRedBlocks)) != TVD_OK) return fail(st);
+    if ((st = dalloc(&p->ticket, 16)) != TVD_OK) return fail(st);
+    if ((st = dalloc(&p->scal, 16)) != TVD_OK) return fail(st);
+    if ((st = dalloc(&p->hx, n)) != TVD_OK) return fail(st);
+    if ((st = dalloc(&p->res, n)) != TVD_OK) return fail(st);
+    if ((st = dalloc(&p->xd, n)) != TVD_OK) return fail(st);
+    if ((st = dalloc(&p->tmp, n)) != TVD_OK) return fail(st);
+    if (cudaMallocHost((void**)&p->hstate, sizeof(CgState)) != cudaSuccess) {
+        cudaGetLastError();
+        set_error("cudaMallocHost failed");
+        return fail(TVD_ENOMEM);
+    }
+    if (cudaMemsetAsync(p->ticket, 0, 16 * sizeof(unsigned int), s) != cudaSuccess ||
+        cudaMemsetAsync(p->state, 0, sizeof(CgState), s) != cudaSuccess) {
+        set_error("cudaMemset failed");
+        return fail(TVD_ECUDA);
+    }
+    if ((st = ops_alloc<double>(*p, p->d, s)) != TVD_OK) return fail(st);
+    if (mode == TVD_MODE_MIXED && (st = ops_alloc<float>(*p, p->f, s)) != TVD_OK) return fail(st);
+    if (cudaStreamSynchronize(s) != cudaSuccess) {
+        set_error("stream synchronisation failed");
+        return fail(TVD_ECUDA);
+    }
+    *out = p;
+    return TVD_OK;
+}
+
+tvd_status tvd_plan_destroy(tvd_plan plan) {
+    if (!plan) return TVD_OK;
+    cudaDeviceSynchronize();
+    plan_free(plan);
+    delete plan;
+    return TVD_OK;
+}
+
+tvd_status ar_blur_apply(tvd_plan plan, int transpose, const void* x, void* y, void* stream) {
+    if (!plan || !x || !y || x == y) {
+        set_error("ar_blur_apply: NULL plan / pointer, or x == y");
+        return TVD_EINVAL;
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    if (plan->mode == TVD_MODE_FP64)
+        return blur_apply<double>(*plan, plan->d, transpose != 0, (const double*)x, (double*)y, s);
+    return blur_apply<float>(*plan, plan->f, transpose != 0, (const float*)x, (float*)y, s);
+}
+
+tvd_status tv_operator_apply(tvd_plan plan, const void* u_lag, double beta, const void* x, void* y, void* stream) {
+    if (!plan || !u_lag || !x || !y || y == x || y == u_lag || !(beta > 0.0)) {
+        set_error("tv_operator_apply: invalid argument");
+        return TVD_EINVAL;
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    if (plan->mode == TVD_MODE_FP64) {
+        TVD_TRY(diffusivity<double>(*plan, (const double*)u_lag, beta, plan->d.t2, s));
+        return tv_apply<double>(*plan, plan->d.t2, (const double*)x, (double*)y, s);
+    }
+    TVD_TRY(diffusivity<float>(*plan, (const float*)u_lag, beta, plan->f.t2, s));
+    return tv_apply<float>(*plan, plan->f.t2, (const float*)x, (float*)y, s);
+}
+
+tvd_status tau_precond_setup(tvd_plan plan, const void* u_lag, double alpha, double beta, void* stream) {
+    if (!plan || !u_lag || !(alpha >= 0.0) || !(beta > 0.0)) {
+        set_error("tau_precond_setup: invalid argument");
+        return TVD_EINVAL;
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    plan->precond_ready = false;
+    if (plan->mode == TVD_MODE_FP64) return setup_precond<double>(*plan, plan->d, (const double*)u_lag, alpha, beta, s);
+    return setup_precond<float>(*plan, plan->f, (const float*)u_lag, alpha, beta, s);
+}
+
+tvd_status tau_precond_solve(tvd_plan plan, const void* r, void* z, void* stream) {
+    if (!plan || !r || !z) {
+        set_error("tau_precond_solve: invalid argument");
+        return TVD_EINVAL;
+    }
+    if (!plan->precond_ready) {
+        set_error("tau_precond_solve: call tau_precond_setup first");
+        return TVD_EINVAL;
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    if (plan->mode == TVD_MODE_FP64) {
+        auto& o = plan->d;
+        if (plan->pc == TVD_PC_NONE || plan->pc == TVD_PC_DIAG)
+            return cg_simple_precond<double>(*plan, (const double*)r, plan->pc == TVD_PC_DIAG ? o.dinv : nullptr,
+                                             (double*)z, nullptr, s);
+        return precond_solve<double>(*plan, o, (const double*)r, (double*)z, nullptr, s);
+    }
+    auto& o = plan->f;
+    if (plan->pc == TVD_PC_NONE || plan->pc == TVD_PC_DIAG)
+        return cg_simple_precond<float>(*plan, (const float*)r, plan->pc == TVD_PC_DIAG ? o.dinv : nullptr,
+                                        (float*)z, nullptr, s);
+    return precond_solve<float>(*plan, o, (const float*)r, (float*)z, nullptr, s);
+}
+
+tvd_status pcg_solve(tvd_plan plan, const void* u_lag, double alpha, double beta, const void* b, void* x_inout,
+                     double tol, int maxit, int* iters, double* relres, void* stream) {
+    if (!plan || !u_lag || !b || !x_inout || !(alpha >= 0.0) || !(beta > 0.0) || !(tol > 0.0) || maxit < 0) {
+        set_error("pcg_solve: invalid argument");
+        return TVD_EINVAL;
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    SolveResult r;
+    TVD_TRY(solve(*plan, (const double*)u_lag, alpha, beta, (const double*)b, (double*)x_inout, tol, maxit, &r, s));
+    if (iters) *iters = r.iters;
+    if (relres) *relres = r.relres;
+    if (r.status != TVD_OK) {
+        set_error(r.status == TVD_ENOCONV ? "pcg_solve: tolerance not reached within maxit"
+                                          : "pcg_solve: CG breakdown (non-positive curvature or non-finite value)");
+    }
+    return r.status;
+}
+
+tvd_status tv_deblur(tvd_plan plan, const void* v, double alpha, double beta, int max_outer, double outer_tol,
+                     double inner_tol, int inner_maxit, void* u_out, tvd_stats* stats, void* stream) {
+    if (!plan || !v || !u_out || !(alpha >= 0.0) || !(beta > 0.0) || max_outer < 0 || !(inner_tol > 0.0) ||
+        inner_maxit < 0) {
+        set_error("tv_deblur: invalid argument");
+        return TVD_EINVAL;
+    }
+    tvd_plan_s& p = *plan;
+    cudaStream_t s = (cudaStream_t)stream;
+    const size_t n = (size_t)p.nr * p.nc;
+    double* u = (double*)u_out;
+    // b = H^T v (into p.xd), u^0 = v
+    TVD_TRY(blur_apply<double>(p, p.d, true, (const double*)v, p.xd, s));
+    if (u != (const double*)v) TVD_CUDA_TRY(cudaMemcpyAsync(u, v, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    if (stats) {
+        stats->outer_iters = 0;
+        stats->total_inner_iters = 0;
+        stats->refinement_sweeps = 0;
+        stats->last_relres = 0.0;
+        stats->last_rel_change = 0.0;
+        stats->last_status = TVD_OK;
+    }
+    tvd_status overall = TVD_OK;
+    for (int k = 0; k < max_outer; ++k) {
+        TVD_CUDA_TRY(cudaMemcpyAsync(p.tmp, u, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+        SolveResult r;
+        // u_lag = u^k (kept in p.tmp), x starts at u^k and becomes u^{k+1} in place
+        TVD_TRY(solve(p, p.tmp, alpha, beta, p.xd, u, inner_tol, inner_maxit, &r, s));
+        double h2[2];
+        TVD_TRY(diffnorm2_d(p, u, p.tmp, p.scal + 2, s));
+        TVD_TRY(norm2_d(p, u, p.scal + 3, s));
+        TVD_CUDA_TRY(cudaMemcpyAsync(h2, p.scal + 2, 2 * sizeof(double), cudaMemcpyDeviceToHost, s));
+        TVD_CUDA_TRY(cudaStreamSynchronize(s));
+        const double change = std::sqrt(h2[0]) / std::max(std::sqrt(h2[1]), 1e-300);
+        if (r.status != TVD_OK) overall = (overall == TVD_OK) ? r.status : overall;
+        if (stats) {
+            if (k < stats->cap && stats->inner_iters) stats->inner_iters[k] = r.iters;
+            stats->outer_iters = k + 1;
+            stats->total_inner_iters += r.iters;
+            stats->refinement_sweeps += r.sweeps;
+            stats->last_relres = r.relres;
+            stats->last_rel_change = change;
+            stats->last_status = r.status;
+        }
+        if (r.status == TVD_EBREAKDOWN) break;
+        if (outer_tol > 0.0 && change < outer_tol) break;
+    }
+    if (overall != TVD_OK)
+        set_error(overall == TVD_ENOCONV ? "tv_deblur: an inner solve did not reach its tolerance"
+                                         : "tv_deblur: an inner solve broke down");
+    return overall;
+}
+
+}  // extern "C"

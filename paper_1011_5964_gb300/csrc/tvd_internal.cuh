@@ -1,0 +1,207 @@
+// Internal declarations shared by the CUDA translation units of libtvd.
+//
+// Layout in device memory: every image-sized array is n_rows x n_cols,
+// row-major, contiguous, in the plan's compute type T (float or double).
+// Small per-plan tables (PSF taps, border tail weights, transform twiddles)
+// are separate device arrays loaded into shared memory by the kernels.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/tvd.h"
+
+namespace tvd {
+
+// ---------------------------------------------------------------- errors
+
+void set_error(const std::string& msg);
+
+struct Status {
+    tvd_status code = TVD_OK;
+    bool ok() const { return code == TVD_OK; }
+};
+
+#define TVD_CUDA_TRY(expr)                                                          \
+    do {                                                                            \
+        cudaError_t _e = (expr);                                                    \
+        if (_e != cudaSuccess) {                                                    \
+            ::tvd::set_error(std::string("CUDA error: ") + cudaGetErrorString(_e) + \
+                             " at " + __FILE__ + ":" + std::to_string(__LINE__));   \
+            return TVD_ECUDA;                                                       \
+        }                                                                           \
+    } while (0)
+
+#define TVD_TRY(expr)                   \
+    do {                                \
+        tvd_status _s = (expr);         \
+        if (_s != TVD_OK) return _s;    \
+    } while (0)
+
+// ---------------------------------------------------------------- small types
+
+template <typename T>
+struct cplx {
+    T re, im;
+};
+
+// Radix plan of a length-L complex FFT (Stockham, mixed radix).
+struct FftPlan {
+    int L = 0;
+    int nstages = 0;
+    int radix[24] = {0};
+};
+
+FftPlan make_fft_plan(int L);
+
+// Device-side scalar state of one CG solve. All scalars are double in both
+// modes (the CG recurrences and the stopping test stay in FP64).
+struct CgState {
+    double rho;        // r^T z of the current iteration
+    double rho_old;    // r^T z of the previous iteration
+    double pq;         // p^T A p
+    double rr;         // ||r||^2 after the last update
+    double rr0;        // ||r_0||^2
+    double alpha;      // step length
+    double beta;       // Fletcher-Reeves coefficient
+    double tol2;       // tol^2 * rr0, the stopping threshold on rr
+    int iter;          // products with A done so far in this solve
+    int maxit;
+    int done;          // 1 once converged / stopped
+    int status;        // tvd_status reached inside the loop
+};
+
+// Reduction slots: each reduction writes one double per block, then the last
+// block (ticket counter) sums them in a fixed order.
+constexpr int kMaxRedBlocks = 1 << 17;
+
+// Per-precision device resources of a plan.
+template <typename T>
+struct Ops {
+    bool allocated = false;
+    // PSF (trimmed), nonzero taps as (a, b, h) for the direct stencil
+    int ntaps = 0;
+    int* tap_ab = nullptr;   // 2 * ntaps ints: a then b (offsets, -m..m)
+    T* tap_h = nullptr;      // ntaps
+    // AR adjoint border tail weights (Sec. 2 folds), sizes in the plan
+    T* crow = nullptr;       // (m_r + 1) x (2 m_c + 1)
+    T* ccol = nullptr;       // (2 m_r + 1) x (m_c + 1)
+    T* ccor = nullptr;       // (m_r + 1) x (m_c + 1)
+    // transform tables: twiddles of the row-direction (length L_c) and
+    // column-direction (length L_r) complex FFTs, plus per-transform aux tables
+    cplx<T>* tw_c = nullptr;
+    cplx<T>* tw_r = nullptr;
+    T* aux_c = nullptr;      // see transform.cu: per-length auxiliary factors
+    T* aux_r = nullptr;
+    // preconditioner data
+    T* lamH2 = nullptr;      // Lambda_H^2
+    T* inv_spec = nullptr;   // 1 / (Lambda_H^2 + alpha Lambda_L)
+    T* w = nullptr;          // diffusivity psi^-1
+    T* dmh = nullptr;        // D^-1/2
+    T* dinv = nullptr;       // D^-1
+    // CG vectors and scratch
+    T* x = nullptr;
+    T* r = nullptr;
+    T* z = nullptr;
+    T* p = nullptr;
+    T* q = nullptr;
+    T* t = nullptr;          // H p, transform intermediate
+    T* t2 = nullptr;         // second transform intermediate (spectrum setup)
+};
+
+struct Psf {
+    int mr = 0, mc = 0;                 // trimmed half-widths
+    std::vector<double> h;              // (2 mr + 1) x (2 mc + 1)
+    std::vector<int> ta, tb;            // nonzero taps
+    std::vector<double> th;
+    std::vector<double> crow, ccol, ccor;
+};
+
+}  // namespace tvd
+
+struct tvd_plan_s {
+    int nr = 0, nc = 0;
+    tvd_bc bc = TVD_BC_ANTIREFLECTIVE;
+    tvd_precond pc = TVD_PC_DFAST;
+    tvd_mode mode = TVD_MODE_FP64;
+    tvd::Psf psf;
+    tvd::FftPlan fft_r, fft_c;          // lengths of the column-direction / row-direction FFTs
+    tvd::Ops<double> d;                 // double resources (always: FP64 residuals)
+    tvd::Ops<float> f;                  // float resources (MIXED only)
+    // CG bookkeeping (device)
+    tvd::CgState* state = nullptr;
+    tvd::CgState* hstate = nullptr;     // pinned host copy of *state
+    double* red = nullptr;              // kMaxRedBlocks partial sums
+    unsigned int* ticket = nullptr;     // last-block counter
+    double* scal = nullptr;             // small double scratch on device
+    // double-only arrays for MIXED refinement
+    double* hx = nullptr;               // H^T H x in double
+    double* res = nullptr;              // double residual
+    double* xd = nullptr;               // double iterate
+    double* tmp = nullptr;              // double scratch
+    bool precond_ready = false;
+    double alpha = 0.0, beta = 0.0;     // parameters of the last setup
+};
+
+namespace tvd {
+
+// ---------------------------------------------------------------- launchers
+// Each launcher is asynchronous on `s` and returns a tvd_status (launch errors).
+
+// y = H x or H^T x. If st is given, the kernel returns at once when st->done.
+template <typename T>
+tvd_status blur_apply(const tvd_plan_s& p, const Ops<T>& o, bool transpose, const T* x, T* y, cudaStream_t s,
+                      CgState* st = nullptr);
+
+// w = psi^-1 of u; then D^-1/2 and D^-1 with D = 1 + alpha diag(L(w)).
+template <typename T>
+tvd_status diffusivity(const tvd_plan_s& p, const T* u, double beta, T* w, cudaStream_t s);
+template <typename T>
+tvd_status diag_scale(const tvd_plan_s& p, const T* w, double alpha, T* dmh, T* dinv, cudaStream_t s);
+
+template <typename T>
+tvd_status tv_apply(const tvd_plan_s& p, const T* w, const T* x, T* y, cudaStream_t s);
+
+// q = H^T t + alpha L(w) pv; with st, also p^T q -> st->pq and alpha = rho / pq.
+template <typename T>
+tvd_status normal_finish(const tvd_plan_s& p, const Ops<T>& o, const T* t, const T* pv, double alpha,
+                         T* q, CgState* st, cudaStream_t s);
+
+// Preconditioner spectrum (requires o.w): inv_spec = 1 / (lamH2 + alpha Lambda_L).
+template <typename T>
+tvd_status spectrum_setup(const tvd_plan_s& p, Ops<T>& o, double alpha, int* bad_flag, cudaStream_t s);
+
+template <typename T>
+tvd_status lamH2_setup(const tvd_plan_s& p, Ops<T>& o, cudaStream_t s);
+
+// z = X^{-1} r. If st != nullptr, also reduce r^T z into st->rho (and run the
+// CG scalar update that follows it).
+template <typename T>
+tvd_status precond_solve(const tvd_plan_s& p, const Ops<T>& o, const T* r, T* z, CgState* st, cudaStream_t s);
+
+// CG kernels
+template <typename T>
+tvd_status cg_init(const tvd_plan_s& p, const T* b, const T* ax, T* r, CgState* st, double tol, int maxit,
+                   cudaStream_t s);
+template <typename T>
+tvd_status cg_pupdate(const tvd_plan_s& p, const T* z, T* pv, CgState* st, cudaStream_t s);
+template <typename T>
+tvd_status cg_xrupdate(const tvd_plan_s& p, T* x, T* r, const T* pv, const T* q, CgState* st, cudaStream_t s);
+template <typename T>
+tvd_status cg_simple_precond(const tvd_plan_s& p, const T* r, const T* dinv, T* z, CgState* st, cudaStream_t s);
+
+// elementwise helpers
+tvd_status residual_d(const tvd_plan_s& p, const double* b, const double* ax, double* r, double* out_norm2,
+                      cudaStream_t s);
+tvd_status norm2_d(const tvd_plan_s& p, const double* a, double* out, cudaStream_t s);
+tvd_status diffnorm2_d(const tvd_plan_s& p, const double* a, const double* b, double* out, cudaStream_t s);
+tvd_status cast_d2f(const double* a, float* b, size_t n, cudaStream_t s);
+tvd_status copy_f(const float* a, float* b, size_t n, cudaStream_t s);
+tvd_status axpy_f2d(double* x, const float* d, size_t n, cudaStream_t s);
+tvd_status fill_zero_f(float* a, size_t n, cudaStream_t s);
+
+int num_sms();
+
+}  // namespace tvd

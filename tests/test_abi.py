@@ -1,0 +1,57 @@
+"""The C-ABI library loads and exports every function that include/tvd.h declares.
+
+No compute call is made here (no GPU is needed). The library is built first if
+it is missing.
+"""
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "tvd.h")
+
+
+def header_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    names = re.findall(r"^\s*(?:const\s+)?[A-Za-z_][A-Za-z0-9_]*\s*\*?\s*([A-Za-z_][A-Za-z0-9_]*)\s*\(", text, flags=re.M)
+    return [n for n in names if n not in ("if", "while")]
+
+
+@pytest.fixture(scope="module")
+def lib():
+    import paper_1011_5964_gb300 as pkg
+    if not os.path.exists(pkg.LIB_PATH):
+        from paper_1011_5964_gb300 import _build
+        _build.build()
+    return pkg.load_library()
+
+
+def test_header_declares_the_abi():
+    import paper_1011_5964_gb300 as pkg
+    names = header_functions()
+    assert set(names) == set(pkg.ABI_FUNCTIONS), names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    for name in header_functions():
+        assert hasattr(lib, name), name
+
+
+def test_version_and_error_without_gpu(lib):
+    assert lib.tvd_version().decode().startswith("tvd-gb300")
+    assert lib.tvd_last_error() is not None
+
+
+def test_plan_create_rejects_bad_arguments_before_touching_the_gpu(lib):
+    """Argument validation is host logic: a NULL out-pointer and a too-small image are refused."""
+    import ctypes
+    import numpy as np
+    import paper_1011_5964_gb300 as pkg
+    h = np.ones((3, 3)) / 9.0
+    hp = h.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+    assert lib.tvd_plan_create(None, 16, 16, hp, 3, 3, 1, 3, 0, None) == pkg.TVD_EINVAL
+    out = ctypes.c_void_p()
+    assert lib.tvd_plan_create(ctypes.byref(out), 2, 16, hp, 3, 3, 1, 3, 0, None) == pkg.TVD_EINVAL
+    assert lib.tvd_plan_create(ctypes.byref(out), 16, 16, hp, 3, 3, 7, 3, 0, None) == pkg.TVD_EINVAL
