@@ -1,0 +1,393 @@
+"""Benchmark: TV deblurring at 1024 x 1024 on one GB300 (or N independent replicas).
+
+Workload (one "step" = one full deblur through the C ABI, every row of the PCG
+hot path): 1024 x 1024 seeded piecewise-constant image, anti-reflective BCs,
+radius-7 out-of-focus disk PSF zero-padded to 31 x 31, 1% Gaussian noise,
+alpha 1e-3, beta 1e-2, 10 lagged-diffusivity FP steps from u^0 = v, each solved
+by PCG with the D_M (hat-S / DST-I) preconditioner to ||r|| / ||r_0|| < 1e-6.
+
+Arms:
+  --impl ours (default): the chosen form (MIXED: float kernels, double CG
+      scalars, double iterative refinement) is the headline ``value``
+      (deblurs/s); the plain FP64 GPU form is measured beside it; PCG
+      iterations/s are reported for both.
+  --impl reference: the FP64 CPU oracle as it stands, timed on the host cores
+      on a bounded sample of the same workload.
+
+Timing: inputs resident in HBM, W untimed warm-up steps, then K steps, each
+bracketed by CUDA events on the launch stream, with the L2 cache flushed (a
+512 MiB write) between steps; barrier + synchronize on both sides; the max over
+ranks. ``e2e`` repeats the step through the public API with pinned host
+buffers (host->device copy of v, deblur, device->host copy of u inside the
+timed region). Under torchrun (N > 1) every rank deblurs its own image
+(replicas only, no collective on the data path).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "PCG iters/s and deblurs/s at 1024², chosen vs plain FP64 GPU, rel err ≤1e-5"
+N_SIDE = 1024
+SEED = 1234
+ALPHA, BETA, OUTER, TOL, NOISE = 1e-3, 1e-2, 10, 1e-6, 0.01
+WORKLOAD = "tv_deblur 1024x1024 AR disk-r7(31x31) 1% noise alpha=1e-3 beta=1e-2 10 FP steps tol=1e-6 D_M"
+
+# Algorithmic bytes per launch of each kernel class, in words of the kernel's
+# type per pixel: the arrays each kernel must read and write once.
+WORDS_PER_PIXEL = {
+    "blur_forward": 2,          # read p, write t = H p
+    "blur_adjoint_L": 4,        # read t, p, w; write q = H^T t + alpha L p
+    "precond_row_forward": 3,   # read r, D^-1/2; write t
+    "precond_column_solve": 3,  # read t, 1/spectrum; write t
+    "precond_row_inverse": 4,   # read t, D^-1/2, r; write z
+    "spectrum_row": 3,          # read w; write E w, G w
+    "spectrum_column": 4,       # read E w, G w, Lambda_H^2; write 1/spectrum
+    "cg_init": 3,               # read b, A x; write r
+    "cg_p_update": 3,           # read z, p; write p
+    "cg_xr_update": 6,          # read x, p, r, q; write x, r
+    "cg_simple_precond": 3,
+    "tv_coefficients": 2,
+    "vector_misc": 2,
+}
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling while the timed region runs."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=2)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[5:9]):
+                if val.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+def make_inputs():
+    import numpy as np
+    from paper_1011_5964_gb300 import synth
+    h = synth.disk_psf(7.0, side=31)
+    u_true = synth.piecewise_constant_image(N_SIDE, N_SIDE, seed=SEED)
+    z = synth.noise_direction(N_SIDE, N_SIDE, SEED)
+    return np, synth, h, u_true, z
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        d = json.load(open(path))
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def cpu_sample(h, v, sample_iters: int):
+    """Oracle as it stands: FP-step set-up plus `sample_iters` PCG iterations of the first
+    FP step at the full workload. Returns (setup_s, seconds per iteration)."""
+    import numpy as np
+    import oracle as O
+    b = O.blur_adjoint(v, h, "ar")
+    t0 = time.perf_counter()
+    P = O.precond_setup(v, h, "ar", ALPHA, BETA, "dfast")
+    t1 = time.perf_counter()
+    w = P["w"]
+    O.pcg(lambda y: O.normal_apply(y, h, "ar", w, ALPHA), lambda r: O.precond_apply(r, P), b, v, 1e-300,
+          sample_iters)
+    t2 = time.perf_counter()
+    # pcg also applies A once to form r_0: charge it as one iteration
+    return (t1 - t0) + (t2 - t1) / (sample_iters + 1), (t2 - t1) / (sample_iters + 1)
+
+
+def oracle_iters_per_deblur():
+    path = os.path.join(ROOT, "tests", "golden", "bench1024_oracle.json")
+    try:
+        d = json.load(open(path))
+        return int(sum(d["inner_iters"])), "stored FP64 oracle run (tests/golden/bench1024_oracle.json)"
+    except Exception:
+        return None, "no stored oracle run"
+
+
+def run_reference(args):
+    """The FP64 CPU oracle, timed on the host cores on a bounded sample of the workload."""
+    ws, rank, local = dist_env()
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("gloo")
+        if rank != 0:
+            dist.barrier()
+            dist.destroy_process_group()
+            return
+    import numpy as np
+    import oracle as O
+    _, synth, h, u_true, z = make_inputs()
+    v = synth.add_noise(O.blur(u_true, h, "ar"), z, NOISE)
+    iters_per_deblur, src = oracle_iters_per_deblur()
+    if iters_per_deblur is None:
+        iters_per_deblur, src = 10 * 60, "assumed 60 inner iterations per FP step (no stored oracle run)"
+    sample_iters = 2
+    times = []
+    for s in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        setup_s, it_s = cpu_sample(h, v, sample_iters)
+        dt = time.perf_counter() - t0
+        if s >= args.warmup:
+            times.append((setup_s, it_s, dt))
+    setup_s = statistics.median(t[0] for t in times)
+    it_s = statistics.median(t[1] for t in times)
+    deblur_s = OUTER * setup_s + iters_per_deblur * it_s
+    value = 1.0 / deblur_s
+    cores = os.cpu_count()
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "deblurs/s", "n_gpus": ws,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * statistics.median(t[2] for t in times),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": WORKLOAD},
+            "pcg_iters_per_s": 1.0 / it_s,
+            "cpu_baseline": {"value": value, "unit": "deblurs/s", "cores": cores, "kind": "oracle",
+                             "sample": f"per step: FP-step set-up + {sample_iters} PCG iterations of the first FP "
+                                       f"step at 1024x1024; deblur time = 10 x set-up + {iters_per_deblur} "
+                                       f"iterations ({src})"},
+            "e2e": {"value": value, "unit": "deblurs/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+    import paper_1011_5964_gb300 as pkg
+    pkg.load_library()
+    _, synth, h, u_true, z = make_inputs()
+    stream = torch.cuda.current_stream()
+
+    mixed = pkg.Plan(N_SIDE, N_SIDE, h, bc="ar", pc="dfast", mode="mixed")
+    plain = pkg.Plan(N_SIDE, N_SIDE, h, bc="ar", pc="dfast", mode="fp64")
+    # observation v = H u_true + eta, blurred by this library's FP64 operator
+    hu = plain.blur(torch.tensor(u_true, dtype=torch.float64, device=dev)).cpu().numpy()
+    v_host = synth.add_noise(hu, z, NOISE)
+    v = torch.tensor(v_host, dtype=torch.float64, device=dev)
+    u = torch.empty_like(v)
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+
+    def barrier():
+        if ws > 1:
+            import torch.distributed as dist
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    def timed(plan, steps, warmup, out):
+        stats = []
+        for _ in range(warmup):
+            plan.deblur(v, ALPHA, BETA, max_outer=OUTER, inner_tol=TOL, inner_maxit=5000, out=out)
+        barrier()
+        ms = 0.0
+        launches0 = pkg.kernel_launches()
+        for _ in range(steps):
+            flush.zero_()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            _, st = plan.deblur(v, ALPHA, BETA, max_outer=OUTER, inner_tol=TOL, inner_maxit=5000, out=out)
+            e1.record(stream)
+            e1.synchronize()
+            ms += e0.elapsed_time(e1)
+            stats.append(st)
+        launches = pkg.kernel_launches() - launches0
+        barrier()
+        return ms, stats, launches
+
+    def max_over_ranks(x):
+        if ws == 1:
+            return x
+        import torch.distributed as dist
+        t = torch.tensor([x], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    sampler = ClockSampler(local)
+    sampler.start()
+    ms_mixed, st_mixed, launches = timed(mixed, args.steps, args.warmup, u)
+    clocks = sampler.stop()
+    ms_mixed = max_over_ranks(ms_mixed)
+    u_mixed = u.clone()
+    iters_mixed = sum(s["total_inner_iters"] for s in st_mixed)
+    ms_per_step = ms_mixed / args.steps
+    value = ws * 1000.0 / ms_per_step
+
+    # plain FP64 GPU form (fewer steps: it is much slower)
+    u64 = torch.empty_like(v)
+    p_steps = max(1, min(2, args.steps))
+    ms_plain, st_plain, _ = timed(plain, p_steps, 1, u64)
+    ms_plain = max_over_ranks(ms_plain)
+    iters_plain = sum(s["total_inner_iters"] for s in st_plain)
+    rel_err = float(torch.linalg.norm(u_mixed - u64) / torch.linalg.norm(u64))
+
+    # per-kernel device time of one more chosen-form step (CUDA events around every launch)
+    pkg.profile_enable(True)
+    flush.zero_()
+    mixed.deblur(v, ALPHA, BETA, max_outer=OUTER, inner_tol=TOL, inner_maxit=5000, out=u)
+    torch.cuda.synchronize()
+    prof = pkg.profile_read()
+    pkg.profile_enable(False)
+    top = max(prof.items(), key=lambda kv: kv[1][0])
+    name, (kms, klaunch) = top
+    base, prec = name.rsplit(".", 1)
+    word = 4 if prec == "f32" else 8
+    bytes_per_launch = WORDS_PER_PIXEL.get(base, 2) * word * N_SIDE * N_SIDE
+    avg_s = kms / 1000.0 / max(klaunch, 1)
+    achieved = bytes_per_launch / avg_s / 1e9
+    peak, peak_src = peaks()
+    roofline = {"bound": "hbm", "kernel": name, "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "traffic": None, "peak_source": peak_src,
+                "bytes_per_launch": bytes_per_launch, "avg_launch_us": avg_s * 1e6, "launches": klaunch,
+                "share": kms / max(sum(v_[0] for v_ in prof.values()), 1e-12)}
+
+    # end to end through the public API with pinned host buffers
+    v_pin = torch.tensor(v_host, dtype=torch.float64).pin_memory()
+    u_pin = torch.empty_like(v_pin).pin_memory()
+    v_dev = torch.empty_like(v)
+    barrier()
+    e2e_ms = 0.0
+    for s in range(args.warmup + args.steps):
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        v_dev.copy_(v_pin, non_blocking=True)
+        mixed.deblur(v_dev, ALPHA, BETA, max_outer=OUTER, inner_tol=TOL, inner_maxit=5000, out=u)
+        u_pin.copy_(u, non_blocking=True)
+        e1.record(stream)
+        e1.synchronize()
+        if s >= args.warmup:
+            e2e_ms += e0.elapsed_time(e1)
+    barrier()
+    e2e_ms = max_over_ranks(e2e_ms)
+    nbytes = N_SIDE * N_SIDE * 8
+
+    line = {"metric": METRIC, "value": value, "unit": "deblurs/s", "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "form": "mixed (float kernels, double scalars + refinement)",
+                       "l2": "flushed between steps (512 MiB write)", "parallelism": f"replicas x{ws}"},
+            "pcg_iters_per_s": ws * iters_mixed / (ms_mixed / 1000.0),
+            "inner_iters_per_deblur": iters_mixed / args.steps,
+            "plain_fp64": {"deblurs_per_s": ws * 1000.0 * p_steps / ms_plain,
+                           "pcg_iters_per_s": ws * iters_plain / (ms_plain / 1000.0),
+                           "inner_iters_per_deblur": iters_plain / p_steps, "ms_per_step": ms_plain / p_steps},
+            "rel_err_vs_plain_fp64": rel_err,
+            "gpu_launches": launches,
+            "roofline": roofline,
+            "clocks": clocks,
+            "e2e": {"value": ws * 1000.0 * args.steps / e2e_ms, "unit": "deblurs/s",
+                    "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes}}
+
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        iters_per_deblur, src = oracle_iters_per_deblur()
+        if iters_per_deblur is None:
+            iters_per_deblur, src = int(round(iters_plain / p_steps)), "iteration count of the FP64 GPU form"
+        setup_s, it_s = cpu_sample(h, v_host, 8)
+        deblur_s = OUTER * setup_s + iters_per_deblur * it_s
+        line["cpu_baseline"] = {"value": 1.0 / deblur_s, "unit": "deblurs/s", "cores": os.cpu_count(),
+                                "kind": "oracle", "pcg_iters_per_s": 1.0 / it_s,
+                                "sample": f"FP-step set-up + 8 PCG iterations of the first FP step at 1024x1024 "
+                                          f"(numpy/scipy default threading); deblur time = 10 x set-up + "
+                                          f"{iters_per_deblur} iterations ({src})"}
+    if rank == 0:
+        print(json.dumps(line))
+    mixed.close()
+    plain.close()
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3 and args.impl == "ours":
+        print("warning: fewer than 3 warm-up steps", file=sys.stderr)
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -186,6 +186,23 @@ const char* tvd_last_error(void);
 /* Library version string. */
 const char* tvd_version(void);
 
+/*
+ * Diagnostics (no counterpart in the paper).
+ * tvd_kernel_launches -- number of CUDA kernels this library has launched in
+ *   the process so far (all plans, all streams).
+ * tvd_profile_enable -- on != 0: from now on record a CUDA event pair around
+ *   the launches of every kernel class (adds host overhead per launch); on = 0
+ *   stops. Either call discards earlier records.
+ * tvd_profile_read -- summed device time (ms) and launch count of class
+ *   `cls` (0 <= cls < tvd_profile_classes()) since profiling was enabled;
+ *   waits for the recorded events. tvd_profile_name gives the class name.
+ */
+unsigned long long tvd_kernel_launches(void);
+tvd_status tvd_profile_enable(int on);
+int tvd_profile_classes(void);
+const char* tvd_profile_name(int cls);
+tvd_status tvd_profile_read(int cls, double* total_ms, long long* launches);
+
 #ifdef __cplusplus
 }
 #endif

@@ -428,11 +428,12 @@ def normal_apply(x, h, bc, w, alpha) -> np.ndarray:
 # PCG (Golub & Van Loan, Algorithm 10.3.1) and the FP loop, Secs. 1 and 5
 # --------------------------------------------------------------------------
 
-def pcg(apply_A, apply_M, b, x0, tol, maxit):
+def pcg(apply_A, apply_M, b, x0, tol, maxit, hist=None):
     """Preconditioned CG on A x = b from x0.
 
     Stops when ||r_k||_2 / ||r_0||_2 < tol (Sec. 5) or after ``maxit`` products
-    with A. Returns (x, iterations, relres, converged).
+    with A. Returns (x, iterations, relres, converged). If ``hist`` is a list,
+    the relative residual after each iteration is appended to it.
     """
     x = np.array(x0, dtype=np.float64, copy=True)
     r = b - apply_A(x)
@@ -457,17 +458,19 @@ def pcg(apply_A, apply_M, b, x0, tol, maxit):
         r = r - a * q
         rho_old = rho
         relres = float(np.sqrt((r * r).sum())) / r0
+        if hist is not None:
+            hist.append(relres)
         if relres < tol:
             return x, k, relres, True
     return x, k, relres, False
 
 
-def fp_step(u, b, h, bc, alpha, beta, kind, tol, maxit):
+def fp_step(u, b, h, bc, alpha, beta, kind, tol, maxit, hist=None):
     """One lagged-diffusivity step: solve (H^T H + alpha L(u)) x = H^T v from x0 = u."""
     P = precond_setup(u, h, bc, alpha, beta, kind)
     w = P["w"]
     return pcg(lambda y: normal_apply(y, h, bc, w, alpha),
-               lambda r: precond_apply(r, P), b, u, tol, maxit)
+               lambda r: precond_apply(r, P), b, u, tol, maxit, hist)
 
 
 def tv_deblur(v, h, bc, alpha, beta, outer=10, tol=1e-6, maxit=1000,
@@ -476,14 +479,17 @@ def tv_deblur(v, h, bc, alpha, beta, outer=10, tol=1e-6, maxit=1000,
 
     Runs ``outer`` FP steps, or stops earlier when ||u^k - u^{k-1}|| / ||u^k||
     < outer_tol (if outer_tol > 0). Returns (u, stats) where stats holds the
-    per-step inner iteration counts, residuals and relative changes.
+    per-step inner iteration counts, residuals, relative changes and the
+    relative residuals of the last two inner iterations of each step.
     """
     v = np.asarray(v, dtype=np.float64)
     b = blur_adjoint(v, h, bc)
     u = v.copy()
-    stats = {"inner_iters": [], "relres": [], "rel_change": [], "converged": []}
+    stats = {"inner_iters": [], "relres": [], "rel_change": [], "converged": [], "relres_tail": []}
     for _ in range(outer):
-        x, k, rr, ok = fp_step(u, b, h, bc, alpha, beta, kind, tol, maxit)
+        hist = []
+        x, k, rr, ok = fp_step(u, b, h, bc, alpha, beta, kind, tol, maxit, hist)
+        stats["relres_tail"].append(hist[-2:])
         change = float(np.linalg.norm(x - u) / max(np.linalg.norm(x), 1e-300))
         stats["inner_iters"].append(k)
         stats["relres"].append(rr)

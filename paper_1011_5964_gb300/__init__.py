@@ -34,7 +34,8 @@ STATUS_NAMES = ["TVD_OK", "TVD_EINVAL", "TVD_EPSF_ASYM", "TVD_EPSF_SIZE", "TVD_E
 # Function names of the C ABI, in include/tvd.h order.
 ABI_FUNCTIONS = ["tvd_plan_create", "tvd_plan_destroy", "ar_blur_apply", "tv_operator_apply",
                  "tau_precond_setup", "tau_precond_solve", "pcg_solve", "tv_deblur",
-                 "tvd_last_error", "tvd_version"]
+                 "tvd_last_error", "tvd_version", "tvd_kernel_launches", "tvd_profile_enable",
+                 "tvd_profile_classes", "tvd_profile_name", "tvd_profile_read"]
 
 
 class TvdError(RuntimeError):
@@ -76,8 +77,13 @@ def load_library(path: str | None = None) -> ctypes.CDLL:
     lib.tv_deblur.argtypes = [vp, vp, d, d, i, d, d, i, vp, ctypes.POINTER(_Stats), vp]
     lib.tvd_last_error.restype = ctypes.c_char_p
     lib.tvd_version.restype = ctypes.c_char_p
+    lib.tvd_kernel_launches.restype = ctypes.c_ulonglong
+    lib.tvd_profile_enable.argtypes = [i]
+    lib.tvd_profile_name.argtypes = [i]
+    lib.tvd_profile_name.restype = ctypes.c_char_p
+    lib.tvd_profile_read.argtypes = [i, ctypes.POINTER(d), ctypes.POINTER(ctypes.c_longlong)]
     for name in ABI_FUNCTIONS:
-        if name not in ("tvd_last_error", "tvd_version"):
+        if name not in ("tvd_last_error", "tvd_version", "tvd_kernel_launches", "tvd_profile_name"):
             getattr(lib, name).restype = ctypes.c_int
     if path is None:
         _lib = lib
@@ -203,6 +209,28 @@ class Plan:
                    "total_inner_iters": stats.total_inner_iters, "refinement_sweeps": stats.refinement_sweeps,
                    "last_relres": stats.last_relres, "last_rel_change": stats.last_rel_change,
                    "last_status": stats.last_status, "status": st}
+
+
+def kernel_launches() -> int:
+    """CUDA kernels launched by the library in this process so far."""
+    return int(load_library().tvd_kernel_launches())
+
+
+def profile_enable(on: bool = True) -> None:
+    """Start (or stop) CUDA-event timing per kernel class; clears earlier records."""
+    _check(load_library().tvd_profile_enable(int(bool(on))))
+
+
+def profile_read() -> dict:
+    """{class name: (total device ms, launches)} since profiling was enabled."""
+    lib = load_library()
+    out = {}
+    for c in range(lib.tvd_profile_classes()):
+        ms = ctypes.c_double(0.0)
+        n = ctypes.c_longlong(0)
+        _check(lib.tvd_profile_read(c, ctypes.byref(ms), ctypes.byref(n)))
+        out[lib.tvd_profile_name(c).decode()] = (ms.value, n.value)
+    return out
 
 
 # Module-level names matching the C ABI.

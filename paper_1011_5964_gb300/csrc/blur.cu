@@ -244,6 +244,7 @@ static tvd_status launch_blur(const tvd_plan_s& p, const Ops<T>& o, bool transpo
     const int nborder = 2 * (nc - 2) + 2 * (nr - 2) + 4;
     const int border_blocks = (nborder + kThreads - 1) / kThreads;
     const bool ar_adj = transpose && p.bc == TVD_BC_ANTIREFLECTIVE;
+    ProfScope prof(prof_class<T>((transpose || fuse) ? PROF_BLUR_ADJ : PROF_BLUR_FWD), s, ar_adj ? 2 : 1);
     if (fa.reduce) {
         fa.total_blocks = tile_blocks + (ar_adj ? border_blocks : 0);
         if (fa.total_blocks > kMaxRedBlocks) {

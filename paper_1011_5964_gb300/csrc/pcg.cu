@@ -135,6 +135,7 @@ template <typename T>
 tvd_status cg_init(const tvd_plan_s& p, const T* b, const T* ax, T* r, CgState* st, double tol, int maxit,
                    cudaStream_t s) {
     const size_t n = (size_t)p.nr * p.nc;
+    ProfScope prof(prof_class<T>(PROF_CG_INIT), s);
     cg_init_kernel<T><<<red_blocks(n), kThreads, 0, s>>>(b, ax, r, n, st, p.red, p.ticket + 0, tol, maxit);
     TVD_CUDA_TRY(cudaGetLastError());
     return TVD_OK;
@@ -143,6 +144,7 @@ tvd_status cg_init(const tvd_plan_s& p, const T* b, const T* ax, T* r, CgState* 
 template <typename T>
 tvd_status cg_pupdate(const tvd_plan_s& p, const T* z, T* pv, CgState* st, cudaStream_t s) {
     const size_t n = (size_t)p.nr * p.nc;
+    ProfScope prof(prof_class<T>(PROF_CG_PUPDATE), s);
     cg_pupdate_kernel<T><<<red_blocks(n), kThreads, 0, s>>>(z, pv, n, st);
     TVD_CUDA_TRY(cudaGetLastError());
     return TVD_OK;
@@ -151,6 +153,7 @@ tvd_status cg_pupdate(const tvd_plan_s& p, const T* z, T* pv, CgState* st, cudaS
 template <typename T>
 tvd_status cg_xrupdate(const tvd_plan_s& p, T* x, T* r, const T* pv, const T* q, CgState* st, cudaStream_t s) {
     const size_t n = (size_t)p.nr * p.nc;
+    ProfScope prof(prof_class<T>(PROF_CG_XR), s);
     cg_xr_kernel<T><<<red_blocks(n), kThreads, 0, s>>>(x, r, pv, q, n, st, p.red, p.ticket + 3);
     TVD_CUDA_TRY(cudaGetLastError());
     return TVD_OK;
@@ -159,6 +162,7 @@ tvd_status cg_xrupdate(const tvd_plan_s& p, T* x, T* r, const T* pv, const T* q,
 template <typename T>
 tvd_status cg_simple_precond(const tvd_plan_s& p, const T* r, const T* dinv, T* z, CgState* st, cudaStream_t s) {
     const size_t n = (size_t)p.nr * p.nc;
+    ProfScope prof(prof_class<T>(PROF_CG_SIMPLE), s);
     cg_simple_precond_kernel<T><<<red_blocks(n), kThreads, 0, s>>>(r, dinv, z, n, st, p.red, p.ticket + 4);
     TVD_CUDA_TRY(cudaGetLastError());
     return TVD_OK;
@@ -207,6 +211,7 @@ __global__ void fill_zero_f_kernel(float* __restrict__ a, size_t n) {
 tvd_status residual_d(const tvd_plan_s& p, const double* b, const double* ax, double* r, double* out_norm2,
                       cudaStream_t s) {
     const size_t n = (size_t)p.nr * p.nc;
+    ProfScope prof(prof_class<double>(PROF_MISC), s);
     residual_kernel<<<red_blocks(n), kThreads, 0, s>>>(b, ax, r, n, out_norm2, p.red, p.ticket + 5);
     TVD_CUDA_TRY(cudaGetLastError());
     return TVD_OK;
@@ -214,6 +219,7 @@ tvd_status residual_d(const tvd_plan_s& p, const double* b, const double* ax, do
 
 tvd_status norm2_d(const tvd_plan_s& p, const double* a, double* out, cudaStream_t s) {
     const size_t n = (size_t)p.nr * p.nc;
+    ProfScope prof(prof_class<double>(PROF_MISC), s);
     diffnorm_kernel<<<red_blocks(n), kThreads, 0, s>>>(a, nullptr, n, out, p.red, p.ticket + 5);
     TVD_CUDA_TRY(cudaGetLastError());
     return TVD_OK;
@@ -221,30 +227,35 @@ tvd_status norm2_d(const tvd_plan_s& p, const double* a, double* out, cudaStream
 
 tvd_status diffnorm2_d(const tvd_plan_s& p, const double* a, const double* b, double* out, cudaStream_t s) {
     const size_t n = (size_t)p.nr * p.nc;
+    ProfScope prof(prof_class<double>(PROF_MISC), s);
     diffnorm_kernel<<<red_blocks(n), kThreads, 0, s>>>(a, b, n, out, p.red, p.ticket + 5);
     TVD_CUDA_TRY(cudaGetLastError());
     return TVD_OK;
 }
 
 tvd_status cast_d2f(const double* a, float* b, size_t n, cudaStream_t s) {
+    ProfScope prof(PROF_MISC, s);
     cast_d2f_kernel<<<red_blocks(n), kThreads, 0, s>>>(a, b, n);
     TVD_CUDA_TRY(cudaGetLastError());
     return TVD_OK;
 }
 
 tvd_status axpy_f2d(double* x, const float* d, size_t n, cudaStream_t s) {
+    ProfScope prof(PROF_MISC, s);
     axpy_f2d_kernel<<<red_blocks(n), kThreads, 0, s>>>(x, d, n);
     TVD_CUDA_TRY(cudaGetLastError());
     return TVD_OK;
 }
 
 tvd_status copy_f(const float* a, float* b, size_t n, cudaStream_t s) {
+    ProfScope prof(PROF_MISC, s);
     copy_f_kernel<<<red_blocks(n), kThreads, 0, s>>>(a, b, n);
     TVD_CUDA_TRY(cudaGetLastError());
     return TVD_OK;
 }
 
 tvd_status fill_zero_f(float* a, size_t n, cudaStream_t s) {
+    ProfScope prof(PROF_MISC, s);
     fill_zero_f_kernel<<<red_blocks(n), kThreads, 0, s>>>(a, n);
     TVD_CUDA_TRY(cudaGetLastError());
     return TVD_OK;

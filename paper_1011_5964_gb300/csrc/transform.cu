@@ -590,6 +590,9 @@ static tvd_status launch_line(LineArgs<T> a, cudaStream_t s) {
         return TVD_EINVAL;
     }
     TVD_CUDA_TRY(cudaFuncSetAttribute(line_kernel<T, BC, OP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    constexpr int cls = OP == OP_ROW_FWD ? PROF_ROW_FWD : OP == OP_COL_SOLVE ? PROF_COL_SOLVE
+                      : OP == OP_ROW_INV ? PROF_ROW_INV : OP == OP_ROW_EG ? PROF_EG_ROW : PROF_EG_COL;
+    ProfScope prof(prof_class<T>(cls), s);
     line_kernel<T, BC, OP><<<blocks, kThreads, smem, s>>>(a);
     TVD_CUDA_TRY(cudaGetLastError());
     return TVD_OK;
@@ -711,6 +714,7 @@ tvd_status lamH2_setup(const tvd_plan_s& p, Ops<T>& o, cudaStream_t s) {
     }
     cudaMemcpyAsync(dcr, cr.data(), cr.size() * sizeof(double), cudaMemcpyHostToDevice, s);
     cudaMemcpyAsync(dG, G.data(), G.size() * sizeof(double), cudaMemcpyHostToDevice, s);
+    count_launches(1);
     lamH2_kernel<T><<<num_sms() * 4, kThreads, 0, s>>>(dcr, dG, o.lamH2, p.nr, p.nc, pr);
     cudaError_t e = cudaStreamSynchronize(s);
     cudaFree(dcr);

@@ -59,6 +59,7 @@ static int ew_blocks(size_t n) {
 template <typename T>
 tvd_status diffusivity(const tvd_plan_s& p, const T* u, double beta, T* w, cudaStream_t s) {
     const size_t n = (size_t)p.nr * p.nc;
+    ProfScope prof(prof_class<T>(PROF_TV), s);
     diffusivity_kernel<T><<<ew_blocks(n), kThreads, 0, s>>>(u, w, p.nr, p.nc, T(beta * beta));
     TVD_CUDA_TRY(cudaGetLastError());
     return TVD_OK;
@@ -67,6 +68,7 @@ tvd_status diffusivity(const tvd_plan_s& p, const T* u, double beta, T* w, cudaS
 template <typename T>
 tvd_status diag_scale(const tvd_plan_s& p, const T* w, double alpha, T* dmh, T* dinv, cudaStream_t s) {
     const size_t n = (size_t)p.nr * p.nc;
+    ProfScope prof(prof_class<T>(PROF_TV), s);
     diag_scale_kernel<T><<<ew_blocks(n), kThreads, 0, s>>>(w, dmh, dinv, p.nr, p.nc, T(alpha));
     TVD_CUDA_TRY(cudaGetLastError());
     return TVD_OK;
@@ -75,6 +77,7 @@ tvd_status diag_scale(const tvd_plan_s& p, const T* w, double alpha, T* dmh, T* 
 template <typename T>
 tvd_status tv_apply(const tvd_plan_s& p, const T* w, const T* x, T* y, cudaStream_t s) {
     const size_t n = (size_t)p.nr * p.nc;
+    ProfScope prof(prof_class<T>(PROF_TV), s);
     tv_apply_kernel<T><<<ew_blocks(n), kThreads, 0, s>>>(w, x, y, p.nr, p.nc);
     TVD_CUDA_TRY(cudaGetLastError());
     return TVD_OK;

@@ -40,6 +40,33 @@ struct Status {
         if (_s != TVD_OK) return _s;    \
     } while (0)
 
+// ---------------------------------------------------------------- launch accounting
+
+enum ProfClass {
+    PROF_BLUR_FWD = 0, PROF_BLUR_ADJ, PROF_ROW_FWD, PROF_COL_SOLVE, PROF_ROW_INV, PROF_EG_ROW, PROF_EG_COL,
+    PROF_CG_INIT, PROF_CG_PUPDATE, PROF_CG_XR, PROF_CG_SIMPLE, PROF_TV, PROF_MISC, PROF_NUM_BASE,
+    PROF_NUM_CLASSES = 2 * PROF_NUM_BASE     // float launches use the base id, double ones base + PROF_NUM_BASE
+};
+template <typename T>
+constexpr int prof_class(int base) { return base + (sizeof(T) == 8 ? PROF_NUM_BASE : 0); }
+
+void count_launches(int k);
+
+// Counts the launches of one launcher call and, when profiling is on, brackets
+// them with CUDA events on the launch stream.
+class ProfScope {
+  public:
+    ProfScope(int cls, cudaStream_t s, int nkernels = 1);
+    ~ProfScope();
+    ProfScope(const ProfScope&) = delete;
+    ProfScope& operator=(const ProfScope&) = delete;
+
+  private:
+    int cls_;
+    cudaStream_t s_;
+    cudaEvent_t start_;
+};
+
 // ---------------------------------------------------------------- small types
 
 template <typename T>

@@ -36,7 +36,8 @@ def run(case):
     u_true = synth.piecewise_constant_image(N, N, seed=SEED)
     v = synth.add_noise(O.blur(u_true, h, case["bc"]), synth.noise_direction(N, N, SEED), case["noise"])
     u, st = O.tv_deblur(v, h, case["bc"], case["alpha"], 1e-2, outer=OUTER, tol=TOL, maxit=5000, kind=case["kind"])
-    return dict(case, inner_iters=st["inner_iters"], u_norm=float((u * u).sum() ** 0.5))
+    return dict(case, inner_iters=st["inner_iters"], relres_tail=st["relres_tail"],
+                u_norm=float((u * u).sum() ** 0.5))
 
 
 if __name__ == "__main__":

@@ -13,10 +13,19 @@ HEADER = os.path.join(ROOT, "include", "tvd.h")
 
 
 def header_functions():
+    """Names of the functions declared in the header (declarations end with ');')."""
     text = open(HEADER).read()
     text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
-    names = re.findall(r"^\s*(?:const\s+)?[A-Za-z_][A-Za-z0-9_]*\s*\*?\s*([A-Za-z_][A-Za-z0-9_]*)\s*\(", text, flags=re.M)
-    return [n for n in names if n not in ("if", "while")]
+    text = "\n".join(ln for ln in text.splitlines() if not ln.lstrip().startswith("#"))
+    names = []
+    for stmt in text.split(";"):
+        stmt = stmt.strip()
+        if not stmt.endswith(")") or "typedef" in stmt or "{" in stmt:
+            continue
+        m = re.search(r"([A-Za-z_][A-Za-z0-9_]*)\s*\(", stmt)
+        if m:
+            names.append(m.group(1))
+    return names
 
 
 @pytest.fixture(scope="module")
