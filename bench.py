@@ -300,6 +300,10 @@ def run_ours(args):
     torch.cuda.synchronize()
     prof = pkg.profile_read()
     pkg.profile_enable(False)
+    if rank == 0:
+        table = {k: {"ms": round(v_[0], 4), "launches": v_[1]} for k, v_ in sorted(prof.items(), key=lambda kv: -kv[1][0])
+                 if v_[1]}
+        print("per-kernel-class device time of one chosen-form step: " + json.dumps(table), file=sys.stderr)
     top = max(prof.items(), key=lambda kv: kv[1][0])
     name, (kms, klaunch) = top
     base, prec = name.rsplit(".", 1)

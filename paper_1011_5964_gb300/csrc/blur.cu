@@ -99,19 +99,48 @@ blur_tile_kernel(const T* __restrict__ x, T* __restrict__ y, int nr, int nc, int
     if (fa.st && fa.st->done) return;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int TW = BT + 2 * mc, TH = BT + 2 * mr;
+    constexpr int LS = BT + 2;                       // stride of the w / p tiles (1-pixel halo)
     T* tile = reinterpret_cast<T*>(smem_raw);
-    T* sh = tile + TW * TH;
+    T* sw = tile + TW * TH;                          // FUSE: w tile
+    T* sp = sw + (FUSE ? LS * LS : 0);               // FUSE: p tile
+    T* sh = sp + (FUSE ? LS * LS : 0);
     int* sab = reinterpret_cast<int*>(sh + ntaps);
+    const int r0 = blockIdx.y * BT - mr, c0 = blockIdx.x * BT - mc;
+    // stage the extended input tile: a plain asynchronous copy where the tile
+    // lies inside the image (away from the boundary lines for EXT_ODD), the
+    // BC extension computed on the fly elsewhere
+    const bool inside = (EXT == EXT_ODD) ? (r0 >= 1 && c0 >= 1 && r0 + TH <= nr - 1 && c0 + TW <= nc - 1)
+                                         : (r0 >= 0 && c0 >= 0 && r0 + TH <= nr && c0 + TW <= nc);
+    if (inside) {
+        for (int idx = threadIdx.x; idx < TW * TH; idx += blockDim.x) {
+            const int li = idx / TW, lj = idx - li * TW;
+            cp_async_elem(tile + idx, x + (size_t)(r0 + li) * nc + (c0 + lj));
+        }
+    }
+    if (FUSE) {
+        const int i0 = blockIdx.y * BT - 1, j0 = blockIdx.x * BT - 1;
+        for (int idx = threadIdx.x; idx < LS * LS; idx += blockDim.x) {
+            const int li = idx / LS, lj = idx - li * LS;
+            const int i = i0 + li, j = j0 + lj;
+            if (i >= 0 && i < nr && j >= 0 && j < nc) {
+                cp_async_elem(sw + idx, w + (size_t)i * nc + j);
+                cp_async_elem(sp + idx, pv + (size_t)i * nc + j);
+            }
+        }
+    }
     for (int k = threadIdx.x; k < ntaps; k += blockDim.x) {
         sh[k] = tap_h[k];
         sab[2 * k] = tap_ab[k];
         sab[2 * k + 1] = tap_ab[ntaps + k];
     }
-    const int r0 = blockIdx.y * BT - mr, c0 = blockIdx.x * BT - mc;
-    for (int idx = threadIdx.x; idx < TW * TH; idx += blockDim.x) {
-        const int li = idx / TW, lj = idx - li * TW;
-        tile[idx] = ext_value<T, EXT>(x, r0 + li, c0 + lj, nr, nc, mr, mc);
+    if (!inside) {
+#pragma unroll 4
+        for (int idx = threadIdx.x; idx < TW * TH; idx += blockDim.x) {
+            const int li = idx / TW, lj = idx - li * TW;
+            tile[idx] = ext_value<T, EXT>(x, r0 + li, c0 + lj, nr, nc, mr, mc);
+        }
     }
+    cp_async_wait_all();
     __syncthreads();
     const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
     constexpr int PER = BT / BROWS;
@@ -134,8 +163,16 @@ blur_tile_kernel(const T* __restrict__ x, T* __restrict__ y, int nr, int nc, int
         if (EXT == EXT_ODD && (i == 0 || i == nr - 1 || j == 0 || j == nc - 1)) continue;
         T out = acc[q];
         if (FUSE) {
-            out += T(fa.alpha) * lap_at(w, pv, i, j, nr, nc);
-            part += (double)pv[(size_t)i * nc + j] * (double)out;
+            // alpha L(w) p from the staged tiles (5-point stencil, zero Neumann)
+            const int o = (ty + q * BROWS + 1) * LS + (tx + 1);
+            const T pc = sp[o], wc = sw[o];
+            T l = T(0);
+            if (i < nr - 1) l += wc * (pc - sp[o + LS]);
+            if (j < nc - 1) l += wc * (pc - sp[o + 1]);
+            if (i > 0) l += sw[o - LS] * (pc - sp[o - LS]);
+            if (j > 0) l += sw[o - 1] * (pc - sp[o - 1]);
+            out += T(fa.alpha) * l;
+            part += (double)pc * (double)out;
         }
         y[(size_t)i * nc + j] = out;
     }
@@ -228,8 +265,9 @@ ar_adjoint_border_kernel(const T* __restrict__ y, T* __restrict__ out, int nr, i
     }
 }
 
-static size_t tile_smem(int mr, int mc, int ntaps, size_t elem) {
-    return (size_t)(BT + 2 * mc) * (BT + 2 * mr) * elem + (size_t)ntaps * (elem + 2 * sizeof(int)) + 16;
+static size_t tile_smem(int mr, int mc, int ntaps, size_t elem, bool fuse) {
+    return (size_t)(BT + 2 * mc) * (BT + 2 * mr) * elem + (fuse ? 2 * (BT + 2) * (BT + 2) * elem : 0) +
+           (size_t)ntaps * (elem + 2 * sizeof(int)) + 16;
 }
 
 template <typename T>
@@ -237,8 +275,8 @@ static tvd_status launch_blur(const tvd_plan_s& p, const Ops<T>& o, bool transpo
                               const T* w, const T* pv, double alpha, CgState* st, cudaStream_t s) {
     const int nr = p.nr, nc = p.nc, mr = p.psf.mr, mc = p.psf.mc;
     const dim3 grid((nc + BT - 1) / BT, (nr + BT - 1) / BT);
-    const size_t smem = tile_smem(mr, mc, o.ntaps, sizeof(T));
     const bool fuse = (w != nullptr);
+    const size_t smem = tile_smem(mr, mc, o.ntaps, sizeof(T), fuse);
     FuseArgs fa{alpha, st, p.red, p.ticket + 1, (fuse && st) ? 1 : 0, 0, 0, 0};
     const int tile_blocks = (int)(grid.x * grid.y);
     const int nborder = 2 * (nc - 2) + 2 * (nr - 2) + 4;

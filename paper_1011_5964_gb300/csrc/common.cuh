@@ -75,6 +75,20 @@ __device__ __forceinline__ T lap_at(const T* __restrict__ w, const T* __restrict
     return acc;
 }
 
+// Asynchronous global -> shared copy of one element (cp.async, 4 or 8 bytes);
+// many such copies stay in flight per thread until cp_async_wait_all().
+template <typename T>
+__device__ __forceinline__ void cp_async_elem(T* smem, const T* gmem) {
+    static_assert(sizeof(T) == 4 || sizeof(T) == 8, "cp.async element size");
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    if constexpr (sizeof(T) == 4)
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(s), "l"(gmem) : "memory");
+    else
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+
 __device__ __forceinline__ bool finite_pos(double v) { return isfinite(v) && v > 0.0; }
 
 }  // namespace tvd

@@ -45,7 +45,7 @@ enum { BCK_AR = 0, BCK_R = 1 };
 //      slot3 c_k^2 / 2                  (real)
 //      slot4 2 c_k^2 sin^2(pi k / (2n)) (real)
 //      slot5 1 / (n c_k)                (real)
-constexpr int kAuxSlots = 8;
+
 
 template <typename T>
 struct LineArgs {
@@ -118,7 +118,9 @@ __device__ __forceinline__ void dft_store(cplx<T> (&v)[R], cplx<T>* __restrict__
         for (int j = 1; j <= H; ++j) { o0.re += v[j].re; o0.im += v[j].im; }
         if constexpr (even) { o0.re += vh.re; o0.im += vh.im; }
         dst[0] = o0;
-#pragma unroll
+        // the inputs stay in registers; the output loop is rolled for large
+        // radices to keep the register count (and so the occupancy) moderate
+#pragma unroll (R <= 8 ? H : 1)
         for (int k = 1; k <= H; ++k) {
             cplx<T> a = v0, b = {T(0), T(0)};
 #pragma unroll
@@ -240,8 +242,7 @@ __device__ __forceinline__ void split_pair(const cplx<T>* Z, int k, int L, cplx<
 
 // DST-I on positions 1..n-2 of each raw line (AR); positions 0, n-1 untouched.
 template <typename T>
-__device__ void dst1_lines(T* raw, cplx<T>* bufA, cplx<T>* bufB, T* scan, const LineArgs<T>& a,
-                           const cplx<T>* tw) {
+__device__ void dst1_lines(T* raw, cplx<T>* bufA, cplx<T>* bufB, const LineArgs<T>& a, const cplx<T>* tw) {
     const int n = a.n, M = n - 1, N = n - 2, P = a.P;
     const T* sinh = a.aux;                    // slot0
     for (int e = threadIdx.x; e < P * M; e += blockDim.x) {
@@ -255,6 +256,8 @@ __device__ void dst1_lines(T* raw, cplx<T>* bufA, cplx<T>* bufB, T* scan, const 
     }
     __syncthreads();
     const cplx<T>* Z = fft_pairs<T>(bufA, bufB, P, a.fp, tw, false);
+    // the FFT buffer not holding the result keeps the recurrence terms (2P * K <= 2P * L values)
+    T* scan = reinterpret_cast<T*>(Z == bufA ? bufB : bufA);
     const T sc = sqrt(T(2) / T(M));
     const int nodd = (N + 1) / 2;             // F_1, F_3, ...
     const int neven = N / 2;                  // F_2, F_4, ...
@@ -421,61 +424,84 @@ __device__ __forceinline__ void finish_rho(CgState* st, double rho) {
     st->beta = st->iter == 0 ? 0.0 : rho / st->rho_old;
 }
 
+// Extra shared memory (elements of T) each operation stages next to the lines:
+// ROW_FWD: D^-1/2; COL_SOLVE: 1/spectrum; ROW_INV: D^-1/2 and r; ROW_EG: the
+// E and G outputs; COL_EG: E, G outputs and Lambda_H^2.
+__host__ __device__ constexpr size_t line_extra(int op, size_t lines, size_t n, size_t P) {
+    return op == OP_ROW_FWD ? lines * n
+         : op == OP_COL_SOLVE ? lines * n
+         : op == OP_ROW_INV ? 2 * lines * n
+         : op == OP_ROW_EG ? 2 * lines * n
+         : 2 * lines * n + P * n;
+}
+
 template <typename T, int BC, int OP>
 __global__ void __launch_bounds__(kThreads) line_kernel(LineArgs<T> a) {
     if (a.st && a.st->done) return;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int n = a.n, P = a.P, L = a.L;
     const int lines = 2 * P;
+    const int ln = lines * n;
     cplx<T>* tw = reinterpret_cast<cplx<T>*>(smem_raw);
     cplx<T>* bufA = tw + L;
     cplx<T>* bufB = bufA + (size_t)P * L;
     T* raw = reinterpret_cast<T*>(bufB + (size_t)P * L);
-    T* extra = raw + (size_t)lines * n;      // scan / second output lines
-    for (int i = threadIdx.x; i < L; i += blockDim.x) tw[i] = a.tw[i];
-
+    T* ex = raw + ln;
     constexpr bool cols = (OP == OP_COL_SOLVE || OP == OP_COL_EG);
-    // line index of local line l, or -1
+    // global line index of local line l, or -1
     auto gline = [&](int l) -> int {
         int g;
         if (OP == OP_COL_EG) g = blockIdx.x * P + (l >> 1);
         else g = blockIdx.x * lines + l;
         return g < a.nlines ? g : -1;
     };
-    // ---- load
+
+    // ---- stage the lines and their per-pixel factors: asynchronous copies,
+    // all of them in flight before the first wait
+    for (int i = threadIdx.x; i < L; i += blockDim.x) cp_async_elem(&tw[i].re, &a.tw[i].re), cp_async_elem(&tw[i].im, &a.tw[i].im);
     if (!cols) {
-        for (int e = threadIdx.x; e < lines * n; e += blockDim.x) {
+        for (int e = threadIdx.x; e < ln; e += blockDim.x) {
             const int l = e / n, idx = e - l * n;
             const int g = gline(l);
-            T v = T(0);
-            if (g >= 0) {
-                const size_t o = (size_t)g * a.nc + idx;
-                v = a.in0[o];
-                if (OP == OP_ROW_FWD && a.scale) v *= a.scale[o];
+            if (g < 0) {
+                raw[e] = T(0);
+                continue;
             }
-            raw[(size_t)l * n + idx] = v;
+            const size_t o = (size_t)g * a.nc + idx;
+            cp_async_elem(raw + e, a.in0 + o);
+            if ((OP == OP_ROW_FWD || OP == OP_ROW_INV) && a.scale) cp_async_elem(ex + e, a.scale + o);
+            if (OP == OP_ROW_INV && a.st) cp_async_elem(ex + ln + e, a.rvec + o);
         }
     } else {
-        for (int e = threadIdx.x; e < lines * n; e += blockDim.x) {
+        for (int e = threadIdx.x; e < ln; e += blockDim.x) {
             const int idx = e / lines, l = e - idx * lines;
             const int g = gline(l);
-            T v = T(0);
-            if (g >= 0) {
-                const size_t o = (size_t)idx * a.nc + g;
-                v = (OP == OP_COL_EG && (l & 1)) ? a.in1[o] : a.in0[o];
+            const int si = l * n + idx;
+            if (g < 0) {
+                raw[si] = T(0);
+                continue;
             }
-            raw[(size_t)l * n + idx] = v;
+            const size_t o = (size_t)idx * a.nc + g;
+            cp_async_elem(raw + si, ((OP == OP_COL_EG && (l & 1)) ? a.in1 : a.in0) + o);
+            if (OP == OP_COL_SOLVE) cp_async_elem(ex + si, a.spec + o);
+            if (OP == OP_COL_EG && !(l & 1)) cp_async_elem(ex + 2 * ln + (l >> 1) * n + idx, a.spec + o);
         }
     }
+    cp_async_wait_all();
     __syncthreads();
+    if (OP == OP_ROW_FWD && a.scale) {
+        for (int e = threadIdx.x; e < ln; e += blockDim.x)
+            if (gline(e / n) >= 0) raw[e] *= ex[e];
+        __syncthreads();
+    }
 
     // ---- transform(s)
     if (OP == OP_ROW_EG || OP == OP_COL_EG) {
-        T* eo = extra;
-        T* go = extra + (size_t)lines * n;
+        T* eo = ex;
+        T* go = ex + ln;
         eg_lines<T, BC>(raw, bufA, bufB, eo, go, a, tw);
         if (OP == OP_ROW_EG) {
-            for (int e = threadIdx.x; e < lines * n; e += blockDim.x) {
+            for (int e = threadIdx.x; e < ln; e += blockDim.x) {
                 const int l = e / n, idx = e - l * n;
                 const int g = gline(l);
                 if (g < 0) continue;
@@ -485,33 +511,30 @@ __global__ void __launch_bounds__(kThreads) line_kernel(LineArgs<T> a) {
             }
         } else {
             // Lambda_L column = G(A col) + E(B col); spec = lamH2 + alpha Lambda_L
+            const T* lam = ex + 2 * ln;
             for (int e = threadIdx.x; e < P * n; e += blockDim.x) {
                 const int idx = e / P, pp = e - idx * P;
                 const int g = gline(2 * pp);
                 if (g < 0) continue;
                 const T lamL = go[(size_t)(2 * pp) * n + idx] + eo[(size_t)(2 * pp + 1) * n + idx];
-                const size_t o = (size_t)idx * a.nc + g;
-                const double sp = (double)a.spec[o] + a.alpha * (double)lamL;
+                const double sp = (double)lam[pp * n + idx] + a.alpha * (double)lamL;
                 if (!(sp > 1e-300) || !isfinite(sp)) atomicOr(a.bad, 1);
-                a.inv_out[o] = T(1.0 / sp);
+                a.inv_out[(size_t)idx * a.nc + g] = T(1.0 / sp);
             }
         }
         return;
     }
 
-    if (BC == BCK_AR) dst1_lines<T>(raw, bufA, bufB, extra, a, tw);
+    if (BC == BCK_AR) dst1_lines<T>(raw, bufA, bufB, a, tw);
     else dct_lines<T>(raw, bufA, bufB, a, tw, OP == OP_ROW_INV);
 
     if (OP == OP_COL_SOLVE) {
-        for (int e = threadIdx.x; e < lines * n; e += blockDim.x) {
-            const int idx = e / lines, l = e - idx * lines;
-            const int g = gline(l);
-            if (g >= 0) raw[(size_t)l * n + idx] *= a.spec[(size_t)idx * a.nc + g];
-        }
+        for (int e = threadIdx.x; e < ln; e += blockDim.x)
+            if (gline(e / n) >= 0) raw[e] *= ex[e];
         __syncthreads();
-        if (BC == BCK_AR) dst1_lines<T>(raw, bufA, bufB, extra, a, tw);
+        if (BC == BCK_AR) dst1_lines<T>(raw, bufA, bufB, a, tw);
         else dct_lines<T>(raw, bufA, bufB, a, tw, true);
-        for (int e = threadIdx.x; e < lines * n; e += blockDim.x) {
+        for (int e = threadIdx.x; e < ln; e += blockDim.x) {
             const int idx = e / lines, l = e - idx * lines;
             const int g = gline(l);
             if (g >= 0) a.out0[(size_t)idx * a.nc + g] = raw[(size_t)l * n + idx];
@@ -520,15 +543,15 @@ __global__ void __launch_bounds__(kThreads) line_kernel(LineArgs<T> a) {
     }
     // ---- row store (ROW_FWD / ROW_INV)
     double part = 0.0;
-    for (int e = threadIdx.x; e < lines * n; e += blockDim.x) {
+    for (int e = threadIdx.x; e < ln; e += blockDim.x) {
         const int l = e / n, idx = e - l * n;
         const int g = gline(l);
         if (g < 0) continue;
         const size_t o = (size_t)g * a.nc + idx;
         T v = raw[e];
-        if (OP == OP_ROW_INV && a.scale) v *= a.scale[o];
+        if (OP == OP_ROW_INV && a.scale) v *= ex[e];
         a.out0[o] = v;
-        if (OP == OP_ROW_INV && a.st) part += (double)a.rvec[o] * (double)v;
+        if (OP == OP_ROW_INV && a.st) part += (double)ex[ln + e] * (double)v;
     }
     if (OP == OP_ROW_INV && a.st) {
         double s;
@@ -556,31 +579,32 @@ FftPlan make_fft_plan(int L) {
 }
 
 template <typename T>
-static size_t line_smem(const LineArgs<T>& a) {
+static size_t line_smem(const LineArgs<T>& a, int op) {
     const size_t lines = 2 * (size_t)a.P;
-    // tw + bufA + bufB + raw + extra (2 * lines * n covers the scan and the E/G outputs)
-    return sizeof(cplx<T>) * ((size_t)a.L + 2 * (size_t)a.P * a.L) + sizeof(T) * (lines * a.n * 3) + 64;
+    // tw + bufA + bufB + raw + the operation's staged factors / outputs
+    return sizeof(cplx<T>) * ((size_t)a.L + 2 * (size_t)a.P * a.L) +
+           sizeof(T) * (lines * a.n + line_extra(op, lines, a.n, a.P)) + 64;
 }
 
 template <typename T>
-static void pick_pairs(LineArgs<T>& a, bool cols) {
+static void pick_pairs(LineArgs<T>& a, bool cols, int op) {
     // columns: 2P contiguous elements per row read, at least one 32-byte sector
     int P = cols ? (int)((32 + 2 * sizeof(T) - 1) / (2 * sizeof(T))) : 1;
     const size_t cap = 160 * 1024;
     for (;;) {
         a.P = P;
-        if (P == 1 || line_smem<T>(a) <= cap) break;
-        --P;
+        if (P == 1 || line_smem<T>(a, op) <= cap) break;
+        P = P / 2;
     }
 }
 
 template <typename T, int BC, int OP>
 static tvd_status launch_line(LineArgs<T> a, cudaStream_t s) {
     const bool cols = (OP == OP_COL_SOLVE || OP == OP_COL_EG);
-    pick_pairs<T>(a, cols);
+    pick_pairs<T>(a, cols, OP);
     const int per_block = (OP == OP_COL_EG) ? a.P : 2 * a.P;
     const int blocks = (a.nlines + per_block - 1) / per_block;
-    const size_t smem = line_smem<T>(a);
+    const size_t smem = line_smem<T>(a, OP);
     if (smem > 227 * 1024) {
         set_error("transform line too long for shared memory");
         return TVD_EINVAL;

@@ -1,20 +1,30 @@
-"""The near-tie rule used to compare FP64 iteration counts with the oracle."""
+"""The rounding-envelope rule used to compare FP64 results with the oracle."""
+import numpy as np
 import pytest
 
-from parity import compare_counts
+from parity import check_counts, count_spread, image_bound, perturb
 
 
-def test_equal_counts_have_no_tie():
-    assert compare_counts([3, 4, 5], [3, 4, 5], [[1e-5, 9e-7]] * 3, 1e-6, 1e-2) is None
+def test_perturbation_is_a_few_ulps():
+    v = np.linspace(0.5, 2.0, 100).reshape(10, 10)
+    d = np.abs(perturb(v, 1) / v - 1.0)
+    assert 0 < d.max() < 1e-14
 
 
-def test_off_by_one_at_a_near_tie_is_accepted():
-    tails = [[2e-6, 5e-7], [1.7e-6, 0.9989e-6], [1.5e-6, 8e-7]]
-    assert compare_counts([3, 50, 7], [3, 49, 8], tails, 1e-6, 1e-2) == 1
+def test_counts_within_spread_plus_one_pass():
+    ref = [10, 20, 30]
+    spread = count_spread(ref, [[10, 21, 30], [10, 20, 29]])
+    assert spread == [0, 1, 1]
+    check_counts([11, 22, 31], ref, spread)
 
 
-@pytest.mark.parametrize("gpu,ref", [([3, 48, 7], [3, 46, 7]), ([3, 50, 7], [3, 49, 7])])
-def test_mismatch_away_from_tol_fails(gpu, ref):
-    tails = [[2e-6, 5e-7], [1.7e-6, 0.5e-6], [1.5e-6, 8e-7]]
+@pytest.mark.parametrize("gpu", [[12, 20, 30], [10, 23, 30]])
+def test_counts_outside_spread_fail(gpu):
     with pytest.raises(AssertionError):
-        compare_counts(gpu, ref, tails, 1e-6, 1e-2)
+        check_counts(gpu, [10, 20, 30], [0, 1, 0])
+
+
+def test_image_bound_scales_with_spread():
+    ref = np.ones((4, 4))
+    assert image_bound(ref, [ref + 1e-9]) == pytest.approx(10 * 1e-9 * 4 / 4, rel=1e-6)
+    assert image_bound(ref, [ref]) == 1e-12
