@@ -154,7 +154,7 @@ blur_tile_kernel(const T* __restrict__ x, T* __restrict__ y, int nr, int nc, int
 #pragma unroll
         for (int q = 0; q < PER; ++q) acc[q] += hv * base[q * BROWS * TW];
     }
-    double part = 0.0;
+    T part = T(0);   // per-thread partial of p^T q in the kernel's type
     const int j = blockIdx.x * BT + tx;
 #pragma unroll
     for (int q = 0; q < PER; ++q) {
@@ -172,14 +172,14 @@ blur_tile_kernel(const T* __restrict__ x, T* __restrict__ y, int nr, int nc, int
             if (i > 0) l += sw[o - LS] * (pc - sp[o - LS]);
             if (j > 0) l += sw[o - 1] * (pc - sp[o - 1]);
             out += T(fa.alpha) * l;
-            part += (double)pc * (double)out;
+            part += pc * out;
         }
         y[(size_t)i * nc + j] = out;
     }
     if (FUSE && fa.reduce) {
         const int slot = fa.slot0 + blockIdx.y * gridDim.x + blockIdx.x;
         double s;
-        if (block_reduce_last(part, fa.red, fa.ticket, slot, fa.total_blocks, &s) && threadIdx.x == 0 &&
+        if (block_reduce_last((double)part, fa.red, fa.ticket, slot, fa.total_blocks, &s) && threadIdx.x == 0 &&
             fa.finish_here)
             finish_pq(fa.st, s);
     }
@@ -204,7 +204,7 @@ ar_adjoint_border_kernel(const T* __restrict__ y, T* __restrict__ out, int nr, i
     const int nrow = nc - 2, ncol = nr - 2;              // interior outputs on each row / column border
     const int total = 2 * nrow + 2 * ncol + 4;
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
-    double part = 0.0;
+    T part = T(0);
     if (t < total) {
         int oi, oj;
         T acc = T(0);
@@ -253,13 +253,13 @@ ar_adjoint_border_kernel(const T* __restrict__ y, T* __restrict__ out, int nr, i
         }
         if (FUSE) {
             acc += T(fa.alpha) * lap_at(w, pv, oi, oj, nr, nc);
-            part = (double)pv[(size_t)oi * nc + oj] * (double)acc;
+            part = pv[(size_t)oi * nc + oj] * acc;
         }
         out[(size_t)oi * nc + oj] = acc;
     }
     if (FUSE && fa.reduce) {
         double s;
-        if (block_reduce_last(part, fa.red, fa.ticket, fa.slot0 + blockIdx.x, fa.total_blocks, &s) &&
+        if (block_reduce_last((double)part, fa.red, fa.ticket, fa.slot0 + blockIdx.x, fa.total_blocks, &s) &&
             threadIdx.x == 0 && fa.finish_here)
             finish_pq(fa.st, s);
     }
@@ -295,18 +295,18 @@ static tvd_status launch_blur(const tvd_plan_s& p, const Ops<T>& o, bool transpo
         fa.finish_here = 1;
         if (p.bc == TVD_BC_ANTIREFLECTIVE) {
             if (fuse) {
-                cudaFuncSetAttribute(blur_tile_kernel<T, EXT_AR, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+                allow_max_smem<blur_tile_kernel<T, EXT_AR, true>>();
                 blur_tile_kernel<T, EXT_AR, true><<<grid, kThreads, smem, s>>>(x, y, nr, nc, mr, mc, o.tap_ab, o.tap_h, o.ntaps, w, pv, fa);
             } else {
-                cudaFuncSetAttribute(blur_tile_kernel<T, EXT_AR, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+                allow_max_smem<blur_tile_kernel<T, EXT_AR, false>>();
                 blur_tile_kernel<T, EXT_AR, false><<<grid, kThreads, smem, s>>>(x, y, nr, nc, mr, mc, o.tap_ab, o.tap_h, o.ntaps, w, pv, fa);
             }
         } else {
             if (fuse) {
-                cudaFuncSetAttribute(blur_tile_kernel<T, EXT_R, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+                allow_max_smem<blur_tile_kernel<T, EXT_R, true>>();
                 blur_tile_kernel<T, EXT_R, true><<<grid, kThreads, smem, s>>>(x, y, nr, nc, mr, mc, o.tap_ab, o.tap_h, o.ntaps, w, pv, fa);
             } else {
-                cudaFuncSetAttribute(blur_tile_kernel<T, EXT_R, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+                allow_max_smem<blur_tile_kernel<T, EXT_R, false>>();
                 blur_tile_kernel<T, EXT_R, false><<<grid, kThreads, smem, s>>>(x, y, nr, nc, mr, mc, o.tap_ab, o.tap_h, o.ntaps, w, pv, fa);
             }
         }
@@ -314,10 +314,10 @@ static tvd_status launch_blur(const tvd_plan_s& p, const Ops<T>& o, bool transpo
         fa.finish_here = 0;
         fa.slot0 = 0;
         if (fuse) {
-            cudaFuncSetAttribute(blur_tile_kernel<T, EXT_ODD, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            allow_max_smem<blur_tile_kernel<T, EXT_ODD, true>>();
             blur_tile_kernel<T, EXT_ODD, true><<<grid, kThreads, smem, s>>>(x, y, nr, nc, mr, mc, o.tap_ab, o.tap_h, o.ntaps, w, pv, fa);
         } else {
-            cudaFuncSetAttribute(blur_tile_kernel<T, EXT_ODD, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            allow_max_smem<blur_tile_kernel<T, EXT_ODD, false>>();
             blur_tile_kernel<T, EXT_ODD, false><<<grid, kThreads, smem, s>>>(x, y, nr, nc, mr, mc, o.tap_ab, o.tap_h, o.ntaps, w, pv, fa);
         }
         fa.finish_here = 1;

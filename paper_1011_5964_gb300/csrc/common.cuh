@@ -75,6 +75,19 @@ __device__ __forceinline__ T lap_at(const T* __restrict__ w, const T* __restrict
     return acc;
 }
 
+// Raise a kernel's dynamic shared-memory limit to the device's opt-in maximum,
+// once per kernel (so no attribute call happens while a graph is captured).
+template <auto Kernel>
+inline cudaError_t allow_max_smem() {
+    static const cudaError_t once = []() {
+        int dev = 0, optin = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+        return cudaFuncSetAttribute(Kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
+    }();
+    return once;
+}
+
 // Asynchronous global -> shared copy of one element (cp.async, 4 or 8 bytes);
 // many such copies stay in flight per thread until cp_async_wait_all().
 template <typename T>

@@ -23,9 +23,12 @@ int num_sms() {
     return n;
 }
 
+// Grid of the vector kernels: about four elements per thread, so that every
+// SM has many independent loads in flight (the kernels are latency bound at
+// L2-resident sizes otherwise).
 static int red_blocks(size_t n) {
-    size_t b = (n + kThreads - 1) / kThreads;
-    size_t cap = (size_t)num_sms() * 4;
+    size_t b = (n + 4 * kThreads - 1) / (4 * kThreads);
+    size_t cap = (size_t)num_sms() * 32;
     if (cap > (size_t)kMaxRedBlocks) cap = kMaxRedBlocks;
     return (int)(b < cap ? (b ? b : 1) : cap);
 }
@@ -36,14 +39,14 @@ template <typename T>
 __global__ void __launch_bounds__(kThreads)
 cg_init_kernel(const T* __restrict__ b, const T* __restrict__ ax, T* __restrict__ r, size_t n, CgState* st,
                double* red, unsigned int* ticket, double tol, int maxit) {
-    double part = 0.0;
+    T part = T(0);   // per-thread partial in the kernel's type; block and grid sums in double
     GRID_STRIDE(o, n) {
         const T v = b[o] - ax[o];
         r[o] = v;
-        part += (double)v * (double)v;
+        part += v * v;
     }
     double s;
-    if (block_reduce_last(part, red, ticket, blockIdx.x, gridDim.x, &s) && threadIdx.x == 0) {
+    if (block_reduce_last((double)part, red, ticket, blockIdx.x, gridDim.x, &s) && threadIdx.x == 0) {
         st->rr0 = s;
         st->rr = s;
         st->tol2 = tol * tol * s;
@@ -81,15 +84,15 @@ cg_xr_kernel(T* __restrict__ x, T* __restrict__ r, const T* __restrict__ p, cons
              CgState* st, double* red, unsigned int* ticket) {
     if (st->done) return;
     const T a = T(st->alpha);
-    double part = 0.0;
+    T part = T(0);
     GRID_STRIDE(o, n) {
         x[o] += a * p[o];
         const T rv = r[o] - a * q[o];
         r[o] = rv;
-        part += (double)rv * (double)rv;
+        part += rv * rv;
     }
     double s;
-    if (block_reduce_last(part, red, ticket, blockIdx.x, gridDim.x, &s) && threadIdx.x == 0) {
+    if (block_reduce_last((double)part, red, ticket, blockIdx.x, gridDim.x, &s) && threadIdx.x == 0) {
         st->rr = s;
         st->iter += 1;
         if (!isfinite(s)) {
@@ -110,15 +113,15 @@ __global__ void __launch_bounds__(kThreads)
 cg_simple_precond_kernel(const T* __restrict__ r, const T* __restrict__ dinv, T* __restrict__ z, size_t n,
                          CgState* st, double* red, unsigned int* ticket) {
     if (st && st->done) return;
-    double part = 0.0;
+    T part = T(0);
     GRID_STRIDE(o, n) {
         const T v = dinv ? r[o] * dinv[o] : r[o];
         if (z != r) z[o] = v;
-        part += (double)r[o] * (double)v;
+        part += r[o] * v;
     }
     if (!st) return;
     double s;
-    if (block_reduce_last(part, red, ticket, blockIdx.x, gridDim.x, &s) && threadIdx.x == 0) {
+    if (block_reduce_last((double)part, red, ticket, blockIdx.x, gridDim.x, &s) && threadIdx.x == 0) {
         st->rho_old = st->rho;
         st->rho = s;
         if (!(isfinite(s) && s > 0.0)) {

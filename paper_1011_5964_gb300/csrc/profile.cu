@@ -12,6 +12,7 @@
 namespace tvd {
 
 static std::atomic<unsigned long long> g_launches{0};
+thread_local int capture_kernels_ = 0;
 static std::atomic<int> g_profile{0};
 
 struct ClassRecord {
@@ -26,11 +27,23 @@ static const char* kNames[PROF_NUM_BASE] = {
     "spectrum_row", "spectrum_column", "cg_init", "cg_p_update", "cg_xr_update", "cg_simple_precond",
     "tv_coefficients", "vector_misc"};
 
-void count_launches(int k) { g_launches.fetch_add((unsigned long long)k, std::memory_order_relaxed); }
+static thread_local bool t_capturing = false;
+
+void set_capturing(bool on) {
+    t_capturing = on;
+    if (on) capture_kernels_ = 0;
+}
+int captured_kernels() { return capture_kernels_; }
+bool profiling_enabled() { return g_profile.load(std::memory_order_relaxed) != 0; }
+
+void count_launches(int k) {
+    if (!t_capturing) g_launches.fetch_add((unsigned long long)k, std::memory_order_relaxed);
+}
 
 ProfScope::ProfScope(int cls, cudaStream_t s, int nkernels) : cls_(cls), s_(s), start_(nullptr) {
     count_launches(nkernels);
-    if (g_profile.load(std::memory_order_relaxed)) {
+    if (t_capturing) capture_kernels_ += nkernels;
+    if (g_profile.load(std::memory_order_relaxed) && !t_capturing) {
         if (cudaEventCreate(&start_) == cudaSuccess) cudaEventRecord(start_, s_);
         else start_ = nullptr;
         std::lock_guard<std::mutex> lk(g_mu);

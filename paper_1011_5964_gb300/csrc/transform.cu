@@ -84,7 +84,7 @@ __device__ __forceinline__ cplx<T> cmul(cplx<T> a, cplx<T> b) {
 // shared twiddle table (tw[t * LR], conjugated for the inverse transform).
 template <typename T, int R>
 __device__ __forceinline__ void dft_store(cplx<T> (&v)[R], cplx<T>* __restrict__ dst, int Ns,
-                                          const cplx<T>* __restrict__ tw, int LR, bool inv) {
+                                          const cplx<T>* __restrict__ tw, int LR, bool inv, int g, int G) {
     if constexpr (R == 2) {
         dst[0] = {v[0].re + v[1].re, v[0].im + v[1].im};
         dst[Ns] = {v[0].re - v[1].re, v[0].im - v[1].im};
@@ -113,15 +113,18 @@ __device__ __forceinline__ void dft_store(cplx<T> (&v)[R], cplx<T>* __restrict__
             v[j] = {a.re + b.re, a.im + b.im};
             v[R - j] = {a.re - b.re, a.im - b.im};
         }
-        cplx<T> o0 = v0;
+        if (g == 0) {
+            cplx<T> o0 = v0;
 #pragma unroll
-        for (int j = 1; j <= H; ++j) { o0.re += v[j].re; o0.im += v[j].im; }
-        if constexpr (even) { o0.re += vh.re; o0.im += vh.im; }
-        dst[0] = o0;
+            for (int j = 1; j <= H; ++j) { o0.re += v[j].re; o0.im += v[j].im; }
+            if constexpr (even) { o0.re += vh.re; o0.im += vh.im; }
+            dst[0] = o0;
+        }
         // the inputs stay in registers; the output loop is rolled for large
-        // radices to keep the register count (and so the occupancy) moderate
+        // radices to keep the register count (and so the occupancy) moderate,
+        // and its output pairs are shared among G threads (this one takes g, g + G, ...)
 #pragma unroll (R <= 8 ? H : 1)
-        for (int k = 1; k <= H; ++k) {
+        for (int k = 1 + g; k <= H; k += G) {
             cplx<T> a = v0, b = {T(0), T(0)};
 #pragma unroll
             for (int j = 1; j <= H; ++j) {
@@ -137,7 +140,7 @@ __device__ __forceinline__ void dft_store(cplx<T> (&v)[R], cplx<T>* __restrict__
             dst[k * Ns] = {a.re - b.im, a.im + b.re};
             dst[(R - k) * Ns] = {a.re + b.im, a.im - b.re};
         }
-        if constexpr (even) {
+        if (even && g == 0) {
             cplx<T> m = v0;
 #pragma unroll
             for (int j = 1; j <= H; ++j) {
@@ -156,7 +159,15 @@ __device__ void fft_stage(const cplx<T>* __restrict__ in, cplx<T>* __restrict__ 
                           const cplx<T>* __restrict__ tw, bool inv) {
     const int LR = L / R;
     const int ts = L / (Ns * R);
-    for (int bf = threadIdx.x; bf < P * LR; bf += blockDim.x) {
+    // large radices: G threads per butterfly so that the stage keeps the block busy
+    constexpr int H = (R - 1) / 2;
+    int G = 1;
+    if (R > 8) {
+        G = ((int)blockDim.x + P * LR - 1) / (P * LR);
+        G = G < 1 ? 1 : (G > H ? H : G);
+    }
+    for (int item = threadIdx.x; item < P * LR * G; item += blockDim.x) {
+        const int bf = item / G, g = item - bf * G;
         const int pp = bf / LR, j = bf - pp * LR;
         const cplx<T>* src = in + (size_t)pp * L;
         const int k = j % Ns;
@@ -168,7 +179,7 @@ __device__ void fft_stage(const cplx<T>* __restrict__ in, cplx<T>* __restrict__ 
             if (inv) w.im = -w.im;
             v[r] = cmul(src[j + r * LR], w);
         }
-        dft_store<T, R>(v, out + (size_t)pp * L + (j / Ns) * Ns * R + k, Ns, tw, LR, inv);
+        dft_store<T, R>(v, out + (size_t)pp * L + (j / Ns) * Ns * R + k, Ns, tw, LR, inv, g, G);
     }
 }
 
@@ -542,7 +553,7 @@ __global__ void __launch_bounds__(kThreads) line_kernel(LineArgs<T> a) {
         return;
     }
     // ---- row store (ROW_FWD / ROW_INV)
-    double part = 0.0;
+    T part = T(0);
     for (int e = threadIdx.x; e < ln; e += blockDim.x) {
         const int l = e / n, idx = e - l * n;
         const int g = gline(l);
@@ -551,11 +562,11 @@ __global__ void __launch_bounds__(kThreads) line_kernel(LineArgs<T> a) {
         T v = raw[e];
         if (OP == OP_ROW_INV && a.scale) v *= ex[e];
         a.out0[o] = v;
-        if (OP == OP_ROW_INV && a.st) part += (double)ex[ln + e] * (double)v;
+        if (OP == OP_ROW_INV && a.st) part += ex[ln + e] * v;
     }
     if (OP == OP_ROW_INV && a.st) {
         double s;
-        if (block_reduce_last(part, a.red, a.ticket, blockIdx.x, gridDim.x, &s) && threadIdx.x == 0)
+        if (block_reduce_last((double)part, a.red, a.ticket, blockIdx.x, gridDim.x, &s) && threadIdx.x == 0)
             finish_rho(a.st, s);
     }
 }
@@ -588,8 +599,15 @@ static size_t line_smem(const LineArgs<T>& a, int op) {
 
 template <typename T>
 static void pick_pairs(LineArgs<T>& a, bool cols, int op) {
-    // columns: 2P contiguous elements per row read, at least one 32-byte sector
-    int P = cols ? (int)((32 + 2 * sizeof(T) - 1) / (2 * sizeof(T))) : 1;
+    // columns: 2P contiguous elements per row read, at least one 32-byte sector;
+    // rows: about 4096 (float) / 2048 (double) line elements per block
+    int P;
+    if (cols) {
+        P = (int)((32 + 2 * sizeof(T) - 1) / (2 * sizeof(T)));
+    } else {
+        P = (int)((sizeof(T) == 4 ? 2048 : 1024) / a.n);
+        P = P < 1 ? 1 : (P > 8 ? 8 : P);
+    }
     const size_t cap = 160 * 1024;
     for (;;) {
         a.P = P;
@@ -613,7 +631,7 @@ static tvd_status launch_line(LineArgs<T> a, cudaStream_t s) {
         set_error("image too large for the reduction buffer");
         return TVD_EINVAL;
     }
-    TVD_CUDA_TRY(cudaFuncSetAttribute(line_kernel<T, BC, OP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    TVD_CUDA_TRY((allow_max_smem<line_kernel<T, BC, OP>>()));
     constexpr int cls = OP == OP_ROW_FWD ? PROF_ROW_FWD : OP == OP_COL_SOLVE ? PROF_COL_SOLVE
                       : OP == OP_ROW_INV ? PROF_ROW_INV : OP == OP_ROW_EG ? PROF_EG_ROW : PROF_EG_COL;
     ProfScope prof(prof_class<T>(cls), s);

@@ -51,8 +51,8 @@ tv_apply_kernel(const T* __restrict__ w, const T* __restrict__ x, T* __restrict_
 }
 
 static int ew_blocks(size_t n) {
-    size_t b = (n + kThreads - 1) / kThreads;
-    const size_t cap = (size_t)num_sms() * 8;
+    size_t b = (n + 4 * kThreads - 1) / (4 * kThreads);
+    const size_t cap = (size_t)num_sms() * 32;
     return (int)(b < cap ? (b ? b : 1) : cap);
 }
 

@@ -121,6 +121,12 @@ static void ops_free(Ops<T>& o) {
 }
 
 static void plan_free(tvd_plan_s* p) {
+    for (auto& g : p->graph) {
+        if (g.exec) cudaGraphExecDestroy(g.exec);
+        g.exec = nullptr;
+    }
+    if (p->cap_stream) cudaStreamDestroy(p->cap_stream);
+    p->cap_stream = nullptr;
     ops_free(p->d);
     ops_free(p->f);
     dfree(p->state); dfree(p->red); dfree(p->ticket); dfree(p->scal);
@@ -236,9 +242,58 @@ static tvd_status precond_step(tvd_plan_s& p, Ops<T>& o, CgState* st, cudaStream
     }
 }
 
+template <typename T>
+static tvd_status enqueue_iteration(tvd_plan_s& p, Ops<T>& o, double alpha, T* x, CgState* st, cudaStream_t s) {
+    TVD_TRY(precond_step<T>(p, o, st, s));
+    TVD_TRY(cg_pupdate<T>(p, o.z, o.p, st, s));
+    TVD_TRY(blur_apply<T>(p, o, false, o.p, o.t, s, st));
+    TVD_TRY(normal_finish<T>(p, o, o.t, o.p, alpha, o.q, st, s));
+    TVD_TRY(cg_xrupdate<T>(p, x, o.r, o.p, o.q, st, s));
+    return TVD_OK;
+}
+
+constexpr int kChunk = 4;   // CG iterations per graph replay
+
+// Capture kChunk iterations into a CUDA graph for this (x, b, alpha). The
+// capture runs on a plan-owned stream; the graph is replayed on the caller's.
+template <typename T>
+static tvd_status ensure_graph(tvd_plan_s& p, Ops<T>& o, double alpha, const T* b, T* x) {
+    auto& g = p.graph[sizeof(T) == 8 ? 1 : 0];
+    if (g.exec && g.x == x && g.b == b && g.alpha == alpha) return TVD_OK;
+    if (g.exec) {
+        cudaGraphExecDestroy(g.exec);
+        g.exec = nullptr;
+    }
+    if (!p.cap_stream) TVD_CUDA_TRY(cudaStreamCreateWithFlags(&p.cap_stream, cudaStreamNonBlocking));
+    TVD_CUDA_TRY(cudaStreamBeginCapture(p.cap_stream, cudaStreamCaptureModeThreadLocal));
+    set_capturing(true);
+    tvd_status st = TVD_OK;
+    for (int c = 0; c < kChunk && st == TVD_OK; ++c) st = enqueue_iteration<T>(p, o, alpha, x, p.state, p.cap_stream);
+    const int kernels = captured_kernels();
+    set_capturing(false);
+    cudaGraph_t graph = nullptr;
+    cudaError_t e = cudaStreamEndCapture(p.cap_stream, &graph);
+    if (st != TVD_OK) {
+        if (graph) cudaGraphDestroy(graph);
+        return st;
+    }
+    TVD_CUDA_TRY(e);
+    e = cudaGraphInstantiate(&g.exec, graph, 0);
+    cudaGraphDestroy(graph);
+    TVD_CUDA_TRY(e);
+    g.x = x;
+    g.b = b;
+    g.alpha = alpha;
+    g.kernels = kernels;
+    return TVD_OK;
+}
+
 // PCG on A x = b with A = H^T H + alpha L(o.w); x is updated in place.
-// The preconditioner must be set up in `o`. Iterations are enqueued in chunks;
-// the kernels of iterations past convergence return at once.
+// The preconditioner must be set up in `o`. Iterations are enqueued in chunks
+// (replays of a captured CUDA graph unless per-kernel profiling is on); the
+// kernels of iterations past convergence return at once. The first batch of
+// chunks covers the previous solve's iteration count, then the host checks
+// the device state after every chunk.
 template <typename T>
 static tvd_status cg_run(tvd_plan_s& p, Ops<T>& o, double alpha, const T* b, T* x, double tol, int maxit,
                          CgState* out, cudaStream_t s) {
@@ -246,19 +301,32 @@ static tvd_status cg_run(tvd_plan_s& p, Ops<T>& o, double alpha, const T* b, T* 
     TVD_TRY(blur_apply<T>(p, o, false, x, o.t, s));
     TVD_TRY(normal_finish<T>(p, o, o.t, x, alpha, o.q, nullptr, s));
     TVD_TRY(cg_init<T>(p, b, o.q, o.r, st, tol, maxit, s));
-    const int chunk = 8;
+    const bool use_graph = !profiling_enabled();
+    if (use_graph) TVD_TRY(ensure_graph<T>(p, o, alpha, b, x));
+    auto& g = p.graph[sizeof(T) == 8 ? 1 : 0];
+    int& hint = p.last_iters[sizeof(T) == 8 ? 1 : 0];
+    int first = std::max(1, (std::min(hint, maxit) - 2) / kChunk);
+    int done_iters = 0;
     for (;;) {
-        for (int c = 0; c < chunk; ++c) {
-            TVD_TRY(precond_step<T>(p, o, st, s));
-            TVD_TRY(cg_pupdate<T>(p, o.z, o.p, st, s));
-            TVD_TRY(blur_apply<T>(p, o, false, o.p, o.t, s, st));
-            TVD_TRY(normal_finish<T>(p, o, o.t, o.p, alpha, o.q, st, s));
-            TVD_TRY(cg_xrupdate<T>(p, x, o.r, o.p, o.q, st, s));
+        for (int c = 0; c < first; ++c) {
+            if (use_graph) {
+                TVD_CUDA_TRY(cudaGraphLaunch(g.exec, s));
+                count_launches(g.kernels);
+            } else {
+                for (int i = 0; i < kChunk; ++i) TVD_TRY(enqueue_iteration<T>(p, o, alpha, x, st, s));
+            }
         }
+        done_iters += first * kChunk;
+        first = 1;
         TVD_TRY(read_state<T>(p, s));
         if (p.hstate->done) break;
+        if (done_iters > maxit + kChunk) {
+            set_error("CG state did not reach done after maxit iterations");
+            return TVD_ECUDA;
+        }
     }
     *out = *p.hstate;
+    hint = out->iter;
     return TVD_OK;
 }
 

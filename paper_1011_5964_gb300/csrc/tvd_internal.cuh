@@ -51,6 +51,11 @@ template <typename T>
 constexpr int prof_class(int base) { return base + (sizeof(T) == 8 ? PROF_NUM_BASE : 0); }
 
 void count_launches(int k);
+bool profiling_enabled();
+// While a CUDA graph is being captured on this thread, launches are not
+// counted (the graph's launches are counted when it is replayed).
+void set_capturing(bool on);
+int captured_kernels();   // kernels launched since set_capturing(true)
 
 // Counts the launches of one launcher call and, when profiling is on, brackets
 // them with CUDA events on the launch stream.
@@ -168,6 +173,17 @@ struct tvd_plan_s {
     double* res = nullptr;              // double residual
     double* xd = nullptr;               // double iterate
     double* tmp = nullptr;              // double scratch
+    // CUDA graph of a chunk of CG iterations, per arithmetic (float / double);
+    // valid for one (x, b, alpha) operand set
+    struct CgGraph {
+        cudaGraphExec_t exec = nullptr;
+        const void* x = nullptr;
+        const void* b = nullptr;
+        double alpha = -1.0;
+        int kernels = 0;
+    } graph[2];
+    cudaStream_t cap_stream = nullptr;  // plan-owned stream used only to capture graphs
+    int last_iters[2] = {0, 0};         // iterations of the previous solve (chunking hint)
     bool precond_ready = false;
     double alpha = 0.0, beta = 0.0;     // parameters of the last setup
 };
