@@ -30,8 +30,9 @@ namespace tvd {
 
 enum { EXT_AR = 0, EXT_R = 1, EXT_ODD = 2 };
 
-constexpr int BT = 32;          // output tile side
-constexpr int BROWS = 8;        // thread rows; each thread computes BT / BROWS outputs
+constexpr int BTW = 32;         // output tile width (one warp across)
+constexpr int RB = 8;           // consecutive output rows per thread (register window)
+constexpr int BTH = RB * (kThreads / 32);   // output tile height: 64 rows
 
 template <typename T, int EXT>
 __device__ __forceinline__ T ext_value(const T* __restrict__ x, int I, int J, int nr, int nc, int mr, int mc) {
@@ -91,21 +92,26 @@ __device__ __forceinline__ void finish_pq(CgState* st, double pq) {
 // Output tile kernel. EXT selects the extension of the input; for EXT_ODD only
 // interior outputs (1..n-2 in both directions) are written. With FUSE, the
 // output is q = conv + alpha L(w) pv and p^T q is reduced.
+// Each thread computes RB consecutive output rows of one column. For every PSF
+// column offset b it walks the rows a of that column's tap range, keeping the
+// RB input values it needs in registers and shifting them by one row per tap,
+// so one shared-memory load feeds RB multiply-adds.
 template <typename T, int EXT, bool FUSE>
 __global__ void __launch_bounds__(kThreads)
 blur_tile_kernel(const T* __restrict__ x, T* __restrict__ y, int nr, int nc, int mr, int mc,
-                 const int* __restrict__ tap_ab, const T* __restrict__ tap_h, int ntaps,
+                 const T* __restrict__ hdense, const int* __restrict__ arange,
                  const T* __restrict__ w, const T* __restrict__ pv, FuseArgs fa) {
     if (fa.st && fa.st->done) return;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    const int TW = BT + 2 * mc, TH = BT + 2 * mr;
-    constexpr int LS = BT + 2;                       // stride of the w / p tiles (1-pixel halo)
+    const int TW = BTW + 2 * mc, TH = BTH + 2 * mr;
+    const int PW = 2 * mc + 1, PH = 2 * mr + 1;
+    constexpr int LSW = BTW + 2, LSH = BTH + 2;      // w / p tiles with a 1-pixel halo
     T* tile = reinterpret_cast<T*>(smem_raw);
     T* sw = tile + TW * TH;                          // FUSE: w tile
-    T* sp = sw + (FUSE ? LS * LS : 0);               // FUSE: p tile
-    T* sh = sp + (FUSE ? LS * LS : 0);
-    int* sab = reinterpret_cast<int*>(sh + ntaps);
-    const int r0 = blockIdx.y * BT - mr, c0 = blockIdx.x * BT - mc;
+    T* sp = sw + (FUSE ? LSW * LSH : 0);             // FUSE: p tile
+    T* sh = sp + (FUSE ? LSW * LSH : 0);             // dense PSF, PH x PW
+    int* sr = reinterpret_cast<int*>(sh + PH * PW);  // per column offset: first and last tap row
+    const int r0 = blockIdx.y * BTH - mr, c0 = blockIdx.x * BTW - mc;
     // stage the extended input tile: a plain asynchronous copy where the tile
     // lies inside the image (away from the boundary lines for EXT_ODD), the
     // BC extension computed on the fly elsewhere
@@ -118,9 +124,9 @@ blur_tile_kernel(const T* __restrict__ x, T* __restrict__ y, int nr, int nc, int
         }
     }
     if (FUSE) {
-        const int i0 = blockIdx.y * BT - 1, j0 = blockIdx.x * BT - 1;
-        for (int idx = threadIdx.x; idx < LS * LS; idx += blockDim.x) {
-            const int li = idx / LS, lj = idx - li * LS;
+        const int i0 = blockIdx.y * BTH - 1, j0 = blockIdx.x * BTW - 1;
+        for (int idx = threadIdx.x; idx < LSW * LSH; idx += blockDim.x) {
+            const int li = idx / LSW, lj = idx - li * LSW;
             const int i = i0 + li, j = j0 + lj;
             if (i >= 0 && i < nr && j >= 0 && j < nc) {
                 cp_async_elem(sw + idx, w + (size_t)i * nc + j);
@@ -128,11 +134,8 @@ blur_tile_kernel(const T* __restrict__ x, T* __restrict__ y, int nr, int nc, int
             }
         }
     }
-    for (int k = threadIdx.x; k < ntaps; k += blockDim.x) {
-        sh[k] = tap_h[k];
-        sab[2 * k] = tap_ab[k];
-        sab[2 * k + 1] = tap_ab[ntaps + k];
-    }
+    for (int k = threadIdx.x; k < PH * PW; k += blockDim.x) sh[k] = hdense[k];
+    for (int k = threadIdx.x; k < 2 * PW; k += blockDim.x) sr[k] = arange[k];
     if (!inside) {
 #pragma unroll 4
         for (int idx = threadIdx.x; idx < TW * TH; idx += blockDim.x) {
@@ -143,33 +146,45 @@ blur_tile_kernel(const T* __restrict__ x, T* __restrict__ y, int nr, int nc, int
     cp_async_wait_all();
     __syncthreads();
     const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
-    constexpr int PER = BT / BROWS;
-    T acc[PER];
+    T acc[RB];
 #pragma unroll
-    for (int q = 0; q < PER; ++q) acc[q] = T(0);
-    for (int k = 0; k < ntaps; ++k) {
-        const T hv = sh[k];
-        const int a = sab[2 * k], b = sab[2 * k + 1];
-        const T* base = tile + (ty + mr - a) * TW + (tx + mc - b);
+    for (int k = 0; k < RB; ++k) acc[k] = T(0);
+    const int row0 = ty * RB + mr;                   // tile row of output row 0 at a = 0
+    for (int b = -mc; b <= mc; ++b) {
+        const int lo = sr[2 * (b + mc)], hi = sr[2 * (b + mc) + 1];
+        if (lo > hi) continue;
+        const T* col = tile + (tx + mc - b);
+        const T* hb = sh + (b + mc);
+        // output k at tap a reads tile row row0 + k - a
+        T win[RB];
 #pragma unroll
-        for (int q = 0; q < PER; ++q) acc[q] += hv * base[q * BROWS * TW];
+        for (int k = 0; k < RB; ++k) win[k] = col[(row0 + k - hi) * TW];
+        for (int a = hi;; --a) {
+            const T hv = hb[(a + mr) * PW];
+#pragma unroll
+            for (int k = 0; k < RB; ++k) acc[k] += hv * win[k];
+            if (a == lo) break;
+#pragma unroll
+            for (int k = 0; k < RB - 1; ++k) win[k] = win[k + 1];
+            win[RB - 1] = col[(row0 + RB - 1 - (a - 1)) * TW];
+        }
     }
     T part = T(0);   // per-thread partial of p^T q in the kernel's type
-    const int j = blockIdx.x * BT + tx;
+    const int j = blockIdx.x * BTW + tx;
 #pragma unroll
-    for (int q = 0; q < PER; ++q) {
-        const int i = blockIdx.y * BT + ty + q * BROWS;
+    for (int k = 0; k < RB; ++k) {
+        const int i = blockIdx.y * BTH + ty * RB + k;
         if (i >= nr || j >= nc) continue;
         if (EXT == EXT_ODD && (i == 0 || i == nr - 1 || j == 0 || j == nc - 1)) continue;
-        T out = acc[q];
+        T out = acc[k];
         if (FUSE) {
             // alpha L(w) p from the staged tiles (5-point stencil, zero Neumann)
-            const int o = (ty + q * BROWS + 1) * LS + (tx + 1);
+            const int o = (ty * RB + k + 1) * LSW + (tx + 1);
             const T pc = sp[o], wc = sw[o];
             T l = T(0);
-            if (i < nr - 1) l += wc * (pc - sp[o + LS]);
+            if (i < nr - 1) l += wc * (pc - sp[o + LSW]);
             if (j < nc - 1) l += wc * (pc - sp[o + 1]);
-            if (i > 0) l += sw[o - LS] * (pc - sp[o - LS]);
+            if (i > 0) l += sw[o - LSW] * (pc - sp[o - LSW]);
             if (j > 0) l += sw[o - 1] * (pc - sp[o - 1]);
             out += T(fa.alpha) * l;
             part += pc * out;
@@ -265,18 +280,18 @@ ar_adjoint_border_kernel(const T* __restrict__ y, T* __restrict__ out, int nr, i
     }
 }
 
-static size_t tile_smem(int mr, int mc, int ntaps, size_t elem, bool fuse) {
-    return (size_t)(BT + 2 * mc) * (BT + 2 * mr) * elem + (fuse ? 2 * (BT + 2) * (BT + 2) * elem : 0) +
-           (size_t)ntaps * (elem + 2 * sizeof(int)) + 16;
+static size_t tile_smem(int mr, int mc, size_t elem, bool fuse) {
+    return (size_t)(BTW + 2 * mc) * (BTH + 2 * mr) * elem + (fuse ? 2 * (BTW + 2) * (BTH + 2) * elem : 0) +
+           (size_t)(2 * mr + 1) * (2 * mc + 1) * elem + 2 * (2 * mc + 1) * sizeof(int) + 16;
 }
 
 template <typename T>
 static tvd_status launch_blur(const tvd_plan_s& p, const Ops<T>& o, bool transpose, const T* x, T* y,
                               const T* w, const T* pv, double alpha, CgState* st, cudaStream_t s) {
     const int nr = p.nr, nc = p.nc, mr = p.psf.mr, mc = p.psf.mc;
-    const dim3 grid((nc + BT - 1) / BT, (nr + BT - 1) / BT);
+    const dim3 grid((nc + BTW - 1) / BTW, (nr + BTH - 1) / BTH);
     const bool fuse = (w != nullptr);
-    const size_t smem = tile_smem(mr, mc, o.ntaps, sizeof(T), fuse);
+    const size_t smem = tile_smem(mr, mc, sizeof(T), fuse);
     FuseArgs fa{alpha, st, p.red, p.ticket + 1, (fuse && st) ? 1 : 0, 0, 0, 0};
     const int tile_blocks = (int)(grid.x * grid.y);
     const int nborder = 2 * (nc - 2) + 2 * (nr - 2) + 4;
@@ -296,18 +311,18 @@ static tvd_status launch_blur(const tvd_plan_s& p, const Ops<T>& o, bool transpo
         if (p.bc == TVD_BC_ANTIREFLECTIVE) {
             if (fuse) {
                 allow_max_smem<blur_tile_kernel<T, EXT_AR, true>>();
-                blur_tile_kernel<T, EXT_AR, true><<<grid, kThreads, smem, s>>>(x, y, nr, nc, mr, mc, o.tap_ab, o.tap_h, o.ntaps, w, pv, fa);
+                blur_tile_kernel<T, EXT_AR, true><<<grid, kThreads, smem, s>>>(x, y, nr, nc, mr, mc, o.hdense, o.arange, w, pv, fa);
             } else {
                 allow_max_smem<blur_tile_kernel<T, EXT_AR, false>>();
-                blur_tile_kernel<T, EXT_AR, false><<<grid, kThreads, smem, s>>>(x, y, nr, nc, mr, mc, o.tap_ab, o.tap_h, o.ntaps, w, pv, fa);
+                blur_tile_kernel<T, EXT_AR, false><<<grid, kThreads, smem, s>>>(x, y, nr, nc, mr, mc, o.hdense, o.arange, w, pv, fa);
             }
         } else {
             if (fuse) {
                 allow_max_smem<blur_tile_kernel<T, EXT_R, true>>();
-                blur_tile_kernel<T, EXT_R, true><<<grid, kThreads, smem, s>>>(x, y, nr, nc, mr, mc, o.tap_ab, o.tap_h, o.ntaps, w, pv, fa);
+                blur_tile_kernel<T, EXT_R, true><<<grid, kThreads, smem, s>>>(x, y, nr, nc, mr, mc, o.hdense, o.arange, w, pv, fa);
             } else {
                 allow_max_smem<blur_tile_kernel<T, EXT_R, false>>();
-                blur_tile_kernel<T, EXT_R, false><<<grid, kThreads, smem, s>>>(x, y, nr, nc, mr, mc, o.tap_ab, o.tap_h, o.ntaps, w, pv, fa);
+                blur_tile_kernel<T, EXT_R, false><<<grid, kThreads, smem, s>>>(x, y, nr, nc, mr, mc, o.hdense, o.arange, w, pv, fa);
             }
         }
     } else {
@@ -315,10 +330,10 @@ static tvd_status launch_blur(const tvd_plan_s& p, const Ops<T>& o, bool transpo
         fa.slot0 = 0;
         if (fuse) {
             allow_max_smem<blur_tile_kernel<T, EXT_ODD, true>>();
-            blur_tile_kernel<T, EXT_ODD, true><<<grid, kThreads, smem, s>>>(x, y, nr, nc, mr, mc, o.tap_ab, o.tap_h, o.ntaps, w, pv, fa);
+            blur_tile_kernel<T, EXT_ODD, true><<<grid, kThreads, smem, s>>>(x, y, nr, nc, mr, mc, o.hdense, o.arange, w, pv, fa);
         } else {
             allow_max_smem<blur_tile_kernel<T, EXT_ODD, false>>();
-            blur_tile_kernel<T, EXT_ODD, false><<<grid, kThreads, smem, s>>>(x, y, nr, nc, mr, mc, o.tap_ab, o.tap_h, o.ntaps, w, pv, fa);
+            blur_tile_kernel<T, EXT_ODD, false><<<grid, kThreads, smem, s>>>(x, y, nr, nc, mr, mc, o.hdense, o.arange, w, pv, fa);
         }
         fa.finish_here = 1;
         fa.slot0 = tile_blocks;

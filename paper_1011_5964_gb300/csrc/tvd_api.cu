@@ -88,15 +88,21 @@ static tvd_status ops_alloc(tvd_plan_s& p, Ops<T>& o, cudaStream_t s) {
     T** arrays[] = {&o.lamH2, &o.inv_spec, &o.w, &o.dmh, &o.dinv, &o.x, &o.r, &o.z, &o.p, &o.q, &o.t, &o.t2};
     for (T** a : arrays) TVD_TRY(dalloc(a, n));
     o.allocated = true;
-    // PSF taps
-    o.ntaps = (int)p.psf.th.size();
-    std::vector<double> ab(2 * (size_t)o.ntaps);
-    for (int k = 0; k < o.ntaps; ++k) {
-        ab[k] = p.psf.ta[k];
-        ab[o.ntaps + k] = p.psf.tb[k];
+    // PSF taps: dense, plus per-column tap-row ranges
+    const int mr = p.psf.mr, mc = p.psf.mc, pw = 2 * mc + 1;
+    std::vector<double> rng(2 * (size_t)pw);
+    for (int b = -mc; b <= mc; ++b) {
+        int lo = mr + 1, hi = -mr - 1;
+        for (int a = -mr; a <= mr; ++a)
+            if (p.psf.h[(size_t)(a + mr) * pw + (b + mc)] != 0.0) {
+                lo = std::min(lo, a);
+                hi = std::max(hi, a);
+            }
+        rng[2 * (b + mc)] = lo;
+        rng[2 * (b + mc) + 1] = hi;
     }
-    TVD_TRY(upload<int>(&o.tap_ab, ab, s));
-    TVD_TRY(upload<T>(&o.tap_h, p.psf.th, s));
+    TVD_TRY(upload<int>(&o.arange, rng, s));
+    TVD_TRY(upload<T>(&o.hdense, p.psf.h, s));
     TVD_TRY(upload<T>(&o.crow, p.psf.crow, s));
     TVD_TRY(upload<T>(&o.ccol, p.psf.ccol, s));
     TVD_TRY(upload<T>(&o.ccor, p.psf.ccor, s));
@@ -113,7 +119,7 @@ static tvd_status ops_alloc(tvd_plan_s& p, Ops<T>& o, cudaStream_t s) {
 
 template <typename T>
 static void ops_free(Ops<T>& o) {
-    dfree(o.tap_ab); dfree(o.tap_h); dfree(o.crow); dfree(o.ccol); dfree(o.ccor);
+    dfree(o.hdense); dfree(o.arange); dfree(o.crow); dfree(o.ccol); dfree(o.ccor);
     dfree(o.tw_c); dfree(o.tw_r); dfree(o.aux_c); dfree(o.aux_r);
     dfree(o.lamH2); dfree(o.inv_spec); dfree(o.w); dfree(o.dmh); dfree(o.dinv);
     dfree(o.x); dfree(o.r); dfree(o.z); dfree(o.p); dfree(o.q); dfree(o.t); dfree(o.t2);

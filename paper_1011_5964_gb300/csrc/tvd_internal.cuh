@@ -113,10 +113,10 @@ constexpr int kMaxRedBlocks = 1 << 17;
 template <typename T>
 struct Ops {
     bool allocated = false;
-    // PSF (trimmed), nonzero taps as (a, b, h) for the direct stencil
-    int ntaps = 0;
-    int* tap_ab = nullptr;   // 2 * ntaps ints: a then b (offsets, -m..m)
-    T* tap_h = nullptr;      // ntaps
+    // PSF (trimmed): dense (2 m_r + 1) x (2 m_c + 1) taps, and for each column
+    // offset b the first and last row offset a with a nonzero tap (lo > hi: none)
+    T* hdense = nullptr;
+    int* arange = nullptr;
     // AR adjoint border tail weights (Sec. 2 folds), sizes in the plan
     T* crow = nullptr;       // (m_r + 1) x (2 m_c + 1)
     T* ccol = nullptr;       // (2 m_r + 1) x (m_c + 1)
