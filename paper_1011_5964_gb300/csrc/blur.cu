@@ -310,18 +310,18 @@ static tvd_status launch_blur(const tvd_plan_s& p, const Ops<T>& o, bool transpo
         fa.finish_here = 1;
         if (p.bc == TVD_BC_ANTIREFLECTIVE) {
             if (fuse) {
-                allow_max_smem<blur_tile_kernel<T, EXT_AR, true>>();
+                TVD_CUDA_TRY((allow_max_smem<blur_tile_kernel<T, EXT_AR, true>>()));
                 blur_tile_kernel<T, EXT_AR, true><<<grid, kThreads, smem, s>>>(x, y, nr, nc, mr, mc, o.hdense, o.arange, w, pv, fa);
             } else {
-                allow_max_smem<blur_tile_kernel<T, EXT_AR, false>>();
+                TVD_CUDA_TRY((allow_max_smem<blur_tile_kernel<T, EXT_AR, false>>()));
                 blur_tile_kernel<T, EXT_AR, false><<<grid, kThreads, smem, s>>>(x, y, nr, nc, mr, mc, o.hdense, o.arange, w, pv, fa);
             }
         } else {
             if (fuse) {
-                allow_max_smem<blur_tile_kernel<T, EXT_R, true>>();
+                TVD_CUDA_TRY((allow_max_smem<blur_tile_kernel<T, EXT_R, true>>()));
                 blur_tile_kernel<T, EXT_R, true><<<grid, kThreads, smem, s>>>(x, y, nr, nc, mr, mc, o.hdense, o.arange, w, pv, fa);
             } else {
-                allow_max_smem<blur_tile_kernel<T, EXT_R, false>>();
+                TVD_CUDA_TRY((allow_max_smem<blur_tile_kernel<T, EXT_R, false>>()));
                 blur_tile_kernel<T, EXT_R, false><<<grid, kThreads, smem, s>>>(x, y, nr, nc, mr, mc, o.hdense, o.arange, w, pv, fa);
             }
         }
@@ -329,10 +329,10 @@ static tvd_status launch_blur(const tvd_plan_s& p, const Ops<T>& o, bool transpo
         fa.finish_here = 0;
         fa.slot0 = 0;
         if (fuse) {
-            allow_max_smem<blur_tile_kernel<T, EXT_ODD, true>>();
+            TVD_CUDA_TRY((allow_max_smem<blur_tile_kernel<T, EXT_ODD, true>>()));
             blur_tile_kernel<T, EXT_ODD, true><<<grid, kThreads, smem, s>>>(x, y, nr, nc, mr, mc, o.hdense, o.arange, w, pv, fa);
         } else {
-            allow_max_smem<blur_tile_kernel<T, EXT_ODD, false>>();
+            TVD_CUDA_TRY((allow_max_smem<blur_tile_kernel<T, EXT_ODD, false>>()));
             blur_tile_kernel<T, EXT_ODD, false><<<grid, kThreads, smem, s>>>(x, y, nr, nc, mr, mc, o.hdense, o.arange, w, pv, fa);
         }
         fa.finish_here = 1;

@@ -107,6 +107,59 @@ cg_xr_kernel(T* __restrict__ x, T* __restrict__ r, const T* __restrict__ p, cons
     }
 }
 
+// (Re)start the CG on the residual already in r (used by the MIXED refinement):
+// rr = ||r||^2, stopping threshold tol2 (absolute). A fresh start also clears
+// the iteration count and the recurrences; a resume after a residual
+// replacement keeps them, so the search direction carries on.
+template <typename T>
+__global__ void __launch_bounds__(kThreads)
+cg_restart_kernel(const T* __restrict__ r, size_t n, CgState* st, double* red, unsigned int* ticket, double tol2,
+                  int maxit, int fresh) {
+    T part = T(0);
+    GRID_STRIDE(o, n) part += r[o] * r[o];
+    double s;
+    if (block_reduce_last((double)part, red, ticket, blockIdx.x, gridDim.x, &s) && threadIdx.x == 0) {
+        if (fresh) {
+            st->iter = 0;
+            st->rho = 0.0;
+            st->rho_old = 0.0;
+            st->beta = 0.0;
+            st->alpha = 0.0;
+            st->pq = 0.0;
+            st->rr0 = s;
+        }
+        st->maxit = maxit;
+        st->rr = s;
+        st->tol2 = tol2;
+        st->status = TVD_OK;
+        st->done = 0;
+        if (!isfinite(s)) {
+            st->status = TVD_EBREAKDOWN;
+            st->done = 1;
+        } else if (s < tol2 || st->iter >= maxit) {
+            st->done = 1;
+        }
+    }
+}
+
+// r = b - hx - alpha L(w) x and ||r||^2 (double): the FP-step residual when
+// hx = H^T H x is already known.
+__global__ void __launch_bounds__(kThreads)
+residual_lx_kernel(const double* __restrict__ b, const double* __restrict__ hx, const double* __restrict__ w,
+                   const double* __restrict__ x, double alpha, double* __restrict__ r, int nr, int nc, double* out,
+                   double* red, unsigned int* ticket) {
+    const size_t n = (size_t)nr * nc;
+    double part = 0.0;
+    GRID_STRIDE(o, n) {
+        const int i = (int)(o / nc), j = (int)(o - (size_t)i * nc);
+        const double v = b[o] - hx[o] - alpha * lap_at(w, x, i, j, nr, nc);
+        r[o] = v;
+        part += v * v;
+    }
+    double s;
+    if (block_reduce_last(part, red, ticket, blockIdx.x, gridDim.x, &s) && threadIdx.x == 0) *out = s;
+}
+
 // z = r (I) or z = r / D (diagonal preconditioner), with r^T z and the beta update.
 template <typename T>
 __global__ void __launch_bounds__(kThreads)
@@ -211,6 +264,26 @@ __global__ void fill_zero_f_kernel(float* __restrict__ a, size_t n) {
     GRID_STRIDE(o, n) a[o] = 0.0f;
 }
 
+template <typename T>
+tvd_status cg_restart(const tvd_plan_s& p, const T* r, CgState* st, double tol2, int maxit, bool fresh,
+                      cudaStream_t s) {
+    const size_t n = (size_t)p.nr * p.nc;
+    ProfScope prof(prof_class<T>(PROF_CG_INIT), s);
+    cg_restart_kernel<T><<<red_blocks(n), kThreads, 0, s>>>(r, n, st, p.red, p.ticket + 6, tol2, maxit, fresh ? 1 : 0);
+    TVD_CUDA_TRY(cudaGetLastError());
+    return TVD_OK;
+}
+
+tvd_status residual_lx(const tvd_plan_s& p, const double* b, const double* hx, const double* w, const double* x,
+                       double alpha, double* r, double* out_norm2, cudaStream_t s) {
+    const size_t n = (size_t)p.nr * p.nc;
+    ProfScope prof(prof_class<double>(PROF_MISC), s);
+    residual_lx_kernel<<<red_blocks(n), kThreads, 0, s>>>(b, hx, w, x, alpha, r, p.nr, p.nc, out_norm2, p.red,
+                                                          p.ticket + 5);
+    TVD_CUDA_TRY(cudaGetLastError());
+    return TVD_OK;
+}
+
 tvd_status residual_d(const tvd_plan_s& p, const double* b, const double* ax, double* r, double* out_norm2,
                       cudaStream_t s) {
     const size_t n = (size_t)p.nr * p.nc;
@@ -268,7 +341,8 @@ tvd_status fill_zero_f(float* a, size_t n, cudaStream_t s) {
     template tvd_status cg_init<T>(const tvd_plan_s&, const T*, const T*, T*, CgState*, double, int, cudaStream_t); \
     template tvd_status cg_pupdate<T>(const tvd_plan_s&, const T*, T*, CgState*, cudaStream_t);                  \
     template tvd_status cg_xrupdate<T>(const tvd_plan_s&, T*, T*, const T*, const T*, CgState*, cudaStream_t);   \
-    template tvd_status cg_simple_precond<T>(const tvd_plan_s&, const T*, const T*, T*, CgState*, cudaStream_t);
+    template tvd_status cg_simple_precond<T>(const tvd_plan_s&, const T*, const T*, T*, CgState*, cudaStream_t); \
+    template tvd_status cg_restart<T>(const tvd_plan_s&, const T*, CgState*, double, int, bool, cudaStream_t);
 INST(float)
 INST(double)
 

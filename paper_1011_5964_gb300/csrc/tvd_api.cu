@@ -400,22 +400,32 @@ struct SolveResult {
     tvd_status status = TVD_OK;
 };
 
-// MIXED: x_{s+1} = x_s + d_s with d_s from float PCG on A d = b - A x_s (the
-// residual in double), until ||b - A x|| / ||b - A x_0|| < tol.
+// MIXED: float PCG with residual replacement ("reliable updates"). The float
+// CG runs on A d = r from d = 0; whenever its recursive residual has fallen by
+// a factor 1e-4 since the last replacement, or claims convergence, the host
+// folds d into the double iterate x, recomputes the residual b - A x in double
+// (H^T H x with the double kernels, cached in p.hx), and the CG resumes from
+// that residual with its search direction kept. The stopping test is on the
+// double residual: ||b - A x|| / ||b - A x_0|| < tol. With cached_hx, p.hx
+// already holds H^T H x for the incoming x (the previous FP step's last check).
 static tvd_status solve_mixed(tvd_plan_s& p, double alpha, const double* b, double* x, double tol, int maxit,
-                              SolveResult* res, cudaStream_t s) {
+                              bool cached_hx, SolveResult* res, cudaStream_t s) {
     const size_t n = (size_t)p.nr * p.nc;
-    double h[2];
-    auto residual = [&](double* out_rr) -> tvd_status {
-        TVD_TRY(blur_apply<double>(p, p.d, false, x, p.d.t, s));
-        TVD_TRY(normal_finish<double>(p, p.d, p.d.t, x, alpha, p.d.q, nullptr, s));
-        TVD_TRY(residual_d(p, b, p.d.q, p.res, p.scal, s));
-        TVD_TRY(read_scalars(p, h, 1, s));
-        *out_rr = h[0];
+    double h1 = 0.0;
+    auto true_residual = [&](bool recompute, double* rr) -> tvd_status {
+        if (recompute) {
+            TVD_TRY(blur_apply<double>(p, p.d, false, x, p.d.t, s));
+            TVD_TRY(blur_apply<double>(p, p.d, true, p.d.t, p.hx, s));
+        }
+        TVD_TRY(residual_lx(p, b, p.hx, p.d.w, x, alpha, p.res, p.scal, s));
+        TVD_TRY(read_scalars(p, &h1, 1, s));
+        *rr = h1;
         return TVD_OK;
     };
+    p.hx_for = nullptr;
     double rr0 = 0.0;
-    TVD_TRY(residual(&rr0));
+    TVD_TRY(true_residual(!cached_hx, &rr0));
+    p.hx_for = x;
     res->iters = 0;
     res->sweeps = 0;
     res->relres = 0.0;
@@ -425,44 +435,66 @@ static tvd_status solve_mixed(tvd_plan_s& p, double alpha, const double* b, doub
         return TVD_OK;
     }
     if (rr0 == 0.0) return TVD_OK;
-    double rr = rr0;
-    const double r0 = std::sqrt(rr0);
-    while (true) {
-        const double rel = std::sqrt(rr) / r0;
-        res->relres = rel;
-        if (rel < tol) break;
-        if (res->iters >= maxit) {
-            res->status = TVD_ENOCONV;
-            break;
+    const double target = tol * tol * rr0;
+    const double delta2 = 1e-8;   // replace once the float residual fell by 1e-4
+    double rr_ref = rr0;
+    res->relres = 1.0;
+    TVD_TRY(cast_d2f(p.res, p.f.r, n, s));
+    TVD_TRY(fill_zero_f(p.f.x, n, s));
+    TVD_TRY(cg_restart<float>(p, p.f.r, p.state, target, maxit, true, s));
+    const bool use_graph = !profiling_enabled();
+    if (use_graph) TVD_TRY(ensure_graph<float>(p, p.f, alpha, nullptr, p.f.x));
+    auto& g = p.graph[0];
+    int& hint = p.last_iters[0];
+    int batch = std::max(1, (std::min(hint, maxit) - 2) / kChunk);
+    int launched = 0;
+    for (;;) {
+        for (int c = 0; c < batch; ++c) {
+            if (use_graph) {
+                TVD_CUDA_TRY(cudaGraphLaunch(g.exec, s));
+                count_launches(g.kernels);
+            } else {
+                for (int i = 0; i < kChunk; ++i) TVD_TRY(enqueue_iteration<float>(p, p.f, alpha, p.f.x, p.state, s));
+            }
         }
-        // float correction solve to the remaining reduction (at most 1e-5 per sweep)
-        const double want = std::max(0.5 * tol / rel, 1e-5);
-        TVD_TRY(cast_d2f(p.res, p.f.t2, n, s));
-        TVD_TRY(fill_zero_f(p.f.x, n, s));
-        CgState cs;
-        TVD_TRY(cg_run<float>(p, p.f, alpha, p.f.t2, p.f.x, std::min(want, 0.5), maxit - res->iters, &cs, s));
-        res->iters += cs.iter;
-        res->sweeps += 1;
-        if (cs.status == TVD_EBREAKDOWN && cs.iter == 0) {
-            res->status = TVD_EBREAKDOWN;
-            break;
+        launched += batch * kChunk;
+        batch = 1;
+        TVD_TRY(read_state<float>(p, s));
+        const CgState h = *p.hstate;
+        res->iters = h.iter;
+        if (!h.done && h.rr >= delta2 * rr_ref) {
+            if (launched > maxit + 2 * kChunk + 64 * kChunk) {
+                set_error("CG state did not reach done after maxit iterations");
+                return TVD_ECUDA;
+            }
+            continue;
         }
+        // fold the float correction into x and check the residual in double
         TVD_TRY(axpy_f2d(x, p.f.x, n, s));
-        TVD_TRY(residual(&rr));
-        if (!std::isfinite(rr)) {
+        TVD_TRY(fill_zero_f(p.f.x, n, s));
+        double rr = 0.0;
+        TVD_TRY(true_residual(true, &rr));
+        res->sweeps += 1;
+        if (!std::isfinite(rr) || h.status == TVD_EBREAKDOWN) {
             res->status = TVD_EBREAKDOWN;
             break;
         }
-        if (res->sweeps > 64) {
+        res->relres = std::sqrt(rr / rr0);
+        if (rr < target) break;
+        if (h.iter >= maxit || res->sweeps > 200) {
             res->status = TVD_ENOCONV;
             break;
         }
+        rr_ref = rr;
+        TVD_TRY(cast_d2f(p.res, p.f.r, n, s));
+        TVD_TRY(cg_restart<float>(p, p.f.r, p.state, target, maxit, false, s));
     }
+    hint = res->iters;
     return TVD_OK;
 }
 
 static tvd_status solve(tvd_plan_s& p, const double* u_lag, double alpha, double beta, const double* b, double* x,
-                        double tol, int maxit, SolveResult* res, cudaStream_t s) {
+                        double tol, int maxit, SolveResult* res, cudaStream_t s, bool cached_hx = false) {
     if (p.mode == TVD_MODE_FP64) {
         TVD_TRY(setup_precond<double>(p, p.d, u_lag, alpha, beta, s));
         CgState cs;
@@ -474,7 +506,7 @@ static tvd_status solve(tvd_plan_s& p, const double* u_lag, double alpha, double
         return TVD_OK;
     }
     TVD_TRY(setup_mixed(p, u_lag, alpha, beta, s));
-    return solve_mixed(p, alpha, b, x, tol, maxit, res, s);
+    return solve_mixed(p, alpha, b, x, tol, maxit, cached_hx && p.hx_for == x, res, s);
 }
 
 }  // namespace tvd
@@ -655,6 +687,7 @@ tvd_status tv_deblur(tvd_plan plan, const void* v, double alpha, double beta, in
     cudaStream_t s = (cudaStream_t)stream;
     const size_t n = (size_t)p.nr * p.nc;
     double* u = (double*)u_out;
+    p.hx_for = nullptr;
     // b = H^T v (into p.xd), u^0 = v
     TVD_TRY(blur_apply<double>(p, p.d, true, (const double*)v, p.xd, s));
     if (u != (const double*)v) TVD_CUDA_TRY(cudaMemcpyAsync(u, v, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
@@ -671,7 +704,8 @@ tvd_status tv_deblur(tvd_plan plan, const void* v, double alpha, double beta, in
         TVD_CUDA_TRY(cudaMemcpyAsync(p.tmp, u, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
         SolveResult r;
         // u_lag = u^k (kept in p.tmp), x starts at u^k and becomes u^{k+1} in place
-        TVD_TRY(solve(p, p.tmp, alpha, beta, p.xd, u, inner_tol, inner_maxit, &r, s));
+        // from the second step on, H^T H u^k is known from the previous step's last residual check
+        TVD_TRY(solve(p, p.tmp, alpha, beta, p.xd, u, inner_tol, inner_maxit, &r, s, k > 0));
         double h2[2];
         TVD_TRY(diffnorm2_d(p, u, p.tmp, p.scal + 2, s));
         TVD_TRY(norm2_d(p, u, p.scal + 3, s));

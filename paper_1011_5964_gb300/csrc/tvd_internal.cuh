@@ -170,6 +170,7 @@ struct tvd_plan_s {
     double* scal = nullptr;             // small double scratch on device
     // double-only arrays for MIXED refinement
     double* hx = nullptr;               // H^T H x in double
+    const double* hx_for = nullptr;     // the x that hx belongs to (nullptr: none)
     double* res = nullptr;              // double residual
     double* xd = nullptr;               // double iterate
     double* tmp = nullptr;              // double scratch
@@ -234,6 +235,12 @@ template <typename T>
 tvd_status cg_xrupdate(const tvd_plan_s& p, T* x, T* r, const T* pv, const T* q, CgState* st, cudaStream_t s);
 template <typename T>
 tvd_status cg_simple_precond(const tvd_plan_s& p, const T* r, const T* dinv, T* z, CgState* st, cudaStream_t s);
+
+template <typename T>
+tvd_status cg_restart(const tvd_plan_s& p, const T* r, CgState* st, double tol2, int maxit, bool fresh,
+                      cudaStream_t s);
+tvd_status residual_lx(const tvd_plan_s& p, const double* b, const double* hx, const double* w, const double* x,
+                       double alpha, double* r, double* out_norm2, cudaStream_t s);
 
 // elementwise helpers
 tvd_status residual_d(const tvd_plan_s& p, const double* b, const double* ax, double* r, double* out_norm2,
