@@ -279,6 +279,14 @@ def run_ours(args):
     sampler.start()
     ms_mixed, st_mixed, launches = timed(mixed, args.steps, args.warmup, u)
     clocks = sampler.stop()
+    if args.only_chosen:
+        # profiler runs: the chosen form's warm-up and timed steps only
+        if rank == 0:
+            print(json.dumps({"metric": METRIC, "value": ws * 1000.0 * args.steps / max_over_ranks(ms_mixed),
+                              "unit": "deblurs/s", "only_chosen": True, "gpu_launches": launches}))
+        mixed.close()
+        plain.close()
+        return
     ms_mixed = max_over_ranks(ms_mixed)
     u_mixed = u.clone()
     iters_mixed = sum(s["total_inner_iters"] for s in st_mixed)
@@ -384,6 +392,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--only-chosen", action="store_true",
+                    help="time the chosen form only (no plain FP64, e2e, per-kernel or CPU legs); for profiler runs")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
         print("warning: fewer than 3 warm-up steps", file=sys.stderr)

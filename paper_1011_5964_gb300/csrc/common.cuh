@@ -48,12 +48,11 @@ __device__ __forceinline__ bool block_reduce_last(double v, double* red, unsigne
     __syncthreads();
     if (!s_last) return false;
     __threadfence();
+    // fixed order: thread t sums slots t, t + blockDim, ... (independent loads
+    // that bypass L1), then the block's fixed reduction tree
     double acc = 0.0;
-    if (threadIdx.x < 32) {
-        // fixed order: lane l sums slots l, l+32, ... in increasing order
-        for (int i = threadIdx.x; i < total; i += 32) acc += ((volatile double*)red)[i];
-        acc = warp_sum(acc);
-    }
+    for (int i = threadIdx.x; i < total; i += blockDim.x) acc += __ldcg(red + i);
+    acc = block_sum(acc);
     if (threadIdx.x == 0) {
         *out = acc;
         *ticket = 0u;

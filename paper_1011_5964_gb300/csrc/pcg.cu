@@ -59,6 +59,7 @@ cg_init_kernel(const T* __restrict__ b, const T* __restrict__ ax, T* __restrict_
         st->pq = 0.0;
         st->status = TVD_OK;
         st->done = 0;
+        st->fresh = 1;
         if (!isfinite(s)) {
             st->status = TVD_EBREAKDOWN;
             st->done = 1;
@@ -73,7 +74,7 @@ template <typename T>
 __global__ void __launch_bounds__(kThreads)
 cg_pupdate_kernel(const T* __restrict__ z, T* __restrict__ p, size_t n, const CgState* st) {
     if (st->done) return;
-    const bool first = st->iter == 0;
+    const bool first = st->fresh != 0;
     const T beta = T(st->beta);
     GRID_STRIDE(o, n) p[o] = first ? z[o] : z[o] + beta * p[o];
 }
@@ -95,6 +96,7 @@ cg_xr_kernel(T* __restrict__ x, T* __restrict__ r, const T* __restrict__ p, cons
     if (block_reduce_last((double)part, red, ticket, blockIdx.x, gridDim.x, &s) && threadIdx.x == 0) {
         st->rr = s;
         st->iter += 1;
+        st->fresh = 0;
         if (!isfinite(s)) {
             st->status = TVD_EBREAKDOWN;
             st->done = 1;
@@ -114,12 +116,13 @@ cg_xr_kernel(T* __restrict__ x, T* __restrict__ r, const T* __restrict__ p, cons
 template <typename T>
 __global__ void __launch_bounds__(kThreads)
 cg_restart_kernel(const T* __restrict__ r, size_t n, CgState* st, double* red, unsigned int* ticket, double tol2,
-                  int maxit, int fresh) {
+                  int maxit, int mode) {
     T part = T(0);
     GRID_STRIDE(o, n) part += r[o] * r[o];
     double s;
     if (block_reduce_last((double)part, red, ticket, blockIdx.x, gridDim.x, &s) && threadIdx.x == 0) {
-        if (fresh) {
+        st->fresh = mode != 1;
+        if (mode == 0) {
             st->iter = 0;
             st->rho = 0.0;
             st->rho_old = 0.0;
@@ -182,7 +185,7 @@ cg_simple_precond_kernel(const T* __restrict__ r, const T* __restrict__ dinv, T*
             st->done = 1;
             st->beta = 0.0;
         } else {
-            st->beta = st->iter == 0 ? 0.0 : s / st->rho_old;
+            st->beta = st->fresh ? 0.0 : s / st->rho_old;
         }
     }
 }
@@ -265,11 +268,11 @@ __global__ void fill_zero_f_kernel(float* __restrict__ a, size_t n) {
 }
 
 template <typename T>
-tvd_status cg_restart(const tvd_plan_s& p, const T* r, CgState* st, double tol2, int maxit, bool fresh,
+tvd_status cg_restart(const tvd_plan_s& p, const T* r, CgState* st, double tol2, int maxit, int mode,
                       cudaStream_t s) {
     const size_t n = (size_t)p.nr * p.nc;
     ProfScope prof(prof_class<T>(PROF_CG_INIT), s);
-    cg_restart_kernel<T><<<red_blocks(n), kThreads, 0, s>>>(r, n, st, p.red, p.ticket + 6, tol2, maxit, fresh ? 1 : 0);
+    cg_restart_kernel<T><<<red_blocks(n), kThreads, 0, s>>>(r, n, st, p.red, p.ticket + 6, tol2, maxit, mode);
     TVD_CUDA_TRY(cudaGetLastError());
     return TVD_OK;
 }
@@ -342,7 +345,7 @@ tvd_status fill_zero_f(float* a, size_t n, cudaStream_t s) {
     template tvd_status cg_pupdate<T>(const tvd_plan_s&, const T*, T*, CgState*, cudaStream_t);                  \
     template tvd_status cg_xrupdate<T>(const tvd_plan_s&, T*, T*, const T*, const T*, CgState*, cudaStream_t);   \
     template tvd_status cg_simple_precond<T>(const tvd_plan_s&, const T*, const T*, T*, CgState*, cudaStream_t); \
-    template tvd_status cg_restart<T>(const tvd_plan_s&, const T*, CgState*, double, int, bool, cudaStream_t);
+    template tvd_status cg_restart<T>(const tvd_plan_s&, const T*, CgState*, double, int, int, cudaStream_t);
 INST(float)
 INST(double)
 

@@ -432,7 +432,7 @@ __device__ __forceinline__ void finish_rho(CgState* st, double rho) {
         st->beta = 0.0;
         return;
     }
-    st->beta = st->iter == 0 ? 0.0 : rho / st->rho_old;
+    st->beta = st->fresh ? 0.0 : rho / st->rho_old;
 }
 
 // Extra shared memory (elements of T) each operation stages next to the lines:

@@ -326,7 +326,7 @@ static tvd_status cg_run(tvd_plan_s& p, Ops<T>& o, double alpha, const T* b, T* 
         first = 1;
         TVD_TRY(read_state<T>(p, s));
         if (p.hstate->done) break;
-        if (done_iters > maxit + kChunk) {
+        if (done_iters > maxit + 2 * kChunk) {   // the kernels always advance a running solve
             set_error("CG state did not reach done after maxit iterations");
             return TVD_ECUDA;
         }
@@ -441,13 +441,13 @@ static tvd_status solve_mixed(tvd_plan_s& p, double alpha, const double* b, doub
     res->relres = 1.0;
     TVD_TRY(cast_d2f(p.res, p.f.r, n, s));
     TVD_TRY(fill_zero_f(p.f.x, n, s));
-    TVD_TRY(cg_restart<float>(p, p.f.r, p.state, target, maxit, true, s));
+    TVD_TRY(cg_restart<float>(p, p.f.r, p.state, target, maxit, 0, s));
     const bool use_graph = !profiling_enabled();
     if (use_graph) TVD_TRY(ensure_graph<float>(p, p.f, alpha, nullptr, p.f.x));
     auto& g = p.graph[0];
     int& hint = p.last_iters[0];
     int batch = std::max(1, (std::min(hint, maxit) - 2) / kChunk);
-    int launched = 0;
+    int last_iter = -1;
     for (;;) {
         for (int c = 0; c < batch; ++c) {
             if (use_graph) {
@@ -457,18 +457,19 @@ static tvd_status solve_mixed(tvd_plan_s& p, double alpha, const double* b, doub
                 for (int i = 0; i < kChunk; ++i) TVD_TRY(enqueue_iteration<float>(p, p.f, alpha, p.f.x, p.state, s));
             }
         }
-        launched += batch * kChunk;
         batch = 1;
         TVD_TRY(read_state<float>(p, s));
         const CgState h = *p.hstate;
         res->iters = h.iter;
         if (!h.done && h.rr >= delta2 * rr_ref) {
-            if (launched > maxit + 2 * kChunk + 64 * kChunk) {
-                set_error("CG state did not reach done after maxit iterations");
+            if (h.iter == last_iter) {   // the kernels always advance a running solve
+                set_error("CG made no progress between two checks");
                 return TVD_ECUDA;
             }
+            last_iter = h.iter;
             continue;
         }
+        last_iter = -1;
         // fold the float correction into x and check the residual in double
         TVD_TRY(axpy_f2d(x, p.f.x, n, s));
         TVD_TRY(fill_zero_f(p.f.x, n, s));
@@ -485,9 +486,12 @@ static tvd_status solve_mixed(tvd_plan_s& p, double alpha, const double* b, doub
             res->status = TVD_ENOCONV;
             break;
         }
+        // keep the search direction only while the float recursion still tracks
+        // the true residual; a larger gap (float operator error) restarts it
+        const int mode = (rr < 4.0 * h.rr) ? 1 : 2;
         rr_ref = rr;
         TVD_TRY(cast_d2f(p.res, p.f.r, n, s));
-        TVD_TRY(cg_restart<float>(p, p.f.r, p.state, target, maxit, false, s));
+        TVD_TRY(cg_restart<float>(p, p.f.r, p.state, target, maxit, mode, s));
     }
     hint = res->iters;
     return TVD_OK;

@@ -103,6 +103,7 @@ struct CgState {
     int maxit;
     int done;          // 1 once converged / stopped
     int status;        // tvd_status reached inside the loop
+    int fresh;         // 1: the next search direction is p = z (start or restart)
 };
 
 // Reduction slots: each reduction writes one double per block, then the last
@@ -236,8 +237,11 @@ tvd_status cg_xrupdate(const tvd_plan_s& p, T* x, T* r, const T* pv, const T* q,
 template <typename T>
 tvd_status cg_simple_precond(const tvd_plan_s& p, const T* r, const T* dinv, T* z, CgState* st, cudaStream_t s);
 
+// mode 0: fresh start (iteration count and recurrences cleared); 1: resume
+// after a residual replacement keeping the search direction; 2: resume with a
+// new search direction p = z (iteration count kept).
 template <typename T>
-tvd_status cg_restart(const tvd_plan_s& p, const T* r, CgState* st, double tol2, int maxit, bool fresh,
+tvd_status cg_restart(const tvd_plan_s& p, const T* r, CgState* st, double tol2, int maxit, int mode,
                       cudaStream_t s);
 tvd_status residual_lx(const tvd_plan_s& p, const double* b, const double* hx, const double* w, const double* x,
                        double alpha, double* r, double* out_norm2, cudaStream_t s);
