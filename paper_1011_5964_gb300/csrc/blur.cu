@@ -34,8 +34,23 @@ constexpr int BTW = 32;         // output tile width (one warp across)
 constexpr int RB = 8;           // consecutive output rows per thread (register window)
 constexpr int BTH = RB * (kThreads / 32);   // output tile height: 64 rows
 
-template <typename T, int EXT>
-__device__ __forceinline__ T ext_value(const T* __restrict__ x, int I, int J, int nr, int nc, int mr, int mc) {
+// Reads the image to be extended: x itself, or the new CG direction
+// z + beta p_old (z alone on a fresh start) when the blur is fused with the
+// direction update.
+template <typename T, bool PUP>
+struct Src {
+    const T* __restrict__ x;     // x, or z
+    const T* __restrict__ pold;
+    T beta;
+    bool fresh;
+    __device__ __forceinline__ T operator[](size_t i) const {
+        if (!PUP) return x[i];
+        return fresh ? x[i] : x[i] + beta * pold[i];
+    }
+};
+
+template <typename T, int EXT, typename S>
+__device__ __forceinline__ T ext_value(const S& x, int I, int J, int nr, int nc, int mr, int mc) {
     if (I < -mr || I >= nr + mr || J < -mc || J >= nc + mc) return T(0);
     if (EXT == EXT_R) {
         int ri = I < 0 ? -I - 1 : (I >= nr ? 2 * nr - 1 - I : I);
@@ -96,18 +111,25 @@ __device__ __forceinline__ void finish_pq(CgState* st, double pq) {
 // column offset b it walks the rows a of that column's tap range, keeping the
 // RB input values it needs in registers and shifting them by one row per tap,
 // so one shared-memory load feeds RB multiply-adds.
-template <typename T, int EXT, bool FUSE>
+template <typename T, int EXT, bool FUSE, bool PUP>
 __global__ void __launch_bounds__(kThreads)
 blur_tile_kernel(const T* __restrict__ x, T* __restrict__ y, int nr, int nc, int mr, int mc,
                  const T* __restrict__ hdense, const int* __restrict__ arange,
-                 const T* __restrict__ w, const T* __restrict__ pv, FuseArgs fa) {
+                 const T* __restrict__ w, T* p0, T* p1, FuseArgs fa) {
     if (fa.st && fa.st->done) return;
+    // FUSE: the direction of this iteration; PUP: old and new direction buffers
+    const int pb = fa.st ? fa.st->pbuf : 0;
+    const T* pv = fa.st ? (pb ? p0 : p1) : p0;
+    const T* pold = pb ? p1 : p0;
+    T* pnew = pb ? p0 : p1;
+    const Src<T, PUP> src{x, pold, PUP ? T(fa.st->beta) : T(0), PUP ? fa.st->fresh != 0 : true};
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int TW = BTW + 2 * mc, TH = BTH + 2 * mr;
     const int PW = 2 * mc + 1, PH = 2 * mr + 1;
     constexpr int LSW = BTW + 2, LSH = BTH + 2;      // w / p tiles with a 1-pixel halo
     T* tile = reinterpret_cast<T*>(smem_raw);
-    T* sw = tile + TW * TH;                          // FUSE: w tile
+    T* ptile = tile + TW * TH;                       // PUP: p_old tile (inside tiles)
+    T* sw = ptile + (PUP ? TW * TH : 0);             // FUSE: w tile
     T* sp = sw + (FUSE ? LSW * LSH : 0);             // FUSE: p tile
     T* sh = sp + (FUSE ? LSW * LSH : 0);             // dense PSF, PH x PW
     int* sr = reinterpret_cast<int*>(sh + PH * PW);  // per column offset: first and last tap row
@@ -120,7 +142,9 @@ blur_tile_kernel(const T* __restrict__ x, T* __restrict__ y, int nr, int nc, int
     if (inside) {
         for (int idx = threadIdx.x; idx < TW * TH; idx += blockDim.x) {
             const int li = idx / TW, lj = idx - li * TW;
-            cp_async_elem(tile + idx, x + (size_t)(r0 + li) * nc + (c0 + lj));
+            const size_t o = (size_t)(r0 + li) * nc + (c0 + lj);
+            cp_async_elem(tile + idx, x + o);
+            if (PUP && !src.fresh) cp_async_elem(ptile + idx, pold + o);
         }
     }
     if (FUSE) {
@@ -140,11 +164,23 @@ blur_tile_kernel(const T* __restrict__ x, T* __restrict__ y, int nr, int nc, int
 #pragma unroll 4
         for (int idx = threadIdx.x; idx < TW * TH; idx += blockDim.x) {
             const int li = idx / TW, lj = idx - li * TW;
-            tile[idx] = ext_value<T, EXT>(x, r0 + li, c0 + lj, nr, nc, mr, mc);
+            tile[idx] = ext_value<T, EXT>(src, r0 + li, c0 + lj, nr, nc, mr, mc);
         }
     }
     cp_async_wait_all();
     __syncthreads();
+    if (PUP && inside && !src.fresh) {
+        for (int idx = threadIdx.x; idx < TW * TH; idx += blockDim.x) tile[idx] += src.beta * ptile[idx];
+        __syncthreads();
+    }
+    if (PUP) {
+        // this block's outputs of the new direction (plain values: inside the image)
+        for (int idx = threadIdx.x; idx < BTW * BTH; idx += blockDim.x) {
+            const int li = idx / BTW, lj = idx - li * BTW;
+            const int i = blockIdx.y * BTH + li, j = blockIdx.x * BTW + lj;
+            if (i < nr && j < nc) pnew[(size_t)i * nc + j] = tile[(li + mr) * TW + (lj + mc)];
+        }
+    }
     const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
     T acc[RB];
 #pragma unroll
@@ -214,8 +250,9 @@ template <typename T, bool FUSE>
 __global__ void __launch_bounds__(kThreads)
 ar_adjoint_border_kernel(const T* __restrict__ y, T* __restrict__ out, int nr, int nc, int mr, int mc,
                          const T* __restrict__ crow, const T* __restrict__ ccol, const T* __restrict__ ccor,
-                         const T* __restrict__ w, const T* __restrict__ pv, FuseArgs fa) {
+                         const T* __restrict__ w, const T* p0, const T* p1, FuseArgs fa) {
     if (fa.st && fa.st->done) return;
+    const T* pv = fa.st ? (fa.st->pbuf ? p0 : p1) : p0;
     const int nrow = nc - 2, ncol = nr - 2;              // interior outputs on each row / column border
     const int total = 2 * nrow + 2 * ncol + 4;
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
@@ -280,18 +317,32 @@ ar_adjoint_border_kernel(const T* __restrict__ y, T* __restrict__ out, int nr, i
     }
 }
 
-static size_t tile_smem(int mr, int mc, size_t elem, bool fuse) {
-    return (size_t)(BTW + 2 * mc) * (BTH + 2 * mr) * elem + (fuse ? 2 * (BTW + 2) * (BTH + 2) * elem : 0) +
+static size_t tile_smem(int mr, int mc, size_t elem, bool fuse, bool pup) {
+    const size_t tile = (size_t)(BTW + 2 * mc) * (BTH + 2 * mr) * elem;
+    return tile * (pup ? 2 : 1) + (fuse ? 2 * (BTW + 2) * (BTH + 2) * elem : 0) +
            (size_t)(2 * mr + 1) * (2 * mc + 1) * elem + 2 * (2 * mc + 1) * sizeof(int) + 16;
 }
 
+enum BlurMode { BLUR_PLAIN = 0, BLUR_PUP = 1, BLUR_FUSE = 2 };
+
+template <typename T, int EXT, bool FUSE, bool PUP>
+static tvd_status launch_tile(dim3 grid, size_t smem, cudaStream_t s, const T* x, T* y, const tvd_plan_s& p,
+                              const Ops<T>& o, const T* w, T* p0, T* p1, const FuseArgs& fa) {
+    TVD_CUDA_TRY((allow_max_smem<blur_tile_kernel<T, EXT, FUSE, PUP>>()));
+    blur_tile_kernel<T, EXT, FUSE, PUP><<<grid, kThreads, smem, s>>>(x, y, p.nr, p.nc, p.psf.mr, p.psf.mc, o.hdense,
+                                                                    o.arange, w, p0, p1, fa);
+    return TVD_OK;
+}
+
+// mode BLUR_PLAIN: y = H x or H^T x. BLUR_PUP: forward blur of the new CG
+// direction (x = z). BLUR_FUSE: y = H^T x + alpha L(w) p and p^T q.
 template <typename T>
-static tvd_status launch_blur(const tvd_plan_s& p, const Ops<T>& o, bool transpose, const T* x, T* y,
-                              const T* w, const T* pv, double alpha, CgState* st, cudaStream_t s) {
+static tvd_status launch_blur(const tvd_plan_s& p, const Ops<T>& o, bool transpose, int mode, const T* x, T* y,
+                              const T* w, T* p0, T* p1, double alpha, CgState* st, cudaStream_t s) {
     const int nr = p.nr, nc = p.nc, mr = p.psf.mr, mc = p.psf.mc;
     const dim3 grid((nc + BTW - 1) / BTW, (nr + BTH - 1) / BTH);
-    const bool fuse = (w != nullptr);
-    const size_t smem = tile_smem(mr, mc, sizeof(T), fuse);
+    const bool fuse = mode == BLUR_FUSE, pup = mode == BLUR_PUP;
+    const size_t smem = tile_smem(mr, mc, sizeof(T), fuse, pup);
     FuseArgs fa{alpha, st, p.red, p.ticket + 1, (fuse && st) ? 1 : 0, 0, 0, 0};
     const int tile_blocks = (int)(grid.x * grid.y);
     const int nborder = 2 * (nc - 2) + 2 * (nr - 2) + 4;
@@ -305,42 +356,32 @@ static tvd_status launch_blur(const tvd_plan_s& p, const Ops<T>& o, bool transpo
             return TVD_EINVAL;
         }
     }
-    if (!ar_adj) {
-        // forward H for both BCs, and H^T = H for reflective BCs
-        fa.finish_here = 1;
+    if (!transpose) {
         if (p.bc == TVD_BC_ANTIREFLECTIVE) {
-            if (fuse) {
-                TVD_CUDA_TRY((allow_max_smem<blur_tile_kernel<T, EXT_AR, true>>()));
-                blur_tile_kernel<T, EXT_AR, true><<<grid, kThreads, smem, s>>>(x, y, nr, nc, mr, mc, o.hdense, o.arange, w, pv, fa);
-            } else {
-                TVD_CUDA_TRY((allow_max_smem<blur_tile_kernel<T, EXT_AR, false>>()));
-                blur_tile_kernel<T, EXT_AR, false><<<grid, kThreads, smem, s>>>(x, y, nr, nc, mr, mc, o.hdense, o.arange, w, pv, fa);
-            }
+            if (pup) TVD_TRY((launch_tile<T, EXT_AR, false, true>(grid, smem, s, x, y, p, o, w, p0, p1, fa)));
+            else TVD_TRY((launch_tile<T, EXT_AR, false, false>(grid, smem, s, x, y, p, o, w, p0, p1, fa)));
         } else {
-            if (fuse) {
-                TVD_CUDA_TRY((allow_max_smem<blur_tile_kernel<T, EXT_R, true>>()));
-                blur_tile_kernel<T, EXT_R, true><<<grid, kThreads, smem, s>>>(x, y, nr, nc, mr, mc, o.hdense, o.arange, w, pv, fa);
-            } else {
-                TVD_CUDA_TRY((allow_max_smem<blur_tile_kernel<T, EXT_R, false>>()));
-                blur_tile_kernel<T, EXT_R, false><<<grid, kThreads, smem, s>>>(x, y, nr, nc, mr, mc, o.hdense, o.arange, w, pv, fa);
-            }
+            if (pup) TVD_TRY((launch_tile<T, EXT_R, false, true>(grid, smem, s, x, y, p, o, w, p0, p1, fa)));
+            else TVD_TRY((launch_tile<T, EXT_R, false, false>(grid, smem, s, x, y, p, o, w, p0, p1, fa)));
         }
+    } else if (!ar_adj) {
+        // H^T = H for reflective BCs
+        fa.finish_here = 1;
+        if (fuse) TVD_TRY((launch_tile<T, EXT_R, true, false>(grid, smem, s, x, y, p, o, w, p0, p1, fa)));
+        else TVD_TRY((launch_tile<T, EXT_R, false, false>(grid, smem, s, x, y, p, o, w, p0, p1, fa)));
     } else {
         fa.finish_here = 0;
         fa.slot0 = 0;
-        if (fuse) {
-            TVD_CUDA_TRY((allow_max_smem<blur_tile_kernel<T, EXT_ODD, true>>()));
-            blur_tile_kernel<T, EXT_ODD, true><<<grid, kThreads, smem, s>>>(x, y, nr, nc, mr, mc, o.hdense, o.arange, w, pv, fa);
-        } else {
-            TVD_CUDA_TRY((allow_max_smem<blur_tile_kernel<T, EXT_ODD, false>>()));
-            blur_tile_kernel<T, EXT_ODD, false><<<grid, kThreads, smem, s>>>(x, y, nr, nc, mr, mc, o.hdense, o.arange, w, pv, fa);
-        }
+        if (fuse) TVD_TRY((launch_tile<T, EXT_ODD, true, false>(grid, smem, s, x, y, p, o, w, p0, p1, fa)));
+        else TVD_TRY((launch_tile<T, EXT_ODD, false, false>(grid, smem, s, x, y, p, o, w, p0, p1, fa)));
         fa.finish_here = 1;
         fa.slot0 = tile_blocks;
         if (fuse)
-            ar_adjoint_border_kernel<T, true><<<border_blocks, kThreads, 0, s>>>(x, y, nr, nc, mr, mc, o.crow, o.ccol, o.ccor, w, pv, fa);
+            ar_adjoint_border_kernel<T, true><<<border_blocks, kThreads, 0, s>>>(x, y, nr, nc, mr, mc, o.crow, o.ccol,
+                                                                              o.ccor, w, p0, p1, fa);
         else
-            ar_adjoint_border_kernel<T, false><<<border_blocks, kThreads, 0, s>>>(x, y, nr, nc, mr, mc, o.crow, o.ccol, o.ccor, w, pv, fa);
+            ar_adjoint_border_kernel<T, false><<<border_blocks, kThreads, 0, s>>>(x, y, nr, nc, mr, mc, o.crow, o.ccol,
+                                                                               o.ccor, w, p0, p1, fa);
     }
     TVD_CUDA_TRY(cudaGetLastError());
     return TVD_OK;
@@ -349,22 +390,28 @@ static tvd_status launch_blur(const tvd_plan_s& p, const Ops<T>& o, bool transpo
 template <typename T>
 tvd_status blur_apply(const tvd_plan_s& p, const Ops<T>& o, bool transpose, const T* x, T* y, cudaStream_t s,
                       CgState* st) {
-    return launch_blur<T>(p, o, transpose, x, y, nullptr, nullptr, 0.0, st, s);
+    return launch_blur<T>(p, o, transpose, BLUR_PLAIN, x, y, nullptr, nullptr, nullptr, 0.0, st, s);
 }
 
 template <typename T>
-tvd_status normal_finish(const tvd_plan_s& p, const Ops<T>& o, const T* t, const T* pv, double alpha, T* q,
-                         CgState* st, cudaStream_t s) {
-    return launch_blur<T>(p, o, true, t, q, o.w, pv, alpha, st, s);
+tvd_status blur_pupdate(const tvd_plan_s& p, const Ops<T>& o, const T* z, T* p0, T* p1, T* t, CgState* st,
+                        cudaStream_t s) {
+    return launch_blur<T>(p, o, false, BLUR_PUP, z, t, nullptr, p0, p1, 0.0, st, s);
 }
 
-template tvd_status blur_apply<float>(const tvd_plan_s&, const Ops<float>&, bool, const float*, float*, cudaStream_t,
-                                      CgState*);
-template tvd_status blur_apply<double>(const tvd_plan_s&, const Ops<double>&, bool, const double*, double*,
-                                       cudaStream_t, CgState*);
-template tvd_status normal_finish<float>(const tvd_plan_s&, const Ops<float>&, const float*, const float*, double,
-                                         float*, CgState*, cudaStream_t);
-template tvd_status normal_finish<double>(const tvd_plan_s&, const Ops<double>&, const double*, const double*, double,
-                                          double*, CgState*, cudaStream_t);
+template <typename T>
+tvd_status normal_finish(const tvd_plan_s& p, const Ops<T>& o, const T* t, const T* p0, const T* p1, double alpha,
+                         T* q, CgState* st, cudaStream_t s) {
+    return launch_blur<T>(p, o, true, BLUR_FUSE, t, q, o.w, const_cast<T*>(p0), const_cast<T*>(p1), alpha, st, s);
+}
+
+#define INST(T)                                                                                                  \
+    template tvd_status blur_apply<T>(const tvd_plan_s&, const Ops<T>&, bool, const T*, T*, cudaStream_t, CgState*); \
+    template tvd_status blur_pupdate<T>(const tvd_plan_s&, const Ops<T>&, const T*, T*, T*, T*, CgState*,       \
+                                        cudaStream_t);                                                           \
+    template tvd_status normal_finish<T>(const tvd_plan_s&, const Ops<T>&, const T*, const T*, const T*, double, \
+                                         T*, CgState*, cudaStream_t);
+INST(float)
+INST(double)
 
 }  // namespace tvd

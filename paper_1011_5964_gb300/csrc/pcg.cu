@@ -35,6 +35,31 @@ static int red_blocks(size_t n) {
 
 #define GRID_STRIDE(o, n) for (size_t o = blockIdx.x * (size_t)blockDim.x + threadIdx.x; o < (n); o += (size_t)gridDim.x * blockDim.x)
 
+// 16-byte vectors: float4 / double2. The vector kernels process one vector per
+// thread (all loads of a thread in flight together) and a scalar tail.
+template <typename T> struct Vec16;
+template <> struct Vec16<float> { using type = float4; static constexpr int N = 4; };
+template <> struct Vec16<double> { using type = double2; static constexpr int N = 2; };
+
+template <typename T>
+__device__ __forceinline__ typename Vec16<T>::type vload(const T* p, size_t i) {
+    return reinterpret_cast<const typename Vec16<T>::type*>(p)[i];
+}
+template <typename T>
+__device__ __forceinline__ void vstore(T* p, size_t i, const typename Vec16<T>::type& v) {
+    reinterpret_cast<typename Vec16<T>::type*>(p)[i] = v;
+}
+template <typename T>
+__device__ __forceinline__ T* el(typename Vec16<T>::type& v) { return reinterpret_cast<T*>(&v); }
+
+static bool aligned16(const void* p) { return ((uintptr_t)p & 15u) == 0; }
+
+static int vec_blocks(size_t n, int vec) {
+    size_t b = (n / vec + kThreads - 1) / kThreads;
+    if (b > (size_t)kMaxRedBlocks) b = kMaxRedBlocks;
+    return (int)(b ? b : 1);
+}
+
 template <typename T>
 __global__ void __launch_bounds__(kThreads)
 cg_init_kernel(const T* __restrict__ b, const T* __restrict__ ax, T* __restrict__ r, size_t n, CgState* st,
@@ -70,23 +95,59 @@ cg_init_kernel(const T* __restrict__ b, const T* __restrict__ ax, T* __restrict_
     }
 }
 
-template <typename T>
+template <typename T, bool VEC>
 __global__ void __launch_bounds__(kThreads)
 cg_pupdate_kernel(const T* __restrict__ z, T* __restrict__ p, size_t n, const CgState* st) {
     if (st->done) return;
     const bool first = st->fresh != 0;
     const T beta = T(st->beta);
-    GRID_STRIDE(o, n) p[o] = first ? z[o] : z[o] + beta * p[o];
+    size_t done = 0;
+    if (VEC) {
+        constexpr int V = Vec16<T>::N;
+        const size_t nv = n / V;
+        GRID_STRIDE(i, nv) {
+            auto zv = vload(z, i);
+            auto pv = vload(p, i);
+#pragma unroll
+            for (int k = 0; k < V; ++k) el<T>(pv)[k] = first ? el<T>(zv)[k] : el<T>(zv)[k] + beta * el<T>(pv)[k];
+            vstore(p, i, pv);
+        }
+        done = nv * V;
+    }
+    for (size_t o = done + blockIdx.x * (size_t)blockDim.x + threadIdx.x; o < n; o += (size_t)gridDim.x * blockDim.x)
+        p[o] = first ? z[o] : z[o] + beta * p[o];
 }
 
-template <typename T>
+template <typename T, bool VEC>
 __global__ void __launch_bounds__(kThreads)
-cg_xr_kernel(T* __restrict__ x, T* __restrict__ r, const T* __restrict__ p, const T* __restrict__ q, size_t n,
+cg_xr_kernel(T* __restrict__ x, T* __restrict__ r, const T* p0, const T* p1, const T* __restrict__ q, size_t n,
              CgState* st, double* red, unsigned int* ticket) {
     if (st->done) return;
+    const T* __restrict__ p = st->pbuf ? p0 : p1;   // the direction this iteration wrote
     const T a = T(st->alpha);
     T part = T(0);
-    GRID_STRIDE(o, n) {
+    size_t done = 0;
+    if (VEC) {
+        constexpr int V = Vec16<T>::N;
+        const size_t nv = n / V;
+        GRID_STRIDE(i, nv) {
+            auto xv = vload<T>(x, i);
+            auto rv = vload<T>(r, i);
+            const auto pv = vload(p, i);
+            const auto qv = vload(q, i);
+#pragma unroll
+            for (int k = 0; k < V; ++k) {
+                el<T>(xv)[k] += a * el<T>(const_cast<typename Vec16<T>::type&>(pv))[k];
+                const T rn = el<T>(rv)[k] - a * el<T>(const_cast<typename Vec16<T>::type&>(qv))[k];
+                el<T>(rv)[k] = rn;
+                part += rn * rn;
+            }
+            vstore(x, i, xv);
+            vstore(r, i, rv);
+        }
+        done = nv * V;
+    }
+    for (size_t o = done + blockIdx.x * (size_t)blockDim.x + threadIdx.x; o < n; o += (size_t)gridDim.x * blockDim.x) {
         x[o] += a * p[o];
         const T rv = r[o] - a * q[o];
         r[o] = rv;
@@ -97,6 +158,7 @@ cg_xr_kernel(T* __restrict__ x, T* __restrict__ r, const T* __restrict__ p, cons
         st->rr = s;
         st->iter += 1;
         st->fresh = 0;
+        st->pbuf ^= 1;
         if (!isfinite(s)) {
             st->status = TVD_EBREAKDOWN;
             st->done = 1;
@@ -204,16 +266,23 @@ template <typename T>
 tvd_status cg_pupdate(const tvd_plan_s& p, const T* z, T* pv, CgState* st, cudaStream_t s) {
     const size_t n = (size_t)p.nr * p.nc;
     ProfScope prof(prof_class<T>(PROF_CG_PUPDATE), s);
-    cg_pupdate_kernel<T><<<red_blocks(n), kThreads, 0, s>>>(z, pv, n, st);
+    if (aligned16(z) && aligned16(pv))
+        cg_pupdate_kernel<T, true><<<vec_blocks(n, Vec16<T>::N), kThreads, 0, s>>>(z, pv, n, st);
+    else
+        cg_pupdate_kernel<T, false><<<red_blocks(n), kThreads, 0, s>>>(z, pv, n, st);
     TVD_CUDA_TRY(cudaGetLastError());
     return TVD_OK;
 }
 
 template <typename T>
-tvd_status cg_xrupdate(const tvd_plan_s& p, T* x, T* r, const T* pv, const T* q, CgState* st, cudaStream_t s) {
+tvd_status cg_xrupdate(const tvd_plan_s& p, T* x, T* r, const T* p0, const T* p1, const T* q, CgState* st,
+                       cudaStream_t s) {
     const size_t n = (size_t)p.nr * p.nc;
     ProfScope prof(prof_class<T>(PROF_CG_XR), s);
-    cg_xr_kernel<T><<<red_blocks(n), kThreads, 0, s>>>(x, r, pv, q, n, st, p.red, p.ticket + 3);
+    if (aligned16(x) && aligned16(r) && aligned16(p0) && aligned16(p1) && aligned16(q))
+        cg_xr_kernel<T, true><<<vec_blocks(n, Vec16<T>::N), kThreads, 0, s>>>(x, r, p0, p1, q, n, st, p.red, p.ticket + 3);
+    else
+        cg_xr_kernel<T, false><<<red_blocks(n), kThreads, 0, s>>>(x, r, p0, p1, q, n, st, p.red, p.ticket + 3);
     TVD_CUDA_TRY(cudaGetLastError());
     return TVD_OK;
 }
@@ -343,7 +412,8 @@ tvd_status fill_zero_f(float* a, size_t n, cudaStream_t s) {
 #define INST(T)                                                                                                  \
     template tvd_status cg_init<T>(const tvd_plan_s&, const T*, const T*, T*, CgState*, double, int, cudaStream_t); \
     template tvd_status cg_pupdate<T>(const tvd_plan_s&, const T*, T*, CgState*, cudaStream_t);                  \
-    template tvd_status cg_xrupdate<T>(const tvd_plan_s&, T*, T*, const T*, const T*, CgState*, cudaStream_t);   \
+    template tvd_status cg_xrupdate<T>(const tvd_plan_s&, T*, T*, const T*, const T*, const T*, CgState*,        \
+                                       cudaStream_t);                                                           \
     template tvd_status cg_simple_precond<T>(const tvd_plan_s&, const T*, const T*, T*, CgState*, cudaStream_t); \
     template tvd_status cg_restart<T>(const tvd_plan_s&, const T*, CgState*, double, int, int, cudaStream_t);
 INST(float)

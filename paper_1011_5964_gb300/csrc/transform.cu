@@ -60,6 +60,7 @@ struct LineArgs {
     const cplx<T>* tw;   // twiddles, length L
     const T* aux;        // auxiliary tables, kAuxSlots * 2n
     int n;               // line length
+    int ns;              // stride of the lines in shared memory (odd: no bank conflicts across lines)
     int nlines;          // number of lines (image lines)
     int nr, nc;          // image shape
     int P;               // line pairs per block
@@ -241,7 +242,7 @@ __device__ cplx<T>* fft_pairs(cplx<T>* a, cplx<T>* b, int P, const FftPlan& fp, 
 }
 
 // ------------------------------------------------------------- line transforms in shared memory
-// raw[l * n + idx]: 2P real lines of length n. bufA, bufB: P complex lines of length L.
+// raw[l * ns + idx]: 2P real lines of length n at the odd stride ns. bufA, bufB: P complex lines of length L.
 
 template <typename T>
 __device__ __forceinline__ void split_pair(const cplx<T>* Z, int k, int L, cplx<T>& Fa, cplx<T>& Fb) {
@@ -254,12 +255,12 @@ __device__ __forceinline__ void split_pair(const cplx<T>* Z, int k, int L, cplx<
 // DST-I on positions 1..n-2 of each raw line (AR); positions 0, n-1 untouched.
 template <typename T>
 __device__ void dst1_lines(T* raw, cplx<T>* bufA, cplx<T>* bufB, const LineArgs<T>& a, const cplx<T>* tw) {
-    const int n = a.n, M = n - 1, N = n - 2, P = a.P;
+    const int n = a.n, ns = a.ns, M = n - 1, N = n - 2, P = a.P;
     const T* sinh = a.aux;                    // slot0
     for (int e = threadIdx.x; e < P * M; e += blockDim.x) {
         const int pp = e / M, j = e - pp * M;
-        const T* xa = raw + (size_t)(2 * pp) * n;
-        const T* xb = xa + n;
+        const T* xa = raw + (size_t)(2 * pp) * ns;
+        const T* xb = xa + ns;
         const T a0 = j >= 1 ? xa[j] : T(0), a1 = j >= 1 ? xa[M - j] : T(0);
         const T b0 = j >= 1 ? xb[j] : T(0), b1 = j >= 1 ? xb[M - j] : T(0);
         const T sj = __ldg(sinh + j);
@@ -279,8 +280,8 @@ __device__ void dst1_lines(T* raw, cplx<T>* bufA, cplx<T>* bufB, const LineArgs<
         cplx<T> Fa, Fb;
         split_pair(Z + (size_t)pp * M, k, M, Fa, Fb);
         if (k >= 1 && k <= neven) {
-            raw[(size_t)(2 * pp) * n + 2 * k] = -sc * Fa.im;
-            raw[(size_t)(2 * pp + 1) * n + 2 * k] = -sc * Fb.im;
+            raw[(size_t)(2 * pp) * ns + 2 * k] = -sc * Fa.im;
+            raw[(size_t)(2 * pp + 1) * ns + 2 * k] = -sc * Fb.im;
         }
         if (k < nodd) {
             scan[(size_t)(2 * pp) * K + k] = k == 0 ? T(0.5) * Fa.re : Fa.re;
@@ -301,7 +302,7 @@ __device__ void dst1_lines(T* raw, cplx<T>* bufA, cplx<T>* bufB, const LineArgs<
                 if (lane >= o) v += u;
             }
             v += carry;
-            if (k < nodd) raw[(size_t)l * n + 2 * k + 1] = sc * v;
+            if (k < nodd) raw[(size_t)l * ns + 2 * k + 1] = sc * v;
             carry = __shfl_sync(0xffffffffu, v, 31);
         }
     }
@@ -311,7 +312,7 @@ __device__ void dst1_lines(T* raw, cplx<T>* bufA, cplx<T>* bufB, const LineArgs<
 // Orthonormal DCT-II (inv = false) or DCT-III (inv = true) of each raw line (R).
 template <typename T>
 __device__ void dct_lines(T* raw, cplx<T>* bufA, cplx<T>* bufB, const LineArgs<T>& a, const cplx<T>* tw, bool inv) {
-    const int n = a.n, P = a.P, h = (n + 1) / 2;
+    const int n = a.n, ns = a.ns, P = a.P, h = (n + 1) / 2;
     const T* ck = a.aux;                                              // slot0
     const cplx<T>* th = reinterpret_cast<const cplx<T>*>(a.aux + 2 * n);  // slot1 (cos, sin)(pi k / 2n)
     const T* icn = a.aux + 10 * n;                                    // slot5 1/(n c_k)
@@ -319,7 +320,7 @@ __device__ void dct_lines(T* raw, cplx<T>* bufA, cplx<T>* bufB, const LineArgs<T
         for (int e = threadIdx.x; e < P * n; e += blockDim.x) {
             const int pp = e / n, p = e - pp * n;
             const int src = p < h ? 2 * p : 2 * (n - 1 - p) + 1;
-            bufA[(size_t)pp * n + p] = {raw[(size_t)(2 * pp) * n + src], raw[(size_t)(2 * pp + 1) * n + src]};
+            bufA[(size_t)pp * n + p] = {raw[(size_t)(2 * pp) * ns + src], raw[(size_t)(2 * pp + 1) * ns + src]};
         }
         __syncthreads();
         const cplx<T>* Z = fft_pairs<T>(bufA, bufB, P, a.fp, tw, false);
@@ -329,15 +330,15 @@ __device__ void dct_lines(T* raw, cplx<T>* bufA, cplx<T>* bufB, const LineArgs<T
             split_pair(Z + (size_t)pp * n, k, n, Va, Vb);
             const cplx<T> cs = th[k];
             const T c = __ldg(ck + k);
-            raw[(size_t)(2 * pp) * n + k] = c * (cs.re * Va.re + cs.im * Va.im);
-            raw[(size_t)(2 * pp + 1) * n + k] = c * (cs.re * Vb.re + cs.im * Vb.im);
+            raw[(size_t)(2 * pp) * ns + k] = c * (cs.re * Va.re + cs.im * Va.im);
+            raw[(size_t)(2 * pp + 1) * ns + k] = c * (cs.re * Vb.re + cs.im * Vb.im);
         }
         __syncthreads();
     } else {
         for (int e = threadIdx.x; e < P * n; e += blockDim.x) {
             const int pp = e / n, k = e - pp * n;
-            const T* xa = raw + (size_t)(2 * pp) * n;
-            const T* xb = xa + n;
+            const T* xa = raw + (size_t)(2 * pp) * ns;
+            const T* xb = xa + ns;
             const T s0 = __ldg(icn + k);
             const T ya = xa[k] * s0, yb = xb[k] * s0;
             T yra = T(0), yrb = T(0);
@@ -357,8 +358,8 @@ __device__ void dct_lines(T* raw, cplx<T>* bufA, cplx<T>* bufB, const LineArgs<T
             const int pp = e / n, p = e - pp * n;
             const int dst = p < h ? 2 * p : 2 * (n - 1 - p) + 1;
             const cplx<T> z = Z[(size_t)pp * n + p];
-            raw[(size_t)(2 * pp) * n + dst] = z.re;
-            raw[(size_t)(2 * pp + 1) * n + dst] = z.im;
+            raw[(size_t)(2 * pp) * ns + dst] = z.re;
+            raw[(size_t)(2 * pp + 1) * ns + dst] = z.im;
         }
         __syncthreads();
     }
@@ -368,18 +369,18 @@ __device__ void dct_lines(T* raw, cplx<T>* bufA, cplx<T>* bufB, const LineArgs<T
 template <typename T, int BC>
 __device__ void eg_lines(const T* raw, cplx<T>* bufA, cplx<T>* bufB, T* eo, T* go, const LineArgs<T>& a,
                          const cplx<T>* tw) {
-    const int n = a.n, P = a.P, L = a.L;
+    const int n = a.n, ns = a.ns, P = a.P, L = a.L;
     for (int e = threadIdx.x; e < P * L; e += blockDim.x) {
         const int pp = e / L, j = e - pp * L;
-        bufA[(size_t)pp * L + j] = {raw[(size_t)(2 * pp) * n + j], raw[(size_t)(2 * pp + 1) * n + j]};
+        bufA[(size_t)pp * L + j] = {raw[(size_t)(2 * pp) * ns + j], raw[(size_t)(2 * pp + 1) * ns + j]};
     }
     __syncthreads();
     const cplx<T>* Z = fft_pairs<T>(bufA, bufB, P, a.fp, tw, false);
     for (int e = threadIdx.x; e < P * n; e += blockDim.x) {
         const int pp = e / n, k = e - pp * n;
         const cplx<T>* Zp = Z + (size_t)pp * L;
-        const T* fa = raw + (size_t)(2 * pp) * n;
-        const T* fb = fa + n;
+        const T* fa = raw + (size_t)(2 * pp) * ns;
+        const T* fb = fa + ns;
         T ea, ga, eb, gb;
         if (BC == BCK_AR) {
             const int M = L;
@@ -413,10 +414,10 @@ __device__ void eg_lines(const T* raw, cplx<T>* bufA, cplx<T>* bufB, T* eo, T* g
             ga = cg * (F0a.re - (w.re * Fa.re - w.im * Fa.im));
             gb = cg * (F0b.re - (w.re * Fb.re - w.im * Fb.im));
         }
-        eo[(size_t)(2 * pp) * n + k] = ea;
-        eo[(size_t)(2 * pp + 1) * n + k] = eb;
-        go[(size_t)(2 * pp) * n + k] = ga;
-        go[(size_t)(2 * pp + 1) * n + k] = gb;
+        eo[(size_t)(2 * pp) * ns + k] = ea;
+        eo[(size_t)(2 * pp + 1) * ns + k] = eb;
+        go[(size_t)(2 * pp) * ns + k] = ga;
+        go[(size_t)(2 * pp + 1) * ns + k] = gb;
     }
     __syncthreads();
 }
@@ -450,14 +451,15 @@ template <typename T, int BC, int OP>
 __global__ void __launch_bounds__(kThreads) line_kernel(LineArgs<T> a) {
     if (a.st && a.st->done) return;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    const int n = a.n, P = a.P, L = a.L;
+    const int n = a.n, ns = a.ns, P = a.P, L = a.L;
     const int lines = 2 * P;
-    const int ln = lines * n;
+    const int ln = lines * n;      // line elements of the block
+    const int lns = lines * ns;    // shared-memory size of one set of lines
     cplx<T>* tw = reinterpret_cast<cplx<T>*>(smem_raw);
     cplx<T>* bufA = tw + L;
     cplx<T>* bufB = bufA + (size_t)P * L;
     T* raw = reinterpret_cast<T*>(bufB + (size_t)P * L);
-    T* ex = raw + ln;
+    T* ex = raw + lns;
     constexpr bool cols = (OP == OP_COL_SOLVE || OP == OP_COL_EG);
     // global line index of local line l, or -1
     auto gline = [&](int l) -> int {
@@ -473,21 +475,22 @@ __global__ void __launch_bounds__(kThreads) line_kernel(LineArgs<T> a) {
     if (!cols) {
         for (int e = threadIdx.x; e < ln; e += blockDim.x) {
             const int l = e / n, idx = e - l * n;
+            const int si = l * ns + idx;
             const int g = gline(l);
             if (g < 0) {
-                raw[e] = T(0);
+                raw[si] = T(0);
                 continue;
             }
             const size_t o = (size_t)g * a.nc + idx;
-            cp_async_elem(raw + e, a.in0 + o);
-            if ((OP == OP_ROW_FWD || OP == OP_ROW_INV) && a.scale) cp_async_elem(ex + e, a.scale + o);
-            if (OP == OP_ROW_INV && a.st) cp_async_elem(ex + ln + e, a.rvec + o);
+            cp_async_elem(raw + si, a.in0 + o);
+            if ((OP == OP_ROW_FWD || OP == OP_ROW_INV) && a.scale) cp_async_elem(ex + si, a.scale + o);
+            if (OP == OP_ROW_INV && a.st) cp_async_elem(ex + lns + si, a.rvec + o);
         }
     } else {
         for (int e = threadIdx.x; e < ln; e += blockDim.x) {
             const int idx = e / lines, l = e - idx * lines;
             const int g = gline(l);
-            const int si = l * n + idx;
+            const int si = l * ns + idx;
             if (g < 0) {
                 raw[si] = T(0);
                 continue;
@@ -495,21 +498,23 @@ __global__ void __launch_bounds__(kThreads) line_kernel(LineArgs<T> a) {
             const size_t o = (size_t)idx * a.nc + g;
             cp_async_elem(raw + si, ((OP == OP_COL_EG && (l & 1)) ? a.in1 : a.in0) + o);
             if (OP == OP_COL_SOLVE) cp_async_elem(ex + si, a.spec + o);
-            if (OP == OP_COL_EG && !(l & 1)) cp_async_elem(ex + 2 * ln + (l >> 1) * n + idx, a.spec + o);
+            if (OP == OP_COL_EG && !(l & 1)) cp_async_elem(ex + 2 * lns + (l >> 1) * ns + idx, a.spec + o);
         }
     }
     cp_async_wait_all();
     __syncthreads();
     if (OP == OP_ROW_FWD && a.scale) {
-        for (int e = threadIdx.x; e < ln; e += blockDim.x)
-            if (gline(e / n) >= 0) raw[e] *= ex[e];
+        for (int e = threadIdx.x; e < ln; e += blockDim.x) {
+            const int l = e / n, si = l * ns + (e - l * n);
+            if (gline(l) >= 0) raw[si] *= ex[si];
+        }
         __syncthreads();
     }
 
     // ---- transform(s)
     if (OP == OP_ROW_EG || OP == OP_COL_EG) {
         T* eo = ex;
-        T* go = ex + ln;
+        T* go = ex + lns;
         eg_lines<T, BC>(raw, bufA, bufB, eo, go, a, tw);
         if (OP == OP_ROW_EG) {
             for (int e = threadIdx.x; e < ln; e += blockDim.x) {
@@ -517,18 +522,18 @@ __global__ void __launch_bounds__(kThreads) line_kernel(LineArgs<T> a) {
                 const int g = gline(l);
                 if (g < 0) continue;
                 const size_t o = (size_t)g * a.nc + idx;
-                a.out0[o] = eo[e];
-                a.out1[o] = go[e];
+                a.out0[o] = eo[l * ns + idx];
+                a.out1[o] = go[l * ns + idx];
             }
         } else {
             // Lambda_L column = G(A col) + E(B col); spec = lamH2 + alpha Lambda_L
-            const T* lam = ex + 2 * ln;
+            const T* lam = ex + 2 * lns;
             for (int e = threadIdx.x; e < P * n; e += blockDim.x) {
                 const int idx = e / P, pp = e - idx * P;
                 const int g = gline(2 * pp);
                 if (g < 0) continue;
-                const T lamL = go[(size_t)(2 * pp) * n + idx] + eo[(size_t)(2 * pp + 1) * n + idx];
-                const double sp = (double)lam[pp * n + idx] + a.alpha * (double)lamL;
+                const T lamL = go[(size_t)(2 * pp) * ns + idx] + eo[(size_t)(2 * pp + 1) * ns + idx];
+                const double sp = (double)lam[pp * ns + idx] + a.alpha * (double)lamL;
                 if (!(sp > 1e-300) || !isfinite(sp)) atomicOr(a.bad, 1);
                 a.inv_out[(size_t)idx * a.nc + g] = T(1.0 / sp);
             }
@@ -540,15 +545,17 @@ __global__ void __launch_bounds__(kThreads) line_kernel(LineArgs<T> a) {
     else dct_lines<T>(raw, bufA, bufB, a, tw, OP == OP_ROW_INV);
 
     if (OP == OP_COL_SOLVE) {
-        for (int e = threadIdx.x; e < ln; e += blockDim.x)
-            if (gline(e / n) >= 0) raw[e] *= ex[e];
+        for (int e = threadIdx.x; e < ln; e += blockDim.x) {
+            const int l = e / n, si = l * ns + (e - l * n);
+            if (gline(l) >= 0) raw[si] *= ex[si];
+        }
         __syncthreads();
         if (BC == BCK_AR) dst1_lines<T>(raw, bufA, bufB, a, tw);
         else dct_lines<T>(raw, bufA, bufB, a, tw, true);
         for (int e = threadIdx.x; e < ln; e += blockDim.x) {
             const int idx = e / lines, l = e - idx * lines;
             const int g = gline(l);
-            if (g >= 0) a.out0[(size_t)idx * a.nc + g] = raw[(size_t)l * n + idx];
+            if (g >= 0) a.out0[(size_t)idx * a.nc + g] = raw[(size_t)l * ns + idx];
         }
         return;
     }
@@ -559,10 +566,11 @@ __global__ void __launch_bounds__(kThreads) line_kernel(LineArgs<T> a) {
         const int g = gline(l);
         if (g < 0) continue;
         const size_t o = (size_t)g * a.nc + idx;
-        T v = raw[e];
-        if (OP == OP_ROW_INV && a.scale) v *= ex[e];
+        const int si = l * ns + idx;
+        T v = raw[si];
+        if (OP == OP_ROW_INV && a.scale) v *= ex[si];
         a.out0[o] = v;
-        if (OP == OP_ROW_INV && a.st) part += ex[ln + e] * v;
+        if (OP == OP_ROW_INV && a.st) part += ex[lns + si] * v;
     }
     if (OP == OP_ROW_INV && a.st) {
         double s;
@@ -594,7 +602,7 @@ static size_t line_smem(const LineArgs<T>& a, int op) {
     const size_t lines = 2 * (size_t)a.P;
     // tw + bufA + bufB + raw + the operation's staged factors / outputs
     return sizeof(cplx<T>) * ((size_t)a.L + 2 * (size_t)a.P * a.L) +
-           sizeof(T) * (lines * a.n + line_extra(op, lines, a.n, a.P)) + 64;
+           sizeof(T) * (lines * a.ns + line_extra(op, lines, a.ns, a.P)) + 64;
 }
 
 template <typename T>
@@ -646,6 +654,7 @@ static LineArgs<T> base_args(const tvd_plan_s& p, const Ops<T>& o, bool cols) {
     a.nr = p.nr;
     a.nc = p.nc;
     a.n = cols ? p.nr : p.nc;
+    a.ns = a.n | 1;
     a.nlines = cols ? p.nc : p.nr;
     a.fp = cols ? p.fft_r : p.fft_c;
     a.L = a.fp.L;

@@ -85,7 +85,7 @@ static void transform_tables(int n, tvd_bc bc, std::vector<double>& tw, std::vec
 template <typename T>
 static tvd_status ops_alloc(tvd_plan_s& p, Ops<T>& o, cudaStream_t s) {
     const size_t n = (size_t)p.nr * p.nc;
-    T** arrays[] = {&o.lamH2, &o.inv_spec, &o.w, &o.dmh, &o.dinv, &o.x, &o.r, &o.z, &o.p, &o.q, &o.t, &o.t2};
+    T** arrays[] = {&o.lamH2, &o.inv_spec, &o.w, &o.dmh, &o.dinv, &o.x, &o.r, &o.z, &o.p, &o.p2, &o.q, &o.t, &o.t2};
     for (T** a : arrays) TVD_TRY(dalloc(a, n));
     o.allocated = true;
     // PSF taps: dense, plus per-column tap-row ranges
@@ -122,7 +122,7 @@ static void ops_free(Ops<T>& o) {
     dfree(o.hdense); dfree(o.arange); dfree(o.crow); dfree(o.ccol); dfree(o.ccor);
     dfree(o.tw_c); dfree(o.tw_r); dfree(o.aux_c); dfree(o.aux_r);
     dfree(o.lamH2); dfree(o.inv_spec); dfree(o.w); dfree(o.dmh); dfree(o.dinv);
-    dfree(o.x); dfree(o.r); dfree(o.z); dfree(o.p); dfree(o.q); dfree(o.t); dfree(o.t2);
+    dfree(o.x); dfree(o.r); dfree(o.z); dfree(o.p); dfree(o.p2); dfree(o.q); dfree(o.t); dfree(o.t2);
     o.allocated = false;
 }
 
@@ -251,10 +251,9 @@ static tvd_status precond_step(tvd_plan_s& p, Ops<T>& o, CgState* st, cudaStream
 template <typename T>
 static tvd_status enqueue_iteration(tvd_plan_s& p, Ops<T>& o, double alpha, T* x, CgState* st, cudaStream_t s) {
     TVD_TRY(precond_step<T>(p, o, st, s));
-    TVD_TRY(cg_pupdate<T>(p, o.z, o.p, st, s));
-    TVD_TRY(blur_apply<T>(p, o, false, o.p, o.t, s, st));
-    TVD_TRY(normal_finish<T>(p, o, o.t, o.p, alpha, o.q, st, s));
-    TVD_TRY(cg_xrupdate<T>(p, x, o.r, o.p, o.q, st, s));
+    TVD_TRY(blur_pupdate<T>(p, o, o.z, o.p, o.p2, o.t, st, s));
+    TVD_TRY(normal_finish<T>(p, o, o.t, o.p, o.p2, alpha, o.q, st, s));
+    TVD_TRY(cg_xrupdate<T>(p, x, o.r, o.p, o.p2, o.q, st, s));
     return TVD_OK;
 }
 
@@ -305,7 +304,7 @@ static tvd_status cg_run(tvd_plan_s& p, Ops<T>& o, double alpha, const T* b, T* 
                          CgState* out, cudaStream_t s) {
     CgState* st = p.state;
     TVD_TRY(blur_apply<T>(p, o, false, x, o.t, s));
-    TVD_TRY(normal_finish<T>(p, o, o.t, x, alpha, o.q, nullptr, s));
+    TVD_TRY(normal_finish<T>(p, o, o.t, x, x, alpha, o.q, nullptr, s));
     TVD_TRY(cg_init<T>(p, b, o.q, o.r, st, tol, maxit, s));
     const bool use_graph = !profiling_enabled();
     if (use_graph) TVD_TRY(ensure_graph<T>(p, o, alpha, b, x));

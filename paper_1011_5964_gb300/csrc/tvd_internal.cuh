@@ -104,6 +104,7 @@ struct CgState {
     int done;          // 1 once converged / stopped
     int status;        // tvd_status reached inside the loop
     int fresh;         // 1: the next search direction is p = z (start or restart)
+    int pbuf;          // which of the two direction buffers holds the current p
 };
 
 // Reduction slots: each reduction writes one double per block, then the last
@@ -138,7 +139,8 @@ struct Ops {
     T* x = nullptr;
     T* r = nullptr;
     T* z = nullptr;
-    T* p = nullptr;
+    T* p = nullptr;          // search direction, double-buffered with p2 (CgState.pbuf)
+    T* p2 = nullptr;
     T* q = nullptr;
     T* t = nullptr;          // H p, transform intermediate
     T* t2 = nullptr;         // second transform intermediate (spectrum setup)
@@ -209,10 +211,19 @@ tvd_status diag_scale(const tvd_plan_s& p, const T* w, double alpha, T* dmh, T* 
 template <typename T>
 tvd_status tv_apply(const tvd_plan_s& p, const T* w, const T* x, T* y, cudaStream_t s);
 
-// q = H^T t + alpha L(w) pv; with st, also p^T q -> st->pq and alpha = rho / pq.
+// q = H^T t + alpha L(w) p; with st, p is the direction buffer the current
+// iteration wrote (p0 / p1 by st->pbuf), and p^T q -> st->pq, alpha = rho / pq;
+// without st, p = p0.
 template <typename T>
-tvd_status normal_finish(const tvd_plan_s& p, const Ops<T>& o, const T* t, const T* pv, double alpha,
+tvd_status normal_finish(const tvd_plan_s& p, const Ops<T>& o, const T* t, const T* p0, const T* p1, double alpha,
                          T* q, CgState* st, cudaStream_t s);
+
+// CG direction update fused with the forward blur: p_new = z (fresh) or
+// z + beta p_old, with p_old / p_new the two direction buffers chosen by
+// st->pbuf; t = H p_new.
+template <typename T>
+tvd_status blur_pupdate(const tvd_plan_s& p, const Ops<T>& o, const T* z, T* p0, T* p1, T* t, CgState* st,
+                        cudaStream_t s);
 
 // Preconditioner spectrum (requires o.w): inv_spec = 1 / (lamH2 + alpha Lambda_L).
 template <typename T>
@@ -232,8 +243,11 @@ tvd_status cg_init(const tvd_plan_s& p, const T* b, const T* ax, T* r, CgState* 
                    cudaStream_t s);
 template <typename T>
 tvd_status cg_pupdate(const tvd_plan_s& p, const T* z, T* pv, CgState* st, cudaStream_t s);
+// x += alpha p, r -= alpha q with p the current iteration's direction buffer;
+// the finisher flips st->pbuf.
 template <typename T>
-tvd_status cg_xrupdate(const tvd_plan_s& p, T* x, T* r, const T* pv, const T* q, CgState* st, cudaStream_t s);
+tvd_status cg_xrupdate(const tvd_plan_s& p, T* x, T* r, const T* p0, const T* p1, const T* q, CgState* st,
+                       cudaStream_t s);
 template <typename T>
 tvd_status cg_simple_precond(const tvd_plan_s& p, const T* r, const T* dinv, T* z, CgState* st, cudaStream_t s);
 
