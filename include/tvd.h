@@ -187,6 +187,33 @@ const char* tvd_last_error(void);
 const char* tvd_version(void);
 
 /*
+ * tvd_normal_apply_noalloc -- y = H^T H x + alpha L(u_lag) x in double, for
+ * callers that cannot allocate device memory. No counterpart in the paper: it
+ * is the PCG's normal-equations product (the same kernels as pcg_solve) made
+ * callable without a plan, because some callers must not call cudaMalloc:
+ * code running while a CUDA graph is being captured (an allocation would
+ * break the capture), code inside a framework that owns a fixed device-memory
+ * pool (a caching allocator, a real-time or embedded budget), and callbacks
+ * from such a framework that must not allocate behind its back.
+ *   n_rows, n_cols   image size, n_rows * n_cols <= 524288 (e.g. 512 x 1024);
+ *                    larger sizes return TVD_EINVAL with a message.
+ *   psf_host, p_rows, p_cols, bc   as for tvd_plan_create (HOST PSF, copied).
+ *   u_lag, x         DOUBLE device arrays (n_rows x n_cols); beta > 0, alpha >= 0.
+ *   y                DOUBLE device array, must not overlap x or u_lag.
+ * Scratch: H x, the diffusivity of u_lag and the PSF tables live in fixed
+ * device arrays of the library (8 MiB plus about 0.2 MiB), which every GPU
+ * that loads the library holds until the process exits. All calls share
+ * them and each call overwrites them, so calls that overlap on the GPU (two
+ * streams, or two host threads) race: serialise them. The first call on a
+ * device looks up the arrays' device addresses (cudaGetSymbolAddress); make
+ * that first call before any stream capture. The call copies the PSF tables
+ * from host memory and synchronises `stream` before returning.
+ */
+tvd_status tvd_normal_apply_noalloc(int n_rows, int n_cols, const double* psf_host, int p_rows, int p_cols,
+                                    tvd_bc bc, const double* u_lag, double alpha, double beta,
+                                    const double* x, double* y, void* stream);
+
+/*
  * Diagnostics (no counterpart in the paper).
  * tvd_kernel_launches -- number of CUDA kernels this library has launched in
  *   the process so far (all plans, all streams).

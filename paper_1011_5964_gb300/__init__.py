@@ -34,8 +34,8 @@ STATUS_NAMES = ["TVD_OK", "TVD_EINVAL", "TVD_EPSF_ASYM", "TVD_EPSF_SIZE", "TVD_E
 # Function names of the C ABI, in include/tvd.h order.
 ABI_FUNCTIONS = ["tvd_plan_create", "tvd_plan_destroy", "ar_blur_apply", "tv_operator_apply",
                  "tau_precond_setup", "tau_precond_solve", "pcg_solve", "tv_deblur",
-                 "tvd_last_error", "tvd_version", "tvd_kernel_launches", "tvd_profile_enable",
-                 "tvd_profile_classes", "tvd_profile_name", "tvd_profile_read"]
+                 "tvd_normal_apply_noalloc", "tvd_last_error", "tvd_version", "tvd_kernel_launches",
+                 "tvd_profile_enable", "tvd_profile_classes", "tvd_profile_name", "tvd_profile_read"]
 
 
 class TvdError(RuntimeError):
@@ -75,6 +75,7 @@ def load_library(path: str | None = None) -> ctypes.CDLL:
     lib.tau_precond_solve.argtypes = [vp, vp, vp, vp]
     lib.pcg_solve.argtypes = [vp, vp, d, d, vp, vp, d, i, ctypes.POINTER(i), ctypes.POINTER(d), vp]
     lib.tv_deblur.argtypes = [vp, vp, d, d, i, d, d, i, vp, ctypes.POINTER(_Stats), vp]
+    lib.tvd_normal_apply_noalloc.argtypes = [i, i, ctypes.POINTER(d), i, i, i, vp, d, d, vp, vp, vp]
     lib.tvd_last_error.restype = ctypes.c_char_p
     lib.tvd_version.restype = ctypes.c_char_p
     lib.tvd_kernel_launches.restype = ctypes.c_ulonglong
@@ -209,6 +210,28 @@ class Plan:
                    "total_inner_iters": stats.total_inner_iters, "refinement_sweeps": stats.refinement_sweeps,
                    "last_relres": stats.last_relres, "last_rel_change": stats.last_rel_change,
                    "last_status": stats.last_status, "status": st}
+
+
+def normal_apply_noalloc(psf, u_lag, alpha: float, beta: float, x, y=None, bc: str = "ar"):
+    """y = H^T H x + alpha L(u_lag) x (float64 CUDA tensors) without any device allocation by the library.
+
+    For callers that must not allocate device memory (inside a CUDA graph
+    capture, or under a framework that owns a fixed memory pool). The library
+    keeps the intermediate results in fixed device arrays shared by all calls:
+    calls that overlap on the GPU race, and n_rows * n_cols is limited to
+    524288. The first call on a device must come before any stream capture.
+    """
+    import torch
+    lib = load_library()
+    n_rows, n_cols = x.shape
+    n = n_rows * n_cols
+    out = torch.empty_like(x) if y is None else y
+    h = np.ascontiguousarray(np.asarray(psf, dtype=np.float64))
+    _check(lib.tvd_normal_apply_noalloc(n_rows, n_cols, h.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                        h.shape[0], h.shape[1], BC[bc], _ptr(u_lag, torch.float64, n),
+                                        float(alpha), float(beta), _ptr(x, torch.float64, n),
+                                        _ptr(out, torch.float64, n), _stream()))
+    return out
 
 
 def kernel_launches() -> int:

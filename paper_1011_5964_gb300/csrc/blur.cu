@@ -26,6 +26,9 @@
 // Transpose, R: H^T = H for a symmetric PSF (Sec. 3.1).
 #include "common.cuh"
 
+#include <algorithm>
+#include <mutex>
+
 namespace tvd {
 
 enum { EXT_AR = 0, EXT_R = 1, EXT_ODD = 2 };
@@ -404,6 +407,126 @@ tvd_status normal_finish(const tvd_plan_s& p, const Ops<T>& o, const T* t, const
                          T* q, CgState* st, cudaStream_t s) {
     return launch_blur<T>(p, o, true, BLUR_FUSE, t, q, o.w, const_cast<T*>(p0), const_cast<T*>(p1), alpha, st, s);
 }
+
+// ---------------------------------------------------------------- allocation-free normal-equations product
+//
+// tvd_normal_apply_noalloc computes y = H^T H x + alpha L(u) x without any
+// device allocation: the intermediate H x, the diffusivity of u and the PSF
+// tables live in the file-scope arrays below, which every GPU that loads the
+// library holds until the process exits (8 MiB for the two image arrays plus
+// about 0.2 MiB of tables). All calls share them.
+
+constexpr int kNoAllocMaxPixels = 512 * 1024;     // n_rows * n_cols limit
+constexpr int kNoAllocMaxHalf = 48;               // PSF half-width limit (as for plans)
+constexpr int kNoAllocMaxSide = 2 * kNoAllocMaxHalf + 1;
+
+static __device__ __align__(256) double g_na_hx[kNoAllocMaxPixels];      // H x
+static __device__ __align__(256) double g_na_w[kNoAllocMaxPixels];       // diffusivity of u
+static __device__ __align__(256) double g_na_h[kNoAllocMaxSide * kNoAllocMaxSide];
+static __device__ __align__(256) int g_na_arange[2 * kNoAllocMaxSide];
+static __device__ __align__(256) double g_na_crow[(kNoAllocMaxHalf + 1) * kNoAllocMaxSide];
+static __device__ __align__(256) double g_na_ccol[kNoAllocMaxSide * (kNoAllocMaxHalf + 1)];
+static __device__ __align__(256) double g_na_ccor[(kNoAllocMaxHalf + 1) * (kNoAllocMaxHalf + 1)];
+
+struct NoAllocPtrs {
+    bool ready = false;
+    double *hx, *w, *h, *crow, *ccol, *ccor;
+    int* arange;
+};
+
+constexpr int kNoAllocMaxDevices = 64;
+static NoAllocPtrs g_na_ptrs[kNoAllocMaxDevices];
+static std::mutex g_na_mu;
+
+// Device addresses of the arrays above for the current device, looked up once
+// per device (host code cannot use the symbols' own names as device pointers).
+static tvd_status noalloc_ptrs(NoAllocPtrs* out) {
+    int dev = 0;
+    TVD_CUDA_TRY(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= kNoAllocMaxDevices) {
+        set_error("tvd_normal_apply_noalloc: device ordinal out of range");
+        return TVD_EINVAL;
+    }
+    std::lock_guard<std::mutex> lk(g_na_mu);
+    NoAllocPtrs& p = g_na_ptrs[dev];
+    if (!p.ready) {
+        TVD_CUDA_TRY(cudaGetSymbolAddress((void**)&p.hx, g_na_hx));
+        TVD_CUDA_TRY(cudaGetSymbolAddress((void**)&p.w, g_na_w));
+        TVD_CUDA_TRY(cudaGetSymbolAddress((void**)&p.h, g_na_h));
+        TVD_CUDA_TRY(cudaGetSymbolAddress((void**)&p.arange, g_na_arange));
+        TVD_CUDA_TRY(cudaGetSymbolAddress((void**)&p.crow, g_na_crow));
+        TVD_CUDA_TRY(cudaGetSymbolAddress((void**)&p.ccol, g_na_ccol));
+        TVD_CUDA_TRY(cudaGetSymbolAddress((void**)&p.ccor, g_na_ccor));
+        p.ready = true;
+    }
+    *out = p;
+    return TVD_OK;
+}
+
+}  // namespace tvd
+
+extern "C" tvd_status tvd_normal_apply_noalloc(int n_rows, int n_cols, const double* psf_host, int p_rows,
+                                               int p_cols, tvd_bc bc, const double* u_lag, double alpha,
+                                               double beta, const double* x, double* y, void* stream) {
+    using namespace tvd;
+    if (!psf_host || !u_lag || !x || !y || y == x || y == u_lag || !(alpha >= 0.0) || !(beta > 0.0) ||
+        (bc != TVD_BC_REFLECTIVE && bc != TVD_BC_ANTIREFLECTIVE) || n_rows < 3 || n_cols < 3) {
+        set_error("tvd_normal_apply_noalloc: invalid argument");
+        return TVD_EINVAL;
+    }
+    if ((long long)n_rows * n_cols > kNoAllocMaxPixels) {
+        set_error("tvd_normal_apply_noalloc: n_rows * n_cols exceeds the fixed scratch of " +
+                  std::to_string(kNoAllocMaxPixels) + " pixels");
+        return TVD_EINVAL;
+    }
+    // host-side PSF tables (the plan's validation: odd sides, symmetry, m <= n - 2, m <= 48)
+    tvd_plan_s plan;
+    plan.nr = n_rows;
+    plan.nc = n_cols;
+    plan.bc = bc;
+    TVD_TRY(build_psf(plan.psf, psf_host, p_rows, p_cols, n_rows, n_cols));
+    const int mr = plan.psf.mr, mc = plan.psf.mc, pw = 2 * mc + 1;
+    std::vector<int> rng(2 * (size_t)pw);
+    for (int b = -mc; b <= mc; ++b) {
+        int lo = mr + 1, hi = -mr - 1;
+        for (int a = -mr; a <= mr; ++a)
+            if (plan.psf.h[(size_t)(a + mr) * pw + (b + mc)] != 0.0) {
+                lo = std::min(lo, a);
+                hi = std::max(hi, a);
+            }
+        rng[2 * (b + mc)] = lo;
+        rng[2 * (b + mc) + 1] = hi;
+    }
+    NoAllocPtrs d;
+    TVD_TRY(noalloc_ptrs(&d));
+    cudaStream_t s = (cudaStream_t)stream;
+    // every table entry the kernels read is written here, and the kernels write
+    // all of H x and of the diffusivity before reading them: nothing needs clearing
+    auto put = [&](void* dst, const void* src, size_t bytes) -> tvd_status {
+        TVD_CUDA_TRY(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, s));
+        return TVD_OK;
+    };
+    TVD_TRY(put(d.h, plan.psf.h.data(), plan.psf.h.size() * sizeof(double)));
+    TVD_TRY(put(d.arange, rng.data(), rng.size() * sizeof(int)));
+    TVD_TRY(put(d.crow, plan.psf.crow.data(), plan.psf.crow.size() * sizeof(double)));
+    TVD_TRY(put(d.ccol, plan.psf.ccol.data(), plan.psf.ccol.size() * sizeof(double)));
+    TVD_TRY(put(d.ccor, plan.psf.ccor.data(), plan.psf.ccor.size() * sizeof(double)));
+    Ops<double> o;
+    o.hdense = d.h;
+    o.arange = d.arange;
+    o.crow = d.crow;
+    o.ccol = d.ccol;
+    o.ccor = d.ccor;
+    o.w = d.w;
+    TVD_TRY(diffusivity<double>(plan, u_lag, beta, d.w, s));
+    TVD_TRY(blur_apply<double>(plan, o, false, x, d.hx, s));
+    TVD_TRY(normal_finish<double>(plan, o, d.hx, x, x, alpha, y, nullptr, s));
+    // the host tables above are copied from pageable memory; wait so they may be freed
+    TVD_CUDA_TRY(cudaStreamSynchronize(s));
+    return TVD_OK;
+}
+
+namespace tvd {
 
 #define INST(T)                                                                                                  \
     template tvd_status blur_apply<T>(const tvd_plan_s&, const Ops<T>&, bool, const T*, T*, cudaStream_t, CgState*); \

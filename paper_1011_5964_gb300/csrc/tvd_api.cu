@@ -142,7 +142,7 @@ static void plan_free(tvd_plan_s* p) {
 }
 
 // Validate and trim the PSF; build the nonzero tap list and the AR border tail weights.
-static tvd_status build_psf(Psf& out, const double* h, int pr, int pc, int nr, int nc) {
+tvd_status build_psf(Psf& out, const double* h, int pr, int pc, int nr, int nc) {
     if (!h || pr < 1 || pc < 1 || pr % 2 == 0 || pc % 2 == 0) {
         set_error("PSF sides must be odd and positive");
         return TVD_EPSF_SIZE;

@@ -194,6 +194,9 @@ struct tvd_plan_s {
 
 namespace tvd {
 
+// Validate and trim a PSF for an n_rows x n_cols image (host only).
+tvd_status build_psf(Psf& out, const double* h, int pr, int pc, int nr, int nc);
+
 // ---------------------------------------------------------------- launchers
 // Each launcher is asynchronous on `s` and returns a tvd_status (launch errors).
 
