@@ -248,7 +248,13 @@ __device__ __forceinline__ int odd_map(int I, int n, int* idx) {
     return 1;
 }
 
-// First/last rows and columns of H^T y under AR BCs (one thread per output).
+// First/last rows and columns of H^T y under AR BCs. Each block computes 32
+// consecutive outputs of one border (or the four corners): it stages the
+// strip of y the tail-weighted sums read (with the odd extension across the
+// other direction) in shared memory, eight thread groups share the strip's
+// rows, and a shared-memory reduction combines them.
+constexpr int kSeg = 32;
+
 template <typename T, bool FUSE>
 __global__ void __launch_bounds__(kThreads)
 ar_adjoint_border_kernel(const T* __restrict__ y, T* __restrict__ out, int nr, int nc, int mr, int mc,
@@ -256,61 +262,79 @@ ar_adjoint_border_kernel(const T* __restrict__ y, T* __restrict__ out, int nr, i
                          const T* __restrict__ w, const T* p0, const T* p1, FuseArgs fa) {
     if (fa.st && fa.st->done) return;
     const T* pv = fa.st ? (fa.st->pbuf ? p0 : p1) : p0;
-    const int nrow = nc - 2, ncol = nr - 2;              // interior outputs on each row / column border
-    const int total = 2 * nrow + 2 * ncol + 4;
-    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T* strip = reinterpret_cast<T*>(smem_raw);
+    __shared__ T partial[kThreads];
+    const int nseg_r = (nc - 2 + kSeg - 1) / kSeg, nseg_c = (nr - 2 + kSeg - 1) / kSeg;
+    int bid = blockIdx.x;
+    const int o = threadIdx.x % kSeg, grp = threadIdx.x / kSeg, ngrp = kThreads / kSeg;
+    T acc = T(0);
+    int oi = -1, oj = -1;
+    if (bid < 2 * nseg_r) {
+        // top (0) / bottom (nr - 1) row, interior columns l0 .. l0 + 31
+        const bool top = bid < nseg_r;
+        const int l0 = 1 + (top ? bid : bid - nseg_r) * kSeg;
+        const int SW = kSeg + 2 * mc;
+        for (int e = threadIdx.x; e < (mr + 1) * SW; e += blockDim.x) {
+            const int i = e / SW, cc = e - i * SW;
+            int ci;
+            const int sg = odd_map(l0 - mc + cc, nc, &ci);
+            const int ri = top ? i : nr - 1 - i;
+            strip[e] = sg ? T(sg) * y[(size_t)ri * nc + ci] : T(0);
+        }
+        __syncthreads();
+        const int l = l0 + o;
+        for (int i = grp; i <= mr; i += ngrp) {
+            const T* crw = crow + (size_t)i * (2 * mc + 1);
+            const T* srow = strip + i * SW + o + mc;
+            for (int b = -mc; b <= mc; ++b) acc += __ldg(crw + b + mc) * srow[b];
+        }
+        if (l <= nc - 2) { oi = top ? 0 : nr - 1; oj = l; }
+    } else if (bid < 2 * nseg_r + 2 * nseg_c) {
+        // left (0) / right (nc - 1) column, interior rows k0 .. k0 + 31
+        bid -= 2 * nseg_r;
+        const bool left = bid < nseg_c;
+        const int k0 = 1 + (left ? bid : bid - nseg_c) * kSeg;
+        const int SH = kSeg + 2 * mr;
+        for (int e = threadIdx.x; e < SH * (mc + 1); e += blockDim.x) {
+            const int r = e / (mc + 1), j = e - r * (mc + 1);
+            int ri;
+            const int sg = odd_map(k0 - mr + r, nr, &ri);
+            const int cj = left ? j : nc - 1 - j;
+            strip[e] = sg ? T(sg) * y[(size_t)ri * nc + cj] : T(0);
+        }
+        __syncthreads();
+        const int k = k0 + o;
+        for (int j = grp; j <= mc; j += ngrp)
+            for (int a = -mr; a <= mr; ++a)
+                acc += __ldg(ccol + (size_t)(a + mr) * (mc + 1) + j) * strip[(o + mr + a) * (mc + 1) + j];
+        if (k <= nr - 2) { oi = k; oj = left ? 0 : nc - 1; }
+    } else {
+        // the four corners: output c = o (< 4); groups share the (mr + 1) rows
+        if (o < 4) {
+            const bool top = (o & 1) == 0, left = (o & 2) == 0;
+            for (int i = grp; i <= mr; i += ngrp) {
+                const int ri = top ? i : nr - 1 - i;
+                for (int j = 0; j <= mc; ++j) {
+                    const int cj = left ? j : nc - 1 - j;
+                    acc += __ldg(ccor + (size_t)i * (mc + 1) + j) * y[(size_t)ri * nc + cj];
+                }
+            }
+            oi = top ? 0 : nr - 1;
+            oj = left ? 0 : nc - 1;
+        }
+    }
+    partial[threadIdx.x] = acc;
+    __syncthreads();
     T part = T(0);
-    if (t < total) {
-        int oi, oj;
-        T acc = T(0);
-        if (t < 2 * nrow) {                                // rows 0 / nr-1, interior columns
-            const bool top = t < nrow;
-            const int l = 1 + (top ? t : t - nrow);
-            oi = top ? 0 : nr - 1;
-            oj = l;
-            for (int i = 0; i <= mr; ++i) {
-                const int ri = top ? i : nr - 1 - i;
-                const T* crw = crow + (size_t)i * (2 * mc + 1);
-                for (int b = -mc; b <= mc; ++b) {
-                    int ci;
-                    const int sg = odd_map(l + b, nc, &ci);
-                    if (sg) acc += crw[b + mc] * T(sg) * y[(size_t)ri * nc + ci];
-                }
-            }
-        } else if (t < 2 * nrow + 2 * ncol) {              // columns 0 / nc-1, interior rows
-            const int u = t - 2 * nrow;
-            const bool left = u < ncol;
-            const int k = 1 + (left ? u : u - ncol);
-            oi = k;
-            oj = left ? 0 : nc - 1;
-            for (int a = -mr; a <= mr; ++a) {
-                int ri;
-                const int sg = odd_map(k + a, nr, &ri);
-                if (!sg) continue;
-                const T* ccl = ccol + (size_t)(a + mr) * (mc + 1);
-                for (int j = 0; j <= mc; ++j) {
-                    const int cj = left ? j : nc - 1 - j;
-                    acc += ccl[j] * T(sg) * y[(size_t)ri * nc + cj];
-                }
-            }
-        } else {                                           // the four corners
-            const int c = t - 2 * nrow - 2 * ncol;
-            const bool top = (c & 1) == 0, left = (c & 2) == 0;
-            oi = top ? 0 : nr - 1;
-            oj = left ? 0 : nc - 1;
-            for (int i = 0; i <= mr; ++i) {
-                const int ri = top ? i : nr - 1 - i;
-                for (int j = 0; j <= mc; ++j) {
-                    const int cj = left ? j : nc - 1 - j;
-                    acc += ccor[(size_t)i * (mc + 1) + j] * y[(size_t)ri * nc + cj];
-                }
-            }
-        }
+    if (grp == 0 && oi >= 0) {
+        T v = T(0);
+        for (int g = 0; g < ngrp; ++g) v += partial[g * kSeg + o];
         if (FUSE) {
-            acc += T(fa.alpha) * lap_at(w, pv, oi, oj, nr, nc);
-            part = pv[(size_t)oi * nc + oj] * acc;
+            v += T(fa.alpha) * lap_at(w, pv, oi, oj, nr, nc);
+            part = pv[(size_t)oi * nc + oj] * v;
         }
-        out[(size_t)oi * nc + oj] = acc;
+        out[(size_t)oi * nc + oj] = v;
     }
     if (FUSE && fa.reduce) {
         double s;
@@ -318,6 +342,11 @@ ar_adjoint_border_kernel(const T* __restrict__ y, T* __restrict__ out, int nr, i
             threadIdx.x == 0 && fa.finish_here)
             finish_pq(fa.st, s);
     }
+}
+
+static size_t border_smem(int mr, int mc, size_t elem) {
+    const size_t a = (size_t)(mr + 1) * (kSeg + 2 * mc), b = (size_t)(kSeg + 2 * mr) * (mc + 1);
+    return (a > b ? a : b) * elem + 16;
 }
 
 static size_t tile_smem(int mr, int mc, size_t elem, bool fuse, bool pup) {
@@ -348,8 +377,7 @@ static tvd_status launch_blur(const tvd_plan_s& p, const Ops<T>& o, bool transpo
     const size_t smem = tile_smem(mr, mc, sizeof(T), fuse, pup);
     FuseArgs fa{alpha, st, p.red, p.ticket + 1, (fuse && st) ? 1 : 0, 0, 0, 0};
     const int tile_blocks = (int)(grid.x * grid.y);
-    const int nborder = 2 * (nc - 2) + 2 * (nr - 2) + 4;
-    const int border_blocks = (nborder + kThreads - 1) / kThreads;
+    const int border_blocks = 2 * ((nc - 2 + kSeg - 1) / kSeg) + 2 * ((nr - 2 + kSeg - 1) / kSeg) + 1;
     const bool ar_adj = transpose && p.bc == TVD_BC_ANTIREFLECTIVE;
     ProfScope prof(prof_class<T>((transpose || fuse) ? PROF_BLUR_ADJ : PROF_BLUR_FWD), s, ar_adj ? 2 : 1);
     if (fa.reduce) {
@@ -379,12 +407,16 @@ static tvd_status launch_blur(const tvd_plan_s& p, const Ops<T>& o, bool transpo
         else TVD_TRY((launch_tile<T, EXT_ODD, false, false>(grid, smem, s, x, y, p, o, w, p0, p1, fa)));
         fa.finish_here = 1;
         fa.slot0 = tile_blocks;
-        if (fuse)
-            ar_adjoint_border_kernel<T, true><<<border_blocks, kThreads, 0, s>>>(x, y, nr, nc, mr, mc, o.crow, o.ccol,
-                                                                              o.ccor, w, p0, p1, fa);
-        else
-            ar_adjoint_border_kernel<T, false><<<border_blocks, kThreads, 0, s>>>(x, y, nr, nc, mr, mc, o.crow, o.ccol,
-                                                                               o.ccor, w, p0, p1, fa);
+        const size_t bsm = border_smem(mr, mc, sizeof(T));
+        if (fuse) {
+            TVD_CUDA_TRY((allow_max_smem<ar_adjoint_border_kernel<T, true>>()));
+            ar_adjoint_border_kernel<T, true><<<border_blocks, kThreads, bsm, s>>>(x, y, nr, nc, mr, mc, o.crow,
+                                                                                o.ccol, o.ccor, w, p0, p1, fa);
+        } else {
+            TVD_CUDA_TRY((allow_max_smem<ar_adjoint_border_kernel<T, false>>()));
+            ar_adjoint_border_kernel<T, false><<<border_blocks, kThreads, bsm, s>>>(x, y, nr, nc, mr, mc, o.crow,
+                                                                                 o.ccol, o.ccor, w, p0, p1, fa);
+        }
     }
     TVD_CUDA_TRY(cudaGetLastError());
     return TVD_OK;
