@@ -428,13 +428,29 @@ def normal_apply(x, h, bc, w, alpha) -> np.ndarray:
 # PCG (Golub & Van Loan, Algorithm 10.3.1) and the FP loop, Secs. 1 and 5
 # --------------------------------------------------------------------------
 
-def pcg(apply_A, apply_M, b, x0, tol, maxit, hist=None):
+def pcg(apply_A, apply_M, b, x0, tol, maxit, hist=None, noise=None):
     """Preconditioned CG on A x = b from x0.
 
     Stops when ||r_k||_2 / ||r_0||_2 < tol (Sec. 5) or after ``maxit`` products
     with A. Returns (x, iterations, relres, converged). If ``hist`` is a list,
     the relative residual after each iteration is appended to it.
+
+    ``noise = (rng, eps)`` (test hook, off by default) multiplies every product
+    with A and every preconditioner output by (1 + eps xi), xi standard normal:
+    it models rounding that differs from this implementation's, to measure how
+    sensitive the iteration is to it.
     """
+    if noise is not None:
+        rng, eps = noise
+        A0, M0 = apply_A, apply_M
+
+        def apply_A(y):
+            q = A0(y)
+            return q * (1.0 + eps * rng.standard_normal(q.shape))
+
+        def apply_M(r):
+            z = M0(r)
+            return z * (1.0 + eps * rng.standard_normal(z.shape))
     x = np.array(x0, dtype=np.float64, copy=True)
     r = b - apply_A(x)
     r0 = float(np.sqrt((r * r).sum()))
@@ -465,16 +481,16 @@ def pcg(apply_A, apply_M, b, x0, tol, maxit, hist=None):
     return x, k, relres, False
 
 
-def fp_step(u, b, h, bc, alpha, beta, kind, tol, maxit, hist=None):
+def fp_step(u, b, h, bc, alpha, beta, kind, tol, maxit, hist=None, noise=None):
     """One lagged-diffusivity step: solve (H^T H + alpha L(u)) x = H^T v from x0 = u."""
     P = precond_setup(u, h, bc, alpha, beta, kind)
     w = P["w"]
     return pcg(lambda y: normal_apply(y, h, bc, w, alpha),
-               lambda r: precond_apply(r, P), b, u, tol, maxit, hist)
+               lambda r: precond_apply(r, P), b, u, tol, maxit, hist, noise)
 
 
 def tv_deblur(v, h, bc, alpha, beta, outer=10, tol=1e-6, maxit=1000,
-              kind=PC_DFAST, outer_tol=0.0):
+              kind=PC_DFAST, outer_tol=0.0, noise=None):
     """Lagged-diffusivity FP iteration with PCG inner solves, u^0 = v (Sec. 5).
 
     Runs ``outer`` FP steps, or stops earlier when ||u^k - u^{k-1}|| / ||u^k||
@@ -488,7 +504,7 @@ def tv_deblur(v, h, bc, alpha, beta, outer=10, tol=1e-6, maxit=1000,
     stats = {"inner_iters": [], "relres": [], "rel_change": [], "converged": [], "relres_tail": []}
     for _ in range(outer):
         hist = []
-        x, k, rr, ok = fp_step(u, b, h, bc, alpha, beta, kind, tol, maxit, hist)
+        x, k, rr, ok = fp_step(u, b, h, bc, alpha, beta, kind, tol, maxit, hist, noise)
         stats["relres_tail"].append(hist[-2:])
         change = float(np.linalg.norm(x - u) / max(np.linalg.norm(x), 1e-300))
         stats["inner_iters"].append(k)

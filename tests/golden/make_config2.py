@@ -5,8 +5,8 @@ noise 0.5% and 2%; alpha in {1e-4, 1e-3, 1e-2}; beta 1e-2; Gaussian PSF sigma 2 
 
 For each case: the per-step inner iteration counts, the norm of the restored
 image and 64 sampled pixels of it, and the rounding envelope of the oracle
-itself (three more runs on the observation perturbed by a relative 2^-50, see
-tests/parity.py): the per-step spread of the counts and the spread of the
+itself (three more runs with every operator output perturbed by a relative
+2^-50, see tests/parity.py): the per-step spread of the counts and the spread of the
 sampled pixels and of the image. Calls only the oracle, the input generator
 and the perturbation helper. Run:  python tests/golden/make_config2.py
 """
@@ -45,14 +45,14 @@ def run(case):
     import oracle as O
     from paper_1011_5964_gb300 import synth
     sys.path.insert(0, os.path.join(ROOT, "tests"))
-    from parity import N_PERTURBED, count_spread, perturb
+    from parity import N_PERTURBED, count_spread, noise
     h = synth.gaussian_psf(2.0, half_width=7)
     u_true = synth.piecewise_constant_image(N, N, seed=SEED)
     v = synth.add_noise(O.blur(u_true, h, case["bc"]), synth.noise_direction(N, N, SEED), case["noise"])
     args = (h, case["bc"], case["alpha"], 1e-2)
     kw = dict(outer=OUTER, tol=TOL, maxit=5000, kind=case["kind"])
     u, st = O.tv_deblur(v, *args, **kw)
-    pert = [O.tv_deblur(perturb(v, j), *args, **kw) for j in range(1, N_PERTURBED + 1)]
+    pert = [O.tv_deblur(v, *args, noise=noise(j), **kw) for j in range(1, N_PERTURBED + 1)]
     idx = sample_index()
     samp = u[idx[:, 0], idx[:, 1]]
     nu = float(np.linalg.norm(u))

@@ -4,12 +4,14 @@ CG residual trajectories are sensitive to rounding: the FP64 oracle itself,
 run on x86 and on Arm numpy builds, gives relative residuals that differ by a
 few percent after ~50 iterations, and stopping decisions near the tolerance
 can go either way. The plain FP64 GPU path is therefore held to the oracle's
-own rounding envelope: the oracle is re-run on inputs perturbed at the level
-of a few units in the last place (relative 2^-50), and the GPU result must lie
-as close to the unperturbed oracle run as those perturbed runs do (iteration
-counts within their spread plus one, images within ten times their spread).
-Where the perturbed runs agree exactly, this is bit-identical counts and
-images within 1e-12 relative (plus rounding).
+own rounding envelope: the oracle is re-run with every product with A and
+every preconditioner output multiplied by (1 + 2^-50 xi), xi standard normal
+(a few units in the last place, fresh noise each time: a model of rounding
+that differs from numpy's in every operation), and the GPU result must lie as
+close to the unperturbed oracle run as those runs do: iteration counts within
+their spread plus one, images within ten times their spread. Where the
+perturbed runs agree exactly this is identical counts and images within
+1e-12 relative (plus rounding).
 """
 import numpy as np
 
@@ -17,8 +19,13 @@ EPS = 2.0 ** -50
 N_PERTURBED = 3
 
 
+def noise(j):
+    """The oracle's noise hook for perturbed run j: (generator, relative size)."""
+    return (np.random.default_rng(10_000 + j), EPS)
+
+
 def perturb(v, j):
-    """v (1 + 2^-50 xi), xi standard normal with seed j."""
+    """v (1 + 2^-50 xi), xi standard normal with seed j (input-only perturbation)."""
     rng = np.random.default_rng(10_000 + j)
     return np.asarray(v, dtype=np.float64) * (1.0 + EPS * rng.standard_normal(np.shape(v)))
 

@@ -1,9 +1,9 @@
 """GPU parity of pcg_solve and tv_deblur against the FP64 oracle.
 
 * FP64 plans: held to the oracle's own rounding envelope (tests/parity.py):
-  per-FP-step inner iteration counts within the spread of oracle runs on
-  inputs perturbed at a relative 2^-50, plus one; restored images within ten
-  times that spread (at least 1e-12 relative).
+  per-FP-step inner iteration counts within the spread of oracle runs whose
+  operator outputs are perturbed at a relative 2^-50, plus one; restored
+  images within ten times that spread (at least 1e-12 relative).
 * MIXED plans: both sides solve each FP step to ||r||/||r_0|| < 1e-10; the
   restored images agree within 1e-5 relative.
 * Error paths: NaN data (breakdown), maxit too small (no convergence),
@@ -17,7 +17,7 @@ import pytest
 
 import oracle as O
 from paper_1011_5964_gb300 import synth
-from parity import N_PERTURBED, check_counts, count_spread, image_bound, perturb
+from parity import N_PERTURBED, check_counts, count_spread, image_bound, noise
 
 pytestmark = pytest.mark.gpu
 
@@ -47,7 +47,7 @@ def test_pcg_solve_fp64_matches_oracle(tdev, bc, kind):
     v = observe(nr, nc, h, bc, 0.01, 11)
     b = O.blur_adjoint(v, h, bc)
     x_ref, k_ref, rr_ref, ok = O.fp_step(v, b, h, bc, 1e-3, 1e-2, kind, 1e-6, 2000)
-    pert = [O.fp_step(perturb(v, j), b, h, bc, 1e-3, 1e-2, kind, 1e-6, 2000) for j in range(1, N_PERTURBED + 1)]
+    pert = [O.fp_step(v, b, h, bc, 1e-3, 1e-2, kind, 1e-6, 2000, noise=noise(j)) for j in range(1, N_PERTURBED + 1)]
     with pkg.Plan(nr, nc, h, bc=bc, pc=kind, mode="fp64") as plan:
         vt = torch.tensor(v, dtype=torch.float64, device=dev)
         bt = torch.tensor(b, dtype=torch.float64, device=dev)
@@ -70,7 +70,7 @@ def test_config1_deblur_fp64_iteration_counts(tdev, kind):
     v = observe(n, n, h, "ar", 0.01, 1234)
     kw = dict(outer=10, tol=1e-6, kind=kind)
     u_ref, st_ref = O.tv_deblur(v, h, "ar", 1e-3, 1e-2, **kw)
-    pert = [O.tv_deblur(perturb(v, j), h, "ar", 1e-3, 1e-2, **kw) for j in range(1, N_PERTURBED + 1)]
+    pert = [O.tv_deblur(v, h, "ar", 1e-3, 1e-2, noise=noise(j), **kw) for j in range(1, N_PERTURBED + 1)]
     with pkg.Plan(n, n, h, bc="ar", pc=kind, mode="fp64") as plan:
         u, st = plan.deblur(torch.tensor(v, dtype=torch.float64, device=dev), 1e-3, 1e-2, max_outer=10,
                             inner_tol=1e-6)
