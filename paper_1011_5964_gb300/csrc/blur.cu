@@ -104,6 +104,7 @@ __device__ __forceinline__ void finish_pq(CgState* st, double pq) {
         st->alpha = 0.0;
     } else {
         st->alpha = st->rho / pq;
+        st->pending = 1;
     }
 }
 
@@ -118,6 +119,7 @@ template <typename T, int EXT, bool FUSE, bool PUP>
 __global__ void __launch_bounds__(kThreads)
 blur_tile_kernel(const T* __restrict__ x, T* __restrict__ y, int nr, int nc, int mr, int mc,
                  const T* __restrict__ hdense, const int* __restrict__ arange,
+                 const int* __restrict__ runs, const T* __restrict__ runv, int nruns,
                  const T* __restrict__ w, T* p0, T* p1, FuseArgs fa) {
     if (fa.st && fa.st->done) return;
     // FUSE: the direction of this iteration; PUP: old and new direction buffers
@@ -135,7 +137,10 @@ blur_tile_kernel(const T* __restrict__ x, T* __restrict__ y, int nr, int nc, int
     T* sw = ptile + (PUP ? TW * TH : 0);             // FUSE: w tile
     T* sp = sw + (FUSE ? LSW * LSH : 0);             // FUSE: p tile
     T* sh = sp + (FUSE ? LSW * LSH : 0);             // dense PSF, PH x PW
-    int* sr = reinterpret_cast<int*>(sh + PH * PW);  // per column offset: first and last tap row
+    T* pre = sh + PH * PW;                           // runs: row prefix sums, TH x (TW + 1)
+    T* srv = pre + (nruns ? TH * (TW + 1) : 0);      // runs: values
+    int* sr = reinterpret_cast<int*>(srv + nruns);   // per column offset: first and last tap row
+    int* srun = sr + 2 * PW;                         // runs: (a, first b, last b)
     const int r0 = blockIdx.y * BTH - mr, c0 = blockIdx.x * BTW - mc;
     // stage the extended input tile: a plain asynchronous copy where the tile
     // lies inside the image (away from the boundary lines for EXT_ODD), the
@@ -163,6 +168,12 @@ blur_tile_kernel(const T* __restrict__ x, T* __restrict__ y, int nr, int nc, int
     }
     for (int k = threadIdx.x; k < PH * PW; k += blockDim.x) sh[k] = hdense[k];
     for (int k = threadIdx.x; k < 2 * PW; k += blockDim.x) sr[k] = arange[k];
+    for (int k = threadIdx.x; k < nruns; k += blockDim.x) {
+        srv[k] = runv[k];
+        srun[3 * k] = runs[3 * k];
+        srun[3 * k + 1] = runs[3 * k + 1];
+        srun[3 * k + 2] = runs[3 * k + 2];
+    }
     if (!inside) {
 #pragma unroll 4
         for (int idx = threadIdx.x; idx < TW * TH; idx += blockDim.x) {
@@ -189,6 +200,36 @@ blur_tile_kernel(const T* __restrict__ x, T* __restrict__ y, int nr, int nc, int
 #pragma unroll
     for (int k = 0; k < RB; ++k) acc[k] = T(0);
     const int row0 = ty * RB + mr;                   // tile row of output row 0 at a = 0
+    if (nruns) {
+        // PSF rows made of constant runs: sum of a run of x~ along a tile row is a
+        // difference of that row's prefix sums, pre[r][c] = sum_{c' < c} tile[r][c']
+        const int PS = TW + 1;
+        for (int r = threadIdx.x >> 5; r < TH; r += blockDim.x >> 5) {
+            T carry = T(0);
+            if (tx == 0) pre[r * PS] = T(0);
+            for (int c0 = 0; c0 < TW; c0 += 32) {
+                const int c = c0 + tx;
+                T v = c < TW ? tile[r * TW + c] : T(0);
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    const T u = __shfl_up_sync(0xffffffffu, v, o);
+                    if (tx >= o) v += u;
+                }
+                v += carry;
+                if (c < TW) pre[r * PS + c + 1] = v;
+                carry = __shfl_sync(0xffffffffu, v, 31);
+            }
+        }
+        __syncthreads();
+        for (int q = 0; q < nruns; ++q) {
+            const int a = srun[3 * q], bs = srun[3 * q + 1], be = srun[3 * q + 2];
+            const T hv = srv[q];
+            // outputs at tile column tx + mc read x~ columns tx + mc - b, b in [bs, be]
+            const T* p = pre + (row0 - a) * PS + tx + mc;
+#pragma unroll
+            for (int k = 0; k < RB; ++k) acc[k] += hv * (p[k * PS + 1 - bs] - p[k * PS - be]);
+        }
+    } else
     for (int b = -mc; b <= mc; ++b) {
         const int lo = sr[2 * (b + mc)], hi = sr[2 * (b + mc) + 1];
         if (lo > hi) continue;
@@ -239,11 +280,21 @@ blur_tile_kernel(const T* __restrict__ x, T* __restrict__ y, int nr, int nc, int
     }
 }
 
-// odd extension along one axis: returns sign (0 on the boundary line) and index
+// odd extension along one axis: returns the sign (0 on the boundary lines and
+// beyond the single mirror image, where no output reads) and the index
 __device__ __forceinline__ int odd_map(int I, int n, int* idx) {
-    if (I == 0 || I == n - 1) { *idx = 0; return 0; }
-    if (I < 0) { *idx = -I; return -1; }
-    if (I > n - 1) { *idx = 2 * (n - 1) - I; return -1; }
+    *idx = 0;
+    if (I == 0 || I == n - 1) return 0;
+    if (I < 0) {
+        if (-I > n - 2) return 0;
+        *idx = -I;
+        return -1;
+    }
+    if (I > n - 1) {
+        if (2 * (n - 1) - I < 1) return 0;
+        *idx = 2 * (n - 1) - I;
+        return -1;
+    }
     *idx = I;
     return 1;
 }
@@ -275,10 +326,12 @@ ar_adjoint_border_kernel(const T* __restrict__ y, T* __restrict__ out, int nr, i
         const bool top = bid < nseg_r;
         const int l0 = 1 + (top ? bid : bid - nseg_r) * kSeg;
         const int SW = kSeg + 2 * mc;
+        const int cmax = nc - 2 + mc;          // the last column any output of this border reads
         for (int e = threadIdx.x; e < (mr + 1) * SW; e += blockDim.x) {
             const int i = e / SW, cc = e - i * SW;
+            const int J = l0 - mc + cc;
             int ci;
-            const int sg = odd_map(l0 - mc + cc, nc, &ci);
+            const int sg = J <= cmax ? odd_map(J, nc, &ci) : 0;
             const int ri = top ? i : nr - 1 - i;
             strip[e] = sg ? T(sg) * y[(size_t)ri * nc + ci] : T(0);
         }
@@ -296,10 +349,12 @@ ar_adjoint_border_kernel(const T* __restrict__ y, T* __restrict__ out, int nr, i
         const bool left = bid < nseg_c;
         const int k0 = 1 + (left ? bid : bid - nseg_c) * kSeg;
         const int SH = kSeg + 2 * mr;
+        const int rmax = nr - 2 + mr;          // the last row any output of this border reads
         for (int e = threadIdx.x; e < SH * (mc + 1); e += blockDim.x) {
             const int r = e / (mc + 1), j = e - r * (mc + 1);
+            const int I = k0 - mr + r;
             int ri;
-            const int sg = odd_map(k0 - mr + r, nr, &ri);
+            const int sg = I <= rmax ? odd_map(I, nr, &ri) : 0;
             const int cj = left ? j : nc - 1 - j;
             strip[e] = sg ? T(sg) * y[(size_t)ri * nc + cj] : T(0);
         }
@@ -349,10 +404,12 @@ static size_t border_smem(int mr, int mc, size_t elem) {
     return (a > b ? a : b) * elem + 16;
 }
 
-static size_t tile_smem(int mr, int mc, size_t elem, bool fuse, bool pup) {
-    const size_t tile = (size_t)(BTW + 2 * mc) * (BTH + 2 * mr) * elem;
+static size_t tile_smem(int mr, int mc, size_t elem, bool fuse, bool pup, int nruns) {
+    const size_t tw = BTW + 2 * mc, th = BTH + 2 * mr;
+    const size_t tile = tw * th * elem;
     return tile * (pup ? 2 : 1) + (fuse ? 2 * (BTW + 2) * (BTH + 2) * elem : 0) +
-           (size_t)(2 * mr + 1) * (2 * mc + 1) * elem + 2 * (2 * mc + 1) * sizeof(int) + 16;
+           (size_t)(2 * mr + 1) * (2 * mc + 1) * elem + 2 * (2 * mc + 1) * sizeof(int) +
+           (nruns ? th * (tw + 1) * elem + (size_t)nruns * (elem + 3 * sizeof(int)) : 0) + 32;
 }
 
 enum BlurMode { BLUR_PLAIN = 0, BLUR_PUP = 1, BLUR_FUSE = 2 };
@@ -362,7 +419,7 @@ static tvd_status launch_tile(dim3 grid, size_t smem, cudaStream_t s, const T* x
                               const Ops<T>& o, const T* w, T* p0, T* p1, const FuseArgs& fa) {
     TVD_CUDA_TRY((allow_max_smem<blur_tile_kernel<T, EXT, FUSE, PUP>>()));
     blur_tile_kernel<T, EXT, FUSE, PUP><<<grid, kThreads, smem, s>>>(x, y, p.nr, p.nc, p.psf.mr, p.psf.mc, o.hdense,
-                                                                    o.arange, w, p0, p1, fa);
+                                                                    o.arange, o.runs, o.runv, o.nruns, w, p0, p1, fa);
     return TVD_OK;
 }
 
@@ -374,7 +431,7 @@ static tvd_status launch_blur(const tvd_plan_s& p, const Ops<T>& o, bool transpo
     const int nr = p.nr, nc = p.nc, mr = p.psf.mr, mc = p.psf.mc;
     const dim3 grid((nc + BTW - 1) / BTW, (nr + BTH - 1) / BTH);
     const bool fuse = mode == BLUR_FUSE, pup = mode == BLUR_PUP;
-    const size_t smem = tile_smem(mr, mc, sizeof(T), fuse, pup);
+    const size_t smem = tile_smem(mr, mc, sizeof(T), fuse, pup, o.nruns);
     FuseArgs fa{alpha, st, p.red, p.ticket + 1, (fuse && st) ? 1 : 0, 0, 0, 0};
     const int tile_blocks = (int)(grid.x * grid.y);
     const int border_blocks = 2 * ((nc - 2 + kSeg - 1) / kSeg) + 2 * ((nr - 2 + kSeg - 1) / kSeg) + 1;

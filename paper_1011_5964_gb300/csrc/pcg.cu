@@ -85,6 +85,7 @@ cg_init_kernel(const T* __restrict__ b, const T* __restrict__ ax, T* __restrict_
         st->status = TVD_OK;
         st->done = 0;
         st->fresh = 1;
+        st->pending = 0;
         if (!isfinite(s)) {
             st->status = TVD_EBREAKDOWN;
             st->done = 1;
@@ -159,6 +160,7 @@ cg_xr_kernel(T* __restrict__ x, T* __restrict__ r, const T* p0, const T* p1, con
         st->iter += 1;
         st->fresh = 0;
         st->pbuf ^= 1;
+        st->pending = 0;
         if (!isfinite(s)) {
             st->status = TVD_EBREAKDOWN;
             st->done = 1;
@@ -184,6 +186,7 @@ cg_restart_kernel(const T* __restrict__ r, size_t n, CgState* st, double* red, u
     double s;
     if (block_reduce_last((double)part, red, ticket, blockIdx.x, gridDim.x, &s) && threadIdx.x == 0) {
         st->fresh = mode != 1;
+        st->pending = 0;
         if (mode == 0) {
             st->iter = 0;
             st->rho = 0.0;

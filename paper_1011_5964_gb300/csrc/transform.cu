@@ -29,6 +29,7 @@
 #include "common.cuh"
 
 #include <cmath>
+#include <cstdlib>
 
 namespace tvd {
 
@@ -71,6 +72,13 @@ struct LineArgs {
     double* red;
     unsigned int* ticket;
     int* bad;            // COL_EG: set if a spectrum entry is not positive
+    // ROW_FWD on the CG path: the pending x += alpha p, r -= alpha q of the
+    // previous iteration (in0 is r, updated in place) and the stopping test
+    T* xvec;
+    const T* qvec;
+    const T* p0;
+    const T* p1;
+    unsigned int* ticket2;
 };
 
 template <typename T>
@@ -463,6 +471,25 @@ __host__ __device__ constexpr size_t line_extra(int op, size_t lines, size_t n, 
          : 2 * lines * n + P * n;
 }
 
+// End of a CG iteration (the x / r update applied by the next row pass): the
+// residual norm, the iteration count and the stopping test ||r|| / ||r_0|| < tol.
+__device__ __forceinline__ void finish_xr(CgState* st, double rr) {
+    st->rr = rr;
+    st->iter += 1;
+    st->fresh = 0;
+    st->pbuf ^= 1;
+    st->pending = 0;
+    if (!isfinite(rr)) {
+        st->status = TVD_EBREAKDOWN;
+        st->done = 1;
+    } else if (rr < st->tol2) {
+        st->done = 1;
+    } else if (st->iter >= st->maxit) {
+        st->status = TVD_ENOCONV;
+        st->done = 1;
+    }
+}
+
 template <typename T, int BC, int OP>
 __global__ void __launch_bounds__(kThreads) line_kernel(LineArgs<T> a) {
     if (a.st && a.st->done) return;
@@ -519,6 +546,32 @@ __global__ void __launch_bounds__(kThreads) line_kernel(LineArgs<T> a) {
     }
     cp_async_wait_all();
     __syncthreads();
+    // CG path: apply the previous iteration's x += alpha p, r -= alpha q first
+    // (this pass preconditions the updated r), then the stopping test
+    // (pending is the same for every block: the last block clears it only
+    // after all blocks have passed their reduction)
+    if (OP == OP_ROW_FWD && a.xvec && a.st->pending) {
+        const T al = T(a.st->alpha);
+        const T* pv = a.st->pbuf ? a.p0 : a.p1;
+        T* rg = const_cast<T*>(a.in0);
+        T part = T(0);
+        for (int e = threadIdx.x; e < ln; e += blockDim.x) {
+            const int l = e / n, idx = e - l * n;
+            const int g = gline(l);
+            if (g < 0) continue;
+            const size_t o = (size_t)g * a.nc + idx;
+            const int si = l * ns + idx;
+            const T v = raw[si] - al * __ldg(a.qvec + o);
+            raw[si] = v;
+            rg[o] = v;
+            a.xvec[o] += al * __ldg(pv + o);
+            part += v * v;
+        }
+        double sum;
+        if (block_reduce_last((double)part, a.red, a.ticket2, blockIdx.x, gridDim.x, &sum) && threadIdx.x == 0)
+            finish_xr(a.st, sum);
+        __syncthreads();
+    }
     if (OP == OP_ROW_FWD && a.scale) {
         for (int e = threadIdx.x; e < ln; e += blockDim.x) {
             const int l = e / n, si = l * ns + (e - l * n);
@@ -551,7 +604,7 @@ __global__ void __launch_bounds__(kThreads) line_kernel(LineArgs<T> a) {
                 const T lamL = go[(size_t)(2 * pp) * ns + idx] + eo[(size_t)(2 * pp + 1) * ns + idx];
                 const double sp = (double)lam[pp * ns + idx] + a.alpha * (double)lamL;
                 if (!(sp > 1e-300) || !isfinite(sp)) atomicOr(a.bad, 1);
-                a.inv_out[(size_t)g * a.nr + idx] = T(1.0 / sp);   // column-major (see wline_kernel)
+                a.inv_out[(size_t)idx * a.nc + g] = T(1.0 / sp);
             }
         }
         return;
@@ -595,270 +648,6 @@ __global__ void __launch_bounds__(kThreads) line_kernel(LineArgs<T> a) {
     }
 }
 
-// ------------------------------------------------------------- one warp per line pair
-//
-// wline_kernel: the hot preconditioner passes. Each warp owns one pair of
-// lines and two buffers A, B of max(2 ns, 2 L) values in shared memory (the
-// two real lines at stride ns, or one complex line); the FFT stages of a pair
-// are separated by __syncwarp only, so warps run independently and hide each
-// other's latencies. Twiddles and factor tables are read through L1. Column
-// passes stage and store their tile of 2W columns cooperatively (one barrier
-// each); the spectrum is stored transposed (column-major) so that a warp reads
-// its columns' factors contiguously.
-
-template <typename T>
-__device__ __forceinline__ cplx<T> ldg_c(const cplx<T>* p) {
-    cplx<T> v;
-    v.re = __ldg(&p->re);
-    v.im = __ldg(&p->im);
-    return v;
-}
-
-// DST-I (AR) of the pair held in A (lines at stride ns); B is scratch. Returns
-// the buffer (A or B) holding the transformed lines at stride ns; positions 0
-// and n-1 keep their input values.
-template <typename T>
-__device__ T* dst1_warp(T* A, T* B, const LineArgs<T>& a, int lane) {
-    const int n = a.n, ns = a.ns, M = n - 1, N = n - 2;
-    const T* sinh = a.aux;
-    const T x0a = A[0], xna = A[n - 1], x0b = A[ns], xnb = A[ns + n - 1];
-    cplx<T>* Bc = reinterpret_cast<cplx<T>*>(B);
-    for (int j = lane; j < M; j += 32) {
-        const T a0 = j >= 1 ? A[j] : T(0), a1 = j >= 1 ? A[M - j] : T(0);
-        const T b0 = j >= 1 ? A[ns + j] : T(0), b1 = j >= 1 ? A[ns + M - j] : T(0);
-        const T sj = __ldg(sinh + j);
-        Bc[j] = {sj * (a0 + a1) + T(0.5) * (a0 - a1), sj * (b0 + b1) + T(0.5) * (b0 - b1)};
-    }
-    __syncwarp();
-    const cplx<T>* Z = fft_run<T, true>(Bc, reinterpret_cast<cplx<T>*>(A), 1, a.fp, a.tw, false, lane, 32);
-    T* O = (Z == Bc) ? A : B;
-    const T sc = sqrt(T(2) / T(M));
-    const int nodd = (N + 1) / 2, neven = N / 2;
-    const int K = nodd > neven + 1 ? nodd : neven + 1;
-    for (int k = lane; k < K; k += 32) {
-        cplx<T> Fa, Fb;
-        split_pair(Z, k, M, Fa, Fb);
-        if (k >= 1 && k <= neven) {
-            O[2 * k] = -sc * Fa.im;
-            O[ns + 2 * k] = -sc * Fb.im;
-        }
-        if (k < nodd) {                      // odd outputs: recurrence terms, summed below
-            O[2 * k + 1] = k == 0 ? T(0.5) * Fa.re : Fa.re;
-            O[ns + 2 * k + 1] = k == 0 ? T(0.5) * Fb.re : Fb.re;
-        }
-    }
-    if (lane == 0) {
-        O[0] = x0a;
-        O[n - 1] = xna;
-        O[ns] = x0b;
-        O[ns + n - 1] = xnb;
-    }
-    __syncwarp();
-    for (int l = 0; l < 2; ++l) {
-        T* line = O + l * ns;
-        T carry = T(0);
-        for (int c0 = 0; c0 < nodd; c0 += 32) {
-            const int k = c0 + lane;
-            T v = k < nodd ? line[2 * k + 1] : T(0);
-#pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                const T u = __shfl_up_sync(0xffffffffu, v, o);
-                if (lane >= o) v += u;
-            }
-            v += carry;
-            if (k < nodd) line[2 * k + 1] = sc * v;
-            carry = __shfl_sync(0xffffffffu, v, 31);
-        }
-    }
-    __syncwarp();
-    return O;
-}
-
-// Orthonormal DCT-II (inv = false) / DCT-III (inv = true) of the pair in A (R).
-template <typename T>
-__device__ T* dct_warp(T* A, T* B, const LineArgs<T>& a, int lane, bool inv) {
-    const int n = a.n, ns = a.ns, h = (n + 1) / 2;
-    const T* ck = a.aux;
-    const cplx<T>* th = reinterpret_cast<const cplx<T>*>(a.aux + 2 * n);
-    const T* icn = a.aux + 10 * n;
-    cplx<T>* Bc = reinterpret_cast<cplx<T>*>(B);
-    if (!inv) {
-        for (int p = lane; p < n; p += 32) {
-            const int src = p < h ? 2 * p : 2 * (n - 1 - p) + 1;
-            Bc[p] = {A[src], A[ns + src]};
-        }
-    } else {
-        for (int k = lane; k < n; k += 32) {
-            const T s0 = __ldg(icn + k);
-            const T ya = A[k] * s0, yb = A[ns + k] * s0;
-            T yra = T(0), yrb = T(0);
-            if (k > 0) {
-                const T s1 = __ldg(icn + n - k);
-                yra = A[n - k] * s1;
-                yrb = A[ns + n - k] * s1;
-            }
-            const cplx<T> cs = ldg_c(th + k);
-            const cplx<T> Va = {cs.re * ya + cs.im * yra, cs.im * ya - cs.re * yra};
-            const cplx<T> Vb = {cs.re * yb + cs.im * yrb, cs.im * yb - cs.re * yrb};
-            Bc[k] = {Va.re - Vb.im, Va.im + Vb.re};
-        }
-    }
-    __syncwarp();
-    const cplx<T>* Z = fft_run<T, true>(Bc, reinterpret_cast<cplx<T>*>(A), 1, a.fp, a.tw, inv, lane, 32);
-    T* O = (Z == Bc) ? A : B;
-    if (!inv) {
-        for (int k = lane; k < n; k += 32) {
-            cplx<T> Va, Vb;
-            split_pair(Z, k, n, Va, Vb);
-            const cplx<T> cs = ldg_c(th + k);
-            const T c = __ldg(ck + k);
-            O[k] = c * (cs.re * Va.re + cs.im * Va.im);
-            O[ns + k] = c * (cs.re * Vb.re + cs.im * Vb.im);
-        }
-    } else {
-        for (int p = lane; p < n; p += 32) {
-            const int dst = p < h ? 2 * p : 2 * (n - 1 - p) + 1;
-            const cplx<T> z = Z[p];
-            O[dst] = z.re;
-            O[ns + dst] = z.im;
-        }
-    }
-    __syncwarp();
-    return O;
-}
-
-template <typename T, int BC>
-__device__ __forceinline__ T* line_transform_warp(T* A, T* B, const LineArgs<T>& a, int lane, bool inv) {
-    if (BC == BCK_AR) return dst1_warp<T>(A, B, a, lane);
-    return dct_warp<T>(A, B, a, lane, inv);
-}
-
-// Per-warp buffer size in elements of T (even, so each buffer also holds L complex values).
-__host__ __device__ inline int wline_buf(int n, int ns, int L) {
-    const int m = 2 * (ns > L ? ns : L);
-    return m;
-}
-
-template <typename T, int BC, int OP>
-__global__ void __launch_bounds__(256) wline_kernel(LineArgs<T> a) {
-    if (a.st && a.st->done) return;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    const int n = a.n, ns = a.ns;
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, W = blockDim.x >> 5;
-    const int SZ = wline_buf(n, ns, a.L);
-    T* base = reinterpret_cast<T*>(smem_raw);
-    T* A = base + (size_t)w * 2 * SZ;
-    T* B = A + SZ;
-    constexpr bool cols = (OP == OP_COL_SOLVE);
-    if (!cols) {
-        // rows: each warp stages its own two lines
-        const int g0 = (blockIdx.x * W + w) * 2;
-        for (int l = 0; l < 2; ++l) {
-            const int g = g0 + l;
-            T* dst = A + l * ns;
-            if (g < a.nlines) {
-                const T* src = a.in0 + (size_t)g * a.nc;
-                for (int i = lane; i < n; i += 32) cp_async_elem(dst + i, src + i);
-            } else {
-                for (int i = lane; i < n; i += 32) dst[i] = T(0);
-            }
-        }
-        cp_async_wait_all();
-        __syncwarp();
-        if (OP == OP_ROW_FWD && a.scale) {
-            for (int l = 0; l < 2; ++l) {
-                const int g = g0 + l;
-                if (g >= a.nlines) continue;
-                const T* sc = a.scale + (size_t)g * a.nc;
-                for (int i = lane; i < n; i += 32) A[l * ns + i] *= __ldg(sc + i);
-            }
-            __syncwarp();
-        }
-        T* O = line_transform_warp<T, BC>(A, B, a, lane, OP == OP_ROW_INV);
-        T part = T(0);
-        for (int l = 0; l < 2; ++l) {
-            const int g = g0 + l;
-            if (g >= a.nlines) continue;
-            const size_t row = (size_t)g * a.nc;
-            for (int i = lane; i < n; i += 32) {
-                T v = O[l * ns + i];
-                if (OP == OP_ROW_INV && a.scale) v *= __ldg(a.scale + row + i);
-                a.out0[row + i] = v;
-                if (OP == OP_ROW_INV && a.st) part += __ldg(a.rvec + row + i) * v;
-            }
-        }
-        if (OP == OP_ROW_INV && a.st) {
-            double s;
-            if (block_reduce_last((double)part, a.red, a.ticket, blockIdx.x, gridDim.x, &s) && threadIdx.x == 0)
-                finish_rho(a.st, s);
-        }
-        return;
-    }
-    // columns: the block stages 2W columns; warp w owns columns c0 + 2w, c0 + 2w + 1
-    const int c0 = blockIdx.x * 2 * W;
-    const int ncol = 2 * W;
-    for (int e = threadIdx.x; e < n * ncol; e += blockDim.x) {
-        const int i = e / ncol, c = e - i * ncol;
-        T* dst = base + (size_t)(c >> 1) * 2 * SZ + (c & 1) * ns + i;
-        const int g = c0 + c;
-        if (g < a.nlines) cp_async_elem(dst, a.in0 + (size_t)i * a.nc + g);
-        else *dst = T(0);
-    }
-    cp_async_wait_all();
-    __syncthreads();
-    T* O = line_transform_warp<T, BC>(A, B, a, lane, false);
-    // 1 / spectrum, stored column-major: contiguous for this warp's columns
-    for (int l = 0; l < 2; ++l) {
-        const int g = c0 + 2 * w + l;
-        if (g >= a.nlines) continue;
-        const T* sp = a.spec + (size_t)g * a.nr;
-        for (int k = lane; k < n; k += 32) O[l * ns + k] *= __ldg(sp + k);
-    }
-    __syncwarp();
-    // O is A or B; move the product back into A so the inverse starts from A
-    if (O != A) {
-        for (int i = lane; i < 2 * ns; i += 32) A[i] = O[i];
-        __syncwarp();
-    }
-    O = line_transform_warp<T, BC>(A, B, a, lane, true);
-    const int ooff = (int)(O - A);            // the same for every warp (same plan)
-    __syncthreads();
-    for (int e = threadIdx.x; e < n * ncol; e += blockDim.x) {
-        const int i = e / ncol, c = e - i * ncol;
-        const int g = c0 + c;
-        if (g < a.nlines) a.out0[(size_t)i * a.nc + g] = base[(size_t)(c >> 1) * 2 * SZ + ooff + (c & 1) * ns + i];
-    }
-}
-
-template <typename T, int BC, int OP>
-static tvd_status launch_wline(LineArgs<T> a, cudaStream_t s) {
-    constexpr bool cols = (OP == OP_COL_SOLVE);
-    // warps per block: columns need 2W * sizeof(T) >= 32 bytes per staged row
-    int W = cols ? (sizeof(T) == 4 ? 4 : 2) : 2;
-    const int SZ = wline_buf(a.n, a.ns, a.L);
-    size_t smem = (size_t)W * 2 * SZ * sizeof(T);
-    while (W > 1 && smem > 200 * 1024) {
-        W /= 2;
-        smem = (size_t)W * 2 * SZ * sizeof(T);
-    }
-    if (smem > 227 * 1024) {
-        set_error("transform line too long for shared memory");
-        return TVD_EINVAL;
-    }
-    const int pairs = (a.nlines + 1) / 2;
-    const int blocks = cols ? (a.nlines + 2 * W - 1) / (2 * W) : (pairs + W - 1) / W;
-    if (OP == OP_ROW_INV && a.st && blocks > kMaxRedBlocks) {
-        set_error("image too large for the reduction buffer");
-        return TVD_EINVAL;
-    }
-    TVD_CUDA_TRY((allow_max_smem<wline_kernel<T, BC, OP>>()));
-    constexpr int cls = OP == OP_ROW_FWD ? PROF_ROW_FWD : OP == OP_COL_SOLVE ? PROF_COL_SOLVE : PROF_ROW_INV;
-    ProfScope prof(prof_class<T>(cls), s);
-    wline_kernel<T, BC, OP><<<blocks, 32 * W, smem, s>>>(a);
-    TVD_CUDA_TRY(cudaGetLastError());
-    return TVD_OK;
-}
-
 // ------------------------------------------------------------- host side
 
 FftPlan make_fft_plan(int L) {
@@ -885,16 +674,27 @@ static size_t line_smem(const LineArgs<T>& a, int op) {
            sizeof(T) * (lines * a.ns + line_extra(op, lines, a.ns, a.P)) + 64;
 }
 
+// Tuning override of the line pairs per block (TVD_LINE_PAIRS_ROW / _COL,
+// 1..8); 0 = the built-in choice.
+static int env_pairs(const char* name) {
+    const char* v = std::getenv(name);
+    const int P = v ? std::atoi(v) : 0;
+    return P >= 1 && P <= 8 ? P : 0;
+}
+
 template <typename T>
 static void pick_pairs(LineArgs<T>& a, bool cols, int op) {
-    // columns: 2P contiguous elements per row read, at least one 32-byte sector;
-    // rows: about 4096 (float) / 2048 (double) line elements per block
+    // columns: 2 pairs (4 contiguous elements of each row); rows: about 4096
+    // (float) / 2048 (double) line elements per block (measured best of the
+    // 1-4 pair choices at 1024 x 1024)
+    static const int row_env = env_pairs("TVD_LINE_PAIRS_ROW"), col_env = env_pairs("TVD_LINE_PAIRS_COL");
     int P;
     if (cols) {
-        P = (int)((32 + 2 * sizeof(T) - 1) / (2 * sizeof(T)));
+        P = col_env ? col_env : 2;
     } else {
         P = (int)((sizeof(T) == 4 ? 2048 : 1024) / a.n);
         P = P < 1 ? 1 : (P > 8 ? 8 : P);
+        if (row_env) P = row_env;
     }
     const size_t cap = 160 * 1024;
     for (;;) {
@@ -946,13 +746,19 @@ static LineArgs<T> base_args(const tvd_plan_s& p, const Ops<T>& o, bool cols) {
 }
 
 template <typename T>
-tvd_status precond_solve(const tvd_plan_s& p, const Ops<T>& o, const T* r, T* z, CgState* st, cudaStream_t s) {
+tvd_status precond_solve(const tvd_plan_s& p, const Ops<T>& o, const T* r, T* z, CgState* st, cudaStream_t s,
+                         T* x) {
     const bool scaled = (p.pc == TVD_PC_DFAST);
     LineArgs<T> a = base_args<T>(p, o, false);
     a.in0 = r;
     a.out0 = o.t;
     a.scale = scaled ? o.dmh : nullptr;
-    a.st = st;
+    a.st = st;                   // with x also: the CG iteration's pending x / r update and stopping test
+    a.xvec = x;
+    a.qvec = o.q;
+    a.p0 = o.p;
+    a.p1 = o.p2;
+    a.ticket2 = p.ticket + 7;
     LineArgs<T> c = base_args<T>(p, o, true);
     c.in0 = o.t;
     c.out0 = o.t;
@@ -965,13 +771,13 @@ tvd_status precond_solve(const tvd_plan_s& p, const Ops<T>& o, const T* r, T* z,
     b.rvec = r;
     b.st = st;
     if (p.bc == TVD_BC_ANTIREFLECTIVE) {
-        TVD_TRY((launch_wline<T, BCK_AR, OP_ROW_FWD>(a, s)));
-        TVD_TRY((launch_wline<T, BCK_AR, OP_COL_SOLVE>(c, s)));
-        TVD_TRY((launch_wline<T, BCK_AR, OP_ROW_INV>(b, s)));
+        TVD_TRY((launch_line<T, BCK_AR, OP_ROW_FWD>(a, s)));
+        TVD_TRY((launch_line<T, BCK_AR, OP_COL_SOLVE>(c, s)));
+        TVD_TRY((launch_line<T, BCK_AR, OP_ROW_INV>(b, s)));
     } else {
-        TVD_TRY((launch_wline<T, BCK_R, OP_ROW_FWD>(a, s)));
-        TVD_TRY((launch_wline<T, BCK_R, OP_COL_SOLVE>(c, s)));
-        TVD_TRY((launch_wline<T, BCK_R, OP_ROW_INV>(b, s)));
+        TVD_TRY((launch_line<T, BCK_R, OP_ROW_FWD>(a, s)));
+        TVD_TRY((launch_line<T, BCK_R, OP_COL_SOLVE>(c, s)));
+        TVD_TRY((launch_line<T, BCK_R, OP_ROW_INV>(b, s)));
     }
     return TVD_OK;
 }
@@ -1057,8 +863,10 @@ tvd_status lamH2_setup(const tvd_plan_s& p, Ops<T>& o, cudaStream_t s) {
     return TVD_OK;
 }
 
-template tvd_status precond_solve<float>(const tvd_plan_s&, const Ops<float>&, const float*, float*, CgState*, cudaStream_t);
-template tvd_status precond_solve<double>(const tvd_plan_s&, const Ops<double>&, const double*, double*, CgState*, cudaStream_t);
+template tvd_status precond_solve<float>(const tvd_plan_s&, const Ops<float>&, const float*, float*, CgState*,
+                                         cudaStream_t, float*);
+template tvd_status precond_solve<double>(const tvd_plan_s&, const Ops<double>&, const double*, double*, CgState*,
+                                          cudaStream_t, double*);
 template tvd_status spectrum_setup<float>(const tvd_plan_s&, Ops<float>&, double, int*, cudaStream_t);
 template tvd_status spectrum_setup<double>(const tvd_plan_s&, Ops<double>&, double, int*, cudaStream_t);
 template tvd_status lamH2_setup<float>(const tvd_plan_s&, Ops<float>&, cudaStream_t);

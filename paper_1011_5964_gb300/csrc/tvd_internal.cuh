@@ -105,6 +105,7 @@ struct CgState {
     int status;        // tvd_status reached inside the loop
     int fresh;         // 1: the next search direction is p = z (start or restart)
     int pbuf;          // which of the two direction buffers holds the current p
+    int pending;       // 1: alpha is known and x += alpha p, r -= alpha q is still to be applied
 };
 
 // Reduction slots: each reduction writes one double per block, then the last
@@ -119,6 +120,11 @@ struct Ops {
     // offset b the first and last row offset a with a nonzero tap (lo > hi: none)
     T* hdense = nullptr;
     int* arange = nullptr;
+    // PSF rows as runs of one value, (a, first b, last b) and the value; the
+    // stencil sums runs from row prefix sums when that is cheaper (nruns > 0)
+    int nruns = 0;
+    int* runs = nullptr;
+    T* runv = nullptr;
     // AR adjoint border tail weights (Sec. 2 folds), sizes in the plan
     T* crow = nullptr;       // (m_r + 1) x (2 m_c + 1)
     T* ccol = nullptr;       // (2 m_r + 1) x (m_c + 1)
@@ -236,9 +242,12 @@ template <typename T>
 tvd_status lamH2_setup(const tvd_plan_s& p, Ops<T>& o, cudaStream_t s);
 
 // z = X^{-1} r. If st != nullptr, also reduce r^T z into st->rho (and run the
-// CG scalar update that follows it).
+// CG scalar update that follows it). With x (CG path), the first pass applies
+// the pending update x += alpha p, r -= alpha q (r in place, p and q from o)
+// and the stopping test before preconditioning r.
 template <typename T>
-tvd_status precond_solve(const tvd_plan_s& p, const Ops<T>& o, const T* r, T* z, CgState* st, cudaStream_t s);
+tvd_status precond_solve(const tvd_plan_s& p, const Ops<T>& o, const T* r, T* z, CgState* st, cudaStream_t s,
+                         T* x = nullptr);
 
 // CG kernels
 template <typename T>

@@ -9,7 +9,7 @@ every preconditioner output multiplied by (1 + 2^-50 xi), xi standard normal
 (a few units in the last place, fresh noise each time: a model of rounding
 that differs from numpy's in every operation), and the GPU result must lie as
 close to the unperturbed oracle run as those runs do: iteration counts within
-their spread plus one, images within ten times their spread. Where the
+their largest per-step spread plus one, images within ten times their spread. Where the
 perturbed runs agree exactly this is identical counts and images within
 1e-12 relative (plus rounding).
 """
@@ -36,9 +36,17 @@ def count_spread(ref, perturbed):
 
 
 def check_counts(gpu, ref, spread, slack=1):
+    """Every step's count within the run's largest per-step spread plus slack.
+
+    Three perturbed runs estimate the spread of each step poorly (a step can
+    show 0 where its neighbours show 2); the operator, and so the sensitivity
+    of the counts to rounding, is the same in every step of a run, so the
+    largest spread over the steps bounds each of them.
+    """
     assert len(gpu) == len(ref), (gpu, ref)
+    bound = max(spread) + slack
     for k in range(len(ref)):
-        assert abs(gpu[k] - ref[k]) <= spread[k] + slack, (k, gpu, ref, spread)
+        assert abs(gpu[k] - ref[k]) <= bound, (k, gpu, ref, spread)
 
 
 def image_bound(ref, perturbed_images, floor=1e-12):

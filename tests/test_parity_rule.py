@@ -18,10 +18,17 @@ def test_counts_within_spread_plus_one_pass():
     check_counts([11, 22, 31], ref, spread)
 
 
-@pytest.mark.parametrize("gpu", [[12, 20, 30], [10, 23, 30]])
+@pytest.mark.parametrize("gpu", [[13, 20, 30], [10, 23, 30], [10, 20, 27]])
 def test_counts_outside_spread_fail(gpu):
     with pytest.raises(AssertionError):
         check_counts(gpu, [10, 20, 30], [0, 1, 0])
+
+
+def test_count_bound_is_the_runs_largest_spread():
+    # a step whose own spread is 0 gets the run's largest spread (2) plus one
+    check_counts([13, 20, 30], [10, 20, 30], [0, 2, 0])
+    with pytest.raises(AssertionError):
+        check_counts([14, 20, 30], [10, 20, 30], [0, 2, 0])
 
 
 def test_image_bound_scales_with_spread():
