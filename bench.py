@@ -49,7 +49,7 @@ WORKLOAD = "tv_deblur 1024x1024 AR disk-r7(31x31) 1% noise alpha=1e-3 beta=1e-2 
 WORDS_PER_PIXEL = {
     "blur_forward": 2,          # read p, write t = H p
     "blur_adjoint_L": 4,        # read t, p, w; write q = H^T t + alpha L p
-    "precond_row_forward": 3,   # read r, D^-1/2; write t
+    "precond_row_forward": 8,   # read r, q, p, x, D^-1/2; write r, x, t (the fused CG x / r update)
     "precond_column_solve": 3,  # read t, 1/spectrum; write t
     "precond_row_inverse": 4,   # read t, D^-1/2, r; write z
     "spectrum_row": 3,          # read w; write E w, G w
@@ -60,6 +60,17 @@ WORDS_PER_PIXEL = {
     "cg_simple_precond": 3,
     "tv_coefficients": 2,
     "vector_misc": 2,
+}
+
+# DRAM bytes per launch (read + write) of the kernels captured with
+# ncu --set full on this workload, as summarised in
+# profiles/transform_and_blur_kernels_1024_mixed.md. Valid only for the kernel
+# versions captured there: remove an entry when its kernel changes.
+NCU_TRAFFIC = {
+    "precond_row_forward.f32": 21074944,
+    "precond_column_solve.f32": 8534272,
+    "precond_row_inverse.f32": 12691200,
+    "blur_adjoint_L.f32": 12625408,
 }
 
 
@@ -321,7 +332,7 @@ def run_ours(args):
     achieved = bytes_per_launch / avg_s / 1e9
     peak, peak_src = peaks()
     roofline = {"bound": "hbm", "kernel": name, "achieved": achieved, "peak": peak, "unit": "GB/s",
-                "frac": achieved / peak, "traffic": None, "peak_source": peak_src,
+                "frac": achieved / peak, "traffic": NCU_TRAFFIC.get(name), "peak_source": peak_src,
                 "bytes_per_launch": bytes_per_launch, "avg_launch_us": avg_s * 1e6, "launches": klaunch,
                 "share": kms / max(sum(v_[0] for v_ in prof.values()), 1e-12)}
 
