@@ -163,30 +163,56 @@ __device__ __forceinline__ void dft_store(cplx<T> (&v)[R], cplx<T>* __restrict__
     }
 }
 
-// One Stockham stage of radix R over P complex lines, run by the nth threads
-// tid = 0..nth-1 of a block or of a warp.
+// Walks e = threadIdx.x, threadIdx.x + kThreads, ... over P blocks of m
+// entries as (hi, lo) = (e / m, e % m) without a division per step.
+struct Walk {
+    int hi, lo;
+    __device__ __forceinline__ explicit Walk(int m) : hi((int)threadIdx.x / m), lo((int)threadIdx.x - hi * m) {}
+    __device__ __forceinline__ void next(int m) {
+        lo += kThreads;
+        while (lo >= m) {
+            lo -= m;
+            ++hi;
+        }
+    }
+};
+
+// One Stockham stage of radix R over P complex lines of length L, run by the
+// block's kThreads threads. Large radices: G threads share a butterfly's output
+// pairs. Thread t takes share g = t % G of butterflies j = t / G, t / G + S, ...
+// (S = kThreads / G) running over the P lines back to back; j = q Ns + k, and
+// since L / R = ts Ns, stepping to the next line keeps k and lowers q by ts, so
+// the loop divides only once per stage.
 template <typename T, int R>
 __device__ void fft_stage(const cplx<T>* __restrict__ in, cplx<T>* __restrict__ out, int P, int L, int Ns,
-                          const cplx<T>* __restrict__ tw, bool inv, int tid, int nth) {
+                          const cplx<T>* __restrict__ tw, bool inv) {
     const int LR = L / R;
     const int ts = L / (Ns * R);
-    // large radices: G threads share a butterfly's output pairs; G minimises the
-    // rounds x per-item cost (per item: the twiddled inputs, then H / G pairs)
     constexpr int H = (R - 1) / 2;
     int G = 1;
-    if (R > 8) {
+    if constexpr (R > 8) {
+        // G minimises rounds x per-item cost (per item: the R inputs, then H / G pairs)
         int best = 1 << 30;
+#pragma unroll
         for (int g = 1; g <= H; ++g) {
-            const int rounds = (P * LR * g + nth - 1) / nth;
+            const int rounds = (P * LR + kThreads / g - 1) / (kThreads / g);
             const int cost = rounds * (5 * R + 4 * R * ((H + g - 1) / g));
             if (cost < best) { best = cost; G = g; }
         }
     }
-    for (int item = tid; item < P * LR * G; item += nth) {
-        const int bf = item / G, g = item - bf * G;
-        const int pp = bf / LR, j = bf - pp * LR;
+    const int S = kThreads / G;
+    const int t = threadIdx.x;
+    if (t >= S * G) return;
+    const int g = t - (t / G) * G;
+    int j = t / G, pp = 0;
+    while (j >= LR && pp < P) {
+        j -= LR;
+        ++pp;
+    }
+    int q = j / Ns, k = j - (j / Ns) * Ns;
+    const int dq = S / Ns, dk = S - dq * Ns;
+    while (pp < P) {
         const cplx<T>* src = in + (size_t)pp * L;
-        const int k = j % Ns;
         cplx<T> v[R];
         v[0] = src[j];
 #pragma unroll
@@ -195,17 +221,29 @@ __device__ void fft_stage(const cplx<T>* __restrict__ in, cplx<T>* __restrict__ 
             if (inv) w.im = -w.im;
             v[r] = cmul(src[j + r * LR], w);
         }
-        dft_store<T, R>(v, out + (size_t)pp * L + (j / Ns) * Ns * R + k, Ns, tw, LR, inv, g, G);
+        dft_store<T, R>(v, out + (size_t)pp * L + q * Ns * R + k, Ns, tw, LR, inv, g, G);
+        j += S;
+        q += dq;
+        k += dk;
+        if (k >= Ns) {
+            k -= Ns;
+            ++q;
+        }
+        while (j >= LR) {
+            j -= LR;
+            q -= ts;
+            ++pp;
+        }
     }
 }
 
 // Radix without a register kernel: one thread per output, direct sum over R inputs.
 template <typename T>
 __device__ void fft_stage_generic(const cplx<T>* __restrict__ in, cplx<T>* __restrict__ out, int P, int L, int Ns,
-                                  int R, const cplx<T>* __restrict__ tw, bool inv, int tid, int nth) {
+                                  int R, const cplx<T>* __restrict__ tw, bool inv) {
     const int LR = L / R;
     const int ts = L / (Ns * R);
-    for (int e = tid; e < P * L; e += nth) {
+    for (int e = threadIdx.x; e < P * L; e += kThreads) {
         const int pp = e / L, q = e - pp * L;
         const int t = q / LR, j = q - t * LR;
         const int k = j % Ns;
@@ -223,35 +261,31 @@ __device__ void fft_stage_generic(const cplx<T>* __restrict__ in, cplx<T>* __res
     }
 }
 
-// Runs all stages with the nth threads tid = 0..nth-1 of the block (WARP =
-// false, __syncthreads between stages) or of one warp (WARP = true, nth = 32,
-// __syncwarp); returns the buffer holding the result.
-template <typename T, bool WARP>
-__device__ cplx<T>* fft_run(cplx<T>* a, cplx<T>* b, int P, const FftPlan& fp, const cplx<T>* tw, bool inv, int tid,
-                            int nth) {
+// Runs all stages, __syncthreads between them; returns the buffer holding the result.
+template <typename T>
+__device__ cplx<T>* fft_pairs(cplx<T>* a, cplx<T>* b, int P, const FftPlan& fp, const cplx<T>* tw, bool inv) {
     const int L = fp.L;
     int Ns = 1;
     for (int s = 0; s < fp.nstages; ++s) {
         const int R = fp.radix[s];
         switch (R) {
-            case 2: fft_stage<T, 2>(a, b, P, L, Ns, tw, inv, tid, nth); break;
-            case 3: fft_stage<T, 3>(a, b, P, L, Ns, tw, inv, tid, nth); break;
-            case 4: fft_stage<T, 4>(a, b, P, L, Ns, tw, inv, tid, nth); break;
-            case 5: fft_stage<T, 5>(a, b, P, L, Ns, tw, inv, tid, nth); break;
-            case 7: fft_stage<T, 7>(a, b, P, L, Ns, tw, inv, tid, nth); break;
-            case 8: fft_stage<T, 8>(a, b, P, L, Ns, tw, inv, tid, nth); break;
-            case 9: fft_stage<T, 9>(a, b, P, L, Ns, tw, inv, tid, nth); break;
-            case 11: fft_stage<T, 11>(a, b, P, L, Ns, tw, inv, tid, nth); break;
-            case 13: fft_stage<T, 13>(a, b, P, L, Ns, tw, inv, tid, nth); break;
-            case 17: fft_stage<T, 17>(a, b, P, L, Ns, tw, inv, tid, nth); break;
-            case 19: fft_stage<T, 19>(a, b, P, L, Ns, tw, inv, tid, nth); break;
-            case 23: fft_stage<T, 23>(a, b, P, L, Ns, tw, inv, tid, nth); break;
-            case 29: fft_stage<T, 29>(a, b, P, L, Ns, tw, inv, tid, nth); break;
-            case 31: fft_stage<T, 31>(a, b, P, L, Ns, tw, inv, tid, nth); break;
-            default: fft_stage_generic<T>(a, b, P, L, Ns, R, tw, inv, tid, nth); break;
+            case 2: fft_stage<T, 2>(a, b, P, L, Ns, tw, inv); break;
+            case 3: fft_stage<T, 3>(a, b, P, L, Ns, tw, inv); break;
+            case 4: fft_stage<T, 4>(a, b, P, L, Ns, tw, inv); break;
+            case 5: fft_stage<T, 5>(a, b, P, L, Ns, tw, inv); break;
+            case 7: fft_stage<T, 7>(a, b, P, L, Ns, tw, inv); break;
+            case 8: fft_stage<T, 8>(a, b, P, L, Ns, tw, inv); break;
+            case 9: fft_stage<T, 9>(a, b, P, L, Ns, tw, inv); break;
+            case 11: fft_stage<T, 11>(a, b, P, L, Ns, tw, inv); break;
+            case 13: fft_stage<T, 13>(a, b, P, L, Ns, tw, inv); break;
+            case 17: fft_stage<T, 17>(a, b, P, L, Ns, tw, inv); break;
+            case 19: fft_stage<T, 19>(a, b, P, L, Ns, tw, inv); break;
+            case 23: fft_stage<T, 23>(a, b, P, L, Ns, tw, inv); break;
+            case 29: fft_stage<T, 29>(a, b, P, L, Ns, tw, inv); break;
+            case 31: fft_stage<T, 31>(a, b, P, L, Ns, tw, inv); break;
+            default: fft_stage_generic<T>(a, b, P, L, Ns, R, tw, inv); break;
         }
-        if (WARP) __syncwarp();
-        else __syncthreads();
+        __syncthreads();
         cplx<T>* t = a;
         a = b;
         b = t;
@@ -260,10 +294,6 @@ __device__ cplx<T>* fft_run(cplx<T>* a, cplx<T>* b, int P, const FftPlan& fp, co
     return a;
 }
 
-template <typename T>
-__device__ cplx<T>* fft_pairs(cplx<T>* a, cplx<T>* b, int P, const FftPlan& fp, const cplx<T>* tw, bool inv) {
-    return fft_run<T, false>(a, b, P, fp, tw, inv, threadIdx.x, blockDim.x);
-}
 
 // ------------------------------------------------------------- line transforms in shared memory
 // raw[l * ns + idx]: 2P real lines of length n at the odd stride ns. bufA, bufB: P complex lines of length L.
@@ -281,8 +311,8 @@ template <typename T>
 __device__ void dst1_lines(T* raw, cplx<T>* bufA, cplx<T>* bufB, const LineArgs<T>& a, const cplx<T>* tw) {
     const int n = a.n, ns = a.ns, M = n - 1, N = n - 2, P = a.P;
     const T* sinh = a.aux;                    // slot0
-    for (int e = threadIdx.x; e < P * M; e += blockDim.x) {
-        const int pp = e / M, j = e - pp * M;
+    for (Walk w(M); w.hi < P; w.next(M)) {
+        const int pp = w.hi, j = w.lo;
         const T* xa = raw + (size_t)(2 * pp) * ns;
         const T* xb = xa + ns;
         const T a0 = j >= 1 ? xa[j] : T(0), a1 = j >= 1 ? xa[M - j] : T(0);
@@ -299,8 +329,8 @@ __device__ void dst1_lines(T* raw, cplx<T>* bufA, cplx<T>* bufB, const LineArgs<
     const int neven = N / 2;                  // F_2, F_4, ...
     // even outputs and the R_k terms of the odd recurrence (into scan[line][k])
     const int K = nodd > neven + 1 ? nodd : neven + 1;
-    for (int e = threadIdx.x; e < P * K; e += blockDim.x) {
-        const int pp = e / K, k = e - pp * K;
+    for (Walk w(K); w.hi < P; w.next(K)) {
+        const int pp = w.hi, k = w.lo;
         cplx<T> Fa, Fb;
         split_pair(Z + (size_t)pp * M, k, M, Fa, Fb);
         if (k >= 1 && k <= neven) {
@@ -314,7 +344,7 @@ __device__ void dst1_lines(T* raw, cplx<T>* bufA, cplx<T>* bufB, const LineArgs<
     }
     __syncthreads();
     // inclusive prefix sums of scan, one warp per line
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = kThreads >> 5;
     for (int l = wid; l < 2 * P; l += nw) {
         T carry = T(0);
         for (int c0 = 0; c0 < nodd; c0 += 32) {
@@ -341,15 +371,15 @@ __device__ void dct_lines(T* raw, cplx<T>* bufA, cplx<T>* bufB, const LineArgs<T
     const cplx<T>* th = reinterpret_cast<const cplx<T>*>(a.aux + 2 * n);  // slot1 (cos, sin)(pi k / 2n)
     const T* icn = a.aux + 10 * n;                                    // slot5 1/(n c_k)
     if (!inv) {
-        for (int e = threadIdx.x; e < P * n; e += blockDim.x) {
-            const int pp = e / n, p = e - pp * n;
+        for (Walk w(n); w.hi < P; w.next(n)) {
+            const int pp = w.hi, p = w.lo;
             const int src = p < h ? 2 * p : 2 * (n - 1 - p) + 1;
             bufA[(size_t)pp * n + p] = {raw[(size_t)(2 * pp) * ns + src], raw[(size_t)(2 * pp + 1) * ns + src]};
         }
         __syncthreads();
         const cplx<T>* Z = fft_pairs<T>(bufA, bufB, P, a.fp, tw, false);
-        for (int e = threadIdx.x; e < P * n; e += blockDim.x) {
-            const int pp = e / n, k = e - pp * n;
+        for (Walk w(n); w.hi < P; w.next(n)) {
+            const int pp = w.hi, k = w.lo;
             cplx<T> Va, Vb;
             split_pair(Z + (size_t)pp * n, k, n, Va, Vb);
             const cplx<T> cs = th[k];
@@ -359,8 +389,8 @@ __device__ void dct_lines(T* raw, cplx<T>* bufA, cplx<T>* bufB, const LineArgs<T
         }
         __syncthreads();
     } else {
-        for (int e = threadIdx.x; e < P * n; e += blockDim.x) {
-            const int pp = e / n, k = e - pp * n;
+        for (Walk w(n); w.hi < P; w.next(n)) {
+            const int pp = w.hi, k = w.lo;
             const T* xa = raw + (size_t)(2 * pp) * ns;
             const T* xb = xa + ns;
             const T s0 = __ldg(icn + k);
@@ -378,8 +408,8 @@ __device__ void dct_lines(T* raw, cplx<T>* bufA, cplx<T>* bufB, const LineArgs<T
         }
         __syncthreads();
         const cplx<T>* Z = fft_pairs<T>(bufA, bufB, P, a.fp, tw, true);
-        for (int e = threadIdx.x; e < P * n; e += blockDim.x) {
-            const int pp = e / n, p = e - pp * n;
+        for (Walk w(n); w.hi < P; w.next(n)) {
+            const int pp = w.hi, p = w.lo;
             const int dst = p < h ? 2 * p : 2 * (n - 1 - p) + 1;
             const cplx<T> z = Z[(size_t)pp * n + p];
             raw[(size_t)(2 * pp) * ns + dst] = z.re;
@@ -394,14 +424,14 @@ template <typename T, int BC>
 __device__ void eg_lines(const T* raw, cplx<T>* bufA, cplx<T>* bufB, T* eo, T* go, const LineArgs<T>& a,
                          const cplx<T>* tw) {
     const int n = a.n, ns = a.ns, P = a.P, L = a.L;
-    for (int e = threadIdx.x; e < P * L; e += blockDim.x) {
-        const int pp = e / L, j = e - pp * L;
+    for (Walk w(L); w.hi < P; w.next(L)) {
+        const int pp = w.hi, j = w.lo;
         bufA[(size_t)pp * L + j] = {raw[(size_t)(2 * pp) * ns + j], raw[(size_t)(2 * pp + 1) * ns + j]};
     }
     __syncthreads();
     const cplx<T>* Z = fft_pairs<T>(bufA, bufB, P, a.fp, tw, false);
-    for (int e = threadIdx.x; e < P * n; e += blockDim.x) {
-        const int pp = e / n, k = e - pp * n;
+    for (Walk w(n); w.hi < P; w.next(n)) {
+        const int pp = w.hi, k = w.lo;
         const cplx<T>* Zp = Z + (size_t)pp * L;
         const T* fa = raw + (size_t)(2 * pp) * ns;
         const T* fb = fa + ns;
@@ -490,12 +520,19 @@ __device__ __forceinline__ void finish_xr(CgState* st, double rr) {
     }
 }
 
+// Resident blocks per SM the register allocation aims for (tuning: more blocks
+// hide more latency, at the price of spilled large-radix butterflies).
+#ifndef TVD_LINE_MINB
+#define TVD_LINE_MINB 2
+#endif
+
 template <typename T, int BC, int OP>
-__global__ void __launch_bounds__(kThreads) line_kernel(LineArgs<T> a) {
+__global__ void __launch_bounds__(kThreads, TVD_LINE_MINB) line_kernel(LineArgs<T> a) {
     if (a.st && a.st->done) return;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int n = a.n, ns = a.ns, P = a.P, L = a.L;
-    const int lines = 2 * P;
+    const int lines = 2 * P;       // a power of two
+    const int lsh = __ffs(lines) - 1;
     const int ln = lines * n;      // line elements of the block
     const int lns = lines * ns;    // shared-memory size of one set of lines
     cplx<T>* tw = reinterpret_cast<cplx<T>*>(smem_raw);
@@ -514,10 +551,10 @@ __global__ void __launch_bounds__(kThreads) line_kernel(LineArgs<T> a) {
 
     // ---- stage the lines and their per-pixel factors: asynchronous copies,
     // all of them in flight before the first wait
-    for (int i = threadIdx.x; i < L; i += blockDim.x) cp_async_elem(&tw[i].re, &a.tw[i].re), cp_async_elem(&tw[i].im, &a.tw[i].im);
+    for (int i = threadIdx.x; i < L; i += kThreads) cp_async_elem(&tw[i].re, &a.tw[i].re), cp_async_elem(&tw[i].im, &a.tw[i].im);
     if (!cols) {
-        for (int e = threadIdx.x; e < ln; e += blockDim.x) {
-            const int l = e / n, idx = e - l * n;
+        for (Walk w(n); w.hi < lines; w.next(n)) {
+            const int l = w.hi, idx = w.lo;
             const int si = l * ns + idx;
             const int g = gline(l);
             if (g < 0) {
@@ -530,8 +567,8 @@ __global__ void __launch_bounds__(kThreads) line_kernel(LineArgs<T> a) {
             if (OP == OP_ROW_INV && a.st) cp_async_elem(ex + lns + si, a.rvec + o);
         }
     } else {
-        for (int e = threadIdx.x; e < ln; e += blockDim.x) {
-            const int idx = e / lines, l = e - idx * lines;
+        for (int e = threadIdx.x; e < ln; e += kThreads) {
+            const int idx = e >> lsh, l = e & (lines - 1);
             const int g = gline(l);
             const int si = l * ns + idx;
             if (g < 0) {
@@ -555,8 +592,8 @@ __global__ void __launch_bounds__(kThreads) line_kernel(LineArgs<T> a) {
         const T* pv = a.st->pbuf ? a.p0 : a.p1;
         T* rg = const_cast<T*>(a.in0);
         T part = T(0);
-        for (int e = threadIdx.x; e < ln; e += blockDim.x) {
-            const int l = e / n, idx = e - l * n;
+        for (Walk w(n); w.hi < lines; w.next(n)) {
+            const int l = w.hi, idx = w.lo;
             const int g = gline(l);
             if (g < 0) continue;
             const size_t o = (size_t)g * a.nc + idx;
@@ -573,8 +610,8 @@ __global__ void __launch_bounds__(kThreads) line_kernel(LineArgs<T> a) {
         __syncthreads();
     }
     if (OP == OP_ROW_FWD && a.scale) {
-        for (int e = threadIdx.x; e < ln; e += blockDim.x) {
-            const int l = e / n, si = l * ns + (e - l * n);
+        for (Walk w(n); w.hi < lines; w.next(n)) {
+            const int l = w.hi, si = l * ns + w.lo;
             if (gline(l) >= 0) raw[si] *= ex[si];
         }
         __syncthreads();
@@ -586,8 +623,8 @@ __global__ void __launch_bounds__(kThreads) line_kernel(LineArgs<T> a) {
         T* go = ex + lns;
         eg_lines<T, BC>(raw, bufA, bufB, eo, go, a, tw);
         if (OP == OP_ROW_EG) {
-            for (int e = threadIdx.x; e < ln; e += blockDim.x) {
-                const int l = e / n, idx = e - l * n;
+            for (Walk w(n); w.hi < lines; w.next(n)) {
+                const int l = w.hi, idx = w.lo;
                 const int g = gline(l);
                 if (g < 0) continue;
                 const size_t o = (size_t)g * a.nc + idx;
@@ -597,8 +634,8 @@ __global__ void __launch_bounds__(kThreads) line_kernel(LineArgs<T> a) {
         } else {
             // Lambda_L column = G(A col) + E(B col); spec = lamH2 + alpha Lambda_L
             const T* lam = ex + 2 * lns;
-            for (int e = threadIdx.x; e < P * n; e += blockDim.x) {
-                const int idx = e / P, pp = e - idx * P;
+            for (int e = threadIdx.x; e < P * n; e += kThreads) {
+                const int idx = e >> (lsh - 1), pp = e & (P - 1);
                 const int g = gline(2 * pp);
                 if (g < 0) continue;
                 const T lamL = go[(size_t)(2 * pp) * ns + idx] + eo[(size_t)(2 * pp + 1) * ns + idx];
@@ -614,15 +651,15 @@ __global__ void __launch_bounds__(kThreads) line_kernel(LineArgs<T> a) {
     else dct_lines<T>(raw, bufA, bufB, a, tw, OP == OP_ROW_INV);
 
     if (OP == OP_COL_SOLVE) {
-        for (int e = threadIdx.x; e < ln; e += blockDim.x) {
-            const int l = e / n, si = l * ns + (e - l * n);
+        for (Walk w(n); w.hi < lines; w.next(n)) {
+            const int l = w.hi, si = l * ns + w.lo;
             if (gline(l) >= 0) raw[si] *= ex[si];
         }
         __syncthreads();
         if (BC == BCK_AR) dst1_lines<T>(raw, bufA, bufB, a, tw);
         else dct_lines<T>(raw, bufA, bufB, a, tw, true);
-        for (int e = threadIdx.x; e < ln; e += blockDim.x) {
-            const int idx = e / lines, l = e - idx * lines;
+        for (int e = threadIdx.x; e < ln; e += kThreads) {
+            const int idx = e >> lsh, l = e & (lines - 1);
             const int g = gline(l);
             if (g >= 0) a.out0[(size_t)idx * a.nc + g] = raw[(size_t)l * ns + idx];
         }
@@ -630,8 +667,8 @@ __global__ void __launch_bounds__(kThreads) line_kernel(LineArgs<T> a) {
     }
     // ---- row store (ROW_FWD / ROW_INV)
     T part = T(0);
-    for (int e = threadIdx.x; e < ln; e += blockDim.x) {
-        const int l = e / n, idx = e - l * n;
+    for (Walk w(n); w.hi < lines; w.next(n)) {
+        const int l = w.hi, idx = w.lo;
         const int g = gline(l);
         if (g < 0) continue;
         const size_t o = (size_t)g * a.nc + idx;
@@ -696,6 +733,7 @@ static void pick_pairs(LineArgs<T>& a, bool cols, int op) {
         P = P < 1 ? 1 : (P > 8 ? 8 : P);
         if (row_env) P = row_env;
     }
+    while (P & (P - 1)) P &= P - 1;   // a power of two (column index maps use shifts)
     const size_t cap = 160 * 1024;
     for (;;) {
         a.P = P;
