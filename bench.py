@@ -146,6 +146,54 @@ def make_inputs():
     return np, synth, h, u_true, z
 
 
+BATCH = 96
+BATCH_WORKERS = 16
+
+
+def batched_leg(pkg, torch, dev, synth):
+    """Config of many independent images: BATCH items (sides from {128, ..., 512},
+    Gaussian sigma ~ U[1,3], alpha log-uniform in [1e-4, 1e-2], 1% noise, AR,
+    D_M, MIXED, 10 FP steps) through tv_deblur_batched, plans made beforehand.
+    Timed by the host clock around the call (which returns when every item is
+    done), after one untimed pass that captures each plan's CUDA graphs."""
+    import math
+    items = synth.batch_items(BATCH, seed=1000)
+    t0 = time.perf_counter()
+    plans, vs = [], []
+    for it in items:
+        n = it["n"]
+        h = synth.gaussian_psf(it["sigma"], half_width=int(math.ceil(3.0 * it["sigma"])))
+        u_true = torch.tensor(synth.piecewise_constant_image(n, n, seed=it["seed"]), dtype=torch.float64, device=dev)
+        with pkg.Plan(n, n, h, bc="ar", pc="dfast", mode="fp64") as p64:
+            hu = p64.blur(u_true).cpu().numpy()
+        v = synth.add_noise(hu, synth.noise_direction(n, n, it["seed"]), it["noise"])
+        vs.append(torch.tensor(v, dtype=torch.float64, device=dev))
+        plans.append(pkg.Plan(n, n, h, bc="ar", pc="dfast", mode="mixed"))
+    torch.cuda.synchronize()
+    setup_s = time.perf_counter() - t0
+    alphas = [it["alpha"] for it in items]
+    betas = [it["beta"] for it in items]
+    outs = [torch.empty_like(v) for v in vs]
+    res = {}
+    for workers in (1, BATCH_WORKERS):
+        pkg.deblur_batched(plans, vs, alphas, betas, OUTER, TOL, 5000, outs, workers)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        _, stats = pkg.deblur_batched(plans, vs, alphas, betas, OUTER, TOL, 5000, outs, workers)
+        torch.cuda.synchronize()
+        res[workers] = (time.perf_counter() - t0, sum(sum(st["inner_iters"]) for st in stats))
+    for p in plans:
+        p.close()
+    pixels = sum(it["n"] * it["n"] for it in items)
+    return {"workload": f"{BATCH} independent tv_deblur, sides from {{128,192,256,384,512}} "
+                        f"({pixels / 1e6:.2f} Mpixel in all), Gaussian sigma U[1,3], alpha log-U[1e-4,1e-2], "
+                        f"beta 1e-2, 1% noise, AR, D_M, MIXED, 10 FP steps, tol 1e-6",
+            "deblurs_per_s": BATCH / res[BATCH_WORKERS][0], "workers": BATCH_WORKERS,
+            "pcg_iters_per_s": res[BATCH_WORKERS][1] / res[BATCH_WORKERS][0],
+            "one_stream_deblurs_per_s": BATCH / res[1][0], "plan_setup_s": setup_s,
+            "timing": "host clock around the call, inputs resident"}
+
+
 def peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     try:
@@ -375,6 +423,9 @@ def run_ours(args):
             "e2e": {"value": ws * 1000.0 * args.steps / e2e_ms, "unit": "deblurs/s",
                     "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes}}
 
+    if not args.no_batch:
+        line["batched"] = batched_leg(pkg, torch, dev, synth)
+
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         iters_per_deblur, src = oracle_iters_per_deblur()
         if iters_per_deblur is None:
@@ -403,6 +454,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-batch", action="store_true", help="skip the batch-of-independent-images leg")
     ap.add_argument("--only-chosen", action="store_true",
                     help="time the chosen form only (no plain FP64, e2e, per-kernel or CPU legs); for profiler runs")
     args = ap.parse_args()

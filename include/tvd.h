@@ -180,6 +180,38 @@ tvd_status tv_deblur(tvd_plan plan, const void* v, double alpha, double beta,
                      int max_outer, double outer_tol, double inner_tol, int inner_maxit,
                      void* u_out, tvd_stats* stats, void* stream);
 
+/*
+ * tv_deblur_batched -- tv_deblur of many independent problems at once (the
+ * batched solve of a set of images, each with its own size, PSF and
+ * parameters; independent problems share nothing, Sec. 5's FP iteration runs
+ * per item). Items are taken largest first by `workers` host threads, each
+ * owning a CUDA stream, so the kernels of different items overlap on the GPU.
+ * Each item runs exactly tv_deblur(plan, v, alpha, beta, max_outer, 0,
+ * inner_tol, inner_maxit, u_out, ...) on its worker's stream: results equal
+ * those of separate tv_deblur calls.
+ *   items       count caller-owned descriptors (host memory); each names a
+ *               plan created by tvd_plan_create. Items that name the same plan
+ *               run one after another on one worker.
+ *   workers     host threads / streams (1..64; 0 selects 8).
+ *   stream      the caller's stream: every item starts after the work queued
+ *               on it so far. The call returns when every item has finished.
+ * Per-item results go to items[i].status and, when non-NULL,
+ * items[i].inner_iters (max_outer entries). Returns TVD_EINVAL for invalid
+ * arguments (nothing run), else the first non-OK item status in item order
+ * (TVD_OK when all items converged), with that item's message.
+ */
+typedef struct {
+    tvd_plan plan;        /* the item's plan (its size, PSF, BC, preconditioner, mode) */
+    const void* v;        /* DOUBLE device array, the observation */
+    void* u_out;          /* DOUBLE device array, the restored image (may equal v) */
+    double alpha, beta;
+    int* inner_iters;     /* optional host array of max_outer entries (NULL: not reported) */
+    tvd_status status;    /* out: the item's tv_deblur status */
+} tvd_batch_item;
+
+tvd_status tv_deblur_batched(tvd_batch_item* items, int count, int max_outer, double inner_tol,
+                             int inner_maxit, int workers, void* stream);
+
 /* Message of the last failed call on the calling thread ("" if none). */
 const char* tvd_last_error(void);
 

@@ -34,7 +34,7 @@ STATUS_NAMES = ["TVD_OK", "TVD_EINVAL", "TVD_EPSF_ASYM", "TVD_EPSF_SIZE", "TVD_E
 # Function names of the C ABI, in include/tvd.h order.
 ABI_FUNCTIONS = ["tvd_plan_create", "tvd_plan_destroy", "ar_blur_apply", "tv_operator_apply",
                  "tau_precond_setup", "tau_precond_solve", "pcg_solve", "tv_deblur",
-                 "tvd_normal_apply_noalloc", "tvd_last_error", "tvd_version", "tvd_kernel_launches",
+                 "tv_deblur_batched", "tvd_normal_apply_noalloc", "tvd_last_error", "tvd_version", "tvd_kernel_launches",
                  "tvd_profile_enable", "tvd_profile_classes", "tvd_profile_name", "tvd_profile_read"]
 
 
@@ -52,6 +52,12 @@ class _Stats(ctypes.Structure):
                 ("cap", ctypes.c_int), ("total_inner_iters", ctypes.c_int),
                 ("refinement_sweeps", ctypes.c_int), ("last_relres", ctypes.c_double),
                 ("last_rel_change", ctypes.c_double), ("last_status", ctypes.c_int)]
+
+
+class _BatchItem(ctypes.Structure):
+    _fields_ = [("plan", ctypes.c_void_p), ("v", ctypes.c_void_p), ("u_out", ctypes.c_void_p),
+                ("alpha", ctypes.c_double), ("beta", ctypes.c_double),
+                ("inner_iters", ctypes.POINTER(ctypes.c_int)), ("status", ctypes.c_int)]
 
 
 _lib = None
@@ -76,6 +82,7 @@ def load_library(path: str | None = None) -> ctypes.CDLL:
     lib.pcg_solve.argtypes = [vp, vp, d, d, vp, vp, d, i, ctypes.POINTER(i), ctypes.POINTER(d), vp]
     lib.tv_deblur.argtypes = [vp, vp, d, d, i, d, d, i, vp, ctypes.POINTER(_Stats), vp]
     lib.tvd_normal_apply_noalloc.argtypes = [i, i, ctypes.POINTER(d), i, i, i, vp, d, d, vp, vp, vp]
+    lib.tv_deblur_batched.argtypes = [ctypes.POINTER(_BatchItem), i, i, d, i, i, vp]
     lib.tvd_last_error.restype = ctypes.c_char_p
     lib.tvd_version.restype = ctypes.c_char_p
     lib.tvd_kernel_launches.restype = ctypes.c_ulonglong
@@ -234,6 +241,37 @@ def normal_apply_noalloc(psf, u_lag, alpha: float, beta: float, x, y=None, bc: s
     return out
 
 
+def deblur_batched(plans, vs, alphas, betas, max_outer: int = 10, inner_tol: float = 1e-6,
+                   inner_maxit: int = 1000, outs=None, workers: int = 8):
+    """tv_deblur of independent problems at once (one Plan per item; float64 CUDA tensors).
+
+    Items run on `workers` host threads with a CUDA stream each, largest
+    first; each item's result equals that of plan.deblur(v, alpha, beta, ...).
+    Returns (list of u, list of per-item dicts {"status", "inner_iters"}).
+    """
+    import torch
+    lib = load_library()
+    count = len(plans)
+    if not (len(vs) == len(alphas) == len(betas) == count):
+        raise ValueError("plans, vs, alphas and betas must have the same length")
+    us = [torch.empty_like(v) for v in vs] if outs is None else list(outs)
+    cap = max(int(max_outer), 1)
+    iters = [(ctypes.c_int * cap)() for _ in range(count)]
+    arr = (_BatchItem * max(count, 1))()
+    for i, pl in enumerate(plans):
+        arr[i].plan = pl.handle
+        arr[i].v = _ptr(vs[i], torch.float64, pl.n)
+        arr[i].u_out = _ptr(us[i], torch.float64, pl.n)
+        arr[i].alpha = float(alphas[i])
+        arr[i].beta = float(betas[i])
+        arr[i].inner_iters = ctypes.cast(iters[i], ctypes.POINTER(ctypes.c_int))
+        arr[i].status = 0
+    st = lib.tv_deblur_batched(arr, count, int(max_outer), float(inner_tol), int(inner_maxit), int(workers),
+                               _stream())
+    _check(st, allow=(TVD_ENOCONV,))
+    return us, [{"status": arr[i].status, "inner_iters": list(iters[i][:max_outer])} for i in range(count)]
+
+
 def kernel_launches() -> int:
     """CUDA kernels launched by the library in this process so far."""
     return int(load_library().tvd_kernel_launches())
@@ -279,3 +317,8 @@ def pcg_solve(plan: Plan, u_lag, alpha, beta, b, x, tol=1e-6, maxit=1000):
 
 def tv_deblur(plan: Plan, v, alpha, beta, max_outer=10, outer_tol=0.0, inner_tol=1e-6, inner_maxit=1000, u=None):
     return plan.deblur(v, alpha, beta, max_outer, outer_tol, inner_tol, inner_maxit, u)
+
+
+def tv_deblur_batched(plans, vs, alphas, betas, max_outer=10, inner_tol=1e-6, inner_maxit=1000, outs=None,
+                      workers=8):
+    return deblur_batched(plans, vs, alphas, betas, max_outer, inner_tol, inner_maxit, outs, workers)

@@ -465,9 +465,12 @@ static tvd_status solve_mixed(tvd_plan_s& p, double alpha, const double* b, doub
     const double delta2 = 1e-8;   // replace once the float residual fell by 1e-4
     double rr_ref = rr0;
     res->relres = 1.0;
+    // each float CG segment stops on the device once its residual fell by delta2
+    // (or below the target): the replacement point is then an iteration count,
+    // independent of how often the host polls
     TVD_TRY(cast_d2f(p.res, p.f.r, n, s));
     TVD_TRY(fill_zero_f(p.f.x, n, s));
-    TVD_TRY(cg_restart<float>(p, p.f.r, p.state, target, maxit, 0, s));
+    TVD_TRY(cg_restart<float>(p, p.f.r, p.state, std::max(target, delta2 * rr_ref), maxit, 0, s));
     const bool use_graph = !profiling_enabled();
     if (use_graph) TVD_TRY(ensure_graph<float>(p, p.f, alpha, nullptr, p.f.x));
     auto& g = p.graph[0];
@@ -487,7 +490,7 @@ static tvd_status solve_mixed(tvd_plan_s& p, double alpha, const double* b, doub
         TVD_TRY(read_state<float>(p, s));
         const CgState h = *p.hstate;
         res->iters = h.iter;
-        if (!h.done && h.rr >= delta2 * rr_ref) {
+        if (!h.done) {
             if (h.iter == last_iter) {   // the kernels always advance a running solve
                 set_error("CG made no progress between two checks");
                 return TVD_ECUDA;
@@ -517,7 +520,7 @@ static tvd_status solve_mixed(tvd_plan_s& p, double alpha, const double* b, doub
         const int mode = (rr < 4.0 * h.rr) ? 1 : 2;
         rr_ref = rr;
         TVD_TRY(cast_d2f(p.res, p.f.r, n, s));
-        TVD_TRY(cg_restart<float>(p, p.f.r, p.state, target, maxit, mode, s));
+        TVD_TRY(cg_restart<float>(p, p.f.r, p.state, std::max(target, delta2 * rr_ref), maxit, mode, s));
     }
     hint = res->iters;
     return TVD_OK;

@@ -64,3 +64,15 @@ def test_plan_create_rejects_bad_arguments_before_touching_the_gpu(lib):
     out = ctypes.c_void_p()
     assert lib.tvd_plan_create(ctypes.byref(out), 2, 16, hp, 3, 3, 1, 3, 0, None) == pkg.TVD_EINVAL
     assert lib.tvd_plan_create(ctypes.byref(out), 16, 16, hp, 3, 3, 7, 3, 0, None) == pkg.TVD_EINVAL
+
+
+def test_batched_argument_checks_without_gpu(lib):
+    """tv_deblur_batched validates before any CUDA call: nothing to do, or invalid arguments."""
+    import paper_1011_5964_gb300 as pkg
+    assert lib.tv_deblur_batched(None, 0, 10, 1e-6, 100, 0, None) == pkg.TVD_OK
+    assert lib.tv_deblur_batched(None, -1, 10, 1e-6, 100, 0, None) == pkg.TVD_EINVAL
+    assert lib.tv_deblur_batched(None, 2, 10, 1e-6, 100, 0, None) == pkg.TVD_EINVAL
+    items = (pkg._BatchItem * 1)()
+    assert lib.tv_deblur_batched(items, 1, 10, 1e-6, 100, 0, None) == pkg.TVD_EINVAL   # null plan
+    assert lib.tv_deblur_batched(items, 1, 10, 0.0, 100, 0, None) == pkg.TVD_EINVAL    # tol <= 0
+    assert lib.tv_deblur_batched(items, 1, 10, 1e-6, 100, 65, None) == pkg.TVD_EINVAL  # workers > 64
