@@ -515,3 +515,77 @@ def tv_deblur(v, h, bc, alpha, beta, outer=10, tol=1e-6, maxit=1000,
         if outer_tol > 0.0 and change < outer_tol:
             break
     return u, stats
+
+
+# --------------------------------------------------------------------------
+# Adjoint of the converged fixed point (implicit differentiation of the
+# Euler-Lagrange equation g(u*, theta) = 0, eq. (el); not a construction of
+# the paper: it differentiates the paper's method with respect to alpha,
+# beta and the PSF)
+# --------------------------------------------------------------------------
+
+def tv_hessian_apply(u, beta, x):
+    """nabla^2 J_beta(u) x for J_beta(u) = sum_pq psi_pq, psi = sqrt(|D u|^2 + beta^2).
+
+    The gradient of J_beta is D^T (psi^-1 D u) = L(u) u; differentiating it
+    once more per cell gives D^T [psi^-1 D x - psi^-3 (D u . D x) D u] with
+    the forward differences D = (D_r, D_c) of ``grad_r`` / ``grad_c``.
+    """
+    u = np.asarray(u, dtype=np.float64)
+    x = np.asarray(x, dtype=np.float64)
+    dr, dc = grad_r(u), grad_c(u)
+    psi = np.sqrt(dr * dr + dc * dc + beta * beta)
+    xr, xc = grad_r(x), grad_c(x)
+    s = (dr * xr + dc * xc) / psi ** 3
+    return grad_r_T(xr / psi - s * dr) + grad_c_T(xc / psi - s * dc)
+
+
+def jacobian_apply(u, h, bc, alpha, beta, x):
+    """J x = H^T H x + alpha nabla^2 J_beta(u) x: the derivative of g(u) of eq. (el) in u (SPD)."""
+    return blur_adjoint(blur(x, h, bc), h, bc) + alpha * tv_hessian_apply(u, beta, x)
+
+
+def adjoint_solve(u, h, bc, alpha, beta, rhs, tol=1e-12, maxit=20000):
+    """lambda with J(u) lambda = rhs, by the PCG of Algorithm 10.3.1 (no preconditioner), from 0.
+
+    Returns (lambda, iterations, ||r|| / ||r_0||, converged).
+    """
+    rhs = np.asarray(rhs, dtype=np.float64)
+    return pcg(lambda y: jacobian_apply(u, h, bc, alpha, beta, y), lambda r: r, rhs, np.zeros_like(rhs), tol, maxit)
+
+
+def unit_psf(h, a, b):
+    """The PSF with a single 1 at tap (a, b) (offsets from the centre): dH/dh_ab."""
+    e = np.zeros_like(np.asarray(h, dtype=np.float64))
+    mr, mc = _psf_halfwidths(e)
+    e[mr + a, mc + b] = 1.0
+    return e
+
+
+def fixed_point_gradients(u, v, h, bc, alpha, beta, lam):
+    """d loss / d theta = -lam^T dF/dtheta at the fixed point u of F(u, theta) = g(u) = 0.
+
+    F = H^T (H u - v) + alpha grad J_beta(u) (eq. (el)), lam solves J lam = d loss / d u. Then
+      dF/dalpha = grad J_beta(u) = L(u) u,
+      dF/dbeta  = alpha D^T [ d(psi^-1)/d beta D u ] = alpha D^T [ -beta psi^-3 D u ],
+      dF/dh_ab  = E_ab^T (H u - v) + H^T E_ab u with E_ab = dH/dh_ab (H is linear in h),
+    so lam^T dF/dh_ab = (E_ab lam) . (H u - v) + (H lam) . (E_ab u).
+    Returns (dl_dalpha, dl_dbeta, dl_dh) with dl_dh shaped like h (every tap free).
+    """
+    u = np.asarray(u, dtype=np.float64)
+    lam = np.asarray(lam, dtype=np.float64)
+    w = diffusivity(u, beta)
+    dl_dalpha = -float(np.sum(lam * tv_apply(w, u)))
+    dr, dc = grad_r(u), grad_c(u)
+    psi3 = (1.0 / w) ** 3
+    dF_dbeta = alpha * (grad_r_T(-beta * dr / psi3) + grad_c_T(-beta * dc / psi3))
+    dl_dbeta = -float(np.sum(lam * dF_dbeta))
+    res = blur(u, h, bc) - np.asarray(v, dtype=np.float64)
+    hlam = blur(lam, h, bc)
+    mr, mc = _psf_halfwidths(h)
+    dl_dh = np.zeros_like(np.asarray(h, dtype=np.float64))
+    for a in range(-mr, mr + 1):
+        for b in range(-mc, mc + 1):
+            e = unit_psf(h, a, b)
+            dl_dh[mr + a, mc + b] = -(float(np.sum(blur(lam, e, bc) * res)) + float(np.sum(hlam * blur(u, e, bc))))
+    return dl_dalpha, dl_dbeta, dl_dh
