@@ -194,6 +194,41 @@ def batched_leg(pkg, torch, dev, synth):
             "timing": "host clock around the call, inputs resident"}
 
 
+def adjoint_leg(pkg, torch, dev, synth):
+    """Adjoint of the converged fixed point at 512 x 512: the observation blurred
+    with a Gaussian sigma = 2.5, the plan's PSF sigma = 2.0 on a 17 x 17 support
+    (half-width ceil(3 x 2.5)), alpha 1e-3, beta 1e-2, AR, D_M, MIXED. u* from
+    tv_deblur run to ||u^k - u^{k-1}|| / ||u^k|| < 1e-8; then one adjoint solve
+    (tol 1e-10) for l = ||u* - u_true||^2 and dl/dsigma by the chain rule through
+    the PSF taps. Device time by CUDA events."""
+    import numpy as np
+    n, seed, m = 512, 77, 8
+    u_true = synth.piecewise_constant_image(n, n, seed=seed)
+    h_true = synth.gaussian_psf(2.5, half_width=m)
+    h = synth.gaussian_psf(2.0, half_width=m)
+    ut = torch.tensor(u_true, dtype=torch.float64, device=dev)
+    with pkg.Plan(n, n, h_true, bc="ar", pc="dfast", mode="fp64") as p64:
+        hu = p64.blur(ut).cpu().numpy()
+    v = torch.tensor(synth.add_noise(hu, synth.noise_direction(n, n, seed), 0.01), dtype=torch.float64, device=dev)
+    stream = torch.cuda.current_stream()
+    with pkg.Plan(n, n, h, bc="ar", pc="dfast", mode="mixed") as plan:
+        e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+        e0.record(stream)
+        u, st = plan.deblur(v, ALPHA, BETA, max_outer=200, outer_tol=1e-8, inner_tol=1e-8, inner_maxit=5000)
+        e1.record(stream)
+        lam, da, db, dh, ast = plan.adjoint(u, v, ALPHA, BETA, 2.0 * (u - ut), tol=1e-10, maxit=5000)
+        e2.record(stream)
+        e2.synchronize()
+    eps = 1e-6
+    dh_dsigma = (synth.gaussian_psf(2.0 + eps, half_width=m) - synth.gaussian_psf(2.0 - eps, half_width=m)) / (2 * eps)
+    return {"workload": "adjoint of the converged fixed point, 512x512 AR, plan PSF Gaussian sigma 2.0 on 17x17, "
+                        "data blurred with sigma 2.5, alpha 1e-3, beta 1e-2, D_M, MIXED",
+            "fixed_point_ms": e0.elapsed_time(e1), "fp_steps": st["outer_iters"],
+            "fp_inner_iters": st["total_inner_iters"], "last_rel_change": st["last_rel_change"],
+            "adjoint_ms": e1.elapsed_time(e2), "adjoint_iters": ast["iters"], "adjoint_relres": ast["relres"],
+            "dl_dalpha": da, "dl_dbeta": db, "dl_dsigma": float(np.sum(dh * dh_dsigma))}
+
+
 def peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     try:
@@ -425,6 +460,7 @@ def run_ours(args):
 
     if not args.no_batch:
         line["batched"] = batched_leg(pkg, torch, dev, synth)
+        line["adjoint"] = adjoint_leg(pkg, torch, dev, synth)
 
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         iters_per_deblur, src = oracle_iters_per_deblur()
@@ -454,7 +490,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--no-batch", action="store_true", help="skip the batch-of-independent-images leg")
+    ap.add_argument("--no-batch", action="store_true", help="skip the batch-of-independent-images and adjoint legs")
     ap.add_argument("--only-chosen", action="store_true",
                     help="time the chosen form only (no plain FP64, e2e, per-kernel or CPU legs); for profiler runs")
     args = ap.parse_args()

@@ -212,6 +212,49 @@ typedef struct {
 tvd_status tv_deblur_batched(tvd_batch_item* items, int count, int max_outer, double inner_tol,
                              int inner_maxit, int workers, void* stream);
 
+/*
+ * tv_hessian_apply -- y = nabla^2 J_beta(u) x, the Hessian of the discrete TV
+ * term J_beta(u) = sum_pq sqrt(|D u|_pq^2 + beta^2) of the functional whose
+ * stationarity is eq. (el): D^T [psi^-1 D x - psi^-3 (D u . D x) D u] per
+ * cell, D the forward differences of L (zero on the last row / column).
+ * u, x, y: DOUBLE device arrays of the plan's size (any mode); y distinct
+ * from u and x. Synchronises the stream (it allocates and frees 2 n doubles).
+ */
+tvd_status tv_hessian_apply(tvd_plan plan, const void* u, double beta, const void* x, void* y, void* stream);
+
+/*
+ * tv_deblur_adjoint -- gradients of a loss l(u*) of the converged fixed point
+ * u* of tv_deblur (g(u*) = H^T (H u* - v) + alpha L(u*) u* = 0, eq. (el)) with
+ * respect to alpha, beta and the PSF taps, by implicit differentiation: one
+ * solve J lambda = dl/du with J = H^T H + alpha nabla^2 J_beta(u*) (SPD) by
+ * PCG from lambda = 0, preconditioned by the plan's preconditioner of the
+ * lagged operator H^T H + alpha L(u*) (set up here at u*, replacing any
+ * earlier tau_precond_setup), then
+ *   dl/dalpha = -lambda^T L(u*) u*,
+ *   dl/dbeta  = alpha beta (D lambda)^T [psi^-3 D u*],
+ *   dl/dh_ab  = -[(E_ab lambda)^T (H u* - v) + (H lambda)^T E_ab u*]
+ * (E_ab = dH/dh_ab: the BC extension shifted by the tap offset). Not a
+ * construction of the paper: it differentiates the paper's method. Runs in
+ * double in both modes.
+ *   u_star, v, dl_du   DOUBLE device arrays (u* should satisfy g(u*) ~ 0:
+ *                      run tv_deblur to a small outer_tol first).
+ *   lambda_out         DOUBLE device array, receives lambda (distinct from the inputs).
+ *   tol, maxit         ||r_k|| / ||r_0|| < tol stopping rule and cap of the adjoint PCG.
+ *   dl_dalpha, dl_dbeta  host doubles (may be NULL).
+ *   dl_dpsf            host array of p_rows x p_cols doubles as reported by
+ *                      tvd_plan_psf_size (the PSF support after trimming zero
+ *                      outer rows / columns), row-major like the PSF; may be NULL.
+ *   iters, relres      host outputs of the adjoint PCG (may be NULL).
+ * Synchronises the stream. Returns TVD_ENOCONV (gradients still written) if
+ * the PCG hit maxit, TVD_EBREAKDOWN if it broke down.
+ */
+tvd_status tv_deblur_adjoint(tvd_plan plan, const void* u_star, const void* v, double alpha, double beta,
+                             const void* dl_du, void* lambda_out, double tol, int maxit, double* dl_dalpha,
+                             double* dl_dbeta, double* dl_dpsf, int* iters, double* relres, void* stream);
+
+/* Size of the plan's PSF support (after trimming all-zero outer rows / columns). */
+tvd_status tvd_plan_psf_size(tvd_plan plan, int* p_rows, int* p_cols);
+
 /* Message of the last failed call on the calling thread ("" if none). */
 const char* tvd_last_error(void);
 

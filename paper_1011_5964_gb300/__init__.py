@@ -34,7 +34,8 @@ STATUS_NAMES = ["TVD_OK", "TVD_EINVAL", "TVD_EPSF_ASYM", "TVD_EPSF_SIZE", "TVD_E
 # Function names of the C ABI, in include/tvd.h order.
 ABI_FUNCTIONS = ["tvd_plan_create", "tvd_plan_destroy", "ar_blur_apply", "tv_operator_apply",
                  "tau_precond_setup", "tau_precond_solve", "pcg_solve", "tv_deblur",
-                 "tv_deblur_batched", "tvd_normal_apply_noalloc", "tvd_last_error", "tvd_version", "tvd_kernel_launches",
+                 "tv_deblur_batched", "tv_hessian_apply", "tv_deblur_adjoint", "tvd_plan_psf_size",
+                 "tvd_normal_apply_noalloc", "tvd_last_error", "tvd_version", "tvd_kernel_launches",
                  "tvd_profile_enable", "tvd_profile_classes", "tvd_profile_name", "tvd_profile_read"]
 
 
@@ -83,6 +84,10 @@ def load_library(path: str | None = None) -> ctypes.CDLL:
     lib.tv_deblur.argtypes = [vp, vp, d, d, i, d, d, i, vp, ctypes.POINTER(_Stats), vp]
     lib.tvd_normal_apply_noalloc.argtypes = [i, i, ctypes.POINTER(d), i, i, i, vp, d, d, vp, vp, vp]
     lib.tv_deblur_batched.argtypes = [ctypes.POINTER(_BatchItem), i, i, d, i, i, vp]
+    lib.tv_hessian_apply.argtypes = [vp, vp, d, vp, vp, vp]
+    lib.tv_deblur_adjoint.argtypes = [vp, vp, vp, d, d, vp, vp, d, i, ctypes.POINTER(d), ctypes.POINTER(d),
+                                      ctypes.POINTER(d), ctypes.POINTER(i), ctypes.POINTER(d), vp]
+    lib.tvd_plan_psf_size.argtypes = [vp, ctypes.POINTER(i), ctypes.POINTER(i)]
     lib.tvd_last_error.restype = ctypes.c_char_p
     lib.tvd_version.restype = ctypes.c_char_p
     lib.tvd_kernel_launches.restype = ctypes.c_ulonglong
@@ -199,6 +204,40 @@ class Plan:
                                 ctypes.byref(it), ctypes.byref(rr), _stream())
         _check(st, allow=(TVD_ENOCONV,))
         return it.value, rr.value, st
+
+    def hessian(self, u, beta: float, x, out=None):
+        """y = nabla^2 J_beta(u) x (float64 CUDA tensors), the Hessian of the TV term."""
+        import torch
+        y = torch.empty_like(x) if out is None else out
+        _check(self.lib.tv_hessian_apply(self.handle, _ptr(u, torch.float64, self.n), float(beta),
+                                         _ptr(x, torch.float64, self.n), _ptr(y, torch.float64, self.n), _stream()))
+        return y
+
+    def psf_size(self):
+        """(p_rows, p_cols) of the plan's PSF support after trimming zero outer rows / columns."""
+        pr, pc = ctypes.c_int(0), ctypes.c_int(0)
+        _check(self.lib.tvd_plan_psf_size(self.handle, ctypes.byref(pr), ctypes.byref(pc)))
+        return pr.value, pc.value
+
+    def adjoint(self, u_star, v, alpha: float, beta: float, dl_du, tol: float = 1e-10, maxit: int = 5000):
+        """Gradients of a loss of the converged fixed point u* (float64 CUDA tensors).
+
+        Solves J lambda = dl_du, J = H^T H + alpha nabla^2 J_beta(u*), and returns
+        (lambda, dl/dalpha, dl/dbeta, dl/dpsf (numpy, psf_size()), stats dict).
+        """
+        import torch
+        lam = torch.empty_like(dl_du)
+        pr, pc = self.psf_size()
+        dpsf = np.zeros((pr, pc), dtype=np.float64)
+        da, db, rr = ctypes.c_double(0.0), ctypes.c_double(0.0), ctypes.c_double(0.0)
+        it = ctypes.c_int(0)
+        st = self.lib.tv_deblur_adjoint(self.handle, _ptr(u_star, torch.float64, self.n), _ptr(v, torch.float64, self.n),
+                                        float(alpha), float(beta), _ptr(dl_du, torch.float64, self.n),
+                                        _ptr(lam, torch.float64, self.n), float(tol), int(maxit), ctypes.byref(da),
+                                        ctypes.byref(db), dpsf.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                        ctypes.byref(it), ctypes.byref(rr), _stream())
+        _check(st, allow=(TVD_ENOCONV,))
+        return lam, da.value, db.value, dpsf, {"iters": it.value, "relres": rr.value, "status": st}
 
     def deblur(self, v, alpha: float, beta: float, max_outer: int = 10, outer_tol: float = 0.0,
                inner_tol: float = 1e-6, inner_maxit: int = 1000, out=None):
@@ -317,6 +356,18 @@ def pcg_solve(plan: Plan, u_lag, alpha, beta, b, x, tol=1e-6, maxit=1000):
 
 def tv_deblur(plan: Plan, v, alpha, beta, max_outer=10, outer_tol=0.0, inner_tol=1e-6, inner_maxit=1000, u=None):
     return plan.deblur(v, alpha, beta, max_outer, outer_tol, inner_tol, inner_maxit, u)
+
+
+def tv_hessian_apply(plan: Plan, u, beta, x, y=None):
+    return plan.hessian(u, beta, x, y)
+
+
+def tv_deblur_adjoint(plan: Plan, u_star, v, alpha, beta, dl_du, tol=1e-10, maxit=5000):
+    return plan.adjoint(u_star, v, alpha, beta, dl_du, tol, maxit)
+
+
+def tvd_plan_psf_size(plan: Plan):
+    return plan.psf_size()
 
 
 def tv_deblur_batched(plans, vs, alphas, betas, max_outer=10, inner_tol=1e-6, inner_maxit=1000, outs=None,

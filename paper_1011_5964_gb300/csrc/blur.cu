@@ -96,18 +96,6 @@ struct FuseArgs {
     int finish_here;      // this kernel holds the last contributing blocks
 };
 
-__device__ __forceinline__ void finish_pq(CgState* st, double pq) {
-    st->pq = pq;
-    if (!finite_pos(pq)) {
-        st->status = TVD_EBREAKDOWN;
-        st->done = 1;
-        st->alpha = 0.0;
-    } else {
-        st->alpha = st->rho / pq;
-        st->pending = 1;
-    }
-}
-
 // Output tile kernel. EXT selects the extension of the input; for EXT_ODD only
 // interior outputs (1..n-2 in both directions) are written. With FUSE, the
 // output is q = conv + alpha L(w) pv and p^T q is reduced.

@@ -109,4 +109,18 @@ __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wai
 
 __device__ __forceinline__ bool finite_pos(double v) { return isfinite(v) && v > 0.0; }
 
+// End of a CG product q = A p: p^T q, the step alpha = rho / p^T q, and the
+// pending x / r update (applied by the next iteration's first pass).
+__device__ __forceinline__ void finish_pq(CgState* st, double pq) {
+    st->pq = pq;
+    if (!finite_pos(pq)) {
+        st->status = TVD_EBREAKDOWN;
+        st->done = 1;
+        st->alpha = 0.0;
+    } else {
+        st->alpha = st->rho / pq;
+        st->pending = 1;
+    }
+}
+
 }  // namespace tvd

@@ -656,6 +656,115 @@ tvd_status tv_operator_apply(tvd_plan plan, const void* u_lag, double beta, cons
     return tv_apply<float>(*plan, plan->f.t2, (const float*)x, (float*)y, s);
 }
 
+tvd_status tv_hessian_apply(tvd_plan plan, const void* u, double beta, const void* x, void* y, void* stream) {
+    if (!plan || !u || !x || !y || y == x || y == u || !(beta > 0.0)) {
+        set_error("tv_hessian_apply: invalid argument");
+        return TVD_EINVAL;
+    }
+    tvd_plan_s& p = *plan;
+    cudaStream_t s = (cudaStream_t)stream;
+    const size_t n = (size_t)p.nr * p.nc;
+    double* g = nullptr;
+    TVD_TRY(dalloc(&g, 2 * n));
+    tvd_status st = diffusivity<double>(p, (const double*)u, beta, p.d.t2, s);
+    if (st == TVD_OK) st = hess_coef(p, (const double*)u, p.d.t2, g, g + n, s);
+    if (st == TVD_OK) st = hess_apply(p, (const double*)x, (double*)y, p.d.t2, g, g + n, s);
+    if (st == TVD_OK && cudaStreamSynchronize(s) != cudaSuccess) {
+        set_error("tv_hessian_apply: CUDA error");
+        st = TVD_ECUDA;
+    }
+    dfree(g);
+    return st;
+}
+
+tvd_status tv_deblur_adjoint(tvd_plan plan, const void* u_star, const void* v, double alpha, double beta,
+                             const void* dl_du, void* lambda_out, double tol, int maxit, double* dl_dalpha,
+                             double* dl_dbeta, double* dl_dpsf, int* iters, double* relres, void* stream) {
+    if (!plan || !u_star || !v || !dl_du || !lambda_out || lambda_out == dl_du || lambda_out == u_star ||
+        lambda_out == v || !(alpha >= 0.0) || !(beta > 0.0) || !(tol > 0.0) || maxit < 0) {
+        set_error("tv_deblur_adjoint: invalid argument");
+        return TVD_EINVAL;
+    }
+    tvd_plan_s& p = *plan;
+    Ops<double>& o = p.d;
+    cudaStream_t s = (cudaStream_t)stream;
+    const size_t n = (size_t)p.nr * p.nc;
+    const int mr = p.psf.mr, mc = p.psf.mc;
+    const size_t ne = (size_t)(p.nr + 2 * mr) * (p.nc + 2 * mc);
+    const size_t ntap = (size_t)(2 * mr + 1) * (2 * mc + 1);
+    const double* u = (const double*)u_star;
+    double* lam = (double*)lambda_out;
+    p.hx_for = nullptr;
+    // the lagged operator's preconditioner at u* (w = psi^-1 of u*, D, the spectrum)
+    TVD_TRY(setup_precond<double>(p, o, u, alpha, beta, s));
+    double* scratch = nullptr;
+    TVD_TRY(dalloc(&scratch, 2 * n + 2 * ne + ntap + 2));
+    double *gr = scratch, *gc = scratch + n, *ext = scratch + 2 * n, *taps = ext + 2 * ne, *out2 = taps + ntap;
+    auto run = [&]() -> tvd_status {
+        TVD_TRY(hess_coef(p, u, o.w, gr, gc, s));
+        TVD_CUDA_TRY(cudaMemsetAsync(lam, 0, n * sizeof(double), s));
+        TVD_CUDA_TRY(cudaMemsetAsync(o.q, 0, n * sizeof(double), s));
+        CgState* st = p.state;
+        TVD_TRY(cg_init<double>(p, (const double*)dl_du, o.q, o.r, st, tol, maxit, s));
+        const bool fused_xr = (p.pc == TVD_PC_FAST || p.pc == TVD_PC_DFAST);
+        int done_iters = 0;
+        for (;;) {
+            for (int k = 0; k < 2 * kChunk; ++k) {
+                switch (p.pc) {
+                    case TVD_PC_NONE: TVD_TRY(cg_simple_precond<double>(p, o.r, nullptr, o.z, st, s)); break;
+                    case TVD_PC_DIAG: TVD_TRY(cg_simple_precond<double>(p, o.r, o.dinv, o.z, st, s)); break;
+                    default: TVD_TRY(precond_solve<double>(p, o, o.r, o.z, st, s, lam)); break;
+                }
+                TVD_TRY(blur_pupdate<double>(p, o, o.z, o.p, o.p2, o.t, st, s));
+                TVD_TRY(blur_apply<double>(p, o, true, o.t, o.q, s, st));
+                TVD_TRY(hess_add(p, o.q, o.p, o.p2, o.w, gr, gc, alpha, st, s));
+                if (!fused_xr) TVD_TRY(cg_xrupdate<double>(p, lam, o.r, o.p, o.p2, o.q, st, s));
+            }
+            done_iters += 2 * kChunk;
+            TVD_TRY(read_state<double>(p, s));
+            if (p.hstate->done) break;
+            if (done_iters > maxit + 4 * kChunk) {
+                set_error("adjoint CG state did not reach done after maxit iterations");
+                return TVD_ECUDA;
+            }
+        }
+        const CgState h = *p.hstate;
+        if (iters) *iters = h.iter;
+        if (relres) *relres = h.rr0 > 0.0 ? std::sqrt(h.rr / h.rr0) : 0.0;
+        if (h.status == TVD_EBREAKDOWN) {
+            set_error("tv_deblur_adjoint: the adjoint CG broke down");
+            return TVD_EBREAKDOWN;
+        }
+        TVD_TRY(adjoint_gradients(p, o, lam, u, (const double*)v, alpha, beta, ext, dl_dpsf ? taps : nullptr, out2,
+                                  s));
+        double h2[2] = {0.0, 0.0};
+        TVD_CUDA_TRY(cudaMemcpyAsync(h2, out2, sizeof(h2), cudaMemcpyDeviceToHost, s));
+        if (dl_dpsf) TVD_CUDA_TRY(cudaMemcpyAsync(dl_dpsf, taps, ntap * sizeof(double), cudaMemcpyDeviceToHost, s));
+        TVD_CUDA_TRY(cudaStreamSynchronize(s));
+        if (dl_dalpha) *dl_dalpha = -h2[0];
+        if (dl_dbeta) *dl_dbeta = alpha * beta * h2[1];
+        if (h.status == TVD_ENOCONV) {
+            set_error("tv_deblur_adjoint: the adjoint CG did not reach its tolerance");
+            return TVD_ENOCONV;
+        }
+        return TVD_OK;
+    };
+    const tvd_status st = run();
+    cudaStreamSynchronize(s);
+    dfree(scratch);
+    return st;
+}
+
+tvd_status tvd_plan_psf_size(tvd_plan plan, int* p_rows, int* p_cols) {
+    if (!plan || !p_rows || !p_cols) {
+        set_error("tvd_plan_psf_size: invalid argument");
+        return TVD_EINVAL;
+    }
+    *p_rows = 2 * plan->psf.mr + 1;
+    *p_cols = 2 * plan->psf.mc + 1;
+    return TVD_OK;
+}
+
 tvd_status tau_precond_setup(tvd_plan plan, const void* u_lag, double alpha, double beta, void* stream) {
     if (!plan || !u_lag || !(alpha >= 0.0) || !(beta > 0.0)) {
         set_error("tau_precond_setup: invalid argument");

@@ -249,6 +249,22 @@ template <typename T>
 tvd_status precond_solve(const tvd_plan_s& p, const Ops<T>& o, const T* r, T* z, CgState* st, cudaStream_t s,
                          T* x = nullptr);
 
+// Adjoint of the converged fixed point (double): per-cell TV Hessian
+// coefficients g = D u psi^-3/2 from u and w = psi^-1; y = nabla^2 J_beta(u) x;
+// the adjoint CG product q += alpha nabla^2 J_beta p with p^T q (p the
+// direction st->pbuf selects); and the gradient reductions: out2[0] =
+// lambda^T L(u) u, out2[1] = sum psi^-3 (D lambda . D u), and with taps the
+// per-tap values -[(E_ab lambda)^T (H u - v) + (H lambda)^T E_ab u] (uses o.t,
+// o.q and scratch_ext of 2 (n_r + 2 m_r)(n_c + 2 m_c) doubles).
+tvd_status hess_coef(const tvd_plan_s& p, const double* u, const double* w, double* gr, double* gc, cudaStream_t s);
+tvd_status hess_apply(const tvd_plan_s& p, const double* x, double* y, const double* w, const double* gr,
+                      const double* gc, cudaStream_t s);
+tvd_status hess_add(const tvd_plan_s& p, double* q, const double* p0, const double* p1, const double* w,
+                    const double* gr, const double* gc, double alpha, CgState* st, cudaStream_t s);
+tvd_status adjoint_gradients(const tvd_plan_s& p, const Ops<double>& o, const double* lam, const double* u,
+                             const double* v, double alpha, double beta, double* scratch_ext, double* taps,
+                             double* out2, cudaStream_t s);
+
 // CG kernels
 template <typename T>
 tvd_status cg_init(const tvd_plan_s& p, const T* b, const T* ax, T* r, CgState* st, double tol, int maxit,
