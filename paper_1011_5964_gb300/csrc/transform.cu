@@ -59,6 +59,7 @@ struct LineArgs {
     T* inv_out;          // COL_EG: inv_spec output
     const T* rvec;       // ROW_INV: r for r^T z
     const cplx<T>* tw;   // twiddles, length L
+    const cplx<T>* blt;  // Bluestein tables (fp.bl): chirp exp(-i pi j^2 / L) (L) | filter spectrum / M2 (M2) | M2 twiddles
     const T* aux;        // auxiliary tables, kAuxSlots * 2n
     int n;               // line length
     int ns;              // stride of the lines in shared memory (odd: no bank conflicts across lines)
@@ -261,13 +262,14 @@ __device__ void fft_stage_generic(const cplx<T>* __restrict__ in, cplx<T>* __res
     }
 }
 
-// Runs all stages, __syncthreads between them; returns the buffer holding the result.
+// Runs all stages of a length-L plan, __syncthreads between them; returns the
+// buffer holding the result.
 template <typename T>
-__device__ cplx<T>* fft_pairs(cplx<T>* a, cplx<T>* b, int P, const FftPlan& fp, const cplx<T>* tw, bool inv) {
-    const int L = fp.L;
+__device__ cplx<T>* fft_run(cplx<T>* a, cplx<T>* b, int P, int L, int nstages, const int* radix, const cplx<T>* tw,
+                            bool inv) {
     int Ns = 1;
-    for (int s = 0; s < fp.nstages; ++s) {
-        const int R = fp.radix[s];
+    for (int s = 0; s < nstages; ++s) {
+        const int R = radix[s];
         switch (R) {
             case 2: fft_stage<T, 2>(a, b, P, L, Ns, tw, inv); break;
             case 3: fft_stage<T, 3>(a, b, P, L, Ns, tw, inv); break;
@@ -294,6 +296,48 @@ __device__ cplx<T>* fft_pairs(cplx<T>* a, cplx<T>* b, int P, const FftPlan& fp, 
     return a;
 }
 
+// P complex lines of length L (stride L in a) -> their DFTs (inverse: conjugate
+// twiddles, unnormalised). Plans with bl use Bluestein's identity
+// jk = (j^2 + k^2 - (k - j)^2) / 2: X_k = c_k sum_j (x_j c_j) conj(c_{k-j}),
+// c_j = exp(-i pi j^2 / L), the sum a circular convolution of length M2 done
+// as IFFT(FFT(x c) FFT(b)) with the filter spectrum FFT(b) / M2 precomputed;
+// the inverse transform is conj(DFT(conj x)). a and b then hold P * M2
+// entries and tw the M2 twiddles. The result is returned at stride L.
+template <typename T>
+__device__ cplx<T>* fft_pairs(cplx<T>* a, cplx<T>* b, int P, const FftPlan& fp, const cplx<T>* tw, bool inv,
+                              const cplx<T>* __restrict__ blt) {
+    if (!fp.bl) return fft_run<T>(a, b, P, fp.L, fp.nstages, fp.radix, tw, inv);
+    const int L = fp.L, M2 = fp.M2;
+    const cplx<T>* __restrict__ chirp = blt;
+    const cplx<T>* __restrict__ filt = blt + L;
+    const T sg = inv ? T(-1) : T(1);
+    for (Walk w(M2); w.hi < P; w.next(M2)) {
+        const int pp = w.hi, m = w.lo;
+        cplx<T> v = {T(0), T(0)};
+        if (m < L) {
+            const cplx<T> x = a[(size_t)pp * L + m];
+            v = cmul(cplx<T>{x.re, sg * x.im}, chirp[m]);
+        }
+        b[(size_t)pp * M2 + m] = v;
+    }
+    __syncthreads();
+    cplx<T>* Z = fft_run<T>(b, a, P, M2, fp.nst2, fp.radix2, tw, false);
+    for (Walk w(M2); w.hi < P; w.next(M2)) {
+        const cplx<T> y = cmul(Z[(size_t)w.hi * M2 + w.lo], filt[w.lo]);
+        Z[(size_t)w.hi * M2 + w.lo] = {y.re, -y.im};   // conj: the inverse FFT by a forward one
+    }
+    __syncthreads();
+    Z = fft_run<T>(Z, Z == a ? b : a, P, M2, fp.nst2, fp.radix2, tw, false);
+    cplx<T>* out = Z == a ? b : a;
+    for (Walk w(L); w.hi < P; w.next(L)) {
+        const int pp = w.hi, k = w.lo;
+        const cplx<T> z = Z[(size_t)pp * M2 + k];
+        const cplx<T> y = cmul(cplx<T>{z.re, -z.im}, chirp[k]);
+        out[(size_t)pp * L + k] = {y.re, sg * y.im};
+    }
+    __syncthreads();
+    return out;
+}
 
 // ------------------------------------------------------------- line transforms in shared memory
 // raw[l * ns + idx]: 2P real lines of length n at the odd stride ns. bufA, bufB: P complex lines of length L.
@@ -321,7 +365,7 @@ __device__ void dst1_lines(T* raw, cplx<T>* bufA, cplx<T>* bufB, const LineArgs<
         bufA[(size_t)pp * M + j] = {sj * (a0 + a1) + T(0.5) * (a0 - a1), sj * (b0 + b1) + T(0.5) * (b0 - b1)};
     }
     __syncthreads();
-    const cplx<T>* Z = fft_pairs<T>(bufA, bufB, P, a.fp, tw, false);
+    const cplx<T>* Z = fft_pairs<T>(bufA, bufB, P, a.fp, tw, false, a.blt);
     // the FFT buffer not holding the result keeps the recurrence terms (2P * K <= 2P * L values)
     T* scan = reinterpret_cast<T*>(Z == bufA ? bufB : bufA);
     const T sc = sqrt(T(2) / T(M));
@@ -377,7 +421,7 @@ __device__ void dct_lines(T* raw, cplx<T>* bufA, cplx<T>* bufB, const LineArgs<T
             bufA[(size_t)pp * n + p] = {raw[(size_t)(2 * pp) * ns + src], raw[(size_t)(2 * pp + 1) * ns + src]};
         }
         __syncthreads();
-        const cplx<T>* Z = fft_pairs<T>(bufA, bufB, P, a.fp, tw, false);
+        const cplx<T>* Z = fft_pairs<T>(bufA, bufB, P, a.fp, tw, false, a.blt);
         for (Walk w(n); w.hi < P; w.next(n)) {
             const int pp = w.hi, k = w.lo;
             cplx<T> Va, Vb;
@@ -407,7 +451,7 @@ __device__ void dct_lines(T* raw, cplx<T>* bufA, cplx<T>* bufB, const LineArgs<T
             bufA[(size_t)pp * n + k] = {Va.re - Vb.im, Va.im + Vb.re};
         }
         __syncthreads();
-        const cplx<T>* Z = fft_pairs<T>(bufA, bufB, P, a.fp, tw, true);
+        const cplx<T>* Z = fft_pairs<T>(bufA, bufB, P, a.fp, tw, true, a.blt);
         for (Walk w(n); w.hi < P; w.next(n)) {
             const int pp = w.hi, p = w.lo;
             const int dst = p < h ? 2 * p : 2 * (n - 1 - p) + 1;
@@ -429,7 +473,7 @@ __device__ void eg_lines(const T* raw, cplx<T>* bufA, cplx<T>* bufB, T* eo, T* g
         bufA[(size_t)pp * L + j] = {raw[(size_t)(2 * pp) * ns + j], raw[(size_t)(2 * pp + 1) * ns + j]};
     }
     __syncthreads();
-    const cplx<T>* Z = fft_pairs<T>(bufA, bufB, P, a.fp, tw, false);
+    const cplx<T>* Z = fft_pairs<T>(bufA, bufB, P, a.fp, tw, false, a.blt);
     for (Walk w(n); w.hi < P; w.next(n)) {
         const int pp = w.hi, k = w.lo;
         const cplx<T>* Zp = Z + (size_t)pp * L;
@@ -461,7 +505,7 @@ __device__ void eg_lines(const T* raw, cplx<T>* bufA, cplx<T>* bufB, T* eo, T* g
             split_pair(Zp, 0, L, F0a, F0b);
             split_pair(Zp, k, L, Fa, Fb);
             const cplx<T> eh = reinterpret_cast<const cplx<T>*>(a.aux + 4 * n)[k];       // exp(i pi k/n)
-            const cplx<T> w = tw[k];                                                     // exp(-2 pi i k/n)
+            const cplx<T> w = a.tw[k];                                                   // exp(-2 pi i k/n)
             const T ce = a.aux[6 * n + k], cg = a.aux[8 * n + k];
             ea = ce * (F0a.re + eh.re * Fa.re + eh.im * Fa.im);
             eb = ce * (F0b.re + eh.re * Fb.re + eh.im * Fb.im);
@@ -520,14 +564,14 @@ __device__ __forceinline__ void finish_xr(CgState* st, double rr) {
     }
 }
 
-// Resident blocks per SM the register allocation aims for (tuning: more blocks
+// Resident blocks per SM the float kernels' register allocation aims for (tuning: more blocks
 // hide more latency, at the price of spilled large-radix butterflies).
 #ifndef TVD_LINE_MINB
 #define TVD_LINE_MINB 2
 #endif
 
 template <typename T, int BC, int OP>
-__global__ void __launch_bounds__(kThreads, TVD_LINE_MINB) line_kernel(LineArgs<T> a) {
+__global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? TVD_LINE_MINB : 1) line_kernel(LineArgs<T> a) {
     if (a.st && a.st->done) return;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int n = a.n, ns = a.ns, P = a.P, L = a.L;
@@ -535,10 +579,14 @@ __global__ void __launch_bounds__(kThreads, TVD_LINE_MINB) line_kernel(LineArgs<
     const int lsh = __ffs(lines) - 1;
     const int ln = lines * n;      // line elements of the block
     const int lns = lines * ns;    // shared-memory size of one set of lines
+    // FFT twiddles in shared memory: L of them, or M2 for a Bluestein plan,
+    // whose FFT buffers also hold M2 entries per line pair
+    const int ntw = a.fp.bl ? a.fp.M2 : L, Lb = a.fp.bl ? a.fp.M2 : L;
+    const cplx<T>* twsrc = a.fp.bl ? a.blt + L + a.fp.M2 : a.tw;
     cplx<T>* tw = reinterpret_cast<cplx<T>*>(smem_raw);
-    cplx<T>* bufA = tw + L;
-    cplx<T>* bufB = bufA + (size_t)P * L;
-    T* raw = reinterpret_cast<T*>(bufB + (size_t)P * L);
+    cplx<T>* bufA = tw + ntw;
+    cplx<T>* bufB = bufA + (size_t)P * Lb;
+    T* raw = reinterpret_cast<T*>(bufB + (size_t)P * Lb);
     T* ex = raw + lns;
     constexpr bool cols = (OP == OP_COL_SOLVE || OP == OP_COL_EG);
     // global line index of local line l, or -1
@@ -551,7 +599,8 @@ __global__ void __launch_bounds__(kThreads, TVD_LINE_MINB) line_kernel(LineArgs<
 
     // ---- stage the lines and their per-pixel factors: asynchronous copies,
     // all of them in flight before the first wait
-    for (int i = threadIdx.x; i < L; i += kThreads) cp_async_elem(&tw[i].re, &a.tw[i].re), cp_async_elem(&tw[i].im, &a.tw[i].im);
+    for (int i = threadIdx.x; i < ntw; i += kThreads)
+        cp_async_elem(&tw[i].re, &twsrc[i].re), cp_async_elem(&tw[i].im, &twsrc[i].im);
     if (!cols) {
         for (Walk w(n); w.hi < lines; w.next(n)) {
             const int l = w.hi, idx = w.lo;
@@ -700,6 +749,16 @@ FftPlan make_fft_plan(int L) {
         while (m % r == 0) push(r);
     for (int r = 37; m > 1; r += 2)
         while (m % r == 0) push(r);
+    for (int s = 0; s < fp.nstages; ++s)
+        if (fp.radix[s] > 31) fp.bl = 1;
+    if (fp.bl) {
+        int M2 = 1;
+        while (M2 < 2 * L - 1) M2 *= 2;
+        fp.M2 = M2;
+        int q = M2;
+        while (q % 4 == 0) fp.radix2[fp.nst2++] = 4, q /= 4;
+        while (q % 2 == 0) fp.radix2[fp.nst2++] = 2, q /= 2;
+    }
     return fp;
 }
 
@@ -707,7 +766,8 @@ template <typename T>
 static size_t line_smem(const LineArgs<T>& a, int op) {
     const size_t lines = 2 * (size_t)a.P;
     // tw + bufA + bufB + raw + the operation's staged factors / outputs
-    return sizeof(cplx<T>) * ((size_t)a.L + 2 * (size_t)a.P * a.L) +
+    const size_t Lb = a.fp.bl ? (size_t)a.fp.M2 : (size_t)a.L;
+    return sizeof(cplx<T>) * (Lb + 2 * (size_t)a.P * Lb) +
            sizeof(T) * (lines * a.ns + line_extra(op, lines, a.ns, a.P)) + 64;
 }
 
@@ -746,6 +806,10 @@ template <typename T, int BC, int OP>
 static tvd_status launch_line(LineArgs<T> a, cudaStream_t s) {
     const bool cols = (OP == OP_COL_SOLVE || OP == OP_COL_EG);
     pick_pairs<T>(a, cols, OP);
+    if (a.fp.bl && line_smem<T>(a, OP) > 227 * 1024) {
+        a.fp.bl = 0;   // the M2-point buffers do not fit: direct sums for the large prime factors
+        pick_pairs<T>(a, cols, OP);
+    }
     const int per_block = (OP == OP_COL_EG) ? a.P : 2 * a.P;
     const int blocks = (a.nlines + per_block - 1) / per_block;
     const size_t smem = line_smem<T>(a, OP);
@@ -777,6 +841,7 @@ static LineArgs<T> base_args(const tvd_plan_s& p, const Ops<T>& o, bool cols) {
     a.fp = cols ? p.fft_r : p.fft_c;
     a.L = a.fp.L;
     a.tw = cols ? o.tw_r : o.tw_c;
+    a.blt = cols ? o.blt_r : o.blt_c;
     a.aux = cols ? o.aux_r : o.aux_c;
     a.red = p.red;
     a.ticket = p.ticket + 2;

@@ -6,6 +6,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <complex>
 #include <cstring>
 
 namespace tvd {
@@ -82,6 +83,49 @@ static void transform_tables(int n, tvd_bc bc, std::vector<double>& tw, std::vec
     }
 }
 
+// Bluestein tables of a plan with fp.bl, as interleaved (re, im) doubles:
+// chirp c_j = exp(-i pi j^2 / L) (j < L); the spectrum of the filter
+// b_m = conj(c_|m|) (m = -(L-1) .. L-1, circular in M2) divided by M2; the M2
+// twiddles exp(-2 pi i k / M2). The filter spectrum comes from a radix-2 FFT
+// on the host in double.
+static void bluestein_tables(const FftPlan& fp, std::vector<double>& out) {
+    const int L = fp.L, M2 = fp.M2;
+    std::vector<std::complex<double>> c(L), b(M2, 0.0);
+    for (int j = 0; j < L; ++j) {
+        const long long q = ((long long)j * j) % (2LL * L);   // exact j^2 mod 2L keeps the angle small
+        c[j] = std::polar(1.0, -M_PI * (double)q / L);
+    }
+    b[0] = std::conj(c[0]);
+    for (int m = 1; m < L; ++m) b[m] = b[M2 - m] = std::conj(c[m]);
+    // iterative radix-2 DFT of b (bit reversal, then butterflies)
+    for (int i = 1, j = 0; i < M2; ++i) {
+        int bit = M2 >> 1;
+        for (; j & bit; bit >>= 1) j ^= bit;
+        j ^= bit;
+        if (i < j) std::swap(b[i], b[j]);
+    }
+    for (int len = 2; len <= M2; len <<= 1)
+        for (int i = 0; i < M2; i += len)
+            for (int k = 0; k < len / 2; ++k) {
+                const std::complex<double> w = std::polar(1.0, -2.0 * M_PI * k / len);
+                const std::complex<double> u = b[i + k], v = b[i + k + len / 2] * w;
+                b[i + k] = u + v;
+                b[i + k + len / 2] = u - v;
+            }
+    out.assign(2 * ((size_t)L + 2 * (size_t)M2), 0.0);
+    for (int j = 0; j < L; ++j) {
+        out[2 * j] = c[j].real();
+        out[2 * j + 1] = c[j].imag();
+    }
+    for (int m = 0; m < M2; ++m) {
+        out[2 * ((size_t)L + m)] = b[m].real() / M2;
+        out[2 * ((size_t)L + m) + 1] = b[m].imag() / M2;
+        const std::complex<double> w = std::polar(1.0, -2.0 * M_PI * m / M2);
+        out[2 * ((size_t)L + M2 + m)] = w.real();
+        out[2 * ((size_t)L + M2 + m) + 1] = w.imag();
+    }
+}
+
 template <typename T>
 static tvd_status ops_alloc(tvd_plan_s& p, Ops<T>& o, cudaStream_t s) {
     const size_t n = (size_t)p.nr * p.nc;
@@ -139,6 +183,14 @@ static tvd_status ops_alloc(tvd_plan_s& p, Ops<T>& o, cudaStream_t s) {
     transform_tables(p.nr, p.bc, tw, aux);
     TVD_TRY(upload<T>((T**)&o.tw_r, tw, s));
     TVD_TRY(upload<T>(&o.aux_r, aux, s));
+    if (p.fft_c.bl) {
+        bluestein_tables(p.fft_c, tw);
+        TVD_TRY(upload<T>((T**)&o.blt_c, tw, s));
+    }
+    if (p.fft_r.bl) {
+        bluestein_tables(p.fft_r, tw);
+        TVD_TRY(upload<T>((T**)&o.blt_r, tw, s));
+    }
     TVD_TRY(lamH2_setup<T>(p, o, s));
     return TVD_OK;
 }
@@ -146,7 +198,7 @@ static tvd_status ops_alloc(tvd_plan_s& p, Ops<T>& o, cudaStream_t s) {
 template <typename T>
 static void ops_free(Ops<T>& o) {
     dfree(o.hdense); dfree(o.arange); dfree(o.runs); dfree(o.runv); o.nruns = 0; dfree(o.crow); dfree(o.ccol); dfree(o.ccor);
-    dfree(o.tw_c); dfree(o.tw_r); dfree(o.aux_c); dfree(o.aux_r);
+    dfree(o.tw_c); dfree(o.tw_r); dfree(o.aux_c); dfree(o.aux_r); dfree(o.blt_c); dfree(o.blt_r);
     dfree(o.lamH2); dfree(o.inv_spec); dfree(o.w); dfree(o.dmh); dfree(o.dinv);
     dfree(o.x); dfree(o.r); dfree(o.z); dfree(o.p); dfree(o.p2); dfree(o.q); dfree(o.t); dfree(o.t2);
     o.allocated = false;

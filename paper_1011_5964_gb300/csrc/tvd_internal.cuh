@@ -79,11 +79,18 @@ struct cplx {
     T re, im;
 };
 
-// Radix plan of a length-L complex FFT (Stockham, mixed radix).
+// Radix plan of a length-L complex FFT (Stockham, mixed radix). When L has a
+// prime factor above 31, bl = 1 and the transform is Bluestein's: a circular
+// convolution of length M2 (a power of two >= 2L - 1) done by M2-point FFTs
+// with the radices radix2.
 struct FftPlan {
     int L = 0;
     int nstages = 0;
     int radix[24] = {0};
+    int bl = 0;
+    int M2 = 0;
+    int nst2 = 0;
+    int radix2[16] = {0};
 };
 
 FftPlan make_fft_plan(int L);
@@ -133,6 +140,8 @@ struct Ops {
     // column-direction (length L_r) complex FFTs, plus per-transform aux tables
     cplx<T>* tw_c = nullptr;
     cplx<T>* tw_r = nullptr;
+    cplx<T>* blt_c = nullptr;   // Bluestein tables (plans with bl): chirp (L) | filter spectrum (M2) | M2 twiddles
+    cplx<T>* blt_r = nullptr;
     T* aux_c = nullptr;      // see transform.cu: per-length auxiliary factors
     T* aux_r = nullptr;
     // preconditioner data
