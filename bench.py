@@ -67,9 +67,6 @@ WORDS_PER_PIXEL = {
 # profiles/transform_and_blur_kernels_1024_mixed.md. Valid only for the kernel
 # versions captured there: remove an entry when its kernel changes.
 NCU_TRAFFIC = {
-    "precond_row_forward.f32": 21074944,
-    "precond_column_solve.f32": 8534272,
-    "precond_row_inverse.f32": 12691200,
     "blur_adjoint_L.f32": 12625408,
 }
 
