@@ -104,12 +104,11 @@ struct FuseArgs {
 // RB input values it needs in registers and shifting them by one row per tap,
 // so one shared-memory load feeds RB multiply-adds.
 template <typename T, int EXT, bool FUSE, bool PUP>
-__global__ void __launch_bounds__(kThreads)
-blur_tile_kernel(const T* __restrict__ x, T* __restrict__ y, int nr, int nc, int mr, int mc,
-                 const T* __restrict__ hdense, const int* __restrict__ arange,
-                 const int* __restrict__ runs, const T* __restrict__ runv, int nruns,
-                 const T* __restrict__ w, T* p0, T* p1, FuseArgs fa) {
-    if (fa.st && fa.st->done) return;
+__device__ __forceinline__ void tile_body(int bx, int by, int gx, const T* __restrict__ x, T* __restrict__ y, int nr,
+                                          int nc, int mr, int mc, const T* __restrict__ hdense,
+                                          const int* __restrict__ arange, const int* __restrict__ runs,
+                                          const T* __restrict__ runv, int nruns, const T* __restrict__ w, T* p0,
+                                          T* p1, const FuseArgs& fa) {
     // FUSE: the direction of this iteration; PUP: old and new direction buffers
     const int pb = fa.st ? fa.st->pbuf : 0;
     const T* pv = fa.st ? (pb ? p0 : p1) : p0;
@@ -129,7 +128,7 @@ blur_tile_kernel(const T* __restrict__ x, T* __restrict__ y, int nr, int nc, int
     T* srv = pre + (nruns ? TH * (TW + 1) : 0);      // runs: values
     int* sr = reinterpret_cast<int*>(srv + nruns);   // per column offset: first and last tap row
     int* srun = sr + 2 * PW;                         // runs: (a, first b, last b)
-    const int r0 = blockIdx.y * BTH - mr, c0 = blockIdx.x * BTW - mc;
+    const int r0 = by * BTH - mr, c0 = bx * BTW - mc;
     // stage the extended input tile: a plain asynchronous copy where the tile
     // lies inside the image (away from the boundary lines for EXT_ODD), the
     // BC extension computed on the fly elsewhere
@@ -144,7 +143,7 @@ blur_tile_kernel(const T* __restrict__ x, T* __restrict__ y, int nr, int nc, int
         }
     }
     if (FUSE) {
-        const int i0 = blockIdx.y * BTH - 1, j0 = blockIdx.x * BTW - 1;
+        const int i0 = by * BTH - 1, j0 = bx * BTW - 1;
         for (int idx = threadIdx.x; idx < LSW * LSH; idx += blockDim.x) {
             const int li = idx / LSW, lj = idx - li * LSW;
             const int i = i0 + li, j = j0 + lj;
@@ -179,7 +178,7 @@ blur_tile_kernel(const T* __restrict__ x, T* __restrict__ y, int nr, int nc, int
         // this block's outputs of the new direction (plain values: inside the image)
         for (int idx = threadIdx.x; idx < BTW * BTH; idx += blockDim.x) {
             const int li = idx / BTW, lj = idx - li * BTW;
-            const int i = blockIdx.y * BTH + li, j = blockIdx.x * BTW + lj;
+            const int i = by * BTH + li, j = bx * BTW + lj;
             if (i < nr && j < nc) pnew[(size_t)i * nc + j] = tile[(li + mr) * TW + (lj + mc)];
         }
     }
@@ -238,10 +237,10 @@ blur_tile_kernel(const T* __restrict__ x, T* __restrict__ y, int nr, int nc, int
         }
     }
     T part = T(0);   // per-thread partial of p^T q in the kernel's type
-    const int j = blockIdx.x * BTW + tx;
+    const int j = bx * BTW + tx;
 #pragma unroll
     for (int k = 0; k < RB; ++k) {
-        const int i = blockIdx.y * BTH + ty * RB + k;
+        const int i = by * BTH + ty * RB + k;
         if (i >= nr || j >= nc) continue;
         if (EXT == EXT_ODD && (i == 0 || i == nr - 1 || j == 0 || j == nc - 1)) continue;
         T out = acc[k];
@@ -260,12 +259,23 @@ blur_tile_kernel(const T* __restrict__ x, T* __restrict__ y, int nr, int nc, int
         y[(size_t)i * nc + j] = out;
     }
     if (FUSE && fa.reduce) {
-        const int slot = fa.slot0 + blockIdx.y * gridDim.x + blockIdx.x;
+        const int slot = fa.slot0 + by * gx + bx;
         double s;
         if (block_reduce_last((double)part, fa.red, fa.ticket, slot, fa.total_blocks, &s) && threadIdx.x == 0 &&
             fa.finish_here)
             finish_pq(fa.st, s);
     }
+}
+
+template <typename T, int EXT, bool FUSE, bool PUP>
+__global__ void __launch_bounds__(kThreads)
+blur_tile_kernel(const T* __restrict__ x, T* __restrict__ y, int nr, int nc, int mr, int mc,
+                 const T* __restrict__ hdense, const int* __restrict__ arange,
+                 const int* __restrict__ runs, const T* __restrict__ runv, int nruns,
+                 const T* __restrict__ w, T* p0, T* p1, FuseArgs fa) {
+    if (fa.st && fa.st->done) return;
+    tile_body<T, EXT, FUSE, PUP>(blockIdx.x, blockIdx.y, gridDim.x, x, y, nr, nc, mr, mc, hdense, arange, runs, runv,
+                                 nruns, w, p0, p1, fa);
 }
 
 // odd extension along one axis: returns the sign (0 on the boundary lines and
@@ -295,17 +305,15 @@ __device__ __forceinline__ int odd_map(int I, int n, int* idx) {
 constexpr int kSeg = 32;
 
 template <typename T, bool FUSE>
-__global__ void __launch_bounds__(kThreads)
-ar_adjoint_border_kernel(const T* __restrict__ y, T* __restrict__ out, int nr, int nc, int mr, int mc,
-                         const T* __restrict__ crow, const T* __restrict__ ccol, const T* __restrict__ ccor,
-                         const T* __restrict__ w, const T* p0, const T* p1, FuseArgs fa) {
-    if (fa.st && fa.st->done) return;
+__device__ __forceinline__ void border_body(int bid, const T* __restrict__ y, T* __restrict__ out, int nr, int nc,
+                                            int mr, int mc, const T* __restrict__ crow, const T* __restrict__ ccol,
+                                            const T* __restrict__ ccor, const T* __restrict__ w, const T* p0,
+                                            const T* p1, const FuseArgs& fa, T* partial) {
+    const int slot = fa.slot0 + bid;
     const T* pv = fa.st ? (fa.st->pbuf ? p0 : p1) : p0;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T* strip = reinterpret_cast<T*>(smem_raw);
-    __shared__ T partial[kThreads];
     const int nseg_r = (nc - 2 + kSeg - 1) / kSeg, nseg_c = (nr - 2 + kSeg - 1) / kSeg;
-    int bid = blockIdx.x;
     const int o = threadIdx.x % kSeg, grp = threadIdx.x / kSeg, ngrp = kThreads / kSeg;
     T acc = T(0);
     int oi = -1, oj = -1;
@@ -381,10 +389,32 @@ ar_adjoint_border_kernel(const T* __restrict__ y, T* __restrict__ out, int nr, i
     }
     if (FUSE && fa.reduce) {
         double s;
-        if (block_reduce_last((double)part, fa.red, fa.ticket, fa.slot0 + blockIdx.x, fa.total_blocks, &s) &&
-            threadIdx.x == 0 && fa.finish_here)
+        if (block_reduce_last((double)part, fa.red, fa.ticket, slot, fa.total_blocks, &s) && threadIdx.x == 0 &&
+            fa.finish_here)
             finish_pq(fa.st, s);
     }
+}
+
+// The AR adjoint in one launch: blocks 0 .. tile_blocks-1 compute the interior
+// tiles (gx tiles per row of tiles), the rest the border lines, so the small
+// border work runs beside the interior instead of after it. Both parts reduce
+// p^T q into one ticket; whichever block arrives last finishes.
+template <typename T, bool FUSE>
+__global__ void __launch_bounds__(kThreads)
+ar_adjoint_kernel(const T* __restrict__ x, T* __restrict__ y, int nr, int nc, int mr, int mc,
+                  const T* __restrict__ hdense, const int* __restrict__ arange, const int* __restrict__ runs,
+                  const T* __restrict__ runv, int nruns, const T* __restrict__ crow, const T* __restrict__ ccol,
+                  const T* __restrict__ ccor, const T* __restrict__ w, T* p0, T* p1, int tile_blocks, int gx,
+                  FuseArgs fa_tile, FuseArgs fa_border) {
+    if (fa_tile.st && fa_tile.st->done) return;
+    __shared__ T partial[kThreads];
+    const int bid = blockIdx.x;
+    if (bid < tile_blocks)
+        tile_body<T, EXT_ODD, FUSE, false>(bid % gx, bid / gx, gx, x, y, nr, nc, mr, mc, hdense, arange, runs, runv,
+                                           nruns, w, p0, p1, fa_tile);
+    else
+        border_body<T, FUSE>(bid - tile_blocks, x, y, nr, nc, mr, mc, crow, ccol, ccor, w, p0, p1, fa_border,
+                             partial);
 }
 
 static size_t border_smem(int mr, int mc, size_t elem) {
@@ -424,7 +454,7 @@ static tvd_status launch_blur(const tvd_plan_s& p, const Ops<T>& o, bool transpo
     const int tile_blocks = (int)(grid.x * grid.y);
     const int border_blocks = 2 * ((nc - 2 + kSeg - 1) / kSeg) + 2 * ((nr - 2 + kSeg - 1) / kSeg) + 1;
     const bool ar_adj = transpose && p.bc == TVD_BC_ANTIREFLECTIVE;
-    ProfScope prof(prof_class<T>((transpose || fuse) ? PROF_BLUR_ADJ : PROF_BLUR_FWD), s, ar_adj ? 2 : 1);
+    ProfScope prof(prof_class<T>((transpose || fuse) ? PROF_BLUR_ADJ : PROF_BLUR_FWD), s);
     if (fa.reduce) {
         fa.total_blocks = tile_blocks + (ar_adj ? border_blocks : 0);
         if (fa.total_blocks > kMaxRedBlocks) {
@@ -446,21 +476,25 @@ static tvd_status launch_blur(const tvd_plan_s& p, const Ops<T>& o, bool transpo
         if (fuse) TVD_TRY((launch_tile<T, EXT_R, true, false>(grid, smem, s, x, y, p, o, w, p0, p1, fa)));
         else TVD_TRY((launch_tile<T, EXT_R, false, false>(grid, smem, s, x, y, p, o, w, p0, p1, fa)));
     } else {
-        fa.finish_here = 0;
-        fa.slot0 = 0;
-        if (fuse) TVD_TRY((launch_tile<T, EXT_ODD, true, false>(grid, smem, s, x, y, p, o, w, p0, p1, fa)));
-        else TVD_TRY((launch_tile<T, EXT_ODD, false, false>(grid, smem, s, x, y, p, o, w, p0, p1, fa)));
+        // interior tiles and border lines in one launch (1D grid: tiles first)
+        FuseArgs fb = fa;
         fa.finish_here = 1;
-        fa.slot0 = tile_blocks;
+        fa.slot0 = 0;
+        fb.finish_here = 1;
+        fb.slot0 = tile_blocks;
         const size_t bsm = border_smem(mr, mc, sizeof(T));
+        const size_t msm = smem > bsm ? smem : bsm;
+        const int blocks = tile_blocks + border_blocks;
         if (fuse) {
-            TVD_CUDA_TRY((allow_max_smem<ar_adjoint_border_kernel<T, true>>()));
-            ar_adjoint_border_kernel<T, true><<<border_blocks, kThreads, bsm, s>>>(x, y, nr, nc, mr, mc, o.crow,
-                                                                                o.ccol, o.ccor, w, p0, p1, fa);
+            TVD_CUDA_TRY((allow_max_smem<ar_adjoint_kernel<T, true>>()));
+            ar_adjoint_kernel<T, true><<<blocks, kThreads, msm, s>>>(
+                x, y, nr, nc, mr, mc, o.hdense, o.arange, o.runs, o.runv, o.nruns, o.crow, o.ccol, o.ccor, w, p0, p1,
+                tile_blocks, (int)grid.x, fa, fb);
         } else {
-            TVD_CUDA_TRY((allow_max_smem<ar_adjoint_border_kernel<T, false>>()));
-            ar_adjoint_border_kernel<T, false><<<border_blocks, kThreads, bsm, s>>>(x, y, nr, nc, mr, mc, o.crow,
-                                                                                 o.ccol, o.ccor, w, p0, p1, fa);
+            TVD_CUDA_TRY((allow_max_smem<ar_adjoint_kernel<T, false>>()));
+            ar_adjoint_kernel<T, false><<<blocks, kThreads, msm, s>>>(
+                x, y, nr, nc, mr, mc, o.hdense, o.arange, o.runs, o.runv, o.nruns, o.crow, o.ccol, o.ccor, w, p0, p1,
+                tile_blocks, (int)grid.x, fa, fb);
         }
     }
     TVD_CUDA_TRY(cudaGetLastError());
