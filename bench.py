@@ -67,7 +67,11 @@ WORDS_PER_PIXEL = {
 # profiles/transform_and_blur_kernels_1024_mixed.md. Valid only for the kernel
 # versions captured there: remove an entry when its kernel changes.
 NCU_TRAFFIC = {
-    "blur_adjoint_L.f32": 12625408,
+    "precond_row_forward.f32": 21096192,
+    "precond_column_solve.f32": 8563200,
+    "precond_row_inverse.f32": 12712192,
+    "blur_adjoint_L.f32": 12653568,
+    "blur_forward.f32": 8432128,
 }
 
 

@@ -797,6 +797,13 @@ static void pick_pairs(LineArgs<T>& a, bool cols, int op) {
     const size_t cap = 160 * 1024;
     for (;;) {
         a.P = P;
+        if (cols) {
+            // column passes stage element idx of line l at l * ns + idx, a warp
+            // covering 32 / 2P indices of all 2P lines: ns = K / 2P (mod K), K the
+            // shared-memory words of T in 128 bytes, spreads them over distinct banks
+            const int K = 128 / (int)sizeof(T), r = K / (2 * P);
+            a.ns = a.n + ((r - a.n % K) % K + K) % K;
+        }
         if (P == 1 || line_smem<T>(a, op) <= cap) break;
         P = P / 2;
     }
