@@ -749,8 +749,15 @@ FftPlan make_fft_plan(int L) {
         while (m % r == 0) push(r);
     for (int r = 37; m > 1; r += 2)
         while (m % r == 0) push(r);
+    // Bluestein from the smallest prime factor that the register butterflies do
+    // not take (32); TVD_BLUESTEIN_MIN_PRIME lowers the threshold (tuning)
+    static const int min_prime = []() {
+        const char* v = std::getenv("TVD_BLUESTEIN_MIN_PRIME");
+        const int q = v ? std::atoi(v) : 0;
+        return q >= 3 && q <= 32 ? q : 32;
+    }();
     for (int s = 0; s < fp.nstages; ++s)
-        if (fp.radix[s] > 31) fp.bl = 1;
+        if (fp.radix[s] >= min_prime) fp.bl = 1;
     if (fp.bl) {
         int M2 = 1;
         while (M2 < 2 * L - 1) M2 *= 2;
