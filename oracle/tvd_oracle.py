@@ -52,6 +52,7 @@ PC_NONE = "none"     # I: no preconditioner
 PC_DIAG = "diag"     # D = I + alpha diag(L(u)), eq. (D)
 PC_FAST = "fast"     # R (reflective) or M (anti-reflective), eqs. (R2), (M)
 PC_DFAST = "dfast"   # D_R = D^1/2 R D^1/2 or D_M = D^1/2 M D^1/2
+PC_FASTD = "fastd"   # R_D / M_D: the optimal preconditioner of the scaled system, eq. (scalesys)
 
 
 # --------------------------------------------------------------------------
@@ -374,6 +375,46 @@ def spectrum_L(w: np.ndarray, bc: str) -> np.ndarray:
     return Gr @ w @ Ec.T + Er @ w @ Gc.T
 
 
+def _E_F(n: int, bc: str):
+    """E[k,p] = b_k(p)^2 and F[k,p] = b_k(p) b_k(p+1) (0 for p = n-1)."""
+    B = transform_matrix(n, bc)
+    F = np.zeros_like(B)
+    F[:, :-1] = B[:, :-1] * B[:, 1:]
+    return B * B, F
+
+
+def spectrum_scaled(w: np.ndarray, d: np.ndarray, bc: str):
+    """(Lambda_D, Lambda_L~) of R_D / M_D (Secs. 2.1, 2.2, 3.2), d = D^-1/2 per pixel.
+
+    Lambda_D = diag(U diag(d) U^T) = E_r d E_c^T, the eigenvalues of the level-2
+    projection of D^-1/2. Lambda_L~ = diag(U L~ U^T) with L~ = D^-1/2 L D^-1/2:
+    for x = d o (b_i (x) b_j), x^T L x = sum_pq w_pq [(D_r x)_pq^2 + (D_c x)_pq^2],
+    and expanding (D_r x)_pq^2 = b_j(q)^2 [d_{p+1,q}^2 b_i(p+1)^2 + d_pq^2 b_i(p)^2
+    - 2 d_{p+1,q} d_pq b_i(p) b_i(p+1)] (and the column analogue) gives
+    Lambda_L~ = E_r S E_c^T - 2 F_r gamma E_c^T - 2 E_r delta F_c^T with
+    S = the D-weighted stencil diagonal, gamma_pq = w_pq d_{p+1,q} d_pq,
+    delta_pq = w_pq d_{p,q+1} d_pq.
+    """
+    w = np.asarray(w, dtype=np.float64)
+    d = np.asarray(d, dtype=np.float64)
+    nr, nc = w.shape
+    Er, Fr = _E_F(nr, bc)
+    Ec, Fc = _E_F(nc, bc)
+    d2 = d * d
+    S = np.zeros_like(w)
+    S[1:, :] += w[:-1, :] * d2[1:, :]
+    S[:-1, :] += w[:-1, :] * d2[:-1, :]
+    S[:, 1:] += w[:, :-1] * d2[:, 1:]
+    S[:, :-1] += w[:, :-1] * d2[:, :-1]
+    gam = np.zeros_like(w)
+    gam[:-1, :] = w[:-1, :] * d[1:, :] * d[:-1, :]
+    dlt = np.zeros_like(w)
+    dlt[:, :-1] = w[:, :-1] * d[:, 1:] * d[:, :-1]
+    lam_d = Er @ d @ Ec.T
+    lam_lt = Er @ S @ Ec.T - 2.0 * (Fr @ gam @ Ec.T) - 2.0 * (Er @ dlt @ Fc.T)
+    return lam_d, lam_lt
+
+
 # --------------------------------------------------------------------------
 # Preconditioners, Sec. 3
 # --------------------------------------------------------------------------
@@ -389,9 +430,16 @@ def precond_setup(u_lag, h, bc, alpha, beta, kind):
     nr, nc = w.shape
     D = 1.0 + alpha * tv_diag(w)
     P = {"kind": kind, "bc": bc, "w": w, "D": D, "alpha": alpha}
-    if kind in (PC_FAST, PC_DFAST):
+    if kind in (PC_FAST, PC_DFAST, PC_FASTD):
         lam_h = spectrum_H(h, nr, nc, bc)
-        spec = lam_h * lam_h + alpha * spectrum_L(w, bc)
+        if kind == PC_FASTD:
+            # R_D / M_D = H^^* H^ + alpha s_2(L~), H^ = s_2(H) s_2(D^-1/2): eigenvalues
+            # Lambda_H^2 Lambda_D^2 + alpha Lambda_L~; applied to the original system as
+            # D^1/2 M_D D^1/2 (PCG on eq. (scalesys) is PCG on eq. (fp) with that preconditioner)
+            lam_d, lam_lt = spectrum_scaled(w, 1.0 / np.sqrt(D), bc)
+            spec = lam_h * lam_h * lam_d * lam_d + alpha * lam_lt
+        else:
+            spec = lam_h * lam_h + alpha * spectrum_L(w, bc)
         if np.min(spec) <= 1e-300:
             raise ValueError("preconditioner spectrum is not positive")
         P["spec"] = spec
@@ -399,7 +447,7 @@ def precond_setup(u_lag, h, bc, alpha, beta, kind):
 
 
 def precond_apply(r: np.ndarray, P) -> np.ndarray:
-    """z = X^{-1} r for X in {I, D, R|M, D_R|D_M}.
+    """z = X^{-1} r for X in {I, D, R|M, D_R|D_M, R_D|M_D}.
 
     X^{-1} r = D^{-1/2} U^{-1} diag(spec)^{-1} U D^{-1/2} r for the scaled
     variants, with U = B_r (x) B_c applied as the 1D transform along each axis.
@@ -410,11 +458,12 @@ def precond_apply(r: np.ndarray, P) -> np.ndarray:
         return r.copy()
     if kind == PC_DIAG:
         return r / P["D"]
-    t = r / np.sqrt(P["D"]) if kind == PC_DFAST else r.copy()
+    scaled = kind in (PC_DFAST, PC_FASTD)
+    t = r / np.sqrt(P["D"]) if scaled else r.copy()
     t = transform_fwd(transform_fwd(t, bc, 1), bc, 0)
     t = t / P["spec"]
     t = transform_inv(transform_inv(t, bc, 0), bc, 1)
-    if kind == PC_DFAST:
+    if scaled:
         t = t / np.sqrt(P["D"])
     return t
 
