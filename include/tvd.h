@@ -60,7 +60,9 @@ typedef enum {
     TVD_PC_NONE = 0,   /* I */
     TVD_PC_DIAG = 1,   /* D = I + alpha diag(L(u)), eq. (D) */
     TVD_PC_FAST = 2,   /* R (reflective, eq. (R2)) or M (anti-reflective, Sec. 3.2) */
-    TVD_PC_DFAST = 3   /* D_R = D^1/2 R D^1/2 or D_M = D^1/2 M D^1/2 (default) */
+    TVD_PC_DFAST = 3,  /* D_R = D^1/2 R D^1/2 or D_M = D^1/2 M D^1/2 (default) */
+    TVD_PC_FASTD = 4   /* R_D or M_D: H^^* H^ + alpha s_2(D^-1/2 L D^-1/2), H^ = s_2(H) s_2(D^-1/2), the
+                          preconditioner of the scaled system eq. (scalesys), applied as D^1/2 M_D D^1/2 */
 } tvd_precond;
 
 /* Arithmetic of the plan. */

@@ -24,7 +24,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libtvd.so")
 
 BC = {"r": 0, "reflective": 0, "ar": 1, "antireflective": 1}
-PC = {"none": 0, "diag": 1, "fast": 2, "dfast": 3}
+PC = {"none": 0, "diag": 1, "fast": 2, "dfast": 3, "fastd": 4}
 MODE = {"fp64": 0, "mixed": 1}
 
 TVD_OK, TVD_EINVAL, TVD_EPSF_ASYM, TVD_EPSF_SIZE, TVD_ENOMEM, TVD_ECUDA, TVD_ENOCONV, TVD_EBREAKDOWN, TVD_ETIMEOUT = range(9)

@@ -33,7 +33,7 @@
 
 namespace tvd {
 
-enum { OP_ROW_FWD = 0, OP_COL_SOLVE = 1, OP_ROW_INV = 2, OP_ROW_EG = 3, OP_COL_EG = 4 };
+enum { OP_ROW_FWD = 0, OP_COL_SOLVE = 1, OP_ROW_INV = 2, OP_ROW_EG = 3, OP_COL_EG = 4, OP_ROW_X = 5, OP_COL_X = 6 };
 enum { BCK_AR = 0, BCK_R = 1 };
 
 // Auxiliary tables per transform length, 8 slots of 2n values of T each:
@@ -73,6 +73,7 @@ struct LineArgs {
     double* red;
     unsigned int* ticket;
     int* bad;            // COL_EG: set if a spectrum entry is not positive
+    int xa, xb;          // ROW_X / COL_X: contraction of line a (in0) / b (in1): 0 = E, 1 = F
     // ROW_FWD on the CG path: the pending x += alpha p, r -= alpha q of the
     // previous iteration (in0 is r, updated in place) and the stopping test
     T* xvec;
@@ -466,7 +467,7 @@ __device__ void dct_lines(T* raw, cplx<T>* bufA, cplx<T>* bufB, const LineArgs<T
 // E f and G f for each raw line pair member; writes E into eo[l*n+k], G into go.
 template <typename T, int BC>
 __device__ void eg_lines(const T* raw, cplx<T>* bufA, cplx<T>* bufB, T* eo, T* go, const LineArgs<T>& a,
-                         const cplx<T>* tw) {
+                         const cplx<T>* tw, bool second_f = false) {
     const int n = a.n, ns = a.ns, P = a.P, L = a.L;
     for (Walk w(L); w.hi < P; w.next(L)) {
         const int pp = w.hi, j = w.lo;
@@ -485,9 +486,11 @@ __device__ void eg_lines(const T* raw, cplx<T>* bufA, cplx<T>* bufB, T* eo, T* g
             if (k == 0) {
                 ea = ga = fa[0];
                 eb = gb = fb[0];
+                if (second_f) ga = gb = T(0);   // e_0: no neighbour product
             } else if (k == n - 1) {
                 ea = fa[n - 1]; ga = fa[n - 2];
                 eb = fb[n - 1]; gb = fb[n - 2];
+                if (second_f) ga = gb = T(0);   // e_{n-1}: no forward neighbour
             } else {
                 cplx<T> F0a, F0b, Fa, Fb;
                 split_pair(Zp, 0, M, F0a, F0b);
@@ -497,8 +500,14 @@ __device__ void eg_lines(const T* raw, cplx<T>* bufA, cplx<T>* bufB, T* eo, T* g
                 const T invM = T(1) / T(M);
                 ea = (F0a.re - Fa.re) * invM;
                 eb = (F0b.re - Fb.re) * invM;
-                ga = g * (F0a.re + eh.re * Fa.re + eh.im * Fa.im);
-                gb = g * (F0b.re + eh.re * Fb.re + eh.im * Fb.im);
+                if (second_f) {
+                    // F[k,p] = b_k(p) b_k(p+1) = (cos(k pi/M) - cos(k (2p+1) pi/M)) / M
+                    ga = (eh.re * F0a.re - (eh.re * Fa.re + eh.im * Fa.im)) * invM;
+                    gb = (eh.re * F0b.re - (eh.re * Fb.re + eh.im * Fb.im)) * invM;
+                } else {
+                    ga = g * (F0a.re + eh.re * Fa.re + eh.im * Fa.im);
+                    gb = g * (F0b.re + eh.re * Fb.re + eh.im * Fb.im);
+                }
             }
         } else {
             cplx<T> F0a, F0b, Fa, Fb;
@@ -509,8 +518,14 @@ __device__ void eg_lines(const T* raw, cplx<T>* bufA, cplx<T>* bufB, T* eo, T* g
             const T ce = a.aux[6 * n + k], cg = a.aux[8 * n + k];
             ea = ce * (F0a.re + eh.re * Fa.re + eh.im * Fa.im);
             eb = ce * (F0b.re + eh.re * Fb.re + eh.im * Fb.im);
-            ga = cg * (F0a.re - (w.re * Fa.re - w.im * Fa.im));
-            gb = cg * (F0b.re - (w.re * Fb.re - w.im * Fb.im));
+            if (second_f) {
+                // F[k,p] = c_k^2 / 2 (cos(pi k/n) + cos(2 pi k (p+1)/n)) for p < n-1, 0 at p = n-1
+                ga = ce * (eh.re * F0a.re + (w.re * Fa.re - w.im * Fa.im) - (eh.re + T(1)) * fa[n - 1]);
+                gb = ce * (eh.re * F0b.re + (w.re * Fb.re - w.im * Fb.im) - (eh.re + T(1)) * fb[n - 1]);
+            } else {
+                ga = cg * (F0a.re - (w.re * Fa.re - w.im * Fa.im));
+                gb = cg * (F0b.re - (w.re * Fb.re - w.im * Fb.im));
+            }
         }
         eo[(size_t)(2 * pp) * ns + k] = ea;
         eo[(size_t)(2 * pp + 1) * ns + k] = eb;
@@ -541,7 +556,7 @@ __host__ __device__ constexpr size_t line_extra(int op, size_t lines, size_t n, 
     return op == OP_ROW_FWD ? lines * n
          : op == OP_COL_SOLVE ? lines * n
          : op == OP_ROW_INV ? 2 * lines * n
-         : op == OP_ROW_EG ? 2 * lines * n
+         : (op == OP_ROW_EG || op == OP_ROW_X || op == OP_COL_X) ? 2 * lines * n
          : 2 * lines * n + P * n;
 }
 
@@ -588,11 +603,13 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? TVD_LINE_MINB : 1) 
     cplx<T>* bufB = bufA + (size_t)P * Lb;
     T* raw = reinterpret_cast<T*>(bufB + (size_t)P * Lb);
     T* ex = raw + lns;
-    constexpr bool cols = (OP == OP_COL_SOLVE || OP == OP_COL_EG);
+    constexpr bool cols = (OP == OP_COL_SOLVE || OP == OP_COL_EG || OP == OP_COL_X);
+    // line pairs from two arrays (line a of pair pp from in0, line b from in1)
+    constexpr bool two_in = (OP == OP_COL_EG || OP == OP_ROW_X || OP == OP_COL_X);
     // global line index of local line l, or -1
     auto gline = [&](int l) -> int {
         int g;
-        if (OP == OP_COL_EG) g = blockIdx.x * P + (l >> 1);
+        if (two_in) g = blockIdx.x * P + (l >> 1);
         else g = blockIdx.x * lines + l;
         return g < a.nlines ? g : -1;
     };
@@ -611,7 +628,7 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? TVD_LINE_MINB : 1) 
                 continue;
             }
             const size_t o = (size_t)g * a.nc + idx;
-            cp_async_elem(raw + si, a.in0 + o);
+            cp_async_elem(raw + si, ((two_in && (l & 1)) ? a.in1 : a.in0) + o);
             if ((OP == OP_ROW_FWD || OP == OP_ROW_INV) && a.scale) cp_async_elem(ex + si, a.scale + o);
             if (OP == OP_ROW_INV && a.st) cp_async_elem(ex + lns + si, a.rvec + o);
         }
@@ -625,7 +642,7 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? TVD_LINE_MINB : 1) 
                 continue;
             }
             const size_t o = (size_t)idx * a.nc + g;
-            cp_async_elem(raw + si, ((OP == OP_COL_EG && (l & 1)) ? a.in1 : a.in0) + o);
+            cp_async_elem(raw + si, ((two_in && (l & 1)) ? a.in1 : a.in0) + o);
             if (OP == OP_COL_SOLVE) cp_async_elem(ex + si, a.spec + o);
             if (OP == OP_COL_EG && !(l & 1)) cp_async_elem(ex + 2 * lns + (l >> 1) * ns + idx, a.spec + o);
         }
@@ -667,6 +684,22 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? TVD_LINE_MINB : 1) 
     }
 
     // ---- transform(s)
+    if (OP == OP_ROW_X || OP == OP_COL_X) {
+        // line a -> out0 = (xa ? F : E) a, line b -> out1 = (xb ? F : E) b, both in the input layout
+        T* eo = ex;
+        T* fo = ex + lns;
+        eg_lines<T, BC>(raw, bufA, bufB, eo, fo, a, tw, true);
+        for (Walk w(n); w.hi < lines; w.next(n)) {
+            const int l = w.hi, idx = w.lo;
+            const int g = gline(l);
+            if (g < 0) continue;
+            const bool second = (l & 1) ? a.xb != 0 : a.xa != 0;
+            const T v = second ? fo[l * ns + idx] : eo[l * ns + idx];
+            T* out = (l & 1) ? a.out1 : a.out0;
+            out[cols ? (size_t)idx * a.nc + g : (size_t)g * a.nc + idx] = v;
+        }
+        return;
+    }
     if (OP == OP_ROW_EG || OP == OP_COL_EG) {
         T* eo = ex;
         T* go = ex + lns;
@@ -818,13 +851,13 @@ static void pick_pairs(LineArgs<T>& a, bool cols, int op) {
 
 template <typename T, int BC, int OP>
 static tvd_status launch_line(LineArgs<T> a, cudaStream_t s) {
-    const bool cols = (OP == OP_COL_SOLVE || OP == OP_COL_EG);
+    const bool cols = (OP == OP_COL_SOLVE || OP == OP_COL_EG || OP == OP_COL_X);
     pick_pairs<T>(a, cols, OP);
     if (a.fp.bl && line_smem<T>(a, OP) > 227 * 1024) {
         a.fp.bl = 0;   // the M2-point buffers do not fit: direct sums for the large prime factors
         pick_pairs<T>(a, cols, OP);
     }
-    const int per_block = (OP == OP_COL_EG) ? a.P : 2 * a.P;
+    const int per_block = (OP == OP_COL_EG || OP == OP_ROW_X || OP == OP_COL_X) ? a.P : 2 * a.P;
     const int blocks = (a.nlines + per_block - 1) / per_block;
     const size_t smem = line_smem<T>(a, OP);
     if (smem > 227 * 1024) {
@@ -837,7 +870,8 @@ static tvd_status launch_line(LineArgs<T> a, cudaStream_t s) {
     }
     TVD_CUDA_TRY((allow_max_smem<line_kernel<T, BC, OP>>()));
     constexpr int cls = OP == OP_ROW_FWD ? PROF_ROW_FWD : OP == OP_COL_SOLVE ? PROF_COL_SOLVE
-                      : OP == OP_ROW_INV ? PROF_ROW_INV : OP == OP_ROW_EG ? PROF_EG_ROW : PROF_EG_COL;
+                      : OP == OP_ROW_INV ? PROF_ROW_INV : (OP == OP_ROW_EG || OP == OP_ROW_X) ? PROF_EG_ROW
+                      : PROF_EG_COL;
     ProfScope prof(prof_class<T>(cls), s);
     line_kernel<T, BC, OP><<<blocks, kThreads, smem, s>>>(a);
     TVD_CUDA_TRY(cudaGetLastError());
@@ -865,7 +899,7 @@ static LineArgs<T> base_args(const tvd_plan_s& p, const Ops<T>& o, bool cols) {
 template <typename T>
 tvd_status precond_solve(const tvd_plan_s& p, const Ops<T>& o, const T* r, T* z, CgState* st, cudaStream_t s,
                          T* x) {
-    const bool scaled = (p.pc == TVD_PC_DFAST);
+    const bool scaled = (p.pc == TVD_PC_DFAST || p.pc == TVD_PC_FASTD);
     LineArgs<T> a = base_args<T>(p, o, false);
     a.in0 = r;
     a.out0 = o.t;
@@ -899,8 +933,83 @@ tvd_status precond_solve(const tvd_plan_s& p, const Ops<T>& o, const T* r, T* z,
     return TVD_OK;
 }
 
+// Weights of the scaled-system spectrum (R_D / M_D), d = D^-1/2: S = d^2 diag(L(w))
+// (the stencil diagonal with d^2 at the pixel), gamma = w d_{i+1,j} d_ij (rows),
+// delta = w d_{i,j+1} d_ij (columns), zero where the forward difference is.
+template <typename T>
+__global__ void __launch_bounds__(kThreads)
+scaled_weights_kernel(const T* __restrict__ w, const T* __restrict__ d, T* __restrict__ S, T* __restrict__ gam,
+                      T* __restrict__ dlt, T* __restrict__ dout, int nr, int nc) {
+    const size_t n = (size_t)nr * nc;
+    for (size_t o = blockIdx.x * (size_t)blockDim.x + threadIdx.x; o < n; o += (size_t)gridDim.x * blockDim.x) {
+        const int i = (int)(o / nc), j = (int)(o - (size_t)i * nc);
+        const T di = d[o];
+        T diag = T(0);
+        if (i < nr - 1) diag += w[o];
+        if (i > 0) diag += w[o - nc];
+        if (j < nc - 1) diag += w[o];
+        if (j > 0) diag += w[o - 1];
+        S[o] = di * di * diag;
+        gam[o] = i < nr - 1 ? w[o] * d[o + nc] * di : T(0);
+        dlt[o] = j < nc - 1 ? w[o] * d[o + 1] * di : T(0);
+        dout[o] = di;
+    }
+}
+
+// 1 / (Lambda_H^2 Lambda_D^2 + alpha Lambda_L~) with Lambda_L~ = U1 - 2 U2 - 2 U3, Lambda_D = U4.
+template <typename T>
+__global__ void __launch_bounds__(kThreads)
+scaled_spec_kernel(const T* __restrict__ lamH2, const T* __restrict__ U1, const T* __restrict__ U2,
+                   const T* __restrict__ U3, const T* __restrict__ U4, double alpha, T* __restrict__ inv_out,
+                   int* bad, size_t n) {
+    for (size_t o = blockIdx.x * (size_t)blockDim.x + threadIdx.x; o < n; o += (size_t)gridDim.x * blockDim.x) {
+        const double ld = (double)U4[o];
+        const double lt = (double)U1[o] - 2.0 * (double)U2[o] - 2.0 * (double)U3[o];
+        const double sp = (double)lamH2[o] * ld * ld + alpha * lt;
+        if (!(sp > 1e-300) || !isfinite(sp)) atomicOr(bad, 1);
+        inv_out[o] = T(1.0 / sp);
+    }
+}
+
+// The R_D / M_D spectrum: Lambda_D = E_r d E_c^T and
+// Lambda_L~ = E_r S E_c^T - 2 F_r gamma E_c^T - 2 E_r delta F_c^T as two row passes
+// (E_c S, E_c gamma | F_c delta, E_c d), two column passes and an elementwise finish.
+// Uses o.z, o.p, o.p2, o.q, o.r, o.x, o.t, o.t2 as scratch (free between solves).
+template <typename T>
+static tvd_status scaled_spectrum_setup(const tvd_plan_s& p, Ops<T>& o, double alpha, int* bad_flag,
+                                        cudaStream_t s) {
+    const size_t n = (size_t)p.nr * p.nc;
+    const int blocks = num_sms() * 4;
+    {
+        ProfScope prof(prof_class<T>(PROF_TV), s);
+        scaled_weights_kernel<T><<<blocks, kThreads, 0, s>>>(o.w, o.dmh, o.z, o.p, o.p2, o.q, p.nr, p.nc);
+        TVD_CUDA_TRY(cudaGetLastError());
+    }
+    auto pass = [&](bool cols, const T* in0, const T* in1, T* out0, T* out1, int xa, int xb) -> tvd_status {
+        LineArgs<T> a = base_args<T>(p, o, cols);
+        a.in0 = in0;
+        a.in1 = in1;
+        a.out0 = out0;
+        a.out1 = out1;
+        a.xa = xa;
+        a.xb = xb;
+        if (p.bc == TVD_BC_ANTIREFLECTIVE)
+            return cols ? launch_line<T, BCK_AR, OP_COL_X>(a, s) : launch_line<T, BCK_AR, OP_ROW_X>(a, s);
+        return cols ? launch_line<T, BCK_R, OP_COL_X>(a, s) : launch_line<T, BCK_R, OP_ROW_X>(a, s);
+    };
+    TVD_TRY(pass(false, o.z, o.p, o.t, o.t2, 0, 0));    // E_c S, E_c gamma
+    TVD_TRY(pass(false, o.p2, o.q, o.r, o.x, 1, 0));    // F_c delta, E_c d
+    TVD_TRY(pass(true, o.t, o.t2, o.z, o.p, 0, 1));     // E_r (E_c S), F_r (E_c gamma)
+    TVD_TRY(pass(true, o.r, o.x, o.p2, o.q, 0, 0));     // E_r (F_c delta), E_r (E_c d)
+    ProfScope prof(prof_class<T>(PROF_EG_COL), s);
+    scaled_spec_kernel<T><<<blocks, kThreads, 0, s>>>(o.lamH2, o.z, o.p, o.p2, o.q, alpha, o.inv_spec, bad_flag, n);
+    TVD_CUDA_TRY(cudaGetLastError());
+    return TVD_OK;
+}
+
 template <typename T>
 tvd_status spectrum_setup(const tvd_plan_s& p, Ops<T>& o, double alpha, int* bad_flag, cudaStream_t s) {
+    if (p.pc == TVD_PC_FASTD) return scaled_spectrum_setup<T>(p, o, alpha, bad_flag, s);
     LineArgs<T> a = base_args<T>(p, o, false);
     a.in0 = o.w;
     a.out0 = o.t;

@@ -324,7 +324,7 @@ static tvd_status read_state(tvd_plan_s& p, cudaStream_t s) {
 // reads r anyway; with I and D they are a kernel of their own.
 template <typename T>
 static tvd_status enqueue_iteration(tvd_plan_s& p, Ops<T>& o, double alpha, T* x, CgState* st, cudaStream_t s) {
-    const bool fused_xr = (p.pc == TVD_PC_FAST || p.pc == TVD_PC_DFAST);
+    const bool fused_xr = (p.pc == TVD_PC_FAST || p.pc == TVD_PC_DFAST || p.pc == TVD_PC_FASTD);
     switch (p.pc) {
         case TVD_PC_NONE: TVD_TRY(cg_simple_precond<T>(p, o.r, nullptr, o.z, st, s)); break;
         case TVD_PC_DIAG: TVD_TRY(cg_simple_precond<T>(p, o.r, o.dinv, o.z, st, s)); break;
@@ -420,7 +420,7 @@ static tvd_status setup_precond(tvd_plan_s& p, Ops<T>& o, const T* u_lag, double
                                 cudaStream_t s) {
     TVD_TRY(diffusivity<T>(p, u_lag, beta, o.w, s));
     TVD_TRY(diag_scale<T>(p, o.w, alpha, o.dmh, o.dinv, s));
-    if (p.pc == TVD_PC_FAST || p.pc == TVD_PC_DFAST) {
+    if (p.pc == TVD_PC_FAST || p.pc == TVD_PC_DFAST || p.pc == TVD_PC_FASTD) {
         int* bad = reinterpret_cast<int*>(p.scal + 8);
         TVD_CUDA_TRY(cudaMemsetAsync(bad, 0, sizeof(int), s));
         TVD_TRY(spectrum_setup<T>(p, o, alpha, bad, s));
@@ -447,7 +447,7 @@ static tvd_status setup_mixed(tvd_plan_s& p, const double* u_lag, double alpha, 
     TVD_TRY(cast_d2f(p.d.w, p.f.w, n, s));
     TVD_TRY(cast_d2f(p.d.dmh, p.f.dmh, n, s));
     TVD_TRY(cast_d2f(p.d.dinv, p.f.dinv, n, s));
-    if (p.pc == TVD_PC_FAST || p.pc == TVD_PC_DFAST) {
+    if (p.pc == TVD_PC_FAST || p.pc == TVD_PC_DFAST || p.pc == TVD_PC_FASTD) {
         int* bad = reinterpret_cast<int*>(p.scal + 8);
         TVD_CUDA_TRY(cudaMemsetAsync(bad, 0, sizeof(int), s));
         TVD_TRY(spectrum_setup<float>(p, p.f, alpha, bad, s));
@@ -620,7 +620,7 @@ tvd_status tvd_plan_create(tvd_plan* out, int n_rows, int n_cols, const double* 
         set_error("image sides must be in [3, 2048] (FP64 plans) or [3, 4096] (MIXED plans)");
         return TVD_EINVAL;
     }
-    if ((bc != TVD_BC_REFLECTIVE && bc != TVD_BC_ANTIREFLECTIVE) || pc < TVD_PC_NONE || pc > TVD_PC_DFAST ||
+    if ((bc != TVD_BC_REFLECTIVE && bc != TVD_BC_ANTIREFLECTIVE) || pc < TVD_PC_NONE || pc > TVD_PC_FASTD ||
         (mode != TVD_MODE_FP64 && mode != TVD_MODE_MIXED)) {
         set_error("invalid bc / preconditioner / mode");
         return TVD_EINVAL;
@@ -758,7 +758,7 @@ tvd_status tv_deblur_adjoint(tvd_plan plan, const void* u_star, const void* v, d
         TVD_CUDA_TRY(cudaMemsetAsync(o.q, 0, n * sizeof(double), s));
         CgState* st = p.state;
         TVD_TRY(cg_init<double>(p, (const double*)dl_du, o.q, o.r, st, tol, maxit, s));
-        const bool fused_xr = (p.pc == TVD_PC_FAST || p.pc == TVD_PC_DFAST);
+        const bool fused_xr = (p.pc == TVD_PC_FAST || p.pc == TVD_PC_DFAST || p.pc == TVD_PC_FASTD);
         int done_iters = 0;
         for (;;) {
             for (int k = 0; k < 2 * kChunk; ++k) {

@@ -105,7 +105,7 @@ PC_SHAPES = [(37, 53), (64, 64), (3, 3), (4, 7), (128, 130), (96, 33)]
 
 
 @pytest.mark.parametrize("mode", ["fp64", "mixed"])
-@pytest.mark.parametrize("kind", ["dfast", "fast", "diag", "none"])
+@pytest.mark.parametrize("kind", ["dfast", "fast", "fastd", "diag", "none"])
 @pytest.mark.parametrize("bc", ["ar", "r"])
 @pytest.mark.parametrize("nr,nc", PC_SHAPES)
 def test_preconditioner_solve(torch_dev, nr, nc, bc, kind, mode):

@@ -37,7 +37,7 @@ def observe(n_rows, n_cols, h, bc, noise, seed):
     return synth.add_noise(O.blur(u_true, h, bc), synth.noise_direction(n_rows, n_cols, seed), noise)
 
 
-@pytest.mark.parametrize("bc,kind", [("ar", "dfast"), ("ar", "fast"), ("r", "dfast"), ("ar", "none"),
+@pytest.mark.parametrize("bc,kind", [("ar", "dfast"), ("ar", "fast"), ("r", "dfast"), ("ar", "fastd"), ("r", "fastd"), ("ar", "none"),
                                      ("r", "diag")])
 def test_pcg_solve_fp64_matches_oracle(tdev, bc, kind):
     torch, dev = tdev
@@ -60,7 +60,7 @@ def test_pcg_solve_fp64_matches_oracle(tdev, bc, kind):
     assert err < image_bound(x_ref, [p[0] for p in pert]), err
 
 
-@pytest.mark.parametrize("kind", ["dfast", "fast"])
+@pytest.mark.parametrize("kind", ["dfast", "fast", "fastd"])
 def test_config1_deblur_fp64_iteration_counts(tdev, kind):
     """64 x 64, AR, Gaussian sigma 1.5 on 9 x 9, 1% noise, alpha 1e-3, beta 1e-2, 10 FP steps, tol 1e-6."""
     torch, dev = tdev
