@@ -195,9 +195,10 @@ def batched_leg(pkg, torch, dev, synth):
             "timing": "host clock around the call, inputs resident"}
 
 
-def size_leg(pkg, torch, dev, synth, n, steps=2, warmup=1):
-    """The same workload at n x n (radius-7 disk on 31 x 31, AR, D_M, MIXED, 10 FP steps):
-    device time per deblur by CUDA events, L2 flushed before each step."""
+def size_leg(pkg, torch, dev, synth, n, steps=2, warmup=1, pc="dfast"):
+    """The same workload at n x n (radius-7 disk on 31 x 31, AR, MIXED, 10 FP steps) with
+    preconditioner pc (D_M, or M_D for 'fastd'): device time per deblur by CUDA events,
+    L2 flushed before each step."""
     h = synth.disk_psf(7.0, side=31)
     u_true = torch.tensor(synth.piecewise_constant_image(n, n, seed=SEED), dtype=torch.float64, device=dev)
     with pkg.Plan(n, n, h, bc="ar", pc="dfast", mode="fp64") as p64:
@@ -207,7 +208,7 @@ def size_leg(pkg, torch, dev, synth, n, steps=2, warmup=1):
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream()
     ms, iters = 0.0, 0
-    with pkg.Plan(n, n, h, bc="ar", pc="dfast", mode="mixed") as plan:
+    with pkg.Plan(n, n, h, bc="ar", pc=pc, mode="mixed") as plan:
         for s_ in range(warmup + steps):
             flush.zero_()
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -218,8 +219,9 @@ def size_leg(pkg, torch, dev, synth, n, steps=2, warmup=1):
             if s_ >= warmup:
                 ms += e0.elapsed_time(e1)
                 iters += st["total_inner_iters"]
+    name = "M_D" if pc == "fastd" else "D_M"
     return {"workload": f"tv_deblur {n}x{n} AR disk-r7(31x31) 1% noise alpha=1e-3 beta=1e-2 10 FP steps tol=1e-6 "
-                        f"D_M, MIXED", "deblurs_per_s": 1000.0 * steps / ms, "ms_per_step": ms / steps,
+                        f"{name}, MIXED", "deblurs_per_s": 1000.0 * steps / ms, "ms_per_step": ms / steps,
             "pcg_iters_per_s": iters / (ms / 1000.0), "inner_iters_per_deblur": iters / steps}
 
 
@@ -491,6 +493,7 @@ def run_ours(args):
         line["batched"] = batched_leg(pkg, torch, dev, synth)
         line["adjoint"] = adjoint_leg(pkg, torch, dev, synth)
         line["size_2048"] = size_leg(pkg, torch, dev, synth, 2048)
+        line["m_d_1024"] = size_leg(pkg, torch, dev, synth, 1024, steps=3, pc="fastd")
 
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         iters_per_deblur, src = oracle_iters_per_deblur()

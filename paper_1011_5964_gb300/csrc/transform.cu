@@ -366,7 +366,7 @@ __device__ void dst1_lines(T* raw, cplx<T>* bufA, cplx<T>* bufB, const LineArgs<
         bufA[(size_t)pp * M + j] = {sj * (a0 + a1) + T(0.5) * (a0 - a1), sj * (b0 + b1) + T(0.5) * (b0 - b1)};
     }
     __syncthreads();
-    const cplx<T>* Z = fft_pairs<T>(bufA, bufB, P, a.fp, tw, false, a.blt);
+    const cplx<T>* Z = fft_pairs<T>(bufA, bufB, P, a.fp, a.fp.bl ? a.blt + a.fp.L + a.fp.M2 : tw, false, a.blt);
     // the FFT buffer not holding the result keeps the recurrence terms (2P * K <= 2P * L values)
     T* scan = reinterpret_cast<T*>(Z == bufA ? bufB : bufA);
     const T sc = sqrt(T(2) / T(M));
@@ -422,7 +422,7 @@ __device__ void dct_lines(T* raw, cplx<T>* bufA, cplx<T>* bufB, const LineArgs<T
             bufA[(size_t)pp * n + p] = {raw[(size_t)(2 * pp) * ns + src], raw[(size_t)(2 * pp + 1) * ns + src]};
         }
         __syncthreads();
-        const cplx<T>* Z = fft_pairs<T>(bufA, bufB, P, a.fp, tw, false, a.blt);
+        const cplx<T>* Z = fft_pairs<T>(bufA, bufB, P, a.fp, a.fp.bl ? a.blt + a.fp.L + a.fp.M2 : tw, false, a.blt);
         for (Walk w(n); w.hi < P; w.next(n)) {
             const int pp = w.hi, k = w.lo;
             cplx<T> Va, Vb;
@@ -452,7 +452,7 @@ __device__ void dct_lines(T* raw, cplx<T>* bufA, cplx<T>* bufB, const LineArgs<T
             bufA[(size_t)pp * n + k] = {Va.re - Vb.im, Va.im + Vb.re};
         }
         __syncthreads();
-        const cplx<T>* Z = fft_pairs<T>(bufA, bufB, P, a.fp, tw, true, a.blt);
+        const cplx<T>* Z = fft_pairs<T>(bufA, bufB, P, a.fp, a.fp.bl ? a.blt + a.fp.L + a.fp.M2 : tw, true, a.blt);
         for (Walk w(n); w.hi < P; w.next(n)) {
             const int pp = w.hi, p = w.lo;
             const int dst = p < h ? 2 * p : 2 * (n - 1 - p) + 1;
@@ -474,7 +474,7 @@ __device__ void eg_lines(const T* raw, cplx<T>* bufA, cplx<T>* bufB, T* eo, T* g
         bufA[(size_t)pp * L + j] = {raw[(size_t)(2 * pp) * ns + j], raw[(size_t)(2 * pp + 1) * ns + j]};
     }
     __syncthreads();
-    const cplx<T>* Z = fft_pairs<T>(bufA, bufB, P, a.fp, tw, false, a.blt);
+    const cplx<T>* Z = fft_pairs<T>(bufA, bufB, P, a.fp, a.fp.bl ? a.blt + a.fp.L + a.fp.M2 : tw, false, a.blt);
     for (Walk w(n); w.hi < P; w.next(n)) {
         const int pp = w.hi, k = w.lo;
         const cplx<T>* Zp = Z + (size_t)pp * L;
@@ -594,10 +594,11 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? TVD_LINE_MINB : 1) 
     const int lsh = __ffs(lines) - 1;
     const int ln = lines * n;      // line elements of the block
     const int lns = lines * ns;    // shared-memory size of one set of lines
-    // FFT twiddles in shared memory: L of them, or M2 for a Bluestein plan,
-    // whose FFT buffers also hold M2 entries per line pair
-    const int ntw = a.fp.bl ? a.fp.M2 : L, Lb = a.fp.bl ? a.fp.M2 : L;
-    const cplx<T>* twsrc = a.fp.bl ? a.blt + L + a.fp.M2 : a.tw;
+    // FFT twiddles: L of them in shared memory; a Bluestein plan reads its M2
+    // twiddles from the (L1-cached) table instead, leaving the shared memory to
+    // its FFT buffers of M2 entries per line pair
+    const int ntw = a.fp.bl ? 0 : L, Lb = a.fp.bl ? a.fp.M2 : L;
+    const cplx<T>* twsrc = a.tw;
     cplx<T>* tw = reinterpret_cast<cplx<T>*>(smem_raw);
     cplx<T>* bufA = tw + ntw;
     cplx<T>* bufB = bufA + (size_t)P * Lb;
@@ -807,7 +808,7 @@ static size_t line_smem(const LineArgs<T>& a, int op) {
     const size_t lines = 2 * (size_t)a.P;
     // tw + bufA + bufB + raw + the operation's staged factors / outputs
     const size_t Lb = a.fp.bl ? (size_t)a.fp.M2 : (size_t)a.L;
-    return sizeof(cplx<T>) * (Lb + 2 * (size_t)a.P * Lb) +
+    return sizeof(cplx<T>) * ((a.fp.bl ? 0 : (size_t)a.L) + 2 * (size_t)a.P * Lb) +
            sizeof(T) * (lines * a.ns + line_extra(op, lines, a.ns, a.P)) + 64;
 }
 
