@@ -158,7 +158,11 @@ def batched_leg(pkg, torch, dev, synth):
     Timed by the host clock around the call (which returns when every item is
     done), after one untimed pass that captures each plan's CUDA graphs."""
     import math
-    items = synth.batch_items(BATCH, seed=1000)
+    from paper_1011_5964_gb300.replicas import reduce_over_ranks, shard
+    ws, rank, _ = dist_env()
+    every = synth.batch_items(BATCH, seed=1000)
+    # with several ranks each takes its share of the items (no exchange between them)
+    items = [every[i] for i in shard([it["n"] ** 2 for it in every], rank, ws)]
     t0 = time.perf_counter()
     plans, vs = [], []
     for it in items:
@@ -182,10 +186,11 @@ def batched_leg(pkg, torch, dev, synth):
         t0 = time.perf_counter()
         _, stats = pkg.deblur_batched(plans, vs, alphas, betas, OUTER, TOL, 5000, outs, workers)
         torch.cuda.synchronize()
-        res[workers] = (time.perf_counter() - t0, sum(sum(st["inner_iters"]) for st in stats))
+        res[workers] = (reduce_over_ranks(time.perf_counter() - t0, "max", dev),
+                        reduce_over_ranks(sum(sum(st["inner_iters"]) for st in stats), "sum", dev))
     for p in plans:
         p.close()
-    pixels = sum(it["n"] * it["n"] for it in items)
+    pixels = sum(it["n"] * it["n"] for it in every)
     return {"workload": f"{BATCH} independent tv_deblur, sides from {{128,192,256,384,512}} "
                         f"({pixels / 1e6:.2f} Mpixel in all), Gaussian sigma U[1,3], alpha log-U[1e-4,1e-2], "
                         f"beta 1e-2, 1% noise, AR, D_M, MIXED, 10 FP steps, tol 1e-6",
@@ -392,13 +397,10 @@ def run_ours(args):
         barrier()
         return ms, stats, launches
 
+    from paper_1011_5964_gb300.replicas import reduce_over_ranks
+
     def max_over_ranks(x):
-        if ws == 1:
-            return x
-        import torch.distributed as dist
-        t = torch.tensor([x], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
+        return reduce_over_ranks(x, "max", device=dev)
 
     sampler = ClockSampler(local)
     sampler.start()
