@@ -7,6 +7,7 @@
 #include <algorithm>
 #include <cmath>
 #include <complex>
+#include <cstdlib>
 #include <cstring>
 
 namespace tvd {
@@ -514,7 +515,12 @@ static tvd_status solve_mixed(tvd_plan_s& p, double alpha, const double* b, doub
     }
     if (rr0 == 0.0) return TVD_OK;
     const double target = tol * tol * rr0;
-    const double delta2 = 1e-8;   // replace once the float residual fell by 1e-4
+    // replace once the float residual fell by 1e-4 (TVD_MIXED_DELTA2 overrides, tuning)
+    static const double delta2 = []() {
+        const char* v = std::getenv("TVD_MIXED_DELTA2");
+        const double d = v ? std::atof(v) : 0.0;
+        return d > 0.0 && d < 1.0 ? d : 1e-8;
+    }();
     double rr_ref = rr0;
     res->relres = 1.0;
     // each float CG segment stops on the device once its residual fell by delta2
