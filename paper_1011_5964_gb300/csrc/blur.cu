@@ -273,6 +273,8 @@ blur_tile_kernel(const T* __restrict__ x, T* __restrict__ y, int nr, int nc, int
                  const T* __restrict__ hdense, const int* __restrict__ arange,
                  const int* __restrict__ runs, const T* __restrict__ runv, int nruns,
                  const T* __restrict__ w, T* p0, T* p1, FuseArgs fa) {
+    // (the implicit trigger at block exit lets the next kernel launch)
+    pdl_wait();
     if (fa.st && fa.st->done) return;
     tile_body<T, EXT, FUSE, PUP>(blockIdx.x, blockIdx.y, gridDim.x, x, y, nr, nc, mr, mc, hdense, arange, runs, runv,
                                  nruns, w, p0, p1, fa);
@@ -406,6 +408,8 @@ ar_adjoint_kernel(const T* __restrict__ x, T* __restrict__ y, int nr, int nc, in
                   const T* __restrict__ runv, int nruns, const T* __restrict__ crow, const T* __restrict__ ccol,
                   const T* __restrict__ ccor, const T* __restrict__ w, T* p0, T* p1, int tile_blocks, int gx,
                   FuseArgs fa_tile, FuseArgs fa_border) {
+    // (the implicit trigger at block exit lets the next kernel launch)
+    pdl_wait();
     if (fa_tile.st && fa_tile.st->done) return;
     __shared__ T partial[kThreads];
     const int bid = blockIdx.x;
@@ -436,8 +440,9 @@ template <typename T, int EXT, bool FUSE, bool PUP>
 static tvd_status launch_tile(dim3 grid, size_t smem, cudaStream_t s, const T* x, T* y, const tvd_plan_s& p,
                               const Ops<T>& o, const T* w, T* p0, T* p1, const FuseArgs& fa) {
     TVD_CUDA_TRY((allow_max_smem<blur_tile_kernel<T, EXT, FUSE, PUP>>()));
-    blur_tile_kernel<T, EXT, FUSE, PUP><<<grid, kThreads, smem, s>>>(x, y, p.nr, p.nc, p.psf.mr, p.psf.mc, o.hdense,
-                                                                    o.arange, o.runs, o.runv, o.nruns, w, p0, p1, fa);
+    TVD_CUDA_TRY(launch_pdl(blur_tile_kernel<T, EXT, FUSE, PUP>, grid, dim3(kThreads), smem, s, x, y, p.nr, p.nc,
+                            p.psf.mr, p.psf.mc, (const T*)o.hdense, (const int*)o.arange, (const int*)o.runs,
+                            (const T*)o.runv, o.nruns, w, p0, p1, fa));
     return TVD_OK;
 }
 
@@ -487,14 +492,16 @@ static tvd_status launch_blur(const tvd_plan_s& p, const Ops<T>& o, bool transpo
         const int blocks = tile_blocks + border_blocks;
         if (fuse) {
             TVD_CUDA_TRY((allow_max_smem<ar_adjoint_kernel<T, true>>()));
-            ar_adjoint_kernel<T, true><<<blocks, kThreads, msm, s>>>(
-                x, y, nr, nc, mr, mc, o.hdense, o.arange, o.runs, o.runv, o.nruns, o.crow, o.ccol, o.ccor, w, p0, p1,
-                tile_blocks, (int)grid.x, fa, fb);
+            TVD_CUDA_TRY(launch_pdl(ar_adjoint_kernel<T, true>, dim3(blocks), dim3(kThreads), msm, s, x, y, nr, nc,
+                                    mr, mc, (const T*)o.hdense, (const int*)o.arange, (const int*)o.runs,
+                                    (const T*)o.runv, o.nruns, (const T*)o.crow, (const T*)o.ccol, (const T*)o.ccor,
+                                    w, p0, p1, tile_blocks, (int)grid.x, fa, fb));
         } else {
             TVD_CUDA_TRY((allow_max_smem<ar_adjoint_kernel<T, false>>()));
-            ar_adjoint_kernel<T, false><<<blocks, kThreads, msm, s>>>(
-                x, y, nr, nc, mr, mc, o.hdense, o.arange, o.runs, o.runv, o.nruns, o.crow, o.ccol, o.ccor, w, p0, p1,
-                tile_blocks, (int)grid.x, fa, fb);
+            TVD_CUDA_TRY(launch_pdl(ar_adjoint_kernel<T, false>, dim3(blocks), dim3(kThreads), msm, s, x, y, nr, nc,
+                                    mr, mc, (const T*)o.hdense, (const int*)o.arange, (const int*)o.runs,
+                                    (const T*)o.runv, o.nruns, (const T*)o.crow, (const T*)o.ccol, (const T*)o.ccor,
+                                    w, p0, p1, tile_blocks, (int)grid.x, fa, fb));
         }
     }
     TVD_CUDA_TRY(cudaGetLastError());

@@ -4,6 +4,8 @@
 
 #include "tvd_internal.cuh"
 
+#include <cstdlib>
+
 namespace tvd {
 
 constexpr int kThreads = 256;
@@ -108,6 +110,37 @@ __device__ __forceinline__ void cp_async_elem(T* smem, const T* gmem) {
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
 
 __device__ __forceinline__ bool finite_pos(double v) { return isfinite(v) && v > 0.0; }
+
+// Programmatic dependent launch (the CG iteration's kernels): a kernel first
+// lets the next kernel in the stream be scheduled (its blocks become resident
+// as this kernel's blocks retire), stages what no earlier kernel writes
+// (constant tables), and waits for the previous kernel to complete before it
+// reads or writes anything that kernel touches. Without a programmatic
+// launch both instructions return at once.
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
+// Launch with programmatic stream serialisation (see pdl_wait).
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
+                              Args... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    // TVD_PDL=0 launches without the programmatic dependency (tuning / comparison)
+    static const bool on = []() {
+        const char* v = std::getenv("TVD_PDL");
+        return !(v && v[0] == '0');
+    }();
+    cfg.numAttrs = on ? 1 : 0;
+    return cudaLaunchKernelEx(&cfg, kernel, static_cast<KArgs>(args)...);
+}
 
 // End of a CG product q = A p: p^T q, the step alpha = rho / p^T q, and the
 // pending x / r update (applied by the next iteration's first pass).

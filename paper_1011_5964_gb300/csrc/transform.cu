@@ -587,7 +587,7 @@ __device__ __forceinline__ void finish_xr(CgState* st, double rr) {
 
 template <typename T, int BC, int OP>
 __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? TVD_LINE_MINB : 1) line_kernel(LineArgs<T> a) {
-    if (a.st && a.st->done) return;
+    // (the implicit trigger at block exit lets the next kernel launch)
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int n = a.n, ns = a.ns, P = a.P, L = a.L;
     const int lines = 2 * P;       // a power of two
@@ -619,6 +619,12 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? TVD_LINE_MINB : 1) 
     // all of them in flight before the first wait
     for (int i = threadIdx.x; i < ntw; i += kThreads)
         cp_async_elem(&tw[i].re, &twsrc[i].re), cp_async_elem(&tw[i].im, &twsrc[i].im);
+    // everything below reads or writes what earlier kernels in the stream touch
+    pdl_wait();
+    if (a.st && a.st->done) {
+        cp_async_wait_all();
+        return;
+    }
     if (!cols) {
         for (Walk w(n); w.hi < lines; w.next(n)) {
             const int l = w.hi, idx = w.lo;
@@ -874,7 +880,7 @@ static tvd_status launch_line(LineArgs<T> a, cudaStream_t s) {
                       : OP == OP_ROW_INV ? PROF_ROW_INV : (OP == OP_ROW_EG || OP == OP_ROW_X) ? PROF_EG_ROW
                       : PROF_EG_COL;
     ProfScope prof(prof_class<T>(cls), s);
-    line_kernel<T, BC, OP><<<blocks, kThreads, smem, s>>>(a);
+    TVD_CUDA_TRY(launch_pdl(line_kernel<T, BC, OP>, dim3(blocks), dim3(kThreads), smem, s, a));
     TVD_CUDA_TRY(cudaGetLastError());
     return TVD_OK;
 }
