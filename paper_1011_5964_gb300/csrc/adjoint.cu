@@ -41,24 +41,24 @@ hess_coef_kernel(const double* __restrict__ u, const double* __restrict__ w, dou
 }
 
 // a = psi^-1 D x - psi^-3 (D u . D x) D u on the cell (i, j) = w Dx - (g . Dx) g.
-__device__ __forceinline__ void hess_cell(const double* __restrict__ x, const double* __restrict__ w,
-                                          const double* __restrict__ gr, const double* __restrict__ gc, int i,
-                                          int j, int nr, int nc, double& ar, double& ac) {
+template <typename T>
+__device__ __forceinline__ void hess_cell(const T* __restrict__ x, const T* __restrict__ w, const T* __restrict__ gr,
+                                          const T* __restrict__ gc, int i, int j, int nr, int nc, T& ar, T& ac) {
     const size_t o = (size_t)i * nc + j;
-    const double xo = x[o];
-    const double xr = i < nr - 1 ? x[o + nc] - xo : 0.0;
-    const double xc = j < nc - 1 ? x[o + 1] - xo : 0.0;
-    const double g1 = gr[o], g2 = gc[o], wo = w[o];
-    const double s = g1 * xr + g2 * xc;
+    const T xo = x[o];
+    const T xr = i < nr - 1 ? x[o + nc] - xo : T(0);
+    const T xc = j < nc - 1 ? x[o + 1] - xo : T(0);
+    const T g1 = gr[o], g2 = gc[o], wo = w[o];
+    const T s = g1 * xr + g2 * xc;
     ar = wo * xr - s * g1;
     ac = wo * xc - s * g2;
 }
 
 // (nabla^2 J_beta x)_ij = (D_r^T a_r + D_c^T a_c)_ij
-__device__ __forceinline__ double hess_at(const double* __restrict__ x, const double* __restrict__ w,
-                                          const double* __restrict__ gr, const double* __restrict__ gc, int i,
-                                          int j, int nr, int nc) {
-    double ar, ac, y = 0.0;
+template <typename T>
+__device__ __forceinline__ T hess_at(const T* __restrict__ x, const T* __restrict__ w, const T* __restrict__ gr,
+                                     const T* __restrict__ gc, int i, int j, int nr, int nc) {
+    T ar, ac, y = T(0);
     hess_cell(x, w, gr, gc, i, j, nr, nc, ar, ac);
     if (i < nr - 1) y -= ar;
     if (j < nc - 1) y -= ac;
@@ -84,22 +84,43 @@ hess_apply_kernel(const double* __restrict__ x, double* __restrict__ y, const do
 }
 
 // CG product of the adjoint solve: q (= H^T H p) += alpha nabla^2 J_beta p, then p^T q.
+template <typename T>
 __global__ void __launch_bounds__(kThreads)
-hess_add_kernel(double* __restrict__ q, const double* p0, const double* p1, const double* __restrict__ w,
-                const double* __restrict__ gr, const double* __restrict__ gc, double alpha, int nr, int nc,
-                CgState* st, double* red, unsigned int* ticket) {
+hess_add_kernel(T* __restrict__ q, const T* p0, const T* p1, const T* __restrict__ w, const T* __restrict__ gr,
+                const T* __restrict__ gc, double alpha, int nr, int nc, CgState* st, double* red,
+                unsigned int* ticket) {
     if (st->done) return;
-    const double* __restrict__ pv = st->pbuf ? p0 : p1;   // the direction this iteration wrote
+    const T* __restrict__ pv = st->pbuf ? p0 : p1;   // the direction this iteration wrote
     const size_t n = (size_t)nr * nc;
-    double part = 0.0;
+    const T al = T(alpha);
+    T part = T(0);
     for (size_t o = blockIdx.x * (size_t)blockDim.x + threadIdx.x; o < n; o += (size_t)gridDim.x * blockDim.x) {
         const int i = (int)(o / nc), j = (int)(o - (size_t)i * nc);
-        const double qn = q[o] + alpha * hess_at(pv, w, gr, gc, i, j, nr, nc);
+        const T qn = q[o] + al * hess_at(pv, w, gr, gc, i, j, nr, nc);
         q[o] = qn;
         part += pv[o] * qn;
     }
     double sum;
-    if (block_reduce_last(part, red, ticket, blockIdx.x, gridDim.x, &sum) && threadIdx.x == 0) finish_pq(st, sum);
+    if (block_reduce_last((double)part, red, ticket, blockIdx.x, gridDim.x, &sum) && threadIdx.x == 0)
+        finish_pq(st, sum);
+}
+
+// Double residual of the adjoint system: r = b - hq - alpha nabla^2 J_beta x (hq = H^T H x), ||r||^2.
+__global__ void __launch_bounds__(kThreads)
+adj_residual_kernel(const double* __restrict__ b, const double* __restrict__ hq, const double* __restrict__ w,
+                    const double* __restrict__ gr, const double* __restrict__ gc, const double* __restrict__ x,
+                    double alpha, double* __restrict__ r, int nr, int nc, double* red, unsigned int* ticket,
+                    double* out) {
+    const size_t n = (size_t)nr * nc;
+    double part = 0.0;
+    for (size_t o = blockIdx.x * (size_t)blockDim.x + threadIdx.x; o < n; o += (size_t)gridDim.x * blockDim.x) {
+        const int i = (int)(o / nc), j = (int)(o - (size_t)i * nc);
+        const double v = b[o] - hq[o] - alpha * hess_at(x, w, gr, gc, i, j, nr, nc);
+        r[o] = v;
+        part += v * v;
+    }
+    double sum;
+    if (block_reduce_last(part, red, ticket, blockIdx.x, gridDim.x, &sum) && threadIdx.x == 0) *out = sum;
 }
 
 // sum_cells psi^-3 (D lambda . D u), psi^-3 = w^3
@@ -210,11 +231,26 @@ tvd_status hess_apply(const tvd_plan_s& p, const double* x, double* y, const dou
     return TVD_OK;
 }
 
-tvd_status hess_add(const tvd_plan_s& p, double* q, const double* p0, const double* p1, const double* w,
-                    const double* gr, const double* gc, double alpha, CgState* st, cudaStream_t s) {
-    ProfScope prof(prof_class<double>(PROF_BLUR_ADJ), s);
-    hess_add_kernel<<<adj_blocks((size_t)p.nr * p.nc), kThreads, 0, s>>>(q, p0, p1, w, gr, gc, alpha, p.nr, p.nc,
-                                                                         st, p.red, p.ticket + 8);
+template <typename T>
+tvd_status hess_add(const tvd_plan_s& p, T* q, const T* p0, const T* p1, const T* w, const T* gr, const T* gc,
+                    double alpha, CgState* st, cudaStream_t s) {
+    ProfScope prof(prof_class<T>(PROF_BLUR_ADJ), s);
+    hess_add_kernel<T><<<adj_blocks((size_t)p.nr * p.nc), kThreads, 0, s>>>(q, p0, p1, w, gr, gc, alpha, p.nr, p.nc,
+                                                                            st, p.red, p.ticket + 8);
+    TVD_CUDA_TRY(cudaGetLastError());
+    return TVD_OK;
+}
+template tvd_status hess_add<float>(const tvd_plan_s&, float*, const float*, const float*, const float*,
+                                    const float*, const float*, double, CgState*, cudaStream_t);
+template tvd_status hess_add<double>(const tvd_plan_s&, double*, const double*, const double*, const double*,
+                                     const double*, const double*, double, CgState*, cudaStream_t);
+
+tvd_status adj_residual(const tvd_plan_s& p, const double* b, const double* hq, const double* w, const double* gr,
+                        const double* gc, const double* x, double alpha, double* r, double* out_norm2,
+                        cudaStream_t s) {
+    ProfScope prof(prof_class<double>(PROF_MISC), s);
+    adj_residual_kernel<<<adj_blocks((size_t)p.nr * p.nc), kThreads, 0, s>>>(b, hq, w, gr, gc, x, alpha, r, p.nr,
+                                                                             p.nc, p.red, p.ticket + 9, out_norm2);
     TVD_CUDA_TRY(cudaGetLastError());
     return TVD_OK;
 }

@@ -735,6 +735,90 @@ tvd_status tv_hessian_apply(tvd_plan plan, const void* u, double beta, const voi
     return st;
 }
 
+}  // extern "C"
+
+// MIXED adjoint solve J lambda = b, J = H^T H + alpha nabla^2 J_beta(u*), lambda from 0 (double):
+// float CG segments with the plan's float preconditioner, each stopping on the device once its
+// recursive residual fell by 1e-4 (or below the target); the float correction is folded into
+// lambda and the residual recomputed in double, which decides convergence (as solve_mixed does
+// for the FP step). gr, gc: double Hessian coefficients; grf, gcf: their float copies.
+static tvd_status adjoint_mixed(tvd_plan_s& p, const double* b, double* lam, const double* gr, const double* gc,
+                                const float* grf, const float* gcf, double alpha, double tol, int maxit,
+                                int* iters_out, double* relres_out, cudaStream_t s) {
+    const size_t n = (size_t)p.nr * p.nc;
+    Ops<float>& f = p.f;
+    CgState* st = p.state;
+    TVD_CUDA_TRY(cudaMemsetAsync(lam, 0, n * sizeof(double), s));
+    TVD_TRY(norm2_d(p, b, p.scal + 10, s));
+    double rr0 = 0.0;
+    TVD_CUDA_TRY(cudaMemcpyAsync(&rr0, p.scal + 10, sizeof(double), cudaMemcpyDeviceToHost, s));
+    TVD_CUDA_TRY(cudaStreamSynchronize(s));
+    *iters_out = 0;
+    *relres_out = 0.0;
+    if (!std::isfinite(rr0)) {
+        set_error("tv_deblur_adjoint: non-finite right-hand side");
+        return TVD_EBREAKDOWN;
+    }
+    if (rr0 == 0.0) return TVD_OK;
+    const double target = tol * tol * rr0, delta2 = 1e-8;
+    const bool transform_pc = (p.pc == TVD_PC_FAST || p.pc == TVD_PC_DFAST || p.pc == TVD_PC_FASTD);
+    double rr_ref = rr0;
+    int sweeps = 0, last_iter = -1;
+    TVD_TRY(cast_d2f(b, f.r, n, s));
+    TVD_TRY(fill_zero_f(f.x, n, s));
+    TVD_TRY(cg_restart<float>(p, f.r, st, std::max(target, delta2 * rr_ref), maxit, 0, s));
+    for (;;) {
+        for (int k = 0; k < 2 * kChunk; ++k) {
+            switch (p.pc) {
+                case TVD_PC_NONE: TVD_TRY(cg_simple_precond<float>(p, f.r, nullptr, f.z, st, s)); break;
+                case TVD_PC_DIAG: TVD_TRY(cg_simple_precond<float>(p, f.r, f.dinv, f.z, st, s)); break;
+                default: TVD_TRY(precond_solve<float>(p, f, f.r, f.z, st, s, f.x)); break;
+            }
+            TVD_TRY(blur_pupdate<float>(p, f, f.z, f.p, f.p2, f.t, st, s));
+            TVD_TRY(blur_apply<float>(p, f, true, f.t, f.q, s, st));
+            TVD_TRY(hess_add<float>(p, f.q, f.p, f.p2, f.w, grf, gcf, alpha, st, s));
+            if (!transform_pc) TVD_TRY(cg_xrupdate<float>(p, f.x, f.r, f.p, f.p2, f.q, st, s));
+        }
+        TVD_TRY(read_state<float>(p, s));
+        const CgState h = *p.hstate;
+        *iters_out = h.iter;
+        if (!h.done) {
+            if (h.iter == last_iter) {   // the kernels always advance a running solve
+                set_error("adjoint CG made no progress between two checks");
+                return TVD_ECUDA;
+            }
+            last_iter = h.iter;
+            continue;
+        }
+        last_iter = -1;
+        TVD_TRY(axpy_f2d(lam, f.x, n, s));
+        TVD_TRY(fill_zero_f(f.x, n, s));
+        TVD_TRY(blur_apply<double>(p, p.d, false, lam, p.d.t, s));
+        TVD_TRY(blur_apply<double>(p, p.d, true, p.d.t, p.d.q, s));
+        TVD_TRY(adj_residual(p, b, p.d.q, p.d.w, gr, gc, lam, alpha, p.res, p.scal + 10, s));
+        double rr = 0.0;
+        TVD_CUDA_TRY(cudaMemcpyAsync(&rr, p.scal + 10, sizeof(double), cudaMemcpyDeviceToHost, s));
+        TVD_CUDA_TRY(cudaStreamSynchronize(s));
+        ++sweeps;
+        if (!std::isfinite(rr) || h.status == TVD_EBREAKDOWN) {
+            set_error("tv_deblur_adjoint: the adjoint CG broke down");
+            return TVD_EBREAKDOWN;
+        }
+        *relres_out = std::sqrt(rr / rr0);
+        if (rr < target) return TVD_OK;
+        if (h.iter >= maxit || sweeps > 200) {
+            set_error("tv_deblur_adjoint: the adjoint CG did not reach its tolerance");
+            return TVD_ENOCONV;
+        }
+        const int mode = (rr < 4.0 * h.rr) ? 1 : 2;
+        rr_ref = rr;
+        TVD_TRY(cast_d2f(p.res, f.r, n, s));
+        TVD_TRY(cg_restart<float>(p, f.r, st, std::max(target, delta2 * rr_ref), maxit, mode, s));
+    }
+}
+
+extern "C" {
+
 tvd_status tv_deblur_adjoint(tvd_plan plan, const void* u_star, const void* v, double alpha, double beta,
                              const void* dl_du, void* lambda_out, double tol, int maxit, double* dl_dalpha,
                              double* dl_dbeta, double* dl_dpsf, int* iters, double* relres, void* stream) {
@@ -753,13 +837,39 @@ tvd_status tv_deblur_adjoint(tvd_plan plan, const void* u_star, const void* v, d
     const double* u = (const double*)u_star;
     double* lam = (double*)lambda_out;
     p.hx_for = nullptr;
-    // the lagged operator's preconditioner at u* (w = psi^-1 of u*, D, the spectrum)
-    TVD_TRY(setup_precond<double>(p, o, u, alpha, beta, s));
+    // the lagged operator's preconditioner at u* (w = psi^-1 of u*, D, the spectrum): in
+    // double for FP64 plans, in float (from the double coefficients) for MIXED plans
+    const bool mixed = p.mode == TVD_MODE_MIXED;
+    if (mixed) TVD_TRY(setup_mixed(p, u, alpha, beta, s));
+    else TVD_TRY(setup_precond<double>(p, o, u, alpha, beta, s));
     double* scratch = nullptr;
-    TVD_TRY(dalloc(&scratch, 2 * n + 2 * ne + ntap + 2));
+    TVD_TRY(dalloc(&scratch, 2 * n + 2 * ne + ntap + 2 + (mixed ? n : 0)));
     double *gr = scratch, *gc = scratch + n, *ext = scratch + 2 * n, *taps = ext + 2 * ne, *out2 = taps + ntap;
+    float* gf = mixed ? reinterpret_cast<float*>(out2 + 2) : nullptr;   // float g_r, g_c (n each)
     auto run = [&]() -> tvd_status {
         TVD_TRY(hess_coef(p, u, o.w, gr, gc, s));
+        if (mixed) {
+            TVD_TRY(cast_d2f(gr, gf, n, s));
+            TVD_TRY(cast_d2f(gc, gf + n, n, s));
+            int it = 0;
+            double rel = 0.0;
+            const tvd_status cg = adjoint_mixed(p, (const double*)dl_du, lam, gr, gc, gf, gf + n, alpha, tol, maxit,
+                                                &it, &rel, s);
+            if (iters) *iters = it;
+            if (relres) *relres = rel;
+            if (cg != TVD_OK && cg != TVD_ENOCONV) return cg;   // gradients still written after ENOCONV
+            TVD_TRY(adjoint_gradients(p, o, lam, u, (const double*)v, alpha, beta, ext, dl_dpsf ? taps : nullptr,
+                                      out2, s));
+            double h2[2] = {0.0, 0.0};
+            TVD_CUDA_TRY(cudaMemcpyAsync(h2, out2, sizeof(h2), cudaMemcpyDeviceToHost, s));
+            if (dl_dpsf)
+                TVD_CUDA_TRY(cudaMemcpyAsync(dl_dpsf, taps, ntap * sizeof(double), cudaMemcpyDeviceToHost, s));
+            TVD_CUDA_TRY(cudaStreamSynchronize(s));
+            if (dl_dalpha) *dl_dalpha = -h2[0];
+            if (dl_dbeta) *dl_dbeta = alpha * beta * h2[1];
+            if (cg == TVD_ENOCONV) set_error("tv_deblur_adjoint: the adjoint CG did not reach its tolerance");
+            return cg;
+        }
         TVD_CUDA_TRY(cudaMemsetAsync(lam, 0, n * sizeof(double), s));
         TVD_CUDA_TRY(cudaMemsetAsync(o.q, 0, n * sizeof(double), s));
         CgState* st = p.state;

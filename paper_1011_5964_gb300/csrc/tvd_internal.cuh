@@ -268,8 +268,13 @@ tvd_status precond_solve(const tvd_plan_s& p, const Ops<T>& o, const T* r, T* z,
 tvd_status hess_coef(const tvd_plan_s& p, const double* u, const double* w, double* gr, double* gc, cudaStream_t s);
 tvd_status hess_apply(const tvd_plan_s& p, const double* x, double* y, const double* w, const double* gr,
                       const double* gc, cudaStream_t s);
-tvd_status hess_add(const tvd_plan_s& p, double* q, const double* p0, const double* p1, const double* w,
-                    const double* gr, const double* gc, double alpha, CgState* st, cudaStream_t s);
+template <typename T>
+tvd_status hess_add(const tvd_plan_s& p, T* q, const T* p0, const T* p1, const T* w, const T* gr, const T* gc,
+                    double alpha, CgState* st, cudaStream_t s);
+// r = b - hq - alpha nabla^2 J_beta x (double), ||r||^2 into *out_norm2
+tvd_status adj_residual(const tvd_plan_s& p, const double* b, const double* hq, const double* w, const double* gr,
+                        const double* gc, const double* x, double alpha, double* r, double* out_norm2,
+                        cudaStream_t s);
 tvd_status adjoint_gradients(const tvd_plan_s& p, const Ops<double>& o, const double* lam, const double* u,
                              const double* v, double alpha, double beta, double* scratch_ext, double* taps,
                              double* out2, cudaStream_t s);
