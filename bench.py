@@ -60,6 +60,9 @@ WORDS_PER_PIXEL = {
     "cg_simple_precond": 3,
     "tv_coefficients": 2,
     "vector_misc": 2,
+    "precond_gemm_vector": 5,   # mean of the GEMM form's three vector kernels: pre (read r, q, p, x, D^-1/2;
+                                # write r, x, s) 8, spectrum scale (read y, 1/spectrum; write y) 3,
+                                # post (read u, D^-1/2, r; write z) 4
 }
 
 # DRAM bytes per launch (read + write) of the kernels captured with
@@ -200,10 +203,10 @@ def batched_leg(pkg, torch, dev, synth):
             "timing": "host clock around the call, inputs resident"}
 
 
-def size_leg(pkg, torch, dev, synth, n, steps=2, warmup=1, pc="dfast"):
+def size_leg(pkg, torch, dev, synth, n, steps=2, warmup=1, pc="dfast", transform=None):
     """The same workload at n x n (radius-7 disk on 31 x 31, AR, MIXED, 10 FP steps) with
-    preconditioner pc (D_M, or M_D for 'fastd'): device time per deblur by CUDA events,
-    L2 flushed before each step."""
+    preconditioner pc (D_M, or M_D for 'fastd') and the plan's default transform form
+    (or `transform`): device time per deblur by CUDA events, L2 flushed before each step."""
     h = synth.disk_psf(7.0, side=31)
     u_true = torch.tensor(synth.piecewise_constant_image(n, n, seed=SEED), dtype=torch.float64, device=dev)
     with pkg.Plan(n, n, h, bc="ar", pc="dfast", mode="fp64") as p64:
@@ -213,7 +216,8 @@ def size_leg(pkg, torch, dev, synth, n, steps=2, warmup=1, pc="dfast"):
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream()
     ms, iters = 0.0, 0
-    with pkg.Plan(n, n, h, bc="ar", pc=pc, mode="mixed") as plan:
+    with pkg.Plan(n, n, h, bc="ar", pc=pc, mode="mixed", transform=transform) as plan:
+        form = plan.transform
         for s_ in range(warmup + steps):
             flush.zero_()
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -226,7 +230,8 @@ def size_leg(pkg, torch, dev, synth, n, steps=2, warmup=1, pc="dfast"):
                 iters += st["total_inner_iters"]
     name = "M_D" if pc == "fastd" else "D_M"
     return {"workload": f"tv_deblur {n}x{n} AR disk-r7(31x31) 1% noise alpha=1e-3 beta=1e-2 10 FP steps tol=1e-6 "
-                        f"{name}, MIXED", "deblurs_per_s": 1000.0 * steps / ms, "ms_per_step": ms / steps,
+                        f"{name}, MIXED, {form} transforms", "deblurs_per_s": 1000.0 * steps / ms,
+            "ms_per_step": ms / steps,
             "pcg_iters_per_s": iters / (ms / 1000.0), "inner_iters_per_deblur": iters / steps}
 
 
@@ -272,6 +277,44 @@ def peaks():
         return float(d["hbm_gbs"]), "measured"
     except Exception:
         return 6800.0, "fallback"
+
+
+# TF32 / bf16 dense tensor rate of GB300 (nominal 1.1 / 2.25 PFLOP/s): the TF32
+# peak is the measured bf16 figure times this ratio.
+TF32_OVER_BF16 = 1.1 / 2.25
+
+
+def tf32_peak():
+    """TF32 tensor peak (TFLOP/s) for a kernel timed inside a long step: the measured sustained
+    bf16 cuBLAS rate x the nominal TF32 / bf16 ratio."""
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        d = json.load(open(path))
+        return float(d["bf16_tflops_sustained"]) * TF32_OVER_BF16, "measured (bf16 sustained x 1.1/2.25)"
+    except Exception:
+        return 1700.0 * TF32_OVER_BF16, "fallback (bf16 sustained 1.7 PF x 1.1/2.25)"
+
+
+def roofline_of(name, kms, klaunch, total_ms):
+    """Roofline entry of one kernel class from its summed device time and launch count."""
+    base, prec = name.rsplit(".", 1)
+    avg_s = kms / 1000.0 / max(klaunch, 1)
+    share = kms / max(total_ms, 1e-12)
+    if base == "precond_gemm_cublas":
+        # one n x n x n product of the transform form: 2 n^3 flops (TF32 inputs, float accumulation)
+        flops = 2.0 * N_SIDE ** 3
+        peak, src = tf32_peak()
+        achieved = flops / avg_s / 1e12
+        return {"bound": "tensor", "kernel": name + " (cuBLASLt TF32 transform GEMM)", "achieved": achieved,
+                "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None, "peak_source": src,
+                "flops_per_launch": flops, "avg_launch_us": avg_s * 1e6, "launches": klaunch, "share": share}
+    word = 4 if prec == "f32" else 8
+    bytes_per_launch = WORDS_PER_PIXEL.get(base, 2) * word * N_SIDE * N_SIDE
+    achieved = bytes_per_launch / avg_s / 1e9
+    peak, peak_src = peaks()
+    return {"bound": "hbm", "kernel": name, "achieved": achieved, "peak": peak, "unit": "GB/s",
+            "frac": achieved / peak, "traffic": NCU_TRAFFIC.get(name), "peak_source": peak_src,
+            "bytes_per_launch": bytes_per_launch, "avg_launch_us": avg_s * 1e6, "launches": klaunch, "share": share}
 
 
 def cpu_sample(h, v, sample_iters: int):
@@ -439,18 +482,12 @@ def run_ours(args):
         table = {k: {"ms": round(v_[0], 4), "launches": v_[1]} for k, v_ in sorted(prof.items(), key=lambda kv: -kv[1][0])
                  if v_[1]}
         print("per-kernel-class device time of one chosen-form step: " + json.dumps(table), file=sys.stderr)
+    total_ms = sum(v_[0] for v_ in prof.values())
     top = max(prof.items(), key=lambda kv: kv[1][0])
-    name, (kms, klaunch) = top
-    base, prec = name.rsplit(".", 1)
-    word = 4 if prec == "f32" else 8
-    bytes_per_launch = WORDS_PER_PIXEL.get(base, 2) * word * N_SIDE * N_SIDE
-    avg_s = kms / 1000.0 / max(klaunch, 1)
-    achieved = bytes_per_launch / avg_s / 1e9
-    peak, peak_src = peaks()
-    roofline = {"bound": "hbm", "kernel": name, "achieved": achieved, "peak": peak, "unit": "GB/s",
-                "frac": achieved / peak, "traffic": NCU_TRAFFIC.get(name), "peak_source": peak_src,
-                "bytes_per_launch": bytes_per_launch, "avg_launch_us": avg_s * 1e6, "launches": klaunch,
-                "share": kms / max(sum(v_[0] for v_ in prof.values()), 1e-12)}
+    roofline = roofline_of(top[0], top[1][0], top[1][1], total_ms)
+    # the library's own dominant kernel (the stencils and the vector kernels are ours; cuBLAS is not)
+    own = max(((k, v_) for k, v_ in prof.items() if not k.startswith("precond_gemm_cublas")), key=lambda kv: kv[1][0])
+    roofline_own = roofline_of(own[0], own[1][0], own[1][1], total_ms)
 
     # end to end through the public API with pinned host buffers
     v_pin = torch.tensor(v_host, dtype=torch.float64).pin_memory()
@@ -487,6 +524,8 @@ def run_ours(args):
             "rel_err_vs_plain_fp64": rel_err,
             "gpu_launches": launches,
             "roofline": roofline,
+            "roofline_own_kernel": roofline_own,
+            "transform_form": mixed.transform,
             "clocks": clocks,
             "e2e": {"value": ws * 1000.0 * args.steps / e2e_ms, "unit": "deblurs/s",
                     "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes}}
@@ -496,6 +535,7 @@ def run_ours(args):
         line["adjoint"] = adjoint_leg(pkg, torch, dev, synth)
         line["size_2048"] = size_leg(pkg, torch, dev, synth, 2048)
         line["m_d_1024"] = size_leg(pkg, torch, dev, synth, 1024, steps=3, pc="fastd")
+        line["fft_form_1024"] = size_leg(pkg, torch, dev, synth, 1024, steps=3, transform="fft")
 
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         iters_per_deblur, src = oracle_iters_per_deblur()

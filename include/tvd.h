@@ -157,6 +157,48 @@ tvd_status tau_precond_setup(tvd_plan plan, const void* u_lag, double alpha, dou
 tvd_status tau_precond_solve(tvd_plan plan, const void* r, void* z, void* stream);
 
 /*
+ * Transform form of the fast preconditioners (R, M, D_R, D_M, R_D, M_D) on a
+ * TVD_MODE_MIXED plan. The 2D transform U = B_r (x) B_c of Secs. 2-3 (B the
+ * orthonormal DST-I hat-S_n = diag(1, S_{n-2}, 1) of eq. (lambda) for AR, the
+ * orthonormal DCT-II C_n of Sec. 3.1 for R) is applied either
+ *   TVD_TRANSFORM_FFT:  as the paper's fast transforms, O(n^2 log n), by FFT
+ *                       line kernels in shared memory (float), or
+ *   TVD_TRANSFORM_GEMM: as four dense products with the n x n matrices B_r,
+ *                       B_c on the tensor cores (cuBLAS, float storage, TF32
+ *                       inputs, float accumulation; TVD_GEMM_COMPUTE=bf16 /
+ *                       bf16x9 / fp32 selects another cuBLAS compute type),
+ *                       O(n^3) flops but tensor-core rate.
+ * Both give the same preconditioner up to rounding; the preconditioner only
+ * shapes the CG iteration, so the form changes iteration counts slightly,
+ * never the converged solution (the MIXED double residual decides).
+ * FP64 plans always use the FFT form.
+ */
+typedef enum {
+    TVD_TRANSFORM_FFT = 0,
+    TVD_TRANSFORM_GEMM = 1
+} tvd_transform;
+
+/*
+ * tvd_plan_set_transform -- choose the transform form of a plan (kind: a
+ * tvd_transform value). A new MIXED plan with a fast preconditioner starts
+ * with the GEMM form when both image sides are at least 256 (the environment
+ * variable TVD_GEMM_MIN_SIDE changes the bound), else with the FFT form; the
+ * environment variable TVD_TRANSFORM ("gemm" / "fft") overrides both. On the
+ * switch to GEMM the candidate cuBLASLt algorithms of the four products are
+ * timed on the plan's stream and the fastest kept (TVD_GEMM_TUNE=0: cuBLAS's
+ * default choice). Switching to GEMM allocates
+ * the transform matrices (n_r^2 + n_c^2 floats), two image-sized float
+ * buffers, a 32 MiB cuBLAS workspace and a cuBLAS handle, owned by the plan;
+ * switching back frees them. Synchronises `stream` (and, when freeing, the
+ * device). Errors: TVD_EINVAL for a NULL plan, an unknown kind, or GEMM on an
+ * FP64 plan or with the I / D preconditioners; TVD_ENOMEM, TVD_ECUDA.
+ */
+tvd_status tvd_plan_set_transform(tvd_plan plan, int kind, void* stream);
+
+/* tvd_plan_transform -- the plan's current tvd_transform (FFT for NULL). */
+int tvd_plan_transform(tvd_plan plan);
+
+/*
  * pcg_solve -- solve (H^T H + alpha L(u_lag)) x = b by preconditioned CG from
  * the initial guess in x_inout, stopping when ||r_k||_2 / ||r_0||_2 < tol
  * (Sec. 5) or after maxit iterations. u_lag, b, x_inout: DOUBLE device arrays.

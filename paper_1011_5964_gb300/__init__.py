@@ -32,10 +32,11 @@ STATUS_NAMES = ["TVD_OK", "TVD_EINVAL", "TVD_EPSF_ASYM", "TVD_EPSF_SIZE", "TVD_E
                 "TVD_ENOCONV", "TVD_EBREAKDOWN", "TVD_ETIMEOUT"]
 
 # Function names of the C ABI, in include/tvd.h order.
+TRANSFORM = {"fft": 0, "gemm": 1}
 ABI_FUNCTIONS = ["tvd_plan_create", "tvd_plan_destroy", "ar_blur_apply", "tv_operator_apply",
                  "tau_precond_setup", "tau_precond_solve", "pcg_solve", "tv_deblur",
                  "tv_deblur_batched", "tv_hessian_apply", "tv_deblur_adjoint", "tvd_plan_psf_size",
-                 "tvd_normal_apply_noalloc", "tvd_last_error", "tvd_version", "tvd_kernel_launches",
+                 "tvd_normal_apply_noalloc", "tvd_plan_set_transform", "tvd_plan_transform", "tvd_last_error", "tvd_version", "tvd_kernel_launches",
                  "tvd_profile_enable", "tvd_profile_classes", "tvd_profile_name", "tvd_profile_read"]
 
 
@@ -88,6 +89,8 @@ def load_library(path: str | None = None) -> ctypes.CDLL:
     lib.tv_deblur_adjoint.argtypes = [vp, vp, vp, d, d, vp, vp, d, i, ctypes.POINTER(d), ctypes.POINTER(d),
                                       ctypes.POINTER(d), ctypes.POINTER(i), ctypes.POINTER(d), vp]
     lib.tvd_plan_psf_size.argtypes = [vp, ctypes.POINTER(i), ctypes.POINTER(i)]
+    lib.tvd_plan_set_transform.argtypes = [vp, i, vp]
+    lib.tvd_plan_transform.argtypes = [vp]
     lib.tvd_last_error.restype = ctypes.c_char_p
     lib.tvd_version.restype = ctypes.c_char_p
     lib.tvd_kernel_launches.restype = ctypes.c_ulonglong
@@ -136,7 +139,8 @@ class Plan:
     mixed mode; solver calls always take float64 tensors.
     """
 
-    def __init__(self, n_rows: int, n_cols: int, psf, bc: str = "ar", pc: str = "dfast", mode: str = "fp64"):
+    def __init__(self, n_rows: int, n_cols: int, psf, bc: str = "ar", pc: str = "dfast", mode: str = "fp64",
+                 transform: str | None = None):
         import torch
         self.lib = load_library()
         self.shape = (int(n_rows), int(n_cols))
@@ -149,6 +153,16 @@ class Plan:
                                         h.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), h.shape[0], h.shape[1],
                                         BC[bc], PC[pc], MODE[mode], _stream()))
         self.handle = handle
+        if transform is not None:
+            self.set_transform(transform)
+
+    def set_transform(self, kind: str):
+        """Transform form of the fast preconditioners on a mixed plan: 'fft' or 'gemm'."""
+        _check(self.lib.tvd_plan_set_transform(self.handle, TRANSFORM[kind], _stream()))
+
+    @property
+    def transform(self) -> str:
+        return "gemm" if self.lib.tvd_plan_transform(self.handle) == TRANSFORM["gemm"] else "fft"
 
     def close(self):
         if getattr(self, "handle", None):

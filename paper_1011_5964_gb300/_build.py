@@ -1,7 +1,8 @@
 """Build libtvd.so in-tree with nvcc for sm_103a (GB300).
 
 Each CUDA translation unit under csrc/ is compiled in parallel, then linked
-into paper_1011_5964_gb300/libtvd.so against the shared CUDA runtime.
+into paper_1011_5964_gb300/libtvd.so against the shared CUDA runtime and
+cuBLAS (the GEMM form of the preconditioner transforms).
 """
 from __future__ import annotations
 
@@ -49,7 +50,7 @@ def build(verbose: bool = False, extra_flags: list[str] | None = None) -> str:
     with cf.ThreadPoolExecutor(max_workers=max(1, min(len(srcs), os.cpu_count() or 4))) as ex:
         objs = list(ex.map(compile_one, srcs))
     tmp = LIB + ".tmp"
-    cmd = [nvcc, *ARCH, "-shared", "-cudart", "shared", "-o", tmp, *objs]
+    cmd = [nvcc, *ARCH, "-shared", "-cudart", "shared", "-o", tmp, *objs, "-lcublas"]
     res = subprocess.run(cmd, capture_output=True, text=True)
     if res.returncode != 0:
         raise RuntimeError(f"link failed:\n{res.stderr}")

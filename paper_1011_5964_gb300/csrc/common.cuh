@@ -156,4 +156,37 @@ __device__ __forceinline__ void finish_pq(CgState* st, double pq) {
     }
 }
 
+// End of a preconditioner solve on the CG path: rho = r^T z and the
+// Fletcher-Reeves coefficient beta = rho / rho_old.
+__device__ __forceinline__ void finish_rho(CgState* st, double rho) {
+    st->rho_old = st->rho;
+    st->rho = rho;
+    if (!(isfinite(rho) && rho > 0.0)) {
+        st->status = TVD_EBREAKDOWN;
+        st->done = 1;
+        st->beta = 0.0;
+        return;
+    }
+    st->beta = st->fresh ? 0.0 : rho / st->rho_old;
+}
+
+// End of a CG iteration (the x / r update applied by the next row pass): the
+// residual norm, the iteration count and the stopping test ||r|| / ||r_0|| < tol.
+__device__ __forceinline__ void finish_xr(CgState* st, double rr) {
+    st->rr = rr;
+    st->iter += 1;
+    st->fresh = 0;
+    st->pbuf ^= 1;
+    st->pending = 0;
+    if (!isfinite(rr)) {
+        st->status = TVD_EBREAKDOWN;
+        st->done = 1;
+    } else if (rr < st->tol2) {
+        st->done = 1;
+    } else if (st->iter >= st->maxit) {
+        st->status = TVD_ENOCONV;
+        st->done = 1;
+    }
+}
+
 }  // namespace tvd

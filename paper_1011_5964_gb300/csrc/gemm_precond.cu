@@ -1,0 +1,438 @@
+// Dense-matrix form of the preconditioner transforms (float plans).
+//
+// The fast preconditioners of Secs. 2-3 (M, D_M, M_D for AR; R, D_R, R_D for R)
+// apply the 2D transform U = B_r (x) B_c, a diagonal, and U^{-1}:
+//   z = d o B_r^T [ (B_r (d o r) B_c^T) o (1 / spectrum) ] B_c,   d = D^-1/2 or 1,
+// with B = hat-S_n = diag(1, S_{n-2}, 1) (S_m the orthonormal DST-I of
+// eq. (lambda), symmetric, an involution) for AR and B = C, the orthonormal
+// DCT-II of Sec. 3.1 (B^{-1} = C^T) for R. Here each 1D transform of all
+// lines is one matrix product with the n x n matrix B on the tensor cores
+// (cuBLAS, float storage, TF32 inputs with float accumulation by default), so
+// the solve is four GEMMs and three vector kernels instead of the three FFT
+// line passes of transform.cu. The preconditioner only shapes the CG
+// iteration: its rounding changes the iteration count, not the solution,
+// whose accuracy the double residual of the MIXED form decides.
+//
+// Layout: images are row-major n_r x n_c; cuBLAS is column-major, so the
+// row-major X is the column-major X^T and
+//   forward  Y^T = B_c X^T B_r^T     (GEMM 1: B_c X^T, GEMM 2: (.) B_r^T)
+//   inverse  Z^T = B_c^T Y^T B_r     (GEMM 3: B_c^T Y^T, GEMM 4: (.) B_r)
+// with B_r, B_c stored row-major (their column-major views are B^T).
+#include "common.cuh"
+
+#include <cublasLt.h>
+#include <cublas_v2.h>
+
+#include <cmath>
+#include <cstdlib>
+#include <cstring>
+#include <vector>
+
+namespace tvd {
+
+// One of the four products with its algorithm, picked at set-up by timing the
+// candidates cuBLASLt proposes (the n^3 products of one image fill few SMs at
+// n = 1024 with the default tiles; split-K / stream-K variants can fill more).
+struct LtGemm {
+    cublasLtMatmulDesc_t op = nullptr;
+    cublasLtMatrixLayout_t a = nullptr, b = nullptr, c = nullptr;
+    cublasLtMatmulAlgo_t algo{};
+    bool tuned = false;
+    float us = 0.0f;      // measured time of the chosen algorithm
+};
+
+struct GemmPrecond {
+    cublasHandle_t h = nullptr;
+    cublasLtHandle_t lt = nullptr;
+    LtGemm g[4];
+    cublasComputeType_t ct = CUBLAS_COMPUTE_32F_FAST_TF32;
+    float* Br = nullptr;     // n_r x n_r, row-major
+    float* Bc = nullptr;     // n_c x n_c, row-major (aliases Br for square images)
+    float* s1 = nullptr;     // n_r x n_c scratch
+    float* s2 = nullptr;     // n_r x n_c scratch
+    void* ws = nullptr;      // cuBLAS workspace (no allocation inside a captured graph)
+    size_t ws_bytes = 0;
+};
+
+static constexpr size_t kGemmWorkspace = 32u << 20;
+
+// Row-major n x n matrix of the 1D transform: AR hat-S_n, R the DCT-II C_n
+// (frequency by space). Arguments are reduced modulo the period in integers.
+static void transform_matrix(int n, tvd_bc bc, std::vector<float>& out) {
+    out.assign((size_t)n * n, 0.0f);
+    const double pi = 3.14159265358979323846;
+    if (bc == TVD_BC_ANTIREFLECTIVE) {
+        const int M = n - 1;   // S_{n-2}: sqrt(2/M) sin(k l pi / M), k, l = 1..n-2
+        const double sc = std::sqrt(2.0 / M);
+        out[0] = 1.0f;
+        out[(size_t)n * n - 1] = 1.0f;
+        for (int k = 1; k <= n - 2; ++k)
+            for (int l = 1; l <= n - 2; ++l) {
+                const long long a = ((long long)k * l) % (2LL * M);
+                out[(size_t)k * n + l] = (float)(sc * std::sin(pi * (double)a / M));
+            }
+    } else {
+        const double c0 = std::sqrt(1.0 / n), c1 = std::sqrt(2.0 / n);
+        for (int k = 0; k < n; ++k)
+            for (int j = 0; j < n; ++j) {
+                const long long a = ((long long)k * (2 * j + 1)) % (4LL * n);
+                out[(size_t)k * n + j] = (float)((k ? c1 : c0) * std::cos(pi * (double)a / (2.0 * n)));
+            }
+    }
+}
+
+static cublasComputeType_t compute_type_from_env() {
+    const char* v = std::getenv("TVD_GEMM_COMPUTE");
+    if (!v) return CUBLAS_COMPUTE_32F_FAST_TF32;
+    if (!std::strcmp(v, "bf16")) return CUBLAS_COMPUTE_32F_FAST_16BF;
+    if (!std::strcmp(v, "bf16x9")) return CUBLAS_COMPUTE_32F_EMULATED_16BFX9;
+    if (!std::strcmp(v, "fp32")) return CUBLAS_COMPUTE_32F;
+    return CUBLAS_COMPUTE_32F_FAST_TF32;
+}
+
+static const char* blas_msg(cublasStatus_t e) {
+    switch (e) {
+        case CUBLAS_STATUS_NOT_INITIALIZED: return "not initialised";
+        case CUBLAS_STATUS_ALLOC_FAILED: return "allocation failed";
+        case CUBLAS_STATUS_INVALID_VALUE: return "invalid value";
+        case CUBLAS_STATUS_ARCH_MISMATCH: return "architecture mismatch";
+        case CUBLAS_STATUS_EXECUTION_FAILED: return "execution failed";
+        case CUBLAS_STATUS_NOT_SUPPORTED: return "not supported";
+        default: return "error";
+    }
+}
+
+#define TVD_BLAS_TRY(expr)                                                                       \
+    do {                                                                                         \
+        cublasStatus_t _b = (expr);                                                              \
+        if (_b != CUBLAS_STATUS_SUCCESS) {                                                       \
+            ::tvd::set_error(std::string("cuBLAS: ") + blas_msg(_b) + " at " + __FILE__ + ":" + \
+                             std::to_string(__LINE__));                                         \
+            return TVD_ECUDA;                                                                    \
+        }                                                                                        \
+    } while (0)
+
+void gemm_precond_destroy(tvd_plan_s& p) {
+    auto* g = static_cast<GemmPrecond*>(p.gemm);
+    if (!g) return;
+    for (auto& q : g->g) {
+        if (q.op) cublasLtMatmulDescDestroy(q.op);
+        if (q.a) cublasLtMatrixLayoutDestroy(q.a);
+        if (q.b) cublasLtMatrixLayoutDestroy(q.b);
+        if (q.c) cublasLtMatrixLayoutDestroy(q.c);
+    }
+    if (g->lt) cublasLtDestroy(g->lt);
+    if (g->h) cublasDestroy(g->h);
+    if (g->Bc && g->Bc != g->Br) cudaFree(g->Bc);
+    if (g->Br) cudaFree(g->Br);
+    if (g->s1) cudaFree(g->s1);
+    if (g->s2) cudaFree(g->s2);
+    if (g->ws) cudaFree(g->ws);
+    delete g;
+    p.gemm = nullptr;
+}
+
+// Shapes of the four products (column-major m x n x k with the operand
+// transposes): forward B_c X^T, (.) B_r^T; inverse B_c^T Y^T, (.) B_r.
+struct GemmShape {
+    cublasOperation_t ta, tb;
+    int m, n, k, lda, ldb;
+    bool a_is_mat;   // A operand is B_c (else the image scratch)
+};
+static GemmShape gemm_shape(int i, int nr, int nc) {
+    switch (i) {
+        case 0: return {CUBLAS_OP_T, CUBLAS_OP_N, nc, nr, nc, nc, nc, true};
+        case 1: return {CUBLAS_OP_N, CUBLAS_OP_N, nc, nr, nr, nc, nr, false};
+        case 2: return {CUBLAS_OP_N, CUBLAS_OP_N, nc, nr, nc, nc, nc, true};
+        default: return {CUBLAS_OP_N, CUBLAS_OP_T, nc, nr, nr, nc, nr, false};
+    }
+}
+
+// Time up to 8 candidate algorithms of each product on the plan's buffers and
+// keep the fastest (3 timed runs after one warm-up each). Products without a
+// usable candidate fall back to cublasGemmEx.
+static tvd_status tune_lt(tvd_plan_s& p, GemmPrecond& g, cudaStream_t s) {
+    if (cublasLtCreate(&g.lt) != CUBLAS_STATUS_SUCCESS) {
+        g.lt = nullptr;
+        return TVD_OK;
+    }
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    TVD_CUDA_TRY(cudaEventCreate(&e0));
+    if (cudaEventCreate(&e1) != cudaSuccess) {
+        cudaEventDestroy(e0);
+        set_error("cudaEventCreate failed");
+        return TVD_ECUDA;
+    }
+    TVD_CUDA_TRY(cudaMemsetAsync(g.s1, 0, (size_t)p.nr * p.nc * sizeof(float), s));
+    const float one = 1.0f, zero = 0.0f;
+    for (int i = 0; i < 4; ++i) {
+        LtGemm& q = g.g[i];
+        const GemmShape sh = gemm_shape(i, p.nr, p.nc);
+        if (cublasLtMatmulDescCreate(&q.op, g.ct, CUDA_R_32F) != CUBLAS_STATUS_SUCCESS) continue;
+        cublasLtMatmulDescSetAttribute(q.op, CUBLASLT_MATMUL_DESC_TRANSA, &sh.ta, sizeof(sh.ta));
+        cublasLtMatmulDescSetAttribute(q.op, CUBLASLT_MATMUL_DESC_TRANSB, &sh.tb, sizeof(sh.tb));
+        const int ar = sh.ta == CUBLAS_OP_N ? sh.m : sh.k, ac = sh.ta == CUBLAS_OP_N ? sh.k : sh.m;
+        const int br = sh.tb == CUBLAS_OP_N ? sh.k : sh.n, bc = sh.tb == CUBLAS_OP_N ? sh.n : sh.k;
+        if (cublasLtMatrixLayoutCreate(&q.a, CUDA_R_32F, ar, ac, sh.lda) != CUBLAS_STATUS_SUCCESS ||
+            cublasLtMatrixLayoutCreate(&q.b, CUDA_R_32F, br, bc, sh.ldb) != CUBLAS_STATUS_SUCCESS ||
+            cublasLtMatrixLayoutCreate(&q.c, CUDA_R_32F, sh.m, sh.n, sh.m) != CUBLAS_STATUS_SUCCESS)
+            continue;
+        cublasLtMatmulPreference_t pref = nullptr;
+        if (cublasLtMatmulPreferenceCreate(&pref) != CUBLAS_STATUS_SUCCESS) continue;
+        const size_t wsb = g.ws_bytes;
+        cublasLtMatmulPreferenceSetAttribute(pref, CUBLASLT_MATMUL_PREF_MAX_WORKSPACE_BYTES, &wsb, sizeof(wsb));
+        cublasLtMatmulHeuristicResult_t res[8];
+        int found = 0;
+        cublasStatus_t hs = cublasLtMatmulAlgoGetHeuristic(g.lt, q.op, q.a, q.b, q.c, q.c, pref, 8, res, &found);
+        cublasLtMatmulPreferenceDestroy(pref);
+        if (hs != CUBLAS_STATUS_SUCCESS) continue;
+        const float* A = sh.a_is_mat ? g.Bc : g.s1;
+        const float* B = sh.a_is_mat ? g.s1 : g.Br;
+        float best = 1e30f;
+        for (int c = 0; c < found; ++c) {
+            if (res[c].state != CUBLAS_STATUS_SUCCESS || res[c].workspaceSize > wsb) continue;
+            bool ok = true;
+            for (int rep = 0; rep < 4 && ok; ++rep) {
+                if (rep == 1) ok = cudaEventRecord(e0, s) == cudaSuccess;
+                ok = ok && cublasLtMatmul(g.lt, q.op, &one, A, q.a, B, q.b, &zero, g.s2, q.c, g.s2, q.c,
+                                          &res[c].algo, g.ws, wsb, s) == CUBLAS_STATUS_SUCCESS;
+            }
+            ok = ok && cudaEventRecord(e1, s) == cudaSuccess && cudaEventSynchronize(e1) == cudaSuccess;
+            float ms = 0.0f;
+            if (!ok || cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) {
+                cudaGetLastError();
+                continue;
+            }
+            if (ms < best) {
+                best = ms;
+                q.algo = res[c].algo;
+                q.tuned = true;
+                q.us = ms * 1000.0f / 3.0f;
+            }
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    return TVD_OK;
+}
+
+tvd_status gemm_precond_create(tvd_plan_s& p, cudaStream_t s) {
+    if (p.gemm) return TVD_OK;
+    auto* g = new GemmPrecond();
+    p.gemm = g;
+    g->ct = compute_type_from_env();
+    auto fail = [&](tvd_status e) {
+        gemm_precond_destroy(p);
+        return e;
+    };
+    const size_t n = (size_t)p.nr * p.nc;
+    auto alloc = [&](void** ptr, size_t bytes) -> bool {
+        if (cudaMalloc(ptr, bytes) != cudaSuccess) {
+            cudaGetLastError();
+            set_error("cudaMalloc failed for the GEMM transform buffers");
+            return false;
+        }
+        return true;
+    };
+    if (!alloc((void**)&g->Br, (size_t)p.nr * p.nr * sizeof(float))) return fail(TVD_ENOMEM);
+    if (p.nc == p.nr) g->Bc = g->Br;
+    else if (!alloc((void**)&g->Bc, (size_t)p.nc * p.nc * sizeof(float))) return fail(TVD_ENOMEM);
+    if (!alloc((void**)&g->s1, n * sizeof(float)) || !alloc((void**)&g->s2, n * sizeof(float)))
+        return fail(TVD_ENOMEM);
+    if (!alloc(&g->ws, kGemmWorkspace)) return fail(TVD_ENOMEM);
+    g->ws_bytes = kGemmWorkspace;
+    std::vector<float> B;
+    transform_matrix(p.nr, p.bc, B);
+    if (cudaMemcpyAsync(g->Br, B.data(), B.size() * sizeof(float), cudaMemcpyHostToDevice, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess) {
+        set_error("upload of the transform matrix failed");
+        return fail(TVD_ECUDA);
+    }
+    if (g->Bc != g->Br) {
+        transform_matrix(p.nc, p.bc, B);
+        if (cudaMemcpyAsync(g->Bc, B.data(), B.size() * sizeof(float), cudaMemcpyHostToDevice, s) != cudaSuccess ||
+            cudaStreamSynchronize(s) != cudaSuccess) {
+            set_error("upload of the transform matrix failed");
+            return fail(TVD_ECUDA);
+        }
+    }
+    if (cublasCreate(&g->h) != CUBLAS_STATUS_SUCCESS) {
+        g->h = nullptr;
+        set_error("cublasCreate failed");
+        return fail(TVD_ECUDA);
+    }
+    if (cublasSetWorkspace(g->h, g->ws, g->ws_bytes) != CUBLAS_STATUS_SUCCESS) {
+        set_error("cublasSetWorkspace failed");
+        return fail(TVD_ECUDA);
+    }
+    // TVD_GEMM_TUNE=0 keeps cuBLAS's default algorithm for every product
+    const char* tv = std::getenv("TVD_GEMM_TUNE");
+    if (!(tv && tv[0] == '0')) {
+        tvd_status ts = tune_lt(p, *g, s);
+        if (ts != TVD_OK) return fail(ts);
+    }
+    return TVD_OK;
+}
+
+// ---------------------------------------------------------------- vector kernels
+
+// First kernel of the solve on the CG path: the previous iteration's pending
+// x += alpha p, r -= alpha q with ||r||^2 and the stopping test (as the first
+// row pass of the FFT form does), then s = d o r.
+__global__ void __launch_bounds__(kThreads)
+gemm_pre_kernel(float* __restrict__ r, float* __restrict__ x, const float* __restrict__ q, const float* p0,
+                const float* p1, const float* __restrict__ d, float* __restrict__ s, size_t n, CgState* st,
+                double* red, unsigned int* ticket) {
+    if (st && st->done) return;
+    // pending is the same for every block: the last block clears it only
+    // after every block has passed its reduction
+    const bool upd = x && st && st->pending;
+    const float al = upd ? (float)st->alpha : 0.0f;
+    const float* __restrict__ pv = (st && st->pbuf) ? p0 : p1;
+    float part = 0.0f;
+    const size_t nv = n / 4;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < nv; i += (size_t)gridDim.x * blockDim.x) {
+        float4 rv = reinterpret_cast<const float4*>(r)[i];
+        if (upd) {
+            const float4 qv = reinterpret_cast<const float4*>(q)[i];
+            const float4 pp = reinterpret_cast<const float4*>(pv)[i];
+            float4 xv = reinterpret_cast<const float4*>(x)[i];
+            rv.x -= al * qv.x; rv.y -= al * qv.y; rv.z -= al * qv.z; rv.w -= al * qv.w;
+            xv.x += al * pp.x; xv.y += al * pp.y; xv.z += al * pp.z; xv.w += al * pp.w;
+            reinterpret_cast<float4*>(r)[i] = rv;
+            reinterpret_cast<float4*>(x)[i] = xv;
+            part += rv.x * rv.x + rv.y * rv.y + rv.z * rv.z + rv.w * rv.w;
+        }
+        if (d) {
+            const float4 dv = reinterpret_cast<const float4*>(d)[i];
+            rv.x *= dv.x; rv.y *= dv.y; rv.z *= dv.z; rv.w *= dv.w;
+        }
+        reinterpret_cast<float4*>(s)[i] = rv;
+    }
+    for (size_t o = nv * 4 + blockIdx.x * (size_t)blockDim.x + threadIdx.x; o < n; o += (size_t)gridDim.x * blockDim.x) {
+        float v = r[o];
+        if (upd) {
+            v -= al * q[o];
+            r[o] = v;
+            x[o] += al * pv[o];
+            part += v * v;
+        }
+        s[o] = d ? v * d[o] : v;
+    }
+    if (!upd) return;
+    double sum;
+    if (block_reduce_last((double)part, red, ticket, blockIdx.x, gridDim.x, &sum) && threadIdx.x == 0)
+        finish_xr(st, sum);
+}
+
+// y = y o f (the division by the spectrum, f = 1 / spectrum).
+__global__ void __launch_bounds__(kThreads)
+gemm_scale_kernel(float* __restrict__ y, const float* __restrict__ f, size_t n, const CgState* st) {
+    if (st && st->done) return;
+    const size_t nv = n / 4;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < nv; i += (size_t)gridDim.x * blockDim.x) {
+        float4 a = reinterpret_cast<const float4*>(y)[i];
+        const float4 b = reinterpret_cast<const float4*>(f)[i];
+        a.x *= b.x; a.y *= b.y; a.z *= b.z; a.w *= b.w;
+        reinterpret_cast<float4*>(y)[i] = a;
+    }
+    for (size_t o = nv * 4 + blockIdx.x * (size_t)blockDim.x + threadIdx.x; o < n; o += (size_t)gridDim.x * blockDim.x)
+        y[o] *= f[o];
+}
+
+// z = d o u, and on the CG path r^T z with the Fletcher-Reeves coefficient.
+__global__ void __launch_bounds__(kThreads)
+gemm_post_kernel(const float* __restrict__ u, const float* __restrict__ d, const float* __restrict__ r,
+                 float* __restrict__ z, size_t n, CgState* st, double* red, unsigned int* ticket) {
+    if (st && st->done) return;
+    float part = 0.0f;
+    const size_t nv = n / 4;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < nv; i += (size_t)gridDim.x * blockDim.x) {
+        float4 v = reinterpret_cast<const float4*>(u)[i];
+        if (d) {
+            const float4 dv = reinterpret_cast<const float4*>(d)[i];
+            v.x *= dv.x; v.y *= dv.y; v.z *= dv.z; v.w *= dv.w;
+        }
+        reinterpret_cast<float4*>(z)[i] = v;
+        if (st) {
+            const float4 rv = reinterpret_cast<const float4*>(r)[i];
+            part += rv.x * v.x + rv.y * v.y + rv.z * v.z + rv.w * v.w;
+        }
+    }
+    for (size_t o = nv * 4 + blockIdx.x * (size_t)blockDim.x + threadIdx.x; o < n; o += (size_t)gridDim.x * blockDim.x) {
+        const float v = d ? u[o] * d[o] : u[o];
+        z[o] = v;
+        if (st) part += r[o] * v;
+    }
+    if (!st) return;
+    double sum;
+    if (block_reduce_last((double)part, red, ticket, blockIdx.x, gridDim.x, &sum) && threadIdx.x == 0)
+        finish_rho(st, sum);
+}
+
+static int ew_blocks(size_t n) {
+    size_t b = (n / 4 + kThreads - 1) / kThreads;
+    const size_t cap = (size_t)num_sms() * 16;
+    if (b > cap) b = cap;
+    return (int)(b ? b : 1);
+}
+
+static bool al16(const void* p) { return ((uintptr_t)p & 15u) == 0; }
+
+// Product i (gemm_shape) C = op(A) op(B) in float storage: the tuned cuBLASLt
+// algorithm, else cublasGemmEx with cuBLAS's own choice.
+static tvd_status gemm(const GemmPrecond& g, int i, int nr, int nc, const float* A, const float* B, float* C,
+                       cudaStream_t s) {
+    const float one = 1.0f, zero = 0.0f;
+    const GemmShape sh = gemm_shape(i, nr, nc);
+    ProfScope prof(PROF_GEMM, s, 1, false);
+    const LtGemm& q = g.g[i];
+    if (q.tuned) {
+        TVD_BLAS_TRY(cublasLtMatmul(g.lt, q.op, &one, A, q.a, B, q.b, &zero, C, q.c, C, q.c, &q.algo, g.ws,
+                                    g.ws_bytes, s));
+        return TVD_OK;
+    }
+    TVD_BLAS_TRY(cublasSetStream(g.h, s));
+    TVD_BLAS_TRY(cublasGemmEx(g.h, sh.ta, sh.tb, sh.m, sh.n, sh.k, &one, A, CUDA_R_32F, sh.lda, B, CUDA_R_32F,
+                              sh.ldb, &zero, C, CUDA_R_32F, sh.m, g.ct, CUBLAS_GEMM_DEFAULT));
+    return TVD_OK;
+}
+
+tvd_status gemm_precond_solve(const tvd_plan_s& p, const Ops<float>& o, const float* r, float* z, CgState* st,
+                              cudaStream_t s, float* x) {
+    const auto* g = static_cast<const GemmPrecond*>(p.gemm);
+    const bool scaled = (p.pc == TVD_PC_DFAST || p.pc == TVD_PC_FASTD);
+    const float* d = scaled ? o.dmh : nullptr;
+    const size_t n = (size_t)p.nr * p.nc;
+    const int nr = p.nr, nc = p.nc;
+    if (!al16(r) || !al16(z) || (x && !al16(x))) {
+        set_error("GEMM preconditioner: vectors must be 16-byte aligned");
+        return TVD_EINVAL;
+    }
+    const int blocks = ew_blocks(n);
+    {
+        ProfScope prof(PROF_GEMM_EW, s);
+        gemm_pre_kernel<<<blocks, kThreads, 0, s>>>(const_cast<float*>(r), x, o.q, o.p, o.p2, d, g->s1, n, st,
+                                                    p.red, p.ticket + 7);
+        TVD_CUDA_TRY(cudaGetLastError());
+    }
+    // forward: s2 = B_c s1 (row pass), s1 = s2 B_r^T (column pass)
+    TVD_TRY(gemm(*g, 0, nr, nc, g->Bc, g->s1, g->s2, s));
+    TVD_TRY(gemm(*g, 1, nr, nc, g->s2, g->Br, g->s1, s));
+    {
+        ProfScope prof(PROF_GEMM_EW, s);
+        gemm_scale_kernel<<<blocks, kThreads, 0, s>>>(g->s1, o.inv_spec, n, st);
+        TVD_CUDA_TRY(cudaGetLastError());
+    }
+    // inverse: s2 = B_c^T s1, s1 = s2 B_r
+    TVD_TRY(gemm(*g, 2, nr, nc, g->Bc, g->s1, g->s2, s));
+    TVD_TRY(gemm(*g, 3, nr, nc, g->s2, g->Br, g->s1, s));
+    {
+        ProfScope prof(PROF_GEMM_EW, s);
+        gemm_post_kernel<<<blocks, kThreads, 0, s>>>(g->s1, d, r, z, n, st, p.red, p.ticket + 2);
+        TVD_CUDA_TRY(cudaGetLastError());
+    }
+    return TVD_OK;
+}
+
+}  // namespace tvd

@@ -537,17 +537,6 @@ __device__ void eg_lines(const T* raw, cplx<T>* bufA, cplx<T>* bufB, T* eo, T* g
 
 // ------------------------------------------------------------- the line kernel
 
-__device__ __forceinline__ void finish_rho(CgState* st, double rho) {
-    st->rho_old = st->rho;
-    st->rho = rho;
-    if (!(isfinite(rho) && rho > 0.0)) {
-        st->status = TVD_EBREAKDOWN;
-        st->done = 1;
-        st->beta = 0.0;
-        return;
-    }
-    st->beta = st->fresh ? 0.0 : rho / st->rho_old;
-}
 
 // Extra shared memory (elements of T) each operation stages next to the lines:
 // ROW_FWD: D^-1/2; COL_SOLVE: 1/spectrum; ROW_INV: D^-1/2 and r; ROW_EG: the
@@ -560,24 +549,6 @@ __host__ __device__ constexpr size_t line_extra(int op, size_t lines, size_t n, 
          : 2 * lines * n + P * n;
 }
 
-// End of a CG iteration (the x / r update applied by the next row pass): the
-// residual norm, the iteration count and the stopping test ||r|| / ||r_0|| < tol.
-__device__ __forceinline__ void finish_xr(CgState* st, double rr) {
-    st->rr = rr;
-    st->iter += 1;
-    st->fresh = 0;
-    st->pbuf ^= 1;
-    st->pending = 0;
-    if (!isfinite(rr)) {
-        st->status = TVD_EBREAKDOWN;
-        st->done = 1;
-    } else if (rr < st->tol2) {
-        st->done = 1;
-    } else if (st->iter >= st->maxit) {
-        st->status = TVD_ENOCONV;
-        st->done = 1;
-    }
-}
 
 // Resident blocks per SM the float kernels' register allocation aims for (tuning: more blocks
 // hide more latency, at the price of spilled large-radix butterflies).
@@ -906,6 +877,9 @@ static LineArgs<T> base_args(const tvd_plan_s& p, const Ops<T>& o, bool cols) {
 template <typename T>
 tvd_status precond_solve(const tvd_plan_s& p, const Ops<T>& o, const T* r, T* z, CgState* st, cudaStream_t s,
                          T* x) {
+    if constexpr (sizeof(T) == 4) {
+        if (p.gemm) return gemm_precond_solve(p, o, r, z, st, s, x);
+    }
     const bool scaled = (p.pc == TVD_PC_DFAST || p.pc == TVD_PC_FASTD);
     LineArgs<T> a = base_args<T>(p, o, false);
     a.in0 = r;

@@ -212,6 +212,7 @@ static void plan_free(tvd_plan_s* p) {
     }
     if (p->cap_stream) cudaStreamDestroy(p->cap_stream);
     p->cap_stream = nullptr;
+    gemm_precond_destroy(*p);
     ops_free(p->d);
     ops_free(p->f);
     dfree(p->state); dfree(p->red); dfree(p->ticket); dfree(p->scal);
@@ -307,6 +308,24 @@ tvd_status build_psf(Psf& out, const double* h, int pr, int pc, int nr, int nc) 
             out.ccor[(size_t)i * (mc + 1) + j] = v;
         }
     return TVD_OK;
+}
+
+// ---------------------------------------------------------------- transform form
+
+static bool fast_pc(tvd_precond pc) { return pc == TVD_PC_FAST || pc == TVD_PC_DFAST || pc == TVD_PC_FASTD; }
+
+// Transform form a new MIXED plan with a fast preconditioner starts with: the
+// GEMM form when both sides are at least TVD_GEMM_MIN_SIDE (default 256;
+// measured faster than the FFT line kernels there), else the FFT form.
+// TVD_TRANSFORM=gemm / fft overrides the rule.
+static tvd_transform default_transform(const tvd_plan_s& p) {
+    if (p.mode != TVD_MODE_MIXED || !fast_pc(p.pc)) return TVD_TRANSFORM_FFT;
+    const char* v = std::getenv("TVD_TRANSFORM");
+    if (v && !std::strcmp(v, "gemm")) return TVD_TRANSFORM_GEMM;
+    if (v && !std::strcmp(v, "fft")) return TVD_TRANSFORM_FFT;
+    const char* m = std::getenv("TVD_GEMM_MIN_SIDE");
+    const int min_side = m ? std::atoi(m) : 256;
+    return std::min(p.nr, p.nc) >= min_side ? TVD_TRANSFORM_GEMM : TVD_TRANSFORM_FFT;
 }
 
 // ---------------------------------------------------------------- CG driver
@@ -610,6 +629,36 @@ extern "C" {
 
 const char* tvd_last_error(void) { return g_err.c_str(); }
 
+tvd_status tvd_plan_set_transform(tvd_plan plan, int kind, void* stream) {
+    if (!plan || (kind != TVD_TRANSFORM_FFT && kind != TVD_TRANSFORM_GEMM)) {
+        set_error("tvd_plan_set_transform: NULL plan or unknown transform kind");
+        return TVD_EINVAL;
+    }
+    if (kind == TVD_TRANSFORM_GEMM && (plan->mode != TVD_MODE_MIXED || !fast_pc(plan->pc))) {
+        set_error("tvd_plan_set_transform: the GEMM form needs a MIXED plan with a fast preconditioner");
+        return TVD_EINVAL;
+    }
+    if ((kind == TVD_TRANSFORM_GEMM) == (plan->gemm != nullptr)) return TVD_OK;
+    cudaStream_t s = (cudaStream_t)stream;
+    if (cudaStreamSynchronize(s) != cudaSuccess) {
+        set_error("stream synchronisation failed");
+        return TVD_ECUDA;
+    }
+    // the captured float CG iterations hold the previous form's launches
+    if (plan->graph[0].exec) {
+        cudaGraphExecDestroy(plan->graph[0].exec);
+        plan->graph[0].exec = nullptr;
+    }
+    if (kind == TVD_TRANSFORM_FFT) {
+        cudaDeviceSynchronize();
+        gemm_precond_destroy(*plan);
+        return TVD_OK;
+    }
+    return gemm_precond_create(*plan, s);
+}
+
+int tvd_plan_transform(tvd_plan plan) { return plan && plan->gemm ? TVD_TRANSFORM_GEMM : TVD_TRANSFORM_FFT; }
+
 const char* tvd_version(void) { return "tvd-gb300 0.1"; }
 
 tvd_status tvd_plan_create(tvd_plan* out, int n_rows, int n_cols, const double* psf_host, int p_rows, int p_cols,
@@ -673,6 +722,9 @@ tvd_status tvd_plan_create(tvd_plan* out, int n_rows, int n_cols, const double* 
     }
     if ((st = ops_alloc<double>(*p, p->d, s)) != TVD_OK) return fail(st);
     if (mode == TVD_MODE_MIXED && (st = ops_alloc<float>(*p, p->f, s)) != TVD_OK) return fail(st);
+    if (mode == TVD_MODE_MIXED && default_transform(*p) == TVD_TRANSFORM_GEMM &&
+        (st = gemm_precond_create(*p, s)) != TVD_OK)
+        return fail(st);
     if (cudaStreamSynchronize(s) != cudaSuccess) {
         set_error("stream synchronisation failed");
         return fail(TVD_ECUDA);

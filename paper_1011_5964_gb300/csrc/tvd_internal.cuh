@@ -44,7 +44,8 @@ struct Status {
 
 enum ProfClass {
     PROF_BLUR_FWD = 0, PROF_BLUR_ADJ, PROF_ROW_FWD, PROF_COL_SOLVE, PROF_ROW_INV, PROF_EG_ROW, PROF_EG_COL,
-    PROF_CG_INIT, PROF_CG_PUPDATE, PROF_CG_XR, PROF_CG_SIMPLE, PROF_TV, PROF_MISC, PROF_NUM_BASE,
+    PROF_CG_INIT, PROF_CG_PUPDATE, PROF_CG_XR, PROF_CG_SIMPLE, PROF_TV, PROF_MISC, PROF_GEMM, PROF_GEMM_EW,
+    PROF_NUM_BASE,
     PROF_NUM_CLASSES = 2 * PROF_NUM_BASE     // float launches use the base id, double ones base + PROF_NUM_BASE
 };
 template <typename T>
@@ -58,10 +59,12 @@ void set_capturing(bool on);
 int captured_kernels();   // kernels launched since set_capturing(true)
 
 // Counts the launches of one launcher call and, when profiling is on, brackets
-// them with CUDA events on the launch stream.
+// them with CUDA events on the launch stream. Library launches (ours = false,
+// cuBLAS) are timed and counted per class but not in the library's own
+// kernel-launch total.
 class ProfScope {
   public:
-    ProfScope(int cls, cudaStream_t s, int nkernels = 1);
+    ProfScope(int cls, cudaStream_t s, int nkernels = 1, bool ours = true);
     ~ProfScope();
     ProfScope(const ProfScope&) = delete;
     ProfScope& operator=(const ProfScope&) = delete;
@@ -205,6 +208,9 @@ struct tvd_plan_s {
     int last_iters[2] = {0, 0};         // iterations of the previous solve (chunking hint)
     bool precond_ready = false;
     double alpha = 0.0, beta = 0.0;     // parameters of the last setup
+    // dense-matrix (GEMM) form of the preconditioner transforms, MIXED plans
+    // with a fast preconditioner only (gemm_precond.cu); nullptr: FFT form
+    void* gemm = nullptr;
 };
 
 namespace tvd {
@@ -254,6 +260,14 @@ tvd_status lamH2_setup(const tvd_plan_s& p, Ops<T>& o, cudaStream_t s);
 // CG scalar update that follows it). With x (CG path), the first pass applies
 // the pending update x += alpha p, r -= alpha q (r in place, p and q from o)
 // and the stopping test before preconditioning r.
+// Dense-matrix (GEMM) form of the fast preconditioners' solve on a float plan
+// (gemm_precond.cu): create / destroy its matrices, scratch and cuBLAS handle,
+// and the solve, with the same contract as precond_solve.
+tvd_status gemm_precond_create(tvd_plan_s& p, cudaStream_t s);
+void gemm_precond_destroy(tvd_plan_s& p);
+tvd_status gemm_precond_solve(const tvd_plan_s& p, const Ops<float>& o, const float* r, float* z, CgState* st,
+                              cudaStream_t s, float* x);
+
 template <typename T>
 tvd_status precond_solve(const tvd_plan_s& p, const Ops<T>& o, const T* r, T* z, CgState* st, cudaStream_t s,
                          T* x = nullptr);
