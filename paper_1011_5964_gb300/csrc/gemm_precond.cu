@@ -24,6 +24,7 @@
 #include <cublas_v2.h>
 
 #include <cmath>
+#include <cstdio>
 #include <cstdlib>
 #include <cstring>
 #include <vector>
@@ -55,6 +56,7 @@ struct GemmPrecond {
 };
 
 static constexpr size_t kGemmWorkspace = 32u << 20;
+static constexpr int kCandidates = 16;   // cuBLASLt heuristic candidates timed per product
 
 // Row-major n x n matrix of the 1D transform: AR hat-S_n, R the DCT-II C_n
 // (frequency by space). Arguments are reduced modulo the period in integers.
@@ -148,9 +150,10 @@ static GemmShape gemm_shape(int i, int nr, int nc) {
     }
 }
 
-// Time up to 8 candidate algorithms of each product on the plan's buffers and
-// keep the fastest (3 timed runs after one warm-up each). Products without a
-// usable candidate fall back to cublasGemmEx.
+// Time the candidate algorithms of each product (up to kCandidates from the
+// heuristic, and their split-K variants) on the plan's buffers and keep the
+// fastest (3 timed runs after one warm-up each). Products without a usable
+// candidate fall back to cublasGemmEx.
 static tvd_status tune_lt(tvd_plan_s& p, GemmPrecond& g, cudaStream_t s) {
     if (cublasLtCreate(&g.lt) != CUBLAS_STATUS_SUCCESS) {
         g.lt = nullptr;
@@ -181,15 +184,46 @@ static tvd_status tune_lt(tvd_plan_s& p, GemmPrecond& g, cudaStream_t s) {
         if (cublasLtMatmulPreferenceCreate(&pref) != CUBLAS_STATUS_SUCCESS) continue;
         const size_t wsb = g.ws_bytes;
         cublasLtMatmulPreferenceSetAttribute(pref, CUBLASLT_MATMUL_PREF_MAX_WORKSPACE_BYTES, &wsb, sizeof(wsb));
-        cublasLtMatmulHeuristicResult_t res[8];
+        cublasLtMatmulHeuristicResult_t heur[kCandidates];
         int found = 0;
-        cublasStatus_t hs = cublasLtMatmulAlgoGetHeuristic(g.lt, q.op, q.a, q.b, q.c, q.c, pref, 8, res, &found);
+        cublasStatus_t hs =
+            cublasLtMatmulAlgoGetHeuristic(g.lt, q.op, q.a, q.b, q.c, q.c, pref, kCandidates, heur, &found);
         cublasLtMatmulPreferenceDestroy(pref);
         if (hs != CUBLAS_STATUS_SUCCESS) continue;
+        // each candidate as proposed, plus split-K variants (2, 4, 8 slices of k, reduced in the
+        // compute type through the workspace) where the algorithm supports them
+        std::vector<cublasLtMatmulHeuristicResult_t> res;
+        for (int c = 0; c < found; ++c) {
+            if (heur[c].state != CUBLAS_STATUS_SUCCESS) continue;
+            res.push_back(heur[c]);
+            int32_t splitk = 0;
+            uint32_t schemes = 0;
+            size_t wr = 0;
+            if (cublasLtMatmulAlgoCapGetAttribute(&heur[c].algo, CUBLASLT_ALGO_CAP_SPLITK_SUPPORT, &splitk,
+                                                  sizeof(splitk), &wr) != CUBLAS_STATUS_SUCCESS || !splitk)
+                continue;
+            if (cublasLtMatmulAlgoCapGetAttribute(&heur[c].algo, CUBLASLT_ALGO_CAP_REDUCTION_SCHEME_MASK, &schemes,
+                                                  sizeof(schemes), &wr) != CUBLAS_STATUS_SUCCESS ||
+                !(schemes & CUBLASLT_REDUCTION_SCHEME_COMPUTE_TYPE))
+                continue;
+            for (int32_t parts : {2, 4, 8}) {
+                cublasLtMatmulHeuristicResult_t v = heur[c];
+                const uint32_t scheme = CUBLASLT_REDUCTION_SCHEME_COMPUTE_TYPE;
+                if (cublasLtMatmulAlgoConfigSetAttribute(&v.algo, CUBLASLT_ALGO_CONFIG_SPLITK_NUM, &parts,
+                                                         sizeof(parts)) != CUBLAS_STATUS_SUCCESS ||
+                    cublasLtMatmulAlgoConfigSetAttribute(&v.algo, CUBLASLT_ALGO_CONFIG_REDUCTION_SCHEME, &scheme,
+                                                         sizeof(scheme)) != CUBLAS_STATUS_SUCCESS)
+                    continue;
+                if (cublasLtMatmulAlgoCheck(g.lt, q.op, q.a, q.b, q.c, q.c, &v.algo, &v) != CUBLAS_STATUS_SUCCESS)
+                    continue;
+                v.state = CUBLAS_STATUS_SUCCESS;
+                res.push_back(v);
+            }
+        }
         const float* A = sh.a_is_mat ? g.Bc : g.s1;
         const float* B = sh.a_is_mat ? g.s1 : g.Br;
         float best = 1e30f;
-        for (int c = 0; c < found; ++c) {
+        for (size_t c = 0; c < res.size(); ++c) {
             if (res[c].state != CUBLAS_STATUS_SUCCESS || res[c].workspaceSize > wsb) continue;
             bool ok = true;
             for (int rep = 0; rep < 4 && ok; ++rep) {
@@ -213,6 +247,19 @@ static tvd_status tune_lt(tvd_plan_s& p, GemmPrecond& g, cudaStream_t s) {
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
+    // TVD_GEMM_VERBOSE=1: the chosen algorithm of each product on stderr
+    const char* vb = std::getenv("TVD_GEMM_VERBOSE");
+    if (vb && vb[0] == '1') {
+        for (int i = 0; i < 4; ++i) {
+            int32_t parts = 1;
+            size_t wr = 0;
+            if (g.g[i].tuned)
+                cublasLtMatmulAlgoConfigGetAttribute(&g.g[i].algo, CUBLASLT_ALGO_CONFIG_SPLITK_NUM, &parts,
+                                                     sizeof(parts), &wr);
+            std::fprintf(stderr, "tvd gemm %dx%d product %d: tuned %d, split-k %d, %.2f us\n", p.nr, p.nc, i,
+                         (int)g.g[i].tuned, parts, g.g[i].us);
+        }
+    }
     return TVD_OK;
 }
 
@@ -283,6 +330,7 @@ __global__ void __launch_bounds__(kThreads)
 gemm_pre_kernel(float* __restrict__ r, float* __restrict__ x, const float* __restrict__ q, const float* p0,
                 const float* p1, const float* __restrict__ d, float* __restrict__ s, size_t n, CgState* st,
                 double* red, unsigned int* ticket) {
+    pdl_wait();   // everything below reads what earlier kernels in the stream write
     if (st && st->done) return;
     // pending is the same for every block: the last block clears it only
     // after every block has passed its reduction
@@ -328,6 +376,7 @@ gemm_pre_kernel(float* __restrict__ r, float* __restrict__ x, const float* __res
 // y = y o f (the division by the spectrum, f = 1 / spectrum).
 __global__ void __launch_bounds__(kThreads)
 gemm_scale_kernel(float* __restrict__ y, const float* __restrict__ f, size_t n, const CgState* st) {
+    pdl_wait();
     if (st && st->done) return;
     const size_t nv = n / 4;
     for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < nv; i += (size_t)gridDim.x * blockDim.x) {
@@ -344,6 +393,7 @@ gemm_scale_kernel(float* __restrict__ y, const float* __restrict__ f, size_t n, 
 __global__ void __launch_bounds__(kThreads)
 gemm_post_kernel(const float* __restrict__ u, const float* __restrict__ d, const float* __restrict__ r,
                  float* __restrict__ z, size_t n, CgState* st, double* red, unsigned int* ticket) {
+    pdl_wait();
     if (st && st->done) return;
     float part = 0.0f;
     const size_t nv = n / 4;
@@ -412,8 +462,8 @@ tvd_status gemm_precond_solve(const tvd_plan_s& p, const Ops<float>& o, const fl
     const int blocks = ew_blocks(n);
     {
         ProfScope prof(PROF_GEMM_EW, s);
-        gemm_pre_kernel<<<blocks, kThreads, 0, s>>>(const_cast<float*>(r), x, o.q, o.p, o.p2, d, g->s1, n, st,
-                                                    p.red, p.ticket + 7);
+        TVD_CUDA_TRY(launch_pdl(gemm_pre_kernel, dim3(blocks), dim3(kThreads), 0, s, const_cast<float*>(r), x,
+                                o.q, o.p, o.p2, d, g->s1, n, st, p.red, p.ticket + 7));
         TVD_CUDA_TRY(cudaGetLastError());
     }
     // forward: s2 = B_c s1 (row pass), s1 = s2 B_r^T (column pass)
@@ -421,7 +471,8 @@ tvd_status gemm_precond_solve(const tvd_plan_s& p, const Ops<float>& o, const fl
     TVD_TRY(gemm(*g, 1, nr, nc, g->s2, g->Br, g->s1, s));
     {
         ProfScope prof(PROF_GEMM_EW, s);
-        gemm_scale_kernel<<<blocks, kThreads, 0, s>>>(g->s1, o.inv_spec, n, st);
+        TVD_CUDA_TRY(launch_pdl(gemm_scale_kernel, dim3(blocks), dim3(kThreads), 0, s, g->s1,
+                                (const float*)o.inv_spec, n, (const CgState*)st));
         TVD_CUDA_TRY(cudaGetLastError());
     }
     // inverse: s2 = B_c^T s1, s1 = s2 B_r
@@ -429,7 +480,8 @@ tvd_status gemm_precond_solve(const tvd_plan_s& p, const Ops<float>& o, const fl
     TVD_TRY(gemm(*g, 3, nr, nc, g->s2, g->Br, g->s1, s));
     {
         ProfScope prof(PROF_GEMM_EW, s);
-        gemm_post_kernel<<<blocks, kThreads, 0, s>>>(g->s1, d, r, z, n, st, p.red, p.ticket + 2);
+        TVD_CUDA_TRY(launch_pdl(gemm_post_kernel, dim3(blocks), dim3(kThreads), 0, s, (const float*)g->s1, d, r, z,
+                                n, st, p.red, p.ticket + 2));
         TVD_CUDA_TRY(cudaGetLastError());
     }
     return TVD_OK;
