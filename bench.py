@@ -295,17 +295,26 @@ def tf32_peak():
         return 1700.0 * TF32_OVER_BF16, "fallback (bf16 sustained 1.7 PF x 1.1/2.25)"
 
 
-def roofline_of(name, kms, klaunch, total_ms):
+def bf16_peak():
+    """bf16 tensor peak (TFLOP/s) for a kernel timed inside a long step: the measured sustained cuBLAS rate."""
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        return float(json.load(open(path))["bf16_tflops_sustained"]), "measured (bf16 sustained)"
+    except Exception:
+        return 1700.0, "fallback (bf16 sustained 1.7 PF)"
+
+
+def roofline_of(name, kms, klaunch, total_ms, storage=None):
     """Roofline entry of one kernel class from its summed device time and launch count."""
     base, prec = name.rsplit(".", 1)
     avg_s = kms / 1000.0 / max(klaunch, 1)
     share = kms / max(total_ms, 1e-12)
     if base == "precond_gemm_cublas":
-        # one n x n x n product of the transform form: 2 n^3 flops (TF32 inputs, float accumulation)
+        # one n x n x n product of the transform form: 2 n^3 flops (bf16 or TF32 operands, float accumulation)
         flops = 2.0 * N_SIDE ** 3
-        peak, src = tf32_peak()
+        peak, src = bf16_peak() if storage == "bf16" else tf32_peak()
         achieved = flops / avg_s / 1e12
-        return {"bound": "tensor", "kernel": name + " (cuBLASLt TF32 transform GEMM)", "achieved": achieved,
+        return {"bound": "tensor", "kernel": f"{name} (cuBLASLt {storage} transform GEMM)", "achieved": achieved,
                 "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None, "peak_source": src,
                 "flops_per_launch": flops, "avg_launch_us": avg_s * 1e6, "launches": klaunch, "share": share}
     word = 4 if prec == "f32" else 8
@@ -484,7 +493,7 @@ def run_ours(args):
         print("per-kernel-class device time of one chosen-form step: " + json.dumps(table), file=sys.stderr)
     total_ms = sum(v_[0] for v_ in prof.values())
     top = max(prof.items(), key=lambda kv: kv[1][0])
-    roofline = roofline_of(top[0], top[1][0], top[1][1], total_ms)
+    roofline = roofline_of(top[0], top[1][0], top[1][1], total_ms, mixed.gemm_storage)
     # the library's own dominant kernel (the stencils and the vector kernels are ours; cuBLAS is not)
     own = max(((k, v_) for k, v_ in prof.items() if not k.startswith("precond_gemm_cublas")), key=lambda kv: kv[1][0])
     roofline_own = roofline_of(own[0], own[1][0], own[1][1], total_ms)
@@ -526,6 +535,7 @@ def run_ours(args):
             "roofline": roofline,
             "roofline_own_kernel": roofline_own,
             "transform_form": mixed.transform,
+            "gemm_operands": mixed.gemm_storage,
             "clocks": clocks,
             "e2e": {"value": ws * 1000.0 * args.steps / e2e_ms, "unit": "deblurs/s",
                     "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes}}

@@ -164,9 +164,11 @@ tvd_status tau_precond_solve(tvd_plan plan, const void* r, void* z, void* stream
  *   TVD_TRANSFORM_FFT:  as the paper's fast transforms, O(n^2 log n), by FFT
  *                       line kernels in shared memory (float), or
  *   TVD_TRANSFORM_GEMM: as four dense products with the n x n matrices B_r,
- *                       B_c on the tensor cores (cuBLAS, float storage, TF32
- *                       inputs, float accumulation; TVD_GEMM_COMPUTE=bf16 /
- *                       bf16x9 / fp32 selects another cuBLAS compute type),
+ *                       B_c on the tensor cores (cuBLASLt, float accumulation;
+ *                       operands in float with TF32 products when a side is
+ *                       below 1024, in bf16 from 1024 on; TVD_GEMM_STORAGE=
+ *                       f32 / bf16 overrides, and TVD_GEMM_COMPUTE=bf16x9 /
+ *                       fp32 selects another compute type for float operands),
  *                       O(n^3) flops but tensor-core rate.
  * Both give the same preconditioner up to rounding; the preconditioner only
  * shapes the CG iteration, so the form changes iteration counts slightly,
@@ -197,6 +199,10 @@ tvd_status tvd_plan_set_transform(tvd_plan plan, int kind, void* stream);
 
 /* tvd_plan_transform -- the plan's current tvd_transform (FFT for NULL). */
 int tvd_plan_transform(tvd_plan plan);
+
+/* tvd_plan_gemm_storage -- operand storage of the plan's GEMM form: 0 none
+ * (FFT form or NULL plan), 1 float operands (TF32 products), 2 bf16 operands. */
+int tvd_plan_gemm_storage(tvd_plan plan);
 
 /*
  * pcg_solve -- solve (H^T H + alpha L(u_lag)) x = b by preconditioned CG from

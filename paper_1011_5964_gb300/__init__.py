@@ -36,7 +36,8 @@ TRANSFORM = {"fft": 0, "gemm": 1}
 ABI_FUNCTIONS = ["tvd_plan_create", "tvd_plan_destroy", "ar_blur_apply", "tv_operator_apply",
                  "tau_precond_setup", "tau_precond_solve", "pcg_solve", "tv_deblur",
                  "tv_deblur_batched", "tv_hessian_apply", "tv_deblur_adjoint", "tvd_plan_psf_size",
-                 "tvd_normal_apply_noalloc", "tvd_plan_set_transform", "tvd_plan_transform", "tvd_last_error", "tvd_version", "tvd_kernel_launches",
+                 "tvd_normal_apply_noalloc", "tvd_plan_set_transform", "tvd_plan_transform", "tvd_plan_gemm_storage",
+                 "tvd_last_error", "tvd_version", "tvd_kernel_launches",
                  "tvd_profile_enable", "tvd_profile_classes", "tvd_profile_name", "tvd_profile_read"]
 
 
@@ -91,6 +92,7 @@ def load_library(path: str | None = None) -> ctypes.CDLL:
     lib.tvd_plan_psf_size.argtypes = [vp, ctypes.POINTER(i), ctypes.POINTER(i)]
     lib.tvd_plan_set_transform.argtypes = [vp, i, vp]
     lib.tvd_plan_transform.argtypes = [vp]
+    lib.tvd_plan_gemm_storage.argtypes = [vp]
     lib.tvd_last_error.restype = ctypes.c_char_p
     lib.tvd_version.restype = ctypes.c_char_p
     lib.tvd_kernel_launches.restype = ctypes.c_ulonglong
@@ -163,6 +165,11 @@ class Plan:
     @property
     def transform(self) -> str:
         return "gemm" if self.lib.tvd_plan_transform(self.handle) == TRANSFORM["gemm"] else "fft"
+
+    @property
+    def gemm_storage(self):
+        """Operand storage of the GEMM form: 'f32' (TF32 products), 'bf16', or None (FFT form)."""
+        return {0: None, 1: "f32", 2: "bf16"}[self.lib.tvd_plan_gemm_storage(self.handle)]
 
     def close(self):
         if getattr(self, "handle", None):

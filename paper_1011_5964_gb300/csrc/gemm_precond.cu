@@ -7,7 +7,8 @@
 // eq. (lambda), symmetric, an involution) for AR and B = C, the orthonormal
 // DCT-II of Sec. 3.1 (B^{-1} = C^T) for R. Here each 1D transform of all
 // lines is one matrix product with the n x n matrix B on the tensor cores
-// (cuBLAS, float storage, TF32 inputs with float accumulation by default), so
+// (cuBLASLt; TF32 products of float operands, or, from sides of 1024 on,
+// bf16 operands; float accumulation in both), so
 // the solve is four GEMMs and three vector kernels instead of the three FFT
 // line passes of transform.cu. The preconditioner only shapes the CG
 // iteration: its rounding changes the iteration count, not the solution,
@@ -22,7 +23,9 @@
 
 #include <cublasLt.h>
 #include <cublas_v2.h>
+#include <cuda_bf16.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>
@@ -47,10 +50,15 @@ struct GemmPrecond {
     cublasLtHandle_t lt = nullptr;
     LtGemm g[4];
     cublasComputeType_t ct = CUBLAS_COMPUTE_32F_FAST_TF32;
-    float* Br = nullptr;     // n_r x n_r, row-major
-    float* Bc = nullptr;     // n_c x n_c, row-major (aliases Br for square images)
-    float* s1 = nullptr;     // n_r x n_c scratch
-    float* s2 = nullptr;     // n_r x n_c scratch
+    // operand storage: float (TF32 products by default), or bf16 (TVD_GEMM_STORAGE=bf16: the matrices
+    // and the inputs of each product rounded to bf16, float accumulation, float outputs of the
+    // column products)
+    bool bf = false;
+    void* Br = nullptr;      // n_r x n_r, row-major, operand type
+    void* Bc = nullptr;      // n_c x n_c, row-major, operand type (aliases Br for square images)
+    void* in = nullptr;      // n_r x n_c, operand type: input of the row products
+    void* mid = nullptr;     // n_r x n_c, operand type: row products' output, column products' input
+    float* s1 = nullptr;     // n_r x n_c float: column products' output
     void* ws = nullptr;      // cuBLAS workspace (no allocation inside a captured graph)
     size_t ws_bytes = 0;
 };
@@ -127,8 +135,9 @@ void gemm_precond_destroy(tvd_plan_s& p) {
     if (g->h) cublasDestroy(g->h);
     if (g->Bc && g->Bc != g->Br) cudaFree(g->Bc);
     if (g->Br) cudaFree(g->Br);
+    if (g->in && g->in != (void*)g->s1) cudaFree(g->in);
+    if (g->mid) cudaFree(g->mid);
     if (g->s1) cudaFree(g->s1);
-    if (g->s2) cudaFree(g->s2);
     if (g->ws) cudaFree(g->ws);
     delete g;
     p.gemm = nullptr;
@@ -166,19 +175,24 @@ static tvd_status tune_lt(tvd_plan_s& p, GemmPrecond& g, cudaStream_t s) {
         set_error("cudaEventCreate failed");
         return TVD_ECUDA;
     }
-    TVD_CUDA_TRY(cudaMemsetAsync(g.s1, 0, (size_t)p.nr * p.nc * sizeof(float), s));
+    const size_t esz = g.bf ? sizeof(__nv_bfloat16) : sizeof(float);
+    TVD_CUDA_TRY(cudaMemsetAsync(g.in, 0, (size_t)p.nr * p.nc * esz, s));
+    TVD_CUDA_TRY(cudaMemsetAsync(g.mid, 0, (size_t)p.nr * p.nc * esz, s));
     const float one = 1.0f, zero = 0.0f;
     for (int i = 0; i < 4; ++i) {
         LtGemm& q = g.g[i];
         const GemmShape sh = gemm_shape(i, p.nr, p.nc);
-        if (cublasLtMatmulDescCreate(&q.op, g.ct, CUDA_R_32F) != CUBLAS_STATUS_SUCCESS) continue;
+        const cudaDataType_t ot = g.bf ? CUDA_R_16BF : CUDA_R_32F;
+        const cudaDataType_t ct = sh.a_is_mat ? ot : CUDA_R_32F;   // row products feed the column products
+        if (cublasLtMatmulDescCreate(&q.op, g.bf ? CUBLAS_COMPUTE_32F : g.ct, CUDA_R_32F) != CUBLAS_STATUS_SUCCESS)
+            continue;
         cublasLtMatmulDescSetAttribute(q.op, CUBLASLT_MATMUL_DESC_TRANSA, &sh.ta, sizeof(sh.ta));
         cublasLtMatmulDescSetAttribute(q.op, CUBLASLT_MATMUL_DESC_TRANSB, &sh.tb, sizeof(sh.tb));
         const int ar = sh.ta == CUBLAS_OP_N ? sh.m : sh.k, ac = sh.ta == CUBLAS_OP_N ? sh.k : sh.m;
         const int br = sh.tb == CUBLAS_OP_N ? sh.k : sh.n, bc = sh.tb == CUBLAS_OP_N ? sh.n : sh.k;
-        if (cublasLtMatrixLayoutCreate(&q.a, CUDA_R_32F, ar, ac, sh.lda) != CUBLAS_STATUS_SUCCESS ||
-            cublasLtMatrixLayoutCreate(&q.b, CUDA_R_32F, br, bc, sh.ldb) != CUBLAS_STATUS_SUCCESS ||
-            cublasLtMatrixLayoutCreate(&q.c, CUDA_R_32F, sh.m, sh.n, sh.m) != CUBLAS_STATUS_SUCCESS)
+        if (cublasLtMatrixLayoutCreate(&q.a, ot, ar, ac, sh.lda) != CUBLAS_STATUS_SUCCESS ||
+            cublasLtMatrixLayoutCreate(&q.b, ot, br, bc, sh.ldb) != CUBLAS_STATUS_SUCCESS ||
+            cublasLtMatrixLayoutCreate(&q.c, ct, sh.m, sh.n, sh.m) != CUBLAS_STATUS_SUCCESS)
             continue;
         cublasLtMatmulPreference_t pref = nullptr;
         if (cublasLtMatmulPreferenceCreate(&pref) != CUBLAS_STATUS_SUCCESS) continue;
@@ -220,16 +234,17 @@ static tvd_status tune_lt(tvd_plan_s& p, GemmPrecond& g, cudaStream_t s) {
                 res.push_back(v);
             }
         }
-        const float* A = sh.a_is_mat ? g.Bc : g.s1;
-        const float* B = sh.a_is_mat ? g.s1 : g.Br;
+        const void* A = sh.a_is_mat ? g.Bc : g.mid;
+        const void* B = sh.a_is_mat ? g.in : g.Br;
+        void* C = sh.a_is_mat ? g.mid : (void*)g.s1;
         float best = 1e30f;
         for (size_t c = 0; c < res.size(); ++c) {
             if (res[c].state != CUBLAS_STATUS_SUCCESS || res[c].workspaceSize > wsb) continue;
             bool ok = true;
             for (int rep = 0; rep < 4 && ok; ++rep) {
                 if (rep == 1) ok = cudaEventRecord(e0, s) == cudaSuccess;
-                ok = ok && cublasLtMatmul(g.lt, q.op, &one, A, q.a, B, q.b, &zero, g.s2, q.c, g.s2, q.c,
-                                          &res[c].algo, g.ws, wsb, s) == CUBLAS_STATUS_SUCCESS;
+                ok = ok && cublasLtMatmul(g.lt, q.op, &one, A, q.a, B, q.b, &zero, C, q.c, C, q.c, &res[c].algo,
+                                          g.ws, wsb, s) == CUBLAS_STATUS_SUCCESS;
             }
             ok = ok && cudaEventRecord(e1, s) == cudaSuccess && cudaEventSynchronize(e1) == cudaSuccess;
             float ms = 0.0f;
@@ -263,6 +278,11 @@ static tvd_status tune_lt(tvd_plan_s& p, GemmPrecond& g, cudaStream_t s) {
     return TVD_OK;
 }
 
+int gemm_precond_storage(const tvd_plan_s& p) {
+    const auto* g = static_cast<const GemmPrecond*>(p.gemm);
+    return g ? (g->bf ? 2 : 1) : 0;
+}
+
 tvd_status gemm_precond_create(tvd_plan_s& p, cudaStream_t s) {
     if (p.gemm) return TVD_OK;
     auto* g = new GemmPrecond();
@@ -281,28 +301,42 @@ tvd_status gemm_precond_create(tvd_plan_s& p, cudaStream_t s) {
         }
         return true;
     };
-    if (!alloc((void**)&g->Br, (size_t)p.nr * p.nr * sizeof(float))) return fail(TVD_ENOMEM);
+    // bf16 operands from sides of 1024 on (measured faster there: 1024^2 10.8 -> 12.0, 2048^2 3.6 ->
+    // 4.3 deblurs/s; at 512^2 float operands are 2% faster); TVD_GEMM_STORAGE=bf16 / f32 overrides
+    const char* sv = std::getenv("TVD_GEMM_STORAGE");
+    if (sv && !std::strcmp(sv, "bf16")) g->bf = true;
+    else if (sv && !std::strcmp(sv, "f32")) g->bf = false;
+    else g->bf = std::min(p.nr, p.nc) >= 1024;
+    const size_t esz = g->bf ? sizeof(__nv_bfloat16) : sizeof(float);
+    if (!alloc(&g->Br, (size_t)p.nr * p.nr * esz)) return fail(TVD_ENOMEM);
     if (p.nc == p.nr) g->Bc = g->Br;
-    else if (!alloc((void**)&g->Bc, (size_t)p.nc * p.nc * sizeof(float))) return fail(TVD_ENOMEM);
-    if (!alloc((void**)&g->s1, n * sizeof(float)) || !alloc((void**)&g->s2, n * sizeof(float)))
-        return fail(TVD_ENOMEM);
+    else if (!alloc(&g->Bc, (size_t)p.nc * p.nc * esz)) return fail(TVD_ENOMEM);
+    if (!alloc((void**)&g->s1, n * sizeof(float)) || !alloc(&g->mid, n * esz)) return fail(TVD_ENOMEM);
+    if (g->bf) {
+        if (!alloc(&g->in, n * esz)) return fail(TVD_ENOMEM);
+    } else {
+        g->in = g->s1;   // float storage: the row products read the column products' output buffer
+    }
     if (!alloc(&g->ws, kGemmWorkspace)) return fail(TVD_ENOMEM);
     g->ws_bytes = kGemmWorkspace;
-    std::vector<float> B;
-    transform_matrix(p.nr, p.bc, B);
-    if (cudaMemcpyAsync(g->Br, B.data(), B.size() * sizeof(float), cudaMemcpyHostToDevice, s) != cudaSuccess ||
-        cudaStreamSynchronize(s) != cudaSuccess) {
-        set_error("upload of the transform matrix failed");
-        return fail(TVD_ECUDA);
-    }
-    if (g->Bc != g->Br) {
-        transform_matrix(p.nc, p.bc, B);
-        if (cudaMemcpyAsync(g->Bc, B.data(), B.size() * sizeof(float), cudaMemcpyHostToDevice, s) != cudaSuccess ||
-            cudaStreamSynchronize(s) != cudaSuccess) {
-            set_error("upload of the transform matrix failed");
-            return fail(TVD_ECUDA);
+    auto upload = [&](int side, void* dst) -> bool {
+        std::vector<float> B;
+        transform_matrix(side, p.bc, B);
+        cudaError_t e;
+        if (g->bf) {
+            std::vector<__nv_bfloat16> Bh(B.size());
+            for (size_t i = 0; i < B.size(); ++i) Bh[i] = __float2bfloat16_rn(B[i]);
+            e = cudaMemcpyAsync(dst, Bh.data(), Bh.size() * esz, cudaMemcpyHostToDevice, s);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        } else {
+            e = cudaMemcpyAsync(dst, B.data(), B.size() * esz, cudaMemcpyHostToDevice, s);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(s);
         }
-    }
+        if (e != cudaSuccess) set_error("upload of the transform matrix failed");
+        return e == cudaSuccess;
+    };
+    if (!upload(p.nr, g->Br)) return fail(TVD_ECUDA);
+    if (g->Bc != g->Br && !upload(p.nc, g->Bc)) return fail(TVD_ECUDA);
     if (cublasCreate(&g->h) != CUBLAS_STATUS_SUCCESS) {
         g->h = nullptr;
         set_error("cublasCreate failed");
@@ -323,12 +357,26 @@ tvd_status gemm_precond_create(tvd_plan_s& p, cudaStream_t s) {
 
 // ---------------------------------------------------------------- vector kernels
 
+// Stores of four consecutive values (index i in units of 4) and of one value
+// in the operand type of the products.
+__device__ __forceinline__ void store4(float* p, size_t i, float4 v) { reinterpret_cast<float4*>(p)[i] = v; }
+__device__ __forceinline__ void store4(__nv_bfloat16* p, size_t i, float4 v) {
+    __nv_bfloat162 lo = __floats2bfloat162_rn(v.x, v.y), hi = __floats2bfloat162_rn(v.z, v.w);
+    uint2 u;
+    u.x = *reinterpret_cast<unsigned int*>(&lo);
+    u.y = *reinterpret_cast<unsigned int*>(&hi);
+    reinterpret_cast<uint2*>(p)[i] = u;
+}
+__device__ __forceinline__ void store1(float* p, size_t o, float v) { p[o] = v; }
+__device__ __forceinline__ void store1(__nv_bfloat16* p, size_t o, float v) { p[o] = __float2bfloat16_rn(v); }
+
 // First kernel of the solve on the CG path: the previous iteration's pending
 // x += alpha p, r -= alpha q with ||r||^2 and the stopping test (as the first
 // row pass of the FFT form does), then s = d o r.
+template <typename OutT>
 __global__ void __launch_bounds__(kThreads)
 gemm_pre_kernel(float* __restrict__ r, float* __restrict__ x, const float* __restrict__ q, const float* p0,
-                const float* p1, const float* __restrict__ d, float* __restrict__ s, size_t n, CgState* st,
+                const float* p1, const float* __restrict__ d, OutT* __restrict__ s, size_t n, CgState* st,
                 double* red, unsigned int* ticket) {
     pdl_wait();   // everything below reads what earlier kernels in the stream write
     if (st && st->done) return;
@@ -355,7 +403,7 @@ gemm_pre_kernel(float* __restrict__ r, float* __restrict__ x, const float* __res
             const float4 dv = reinterpret_cast<const float4*>(d)[i];
             rv.x *= dv.x; rv.y *= dv.y; rv.z *= dv.z; rv.w *= dv.w;
         }
-        reinterpret_cast<float4*>(s)[i] = rv;
+        store4(s, i, rv);
     }
     for (size_t o = nv * 4 + blockIdx.x * (size_t)blockDim.x + threadIdx.x; o < n; o += (size_t)gridDim.x * blockDim.x) {
         float v = r[o];
@@ -365,7 +413,7 @@ gemm_pre_kernel(float* __restrict__ r, float* __restrict__ x, const float* __res
             x[o] += al * pv[o];
             part += v * v;
         }
-        s[o] = d ? v * d[o] : v;
+        store1(s, o, d ? v * d[o] : v);
     }
     if (!upd) return;
     double sum;
@@ -373,9 +421,11 @@ gemm_pre_kernel(float* __restrict__ r, float* __restrict__ x, const float* __res
         finish_xr(st, sum);
 }
 
-// y = y o f (the division by the spectrum, f = 1 / spectrum).
+// out = y o f (the division by the spectrum, f = 1 / spectrum), in the operand
+// type of the products (out may be y for float storage).
+template <typename OutT>
 __global__ void __launch_bounds__(kThreads)
-gemm_scale_kernel(float* __restrict__ y, const float* __restrict__ f, size_t n, const CgState* st) {
+gemm_scale_kernel(const float* y, const float* __restrict__ f, OutT* out, size_t n, const CgState* st) {
     pdl_wait();
     if (st && st->done) return;
     const size_t nv = n / 4;
@@ -383,10 +433,10 @@ gemm_scale_kernel(float* __restrict__ y, const float* __restrict__ f, size_t n, 
         float4 a = reinterpret_cast<const float4*>(y)[i];
         const float4 b = reinterpret_cast<const float4*>(f)[i];
         a.x *= b.x; a.y *= b.y; a.z *= b.z; a.w *= b.w;
-        reinterpret_cast<float4*>(y)[i] = a;
+        store4(out, i, a);
     }
     for (size_t o = nv * 4 + blockIdx.x * (size_t)blockDim.x + threadIdx.x; o < n; o += (size_t)gridDim.x * blockDim.x)
-        y[o] *= f[o];
+        store1(out, o, y[o] * f[o]);
 }
 
 // z = d o u, and on the CG path r^T z with the Fletcher-Reeves coefficient.
@@ -429,9 +479,9 @@ static int ew_blocks(size_t n) {
 
 static bool al16(const void* p) { return ((uintptr_t)p & 15u) == 0; }
 
-// Product i (gemm_shape) C = op(A) op(B) in float storage: the tuned cuBLASLt
-// algorithm, else cublasGemmEx with cuBLAS's own choice.
-static tvd_status gemm(const GemmPrecond& g, int i, int nr, int nc, const float* A, const float* B, float* C,
+// Product i (gemm_shape) C = op(A) op(B): the tuned cuBLASLt algorithm, else
+// cublasGemmEx with cuBLAS's own choice.
+static tvd_status gemm(const GemmPrecond& g, int i, int nr, int nc, const void* A, const void* B, void* C,
                        cudaStream_t s) {
     const float one = 1.0f, zero = 0.0f;
     const GemmShape sh = gemm_shape(i, nr, nc);
@@ -442,9 +492,11 @@ static tvd_status gemm(const GemmPrecond& g, int i, int nr, int nc, const float*
                                     g.ws_bytes, s));
         return TVD_OK;
     }
+    const cudaDataType_t ot = g.bf ? CUDA_R_16BF : CUDA_R_32F;
     TVD_BLAS_TRY(cublasSetStream(g.h, s));
-    TVD_BLAS_TRY(cublasGemmEx(g.h, sh.ta, sh.tb, sh.m, sh.n, sh.k, &one, A, CUDA_R_32F, sh.lda, B, CUDA_R_32F,
-                              sh.ldb, &zero, C, CUDA_R_32F, sh.m, g.ct, CUBLAS_GEMM_DEFAULT));
+    TVD_BLAS_TRY(cublasGemmEx(g.h, sh.ta, sh.tb, sh.m, sh.n, sh.k, &one, A, ot, sh.lda, B, ot, sh.ldb, &zero, C,
+                              sh.a_is_mat ? ot : CUDA_R_32F, sh.m, g.bf ? CUBLAS_COMPUTE_32F : g.ct,
+                              CUBLAS_GEMM_DEFAULT));
     return TVD_OK;
 }
 
@@ -460,24 +512,34 @@ tvd_status gemm_precond_solve(const tvd_plan_s& p, const Ops<float>& o, const fl
         return TVD_EINVAL;
     }
     const int blocks = ew_blocks(n);
+    using bf16 = __nv_bfloat16;
     {
         ProfScope prof(PROF_GEMM_EW, s);
-        TVD_CUDA_TRY(launch_pdl(gemm_pre_kernel, dim3(blocks), dim3(kThreads), 0, s, const_cast<float*>(r), x,
-                                o.q, o.p, o.p2, d, g->s1, n, st, p.red, p.ticket + 7));
+        if (g->bf)
+            TVD_CUDA_TRY(launch_pdl(gemm_pre_kernel<bf16>, dim3(blocks), dim3(kThreads), 0, s, const_cast<float*>(r),
+                                    x, o.q, o.p, o.p2, d, (bf16*)g->in, n, st, p.red, p.ticket + 7));
+        else
+            TVD_CUDA_TRY(launch_pdl(gemm_pre_kernel<float>, dim3(blocks), dim3(kThreads), 0, s, const_cast<float*>(r),
+                                    x, o.q, o.p, o.p2, d, (float*)g->in, n, st, p.red, p.ticket + 7));
         TVD_CUDA_TRY(cudaGetLastError());
     }
-    // forward: s2 = B_c s1 (row pass), s1 = s2 B_r^T (column pass)
-    TVD_TRY(gemm(*g, 0, nr, nc, g->Bc, g->s1, g->s2, s));
-    TVD_TRY(gemm(*g, 1, nr, nc, g->s2, g->Br, g->s1, s));
+    // forward: mid = B_c in (row pass), s1 = mid B_r^T (column pass)
+    TVD_TRY(gemm(*g, 0, nr, nc, g->Bc, g->in, g->mid, s));
+    TVD_TRY(gemm(*g, 1, nr, nc, g->mid, g->Br, g->s1, s));
     {
         ProfScope prof(PROF_GEMM_EW, s);
-        TVD_CUDA_TRY(launch_pdl(gemm_scale_kernel, dim3(blocks), dim3(kThreads), 0, s, g->s1,
-                                (const float*)o.inv_spec, n, (const CgState*)st));
+        if (g->bf)
+            TVD_CUDA_TRY(launch_pdl(gemm_scale_kernel<bf16>, dim3(blocks), dim3(kThreads), 0, s, (const float*)g->s1,
+                                    (const float*)o.inv_spec, (bf16*)g->in, n, (const CgState*)st));
+        else
+            TVD_CUDA_TRY(launch_pdl(gemm_scale_kernel<float>, dim3(blocks), dim3(kThreads), 0, s,
+                                    (const float*)g->s1, (const float*)o.inv_spec, (float*)g->in, n,
+                                    (const CgState*)st));
         TVD_CUDA_TRY(cudaGetLastError());
     }
-    // inverse: s2 = B_c^T s1, s1 = s2 B_r
-    TVD_TRY(gemm(*g, 2, nr, nc, g->Bc, g->s1, g->s2, s));
-    TVD_TRY(gemm(*g, 3, nr, nc, g->s2, g->Br, g->s1, s));
+    // inverse: mid = B_c^T in, s1 = mid B_r
+    TVD_TRY(gemm(*g, 2, nr, nc, g->Bc, g->in, g->mid, s));
+    TVD_TRY(gemm(*g, 3, nr, nc, g->mid, g->Br, g->s1, s));
     {
         ProfScope prof(PROF_GEMM_EW, s);
         TVD_CUDA_TRY(launch_pdl(gemm_post_kernel, dim3(blocks), dim3(kThreads), 0, s, (const float*)g->s1, d, r, z,

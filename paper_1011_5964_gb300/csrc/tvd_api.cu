@@ -659,6 +659,8 @@ tvd_status tvd_plan_set_transform(tvd_plan plan, int kind, void* stream) {
 
 int tvd_plan_transform(tvd_plan plan) { return plan && plan->gemm ? TVD_TRANSFORM_GEMM : TVD_TRANSFORM_FFT; }
 
+int tvd_plan_gemm_storage(tvd_plan plan) { return plan ? gemm_precond_storage(*plan) : 0; }
+
 const char* tvd_version(void) { return "tvd-gb300 0.1"; }
 
 tvd_status tvd_plan_create(tvd_plan* out, int n_rows, int n_cols, const double* psf_host, int p_rows, int p_cols,

@@ -265,6 +265,7 @@ tvd_status lamH2_setup(const tvd_plan_s& p, Ops<T>& o, cudaStream_t s);
 // and the solve, with the same contract as precond_solve.
 tvd_status gemm_precond_create(tvd_plan_s& p, cudaStream_t s);
 void gemm_precond_destroy(tvd_plan_s& p);
+int gemm_precond_storage(const tvd_plan_s& p);   // 0: no GEMM form, 1: float operands, 2: bf16 operands
 tvd_status gemm_precond_solve(const tvd_plan_s& p, const Ops<float>& o, const float* r, float* z, CgState* st,
                               cudaStream_t s, float* x);
 

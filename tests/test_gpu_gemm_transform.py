@@ -15,7 +15,10 @@ cores. Checks, against the FP64 oracle on the same seeded inputs:
   decides convergence);
 * one FP step of the 1024 x 1024 workload reaching its tolerance, measured
   with the oracle's operator;
-* argument validation of tvd_plan_set_transform.
+* argument validation of tvd_plan_set_transform; the operand storage.
+
+Operand storage: float (TF32 products) below sides of 1024, bf16 from 1024
+on; the tests set TVD_GEMM_STORAGE to cover both at every size.
 """
 import os
 
@@ -44,27 +47,36 @@ def observe(n_rows, n_cols, h, bc, noise, seed):
 SHAPES = [(37, 53), (64, 64), (3, 3), (4, 7), (128, 130), (96, 33)]
 
 
-def _solve(torch, dev, nr, nc, bc, kind, transform, compute=None):
+class _env:
+    """Set environment variables for the plan set-up inside the block (read by the library then)."""
+
+    def __init__(self, **kv):
+        self.kv = {k: v for k, v in kv.items() if v is not None}
+
+    def __enter__(self):
+        self.old = {k: os.environ.get(k) for k in self.kv}
+        os.environ.update(self.kv)
+
+    def __exit__(self, *exc):
+        for k, v in self.old.items():
+            if v is None:
+                os.environ.pop(k, None)
+            else:
+                os.environ[k] = v
+
+
+def _solve(torch, dev, nr, nc, bc, kind, transform, compute=None, storage=None):
     import paper_1011_5964_gb300 as pkg
     h = synth.gaussian_psf(1.0, half_width=min(3, nr - 2, nc - 2))
     rng = np.random.default_rng(nr + 17 * nc)
     u = synth.piecewise_constant_image(nr, nc, seed=nr).astype(np.float32).astype(np.float64)
     r = rng.standard_normal((nr, nc)).astype(np.float32).astype(np.float64)
     alpha, beta = 1e-2, 0.05
-    old = os.environ.get("TVD_GEMM_COMPUTE")
-    if compute:
-        os.environ["TVD_GEMM_COMPUTE"] = compute
-    try:
+    with _env(TVD_GEMM_COMPUTE=compute, TVD_GEMM_STORAGE=storage):
         with pkg.Plan(nr, nc, h, bc=bc, pc=kind, mode="mixed", transform=transform) as plan:
             assert plan.transform == transform
             plan.precond_setup(torch.tensor(u, dtype=torch.float32, device=dev), alpha, beta)
             z = plan.precond_solve(torch.tensor(r, dtype=torch.float32, device=dev)).double().cpu().numpy()
-    finally:
-        if compute:
-            if old is None:
-                os.environ.pop("TVD_GEMM_COMPUTE", None)
-            else:
-                os.environ["TVD_GEMM_COMPUTE"] = old
     P = O.precond_setup(u, h, bc, alpha, beta, kind)
     return z, O.precond_apply(r, P)
 
@@ -89,6 +101,18 @@ def test_gemm_preconditioner_solve_fp32(tdev, nr, nc, bc, kind):
     assert err < 1e-4, err
 
 
+@pytest.mark.parametrize("kind", ["dfast", "fastd"])
+@pytest.mark.parametrize("bc", ["ar", "r"])
+@pytest.mark.parametrize("nr,nc", [(37, 53), (64, 64), (128, 130), (3, 3)])
+def test_gemm_preconditioner_solve_bf16_storage(tdev, nr, nc, bc, kind):
+    """bf16 operands (unit roundoff 2^-9 for each of the matrices and the four product inputs,
+    float accumulation): about 8 roundings of 2e-3, so 3e-2."""
+    torch, dev = tdev
+    z, ref = _solve(torch, dev, nr, nc, bc, kind, "gemm", storage="bf16")
+    err = float(np.linalg.norm(z - ref) / np.linalg.norm(ref))
+    assert err < 3e-2, err
+
+
 @pytest.mark.parametrize("bc", ["ar", "r"])
 def test_gemm_form_matches_fft_form(tdev, bc):
     torch, dev = tdev
@@ -98,15 +122,16 @@ def test_gemm_form_matches_fft_form(tdev, bc):
     assert err < 1e-2, err
 
 
+@pytest.mark.parametrize("storage", ["f32", "bf16"])
 @pytest.mark.parametrize("bc,kind", [("ar", "dfast"), ("r", "dfast"), ("ar", "fastd"), ("ar", "fast")])
-def test_mixed_deblur_gemm_within_1e5_of_oracle(tdev, bc, kind):
+def test_mixed_deblur_gemm_within_1e5_of_oracle(tdev, bc, kind, storage):
     torch, dev = tdev
     import paper_1011_5964_gb300 as pkg
     n = 96
     h = synth.gaussian_psf(2.0, half_width=7)
     v = observe(n, n, h, bc, 0.01, 77)
     u_ref, _ = O.tv_deblur(v, h, bc, 1e-3, 1e-2, outer=4, tol=1e-10, maxit=5000, kind=kind)
-    with pkg.Plan(n, n, h, bc=bc, pc=kind, mode="mixed", transform="gemm") as plan:
+    with _env(TVD_GEMM_STORAGE=storage), pkg.Plan(n, n, h, bc=bc, pc=kind, mode="mixed", transform="gemm") as plan:
         u, st = plan.deblur(torch.tensor(v, dtype=torch.float64, device=dev), 1e-3, 1e-2, max_outer=4,
                             inner_tol=1e-10, inner_maxit=5000)
         u = u.cpu().numpy()
@@ -115,7 +140,8 @@ def test_mixed_deblur_gemm_within_1e5_of_oracle(tdev, bc, kind):
     assert err < 1e-5, err
 
 
-def test_gemm_full_size_step_residual(tdev):
+@pytest.mark.parametrize("storage", ["f32", "bf16"])
+def test_gemm_full_size_step_residual(tdev, storage):
     """1024 x 1024, AR, radius-7 disk on 31 x 31, 1% noise, alpha 1e-3, GEMM transforms: one FP step
     from u^0 = v reaches the tolerance, measured with the oracle's operator at full size."""
     torch, dev = tdev
@@ -125,7 +151,8 @@ def test_gemm_full_size_step_residual(tdev):
     v = observe(n, n, h, "ar", 0.01, 1234)
     b = O.blur_adjoint(v, h, "ar")
     tol = 1e-6
-    with pkg.Plan(n, n, h, bc="ar", pc="dfast", mode="mixed", transform="gemm") as plan:
+    with _env(TVD_GEMM_STORAGE=storage), pkg.Plan(n, n, h, bc="ar", pc="dfast", mode="mixed",
+                                                  transform="gemm") as plan:
         vt = torch.tensor(v, dtype=torch.float64, device=dev)
         x = vt.clone()
         k, rr, st = plan.pcg_solve(vt, 1e-3, 1e-2, torch.tensor(b, dtype=torch.float64, device=dev), x,
@@ -154,6 +181,9 @@ def test_set_transform_validation(tdev):
         for kind in ("gemm", "fft", "gemm"):
             plan.set_transform(kind)
             assert plan.transform == kind
+        assert plan.gemm_storage == "f32"   # float operands below sides of 1024
+    with _env(TVD_GEMM_STORAGE="bf16"), pkg.Plan(16, 16, h, bc="r", pc="fast", mode="mixed", transform="gemm") as plan:
+        assert plan.gemm_storage == "bf16"
 
 
 def test_batched_gemm_plans_equal_individual_calls(tdev):
