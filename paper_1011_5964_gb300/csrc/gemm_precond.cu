@@ -470,9 +470,19 @@ gemm_post_kernel(const float* __restrict__ u, const float* __restrict__ d, const
         finish_rho(st, sum);
 }
 
+// Grid of the vector kernels: at most TVD_EW_BLOCKS_PER_SM (default 2) blocks
+// per SM, each thread walking several float4 by the grid-stride loops. With
+// one float4 per thread the block reductions dominated (ncu: barrier and
+// scoreboard stalls); measured at 1024^2: 16 blocks per SM 11.8, 8 12.0,
+// 4 12.8, 2 13.0 deblurs/s.
 static int ew_blocks(size_t n) {
+    static const int per_sm = []() {
+        const char* v = std::getenv("TVD_EW_BLOCKS_PER_SM");
+        const int k = v ? std::atoi(v) : 2;
+        return k > 0 ? k : 2;
+    }();
     size_t b = (n / 4 + kThreads - 1) / kThreads;
-    const size_t cap = (size_t)num_sms() * 16;
+    const size_t cap = (size_t)num_sms() * per_sm;
     if (b > cap) b = cap;
     return (int)(b ? b : 1);
 }
