@@ -75,6 +75,10 @@ NCU_TRAFFIC = {
     "precond_row_inverse.f32": 12712192,
     "blur_adjoint_L.f32": 12653568,
     "blur_forward.f32": 8432128,
+    # GEMM form (profiles/dram_traffic_gemm_solve_1024_mixed.md): the mean over the three vector
+    # kernels of the solve (pre 20993536, scale 8397568, post 12610560) and over the four bf16 products
+    "precond_gemm_vector.f32": 14000555,
+    "precond_gemm_cublas.f32": 4211456,
 }
 
 
@@ -315,7 +319,8 @@ def roofline_of(name, kms, klaunch, total_ms, storage=None):
         peak, src = bf16_peak() if storage == "bf16" else tf32_peak()
         achieved = flops / avg_s / 1e12
         return {"bound": "tensor", "kernel": f"{name} (cuBLASLt {storage} transform GEMM)", "achieved": achieved,
-                "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None, "peak_source": src,
+                "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                "traffic": NCU_TRAFFIC.get(name) if storage == "bf16" else None, "peak_source": src,
                 "flops_per_launch": flops, "avg_launch_us": avg_s * 1e6, "launches": klaunch, "share": share}
     word = 4 if prec == "f32" else 8
     bytes_per_launch = WORDS_PER_PIXEL.get(base, 2) * word * N_SIDE * N_SIDE

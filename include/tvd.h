@@ -183,7 +183,7 @@ typedef enum {
 /*
  * tvd_plan_set_transform -- choose the transform form of a plan (kind: a
  * tvd_transform value). A new MIXED plan with a fast preconditioner starts
- * with the GEMM form when both image sides are at least 256 (the environment
+ * with the GEMM form when both image sides are at least 128 (the environment
  * variable TVD_GEMM_MIN_SIDE changes the bound), else with the FFT form; the
  * environment variable TVD_TRANSFORM ("gemm" / "fft") overrides both. On the
  * switch to GEMM the candidate cuBLASLt algorithms of the four products are

@@ -120,7 +120,8 @@ def test_preconditioner_solve(torch_dev, nr, nc, bc, kind, mode):
     if mode == "mixed":
         u = u.astype(np.float32).astype(np.float64)
         r = r.astype(np.float32).astype(np.float64)
-    with pkg.Plan(nr, nc, h, bc=bc, pc=kind, mode=mode) as plan:
+    # the FFT form of the transforms (the GEMM form has its own tests in test_gpu_gemm_transform.py)
+    with pkg.Plan(nr, nc, h, bc=bc, pc=kind, mode=mode, transform="fft") as plan:
         plan.precond_setup(torch.tensor(u, dtype=dt, device=dev), alpha, beta)
         z = plan.precond_solve(torch.tensor(r, dtype=dt, device=dev)).double().cpu().numpy()
     P = O.precond_setup(u, h, bc, alpha, beta, kind)
