@@ -152,7 +152,9 @@ tvd_status tau_precond_setup(tvd_plan plan, const void* u_lag, double alpha, dou
  * tau_precond_solve -- z = X^{-1} r with the preconditioner last set up
  * (X = D^1/2 U^{-1} diag(Lambda_H^2 + alpha Lambda_L) U D^1/2 for D_R / D_M,
  * U the 2D DCT-II or hat-S transform). r and z: device arrays of the plan's
- * operator type; r == z is allowed.
+ * operator type; r == z is allowed. On a MIXED plan in the GEMM transform form
+ * (tvd_plan_set_transform) the result carries the products' rounding: about
+ * 1e-3 relative with float operands (TF32 products), 1e-2 with bf16 operands.
  */
 tvd_status tau_precond_solve(tvd_plan plan, const void* r, void* z, void* stream);
 
