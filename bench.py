@@ -47,7 +47,7 @@ WORKLOAD = "tv_deblur 1024x1024 AR disk-r7(31x31) 1% noise alpha=1e-3 beta=1e-2 
 # Algorithmic bytes per launch of each kernel class, in words of the kernel's
 # type per pixel: the arrays each kernel must read and write once.
 WORDS_PER_PIXEL = {
-    "blur_forward": 2,          # read p, write t = H p
+    "blur_forward": 4,          # read z, p; write p = z + beta p, t = H p (the fused direction update)
     "blur_adjoint_L": 4,        # read t, p, w; write q = H^T t + alpha L p
     "precond_row_forward": 8,   # read r, q, p, x, D^-1/2; write r, x, t (the fused CG x / r update)
     "precond_column_solve": 3,  # read t, 1/spectrum; write t
@@ -60,26 +60,27 @@ WORDS_PER_PIXEL = {
     "cg_simple_precond": 3,
     "tv_coefficients": 2,
     "vector_misc": 2,
-    "precond_gemm_vector": 5,   # mean of the GEMM form's three vector kernels: pre (read r, q, p, x, D^-1/2;
-                                # write r, x, s) 8, spectrum scale (read y, 1/spectrum; write y) 3,
-                                # post (read u, D^-1/2, r; write z) 4
+    "precond_gemm_vector": 8,   # the GEMM form's vector pass: read r, q, p, x, D^-1/2; write r, x, S
 }
 
-# DRAM bytes per launch (read + write) of the kernels captured with
-# ncu --set full on this workload, as summarised in
-# profiles/transform_and_blur_kernels_1024_mixed.md. Valid only for the kernel
-# versions captured there: remove an entry when its kernel changes.
-NCU_TRAFFIC = {
-    "precond_row_forward.f32": 21096192,
-    "precond_column_solve.f32": 8563200,
-    "precond_row_inverse.f32": 12712192,
-    "blur_adjoint_L.f32": 12653568,
-    "blur_forward.f32": 8432128,
-    # GEMM form (profiles/dram_traffic_gemm_solve_1024_mixed.md): the mean over the three vector
-    # kernels of the solve (pre 20993536, scale 8397568, post 12610560) and over the four bf16 products
-    "precond_gemm_vector.f32": 14000555,
-    "precond_gemm_cublas.f32": 4211456,
-}
+# DRAM bytes per launch (read + write) of kernels captured with ncu on this
+# workload, each with the SHA-256 (first 16 hex digits) of the source file of
+# its kernel at capture time: an entry is used only while that file is
+# unchanged, so a stale figure is reported as null.
+NCU_TRAFFIC = {}
+
+
+def traffic_of(name):
+    entry = NCU_TRAFFIC.get(name)
+    if not entry:
+        return None
+    import hashlib
+    path = os.path.join(ROOT, "paper_1011_5964_gb300", "csrc", entry["source"])
+    try:
+        digest = hashlib.sha256(open(path, "rb").read()).hexdigest()[:16]
+    except OSError:
+        return None
+    return entry["bytes"] if digest == entry["sha16"] else None
 
 
 def dist_env():
@@ -313,21 +314,22 @@ def roofline_of(name, kms, klaunch, total_ms, storage=None):
     base, prec = name.rsplit(".", 1)
     avg_s = kms / 1000.0 / max(klaunch, 1)
     share = kms / max(total_ms, 1e-12)
-    if base == "precond_gemm_cublas":
-        # one n x n x n product of the transform form: 2 n^3 flops (bf16 or TF32 operands, float accumulation)
+    if base == "precond_gemm_tc":
+        # one n x n x n product of the transform form (the library's tcgen05 kernel): 2 n^3 flops
+        # (bf16 or tf32 operands, float accumulation)
         flops = 2.0 * N_SIDE ** 3
         peak, src = bf16_peak() if storage == "bf16" else tf32_peak()
         achieved = flops / avg_s / 1e12
-        return {"bound": "tensor", "kernel": f"{name} (cuBLASLt {storage} transform GEMM)", "achieved": achieved,
+        return {"bound": "tensor", "kernel": f"{name} ({storage} transform product, tcgen05)", "achieved": achieved,
                 "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                "traffic": NCU_TRAFFIC.get(name) if storage == "bf16" else None, "peak_source": src,
+                "traffic": traffic_of(name), "peak_source": src,
                 "flops_per_launch": flops, "avg_launch_us": avg_s * 1e6, "launches": klaunch, "share": share}
     word = 4 if prec == "f32" else 8
     bytes_per_launch = WORDS_PER_PIXEL.get(base, 2) * word * N_SIDE * N_SIDE
     achieved = bytes_per_launch / avg_s / 1e9
     peak, peak_src = peaks()
     return {"bound": "hbm", "kernel": name, "achieved": achieved, "peak": peak, "unit": "GB/s",
-            "frac": achieved / peak, "traffic": NCU_TRAFFIC.get(name), "peak_source": peak_src,
+            "frac": achieved / peak, "traffic": traffic_of(name), "peak_source": peak_src,
             "bytes_per_launch": bytes_per_launch, "avg_launch_us": avg_s * 1e6, "launches": klaunch, "share": share}
 
 

@@ -80,7 +80,9 @@ typedef enum {
     TVD_ECUDA = 5,        /* a CUDA runtime call failed */
     TVD_ENOCONV = 6,      /* CG hit maxit before ||r_k|| / ||r_0|| < tol */
     TVD_EBREAKDOWN = 7,   /* p^T A p <= 0, r^T z <= 0 with r != 0, or a non-finite scalar */
-    TVD_ETIMEOUT = 8      /* reserved: a bounded device-side wait gave up */
+    TVD_ETIMEOUT = 8      /* a bounded device-side wait gave up (a tensor-core transform product waited
+                             about a second for operands that never arrived); the solve stops, the
+                             plan stays usable */
 } tvd_status;
 
 /* Per-call statistics of tv_deblur. inner_iters is caller-owned host memory
@@ -154,7 +156,9 @@ tvd_status tau_precond_setup(tvd_plan plan, const void* u_lag, double alpha, dou
  * U the 2D DCT-II or hat-S transform). r and z: device arrays of the plan's
  * operator type; r == z is allowed. On a MIXED plan in the GEMM transform form
  * (tvd_plan_set_transform) the result carries the products' rounding: about
- * 1e-3 relative with float operands (TF32 products), 1e-2 with bf16 operands.
+ * 3e-3 of max |z| element by element with float operands (tf32 products),
+ * 6e-3 with bf16 operands. A GEMM-form product whose bounded wait expired is
+ * reported as TVD_ETIMEOUT by the next pcg_solve / tv_deblur on the plan.
  */
 tvd_status tau_precond_solve(tvd_plan plan, const void* r, void* z, void* stream);
 
@@ -166,12 +170,12 @@ tvd_status tau_precond_solve(tvd_plan plan, const void* r, void* z, void* stream
  *   TVD_TRANSFORM_FFT:  as the paper's fast transforms, O(n^2 log n), by FFT
  *                       line kernels in shared memory (float), or
  *   TVD_TRANSFORM_GEMM: as four dense products with the n x n matrices B_r,
- *                       B_c on the tensor cores (cuBLASLt, float accumulation;
- *                       operands in float with TF32 products when a side is
- *                       below 1024, in bf16 from 1024 on; TVD_GEMM_STORAGE=
- *                       f32 / bf16 overrides, and TVD_GEMM_COMPUTE=bf16x9 /
- *                       fp32 selects another compute type for float operands),
- *                       O(n^3) flops but tensor-core rate.
+ *                       B_c on the tensor cores by the library's own kernel
+ *                       (TMA operand tiles, tcgen05.mma with the accumulator
+ *                       in tensor memory, float accumulation; operands in
+ *                       float with tf32 products when a side is below 1024,
+ *                       in bf16 from 1024 on; TVD_GEMM_STORAGE=f32 / bf16
+ *                       overrides), O(n^3) flops but tensor-core rate.
  * Both give the same preconditioner up to rounding; the preconditioner only
  * shapes the CG iteration, so the form changes iteration counts slightly,
  * never the converged solution (the MIXED double residual decides).
@@ -187,15 +191,15 @@ typedef enum {
  * tvd_transform value). A new MIXED plan with a fast preconditioner starts
  * with the GEMM form when both image sides are at least 128 (the environment
  * variable TVD_GEMM_MIN_SIDE changes the bound), else with the FFT form; the
- * environment variable TVD_TRANSFORM ("gemm" / "fft") overrides both. On the
- * switch to GEMM the candidate cuBLASLt algorithms of the four products are
- * timed on the plan's stream and the fastest kept (TVD_GEMM_TUNE=0: cuBLAS's
- * default choice). Switching to GEMM allocates
- * the transform matrices (n_r^2 + n_c^2 floats), two image-sized float
- * buffers, a 32 MiB cuBLAS workspace and a cuBLAS handle, owned by the plan;
- * switching back frees them. Synchronises `stream` (and, when freeing, the
- * device). Errors: TVD_EINVAL for a NULL plan, an unknown kind, or GEMM on an
- * FP64 plan or with the I / D preconditioners; TVD_ENOMEM, TVD_ECUDA.
+ * environment variable TVD_TRANSFORM ("gemm" / "fft") overrides both.
+ * Switching to GEMM allocates the transform matrices (B_r, B_c and, for
+ * reflective BCs, their transposes; rows padded to a multiple of 8 elements)
+ * and two image-sized operand buffers in the operand type, owned by the plan,
+ * and encodes their TMA tensor maps (cuTensorMapEncodeTiled, taken from the
+ * driver); switching back frees them. Synchronises `stream` (and, when
+ * freeing, the device). Errors: TVD_EINVAL for a NULL plan, an unknown kind,
+ * or GEMM on an FP64 plan or with the I / D preconditioners; TVD_ENOMEM,
+ * TVD_ECUDA (also when the driver offers no tensor-map encoder).
  */
 tvd_status tvd_plan_set_transform(tvd_plan plan, int kind, void* stream);
 
@@ -203,7 +207,7 @@ tvd_status tvd_plan_set_transform(tvd_plan plan, int kind, void* stream);
 int tvd_plan_transform(tvd_plan plan);
 
 /* tvd_plan_gemm_storage -- operand storage of the plan's GEMM form: 0 none
- * (FFT form or NULL plan), 1 float operands (TF32 products), 2 bf16 operands. */
+ * (FFT form or NULL plan), 1 float operands (tf32 products), 2 bf16 operands. */
 int tvd_plan_gemm_storage(tvd_plan plan);
 
 /*
@@ -318,10 +322,10 @@ const char* tvd_version(void);
  * callers that cannot allocate device memory. No counterpart in the paper: it
  * is the PCG's normal-equations product (the same kernels as pcg_solve) made
  * callable without a plan, because some callers must not call cudaMalloc:
- * code running while a CUDA graph is being captured (an allocation would
- * break the capture), code inside a framework that owns a fixed device-memory
- * pool (a caching allocator, a real-time or embedded budget), and callbacks
- * from such a framework that must not allocate behind its back.
+ * code inside a framework that owns a fixed device-memory pool (a caching
+ * allocator, a real-time or embedded memory budget) and callbacks from such
+ * a framework, where a cudaMalloc behind the framework's back would break
+ * its accounting or synchronise the device at a point it does not expect.
  *   n_rows, n_cols   image size, n_rows * n_cols <= 524288 (e.g. 512 x 1024);
  *                    larger sizes return TVD_EINVAL with a message.
  *   psf_host, p_rows, p_cols, bc   as for tvd_plan_create (HOST PSF, copied).
@@ -332,9 +336,10 @@ const char* tvd_version(void);
  * that loads the library holds until the process exits. All calls share
  * them and each call overwrites them, so calls that overlap on the GPU (two
  * streams, or two host threads) race: serialise them. The first call on a
- * device looks up the arrays' device addresses (cudaGetSymbolAddress); make
- * that first call before any stream capture. The call copies the PSF tables
- * from host memory and synchronises `stream` before returning.
+ * device looks up the arrays' device addresses (cudaGetSymbolAddress); that
+ * first call should come before any stream capture. The call copies the PSF
+ * tables from pageable host memory and synchronises `stream` before
+ * returning, so it blocks the calling thread until the product is done.
  */
 tvd_status tvd_normal_apply_noalloc(int n_rows, int n_cols, const double* psf_host, int p_rows, int p_cols,
                                     tvd_bc bc, const double* u_lag, double alpha, double beta,

@@ -282,11 +282,12 @@ class Plan:
 def normal_apply_noalloc(psf, u_lag, alpha: float, beta: float, x, y=None, bc: str = "ar"):
     """y = H^T H x + alpha L(u_lag) x (float64 CUDA tensors) without any device allocation by the library.
 
-    For callers that must not allocate device memory (inside a CUDA graph
-    capture, or under a framework that owns a fixed memory pool). The library
-    keeps the intermediate results in fixed device arrays shared by all calls:
-    calls that overlap on the GPU race, and n_rows * n_cols is limited to
-    524288. The first call on a device must come before any stream capture.
+    For callers that must not allocate device memory (code under a framework
+    that owns a fixed device-memory pool or budget, and its callbacks). The
+    library keeps the intermediate results in fixed device arrays shared by all
+    calls: calls that overlap on the GPU race, and n_rows * n_cols is limited
+    to 524288. The first call on a device looks up those arrays and should come
+    before any stream capture; every call synchronises its stream.
     """
     import torch
     lib = load_library()

@@ -1,8 +1,9 @@
 """Build libtvd.so in-tree with nvcc for sm_103a (GB300).
 
 Each CUDA translation unit under csrc/ is compiled in parallel, then linked
-into paper_1011_5964_gb300/libtvd.so against the shared CUDA runtime and
-cuBLAS (the GEMM form of the preconditioner transforms).
+into paper_1011_5964_gb300/libtvd.so against the shared CUDA runtime only
+(every kernel is the library's own; the tensor-map encoder is taken from the
+driver at run time).
 """
 from __future__ import annotations
 
@@ -50,7 +51,7 @@ def build(verbose: bool = False, extra_flags: list[str] | None = None) -> str:
     with cf.ThreadPoolExecutor(max_workers=max(1, min(len(srcs), os.cpu_count() or 4))) as ex:
         objs = list(ex.map(compile_one, srcs))
     tmp = LIB + ".tmp"
-    cmd = [nvcc, *ARCH, "-shared", "-cudart", "shared", "-o", tmp, *objs, "-lcublas"]
+    cmd = [nvcc, *ARCH, "-shared", "-cudart", "shared", "-o", tmp, *objs]
     res = subprocess.run(cmd, capture_output=True, text=True)
     if res.returncode != 0:
         raise RuntimeError(f"link failed:\n{res.stderr}")

@@ -267,6 +267,236 @@ __device__ __forceinline__ void tile_body(int bx, int by, int gx, const T* __res
     }
 }
 
+// Stencil paths: the general tile stencil (dense taps or row runs), the flat
+// PSF on a centred convex support, and the flat disk of radius DR.
+enum { PATH_TILE = 0, PATH_FLAT = 1, PATH_DISK = 2 };
+
+// ---------------------------------------------------------------- flat stencil
+//
+// For a flat PSF, h_{a,b} = v on a support that is symmetric in both axes and
+// whose rows and columns are runs centred on 0 (the out-of-focus disk of
+// Sec. 5: |b| <= w_|a| exactly when |a| <= g_|b|),
+//   y_ij = v sum_{|b| <= m_c} C_{g_|b|}(i, j - b),   C_g(i, c) = sum_{|a| <= g} x~_{i-a, c}.
+// Vertical pass: a thread walks one staged column c of the block over 16
+// output rows with a register window of the 16 + 2 FMAXM extended values it
+// needs and writes the centred vertical sums C_0 .. C_FMAXM of every row to
+// shared memory (two adds per level). Horizontal pass: a thread owns one
+// output column and FR rows and adds C_{g_|b|}(i, j - b) over the support's
+// columns. About 2 (FMAXM + 1) shared-memory accesses per extended pixel and
+// 2 (2 m_c + 1) per output, against one load and one multiply-add per tap
+// for the direct stencil.
+constexpr int FMAXM = 8;                         // largest PSF half-width of the flat path
+constexpr int FBW = 64;                          // output columns per block
+constexpr int FSEG = 16;                         // output rows per vertical-pass thread
+constexpr int FBH = 32;                          // output rows per block
+constexpr int FR = FBH * FBW / kThreads;         // output rows per horizontal-pass thread: 8
+constexpr int FCS = FBW + 2 * FMAXM;             // shared row stride of the C arrays
+
+template <typename T>
+__host__ __device__ constexpr size_t flat_smem_bytes() {
+    return (size_t)(FMAXM + 1) * FBH * FCS * sizeof(T) + (2 * FMAXM + 1) * sizeof(int);
+}
+
+template <typename T, int EXT, bool FUSE, bool PUP>
+__device__ __forceinline__ void flat_body(int bx, int by, int gx, const T* __restrict__ x, T* __restrict__ y, int nr,
+                                          int nc, int mr, int mc, const int* __restrict__ colh, T v,
+                                          const T* __restrict__ w, T* p0, T* p1, const FuseArgs& fa) {
+    const int pb = fa.st ? fa.st->pbuf : 0;
+    const T* pv = fa.st ? (pb ? p0 : p1) : p0;
+    const T* pold = pb ? p1 : p0;
+    T* pnew = pb ? p0 : p1;
+    const Src<T, PUP> src{x, pold, PUP ? T(fa.st->beta) : T(0), PUP ? fa.st->fresh != 0 : true};
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T* C = reinterpret_cast<T*>(smem_raw);           // [g][row][FCS]: C_g of the block's rows
+    int* sh = reinterpret_cast<int*>(C + (FMAXM + 1) * FBH * FCS);   // column heights g_|b|, b = -mc..mc
+    const int i0 = by * FBH, j0 = bx * FBW;
+    const int TW = FBW + 2 * mc;                     // staged columns j0 - mc .. j0 + FBW + mc - 1
+    for (int k = threadIdx.x; k < 2 * mc + 1; k += blockDim.x) sh[k] = colh[k];
+    // vertical pass: task = (staged column, 16-row segment)
+    const int ntask = TW * (FBH / FSEG);
+    if (threadIdx.x < ntask) {
+        const int cl = threadIdx.x % TW, seg = threadIdx.x / TW;
+        const int J = j0 - mc + cl;
+        const int ib = i0 + seg * FSEG;              // first output row of the segment
+        const bool inside = (EXT == EXT_ODD)
+                                ? (ib - FMAXM >= 1 && ib + FSEG + FMAXM <= nr - 1 && J >= 1 && J <= nc - 2)
+                                : (ib - FMAXM >= 0 && ib + FSEG + FMAXM <= nr && J >= 0 && J < nc);
+        T win[FSEG + 2 * FMAXM];
+        if (inside) {
+            const size_t o = (size_t)(ib - FMAXM) * nc + J;
+#pragma unroll
+            for (int t = 0; t < FSEG + 2 * FMAXM; ++t) win[t] = src[o + (size_t)t * nc];
+        } else {
+#pragma unroll
+            for (int t = 0; t < FSEG + 2 * FMAXM; ++t) win[t] = ext_value<T, EXT>(src, ib - FMAXM + t, J, nr, nc, mr, mc);
+        }
+        if (PUP && cl >= mc && cl < mc + FBW && J < nc) {
+            // this block's outputs of the new direction z + beta p_old (plain values: inside the image)
+#pragma unroll
+            for (int t = 0; t < FSEG; ++t)
+                if (ib + t < nr) pnew[(size_t)(ib + t) * nc + J] = win[t + FMAXM];
+        }
+        T* cw = C + (size_t)(seg * FSEG) * FCS + cl;
+#pragma unroll
+        for (int t = 0; t < FSEG; ++t) {
+            T acc = win[t + FMAXM];
+            cw[t * FCS] = acc;
+#pragma unroll
+            for (int g = 1; g <= FMAXM; ++g) {
+                acc += win[t + FMAXM - g] + win[t + FMAXM + g];
+                cw[(size_t)g * FBH * FCS + t * FCS] = acc;
+            }
+        }
+    }
+    __syncthreads();
+    // horizontal pass: column tx, rows ty * FR .. + FR - 1
+    const int tx = threadIdx.x % FBW, ty = threadIdx.x / FBW;
+    T acc[FR];
+#pragma unroll
+    for (int k = 0; k < FR; ++k) acc[k] = T(0);
+    for (int b = -mc; b <= mc; ++b) {
+        const int g = sh[b + mc];
+        if (g < 0) continue;
+        const T* cr = C + (size_t)g * FBH * FCS + (size_t)(ty * FR) * FCS + (tx + mc - b);
+#pragma unroll
+        for (int k = 0; k < FR; ++k) acc[k] += cr[k * FCS];
+    }
+    T part = T(0);   // per-thread partial of p^T q in the kernel's type
+    const int j = j0 + tx;
+#pragma unroll
+    for (int k = 0; k < FR; ++k) {
+        const int i = i0 + ty * FR + k;
+        if (i >= nr || j >= nc) continue;
+        if (EXT == EXT_ODD && (i == 0 || i == nr - 1 || j == 0 || j == nc - 1)) continue;
+        T out = v * acc[k];
+        if (FUSE) {
+            // alpha L(w) p (5-point stencil, zero Neumann), read through the L1 cache
+            out += T(fa.alpha) * lap_at(w, pv, i, j, nr, nc);
+            part += __ldg(pv + (size_t)i * nc + j) * out;
+        }
+        y[(size_t)i * nc + j] = out;
+    }
+    if (FUSE && fa.reduce) {
+        const int slot = fa.slot0 + by * gx + bx;
+        double sres;
+        if (block_reduce_last((double)part, fa.red, fa.ticket, slot, fa.total_blocks, &sres) && threadIdx.x == 0 &&
+            fa.finish_here)
+            finish_pq(fa.st, sres);
+    }
+}
+
+// ---------------------------------------------------------------- disk stencil
+//
+// The flat disk of radius R (h_{a,b} = v where a^2 + b^2 <= R^2, the
+// out-of-focus PSF of Sec. 5) has column heights g_b = floor(sqrt(R^2 - b^2))
+// known at compile time, so
+//   y_ij = v sum_{|b| <= R} C_{g_b}(i, j - b),   C_g(i, c) = sum_{|a| <= g} x~_{i-a, c},
+// runs with no shared memory and no block barrier: each warp owns a strip of
+// 32 consecutive columns (18 outputs and R halo columns on each side) and 16
+// rows; a lane keeps its column's 16 + 2R extended values in registers, forms
+// the vertical sums C_g of each row by nested pair additions, and takes the 15
+// horizontal terms from its neighbours with warp shuffles.
+constexpr int DR = 7;                            // disk radius of the specialised path
+constexpr int DOUT = 32 - 2 * DR;                // output columns per warp strip
+constexpr int DROWS = 16;                        // output rows per warp strip
+constexpr int DWX = 4, DWY = kThreads / 32 / DWX;   // warps per block across / down
+constexpr int DBW = DWX * DOUT, DBH = DWY * DROWS;  // block tile: 72 x 32 outputs
+
+__host__ __device__ constexpr int disk_height(int b) {
+    int g = 0;
+    while ((g + 1) * (g + 1) + b * b <= DR * DR) ++g;
+    return g;
+}
+
+// x~ at (I, J) for a warp whose lanes straddle the image border: the extension
+// of Sec. 2 (AR: reflection through the boundary value; R: mirror; ODD: the
+// odd extension used by the AR transpose), from at most four image values.
+template <typename T, int EXT, typename S>
+__device__ __forceinline__ T ext_at(const S& x, int I, int J, int nr, int nc) {
+    return ext_value<T, EXT>(x, I, J, nr, nc, DR, DR);
+}
+
+template <typename T, int EXT, bool FUSE, bool PUP>
+__device__ __forceinline__ void disk_body(int bx, int by, int gx, const T* __restrict__ x, T* __restrict__ y, int nr,
+                                          int nc, T v, const T* __restrict__ w, T* p0, T* p1, const FuseArgs& fa) {
+    const int pb = fa.st ? fa.st->pbuf : 0;
+    const T* pv = fa.st ? (pb ? p0 : p1) : p0;
+    const T* pold = pb ? p1 : p0;
+    T* pnew = pb ? p0 : p1;
+    const Src<T, PUP> src{x, pold, PUP ? T(fa.st->beta) : T(0), PUP ? fa.st->fresh != 0 : true};
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int jo = bx * DBW + (wid % DWX) * DOUT;   // first output column of the strip
+    const int i0 = by * DBH + (wid / DWX) * DROWS;   // first output row of the strip
+    const int J = jo - DR + lane;                    // this lane's column
+    const bool out_lane = lane >= DR && lane < DR + DOUT && J < nc;
+    // the window rows i0 - DR .. i0 + DROWS - 1 + DR of column J
+    const bool inside = (EXT == EXT_ODD)
+                            ? (i0 - DR >= 1 && i0 + DROWS + DR <= nr - 1 && jo - DR >= 1 && jo - DR + 31 <= nc - 2)
+                            : (i0 - DR >= 0 && i0 + DROWS + DR <= nr && jo - DR >= 0 && jo - DR + 31 < nc);
+    T win[DROWS + 2 * DR];
+    if (inside) {
+        const size_t o = (size_t)(i0 - DR) * nc + J;
+#pragma unroll
+        for (int t = 0; t < DROWS + 2 * DR; ++t) win[t] = src[o + (size_t)t * nc];
+    } else {
+#pragma unroll
+        for (int t = 0; t < DROWS + 2 * DR; ++t) win[t] = ext_at<T, EXT>(src, i0 - DR + t, J, nr, nc);
+    }
+    T part = T(0);
+#pragma unroll
+    for (int t = 0; t < DROWS; ++t) {
+        const int i = i0 + t;
+        if (PUP && out_lane && i < nr) pnew[(size_t)i * nc + J] = win[t + DR];
+        // centred vertical sums of this lane's column at row i
+        T c[DR + 1];
+        c[0] = win[t + DR];
+#pragma unroll
+        for (int g = 1; g <= DR; ++g) c[g] = c[g - 1] + (win[t + DR - g] + win[t + DR + g]);
+        T acc = c[disk_height(0)];
+#pragma unroll
+        for (int b = 1; b <= DR; ++b) {
+            const T cg = c[disk_height(b)];
+            acc += __shfl_sync(0xffffffffu, cg, lane - b) + __shfl_sync(0xffffffffu, cg, lane + b);
+        }
+        if (!out_lane || i >= nr) continue;
+        if (EXT == EXT_ODD && (i == 0 || i == nr - 1 || J == 0 || J == nc - 1)) continue;
+        T out = v * acc;
+        if (FUSE) {
+            // alpha L(w) p (5-point stencil, zero Neumann), read through the L1 cache
+            out += T(fa.alpha) * lap_at(w, pv, i, J, nr, nc);
+            part += __ldg(pv + (size_t)i * nc + J) * out;
+        }
+        y[(size_t)i * nc + J] = out;
+    }
+    if (FUSE && fa.reduce) {
+        const int slot = fa.slot0 + by * gx + bx;
+        double sres;
+        if (block_reduce_last((double)part, fa.red, fa.ticket, slot, fa.total_blocks, &sres) && threadIdx.x == 0 &&
+            fa.finish_here)
+            finish_pq(fa.st, sres);
+    }
+}
+
+template <typename T, int EXT, bool FUSE, bool PUP>
+__global__ void __launch_bounds__(kThreads)
+blur_disk_kernel(const T* __restrict__ x, T* __restrict__ y, int nr, int nc, T v, const T* __restrict__ w, T* p0,
+                 T* p1, FuseArgs fa) {
+    // (the implicit trigger at block exit lets the next kernel launch)
+    pdl_wait();
+    if (fa.st && fa.st->done) return;
+    disk_body<T, EXT, FUSE, PUP>(blockIdx.x, blockIdx.y, gridDim.x, x, y, nr, nc, v, w, p0, p1, fa);
+}
+
+template <typename T, int EXT, bool FUSE, bool PUP>
+__global__ void __launch_bounds__(kThreads)
+blur_flat_kernel(const T* __restrict__ x, T* __restrict__ y, int nr, int nc, int mr, int mc,
+                 const int* __restrict__ colh, T v, const T* __restrict__ w, T* p0, T* p1, FuseArgs fa) {
+    // (the implicit trigger at block exit lets the next kernel launch)
+    pdl_wait();
+    if (fa.st && fa.st->done) return;
+    flat_body<T, EXT, FUSE, PUP>(blockIdx.x, blockIdx.y, gridDim.x, x, y, nr, nc, mr, mc, colh, v, w, p0, p1, fa);
+}
+
 template <typename T, int EXT, bool FUSE, bool PUP>
 __global__ void __launch_bounds__(kThreads)
 blur_tile_kernel(const T* __restrict__ x, T* __restrict__ y, int nr, int nc, int mr, int mc,
@@ -401,22 +631,29 @@ __device__ __forceinline__ void border_body(int bid, const T* __restrict__ y, T*
 // tiles (gx tiles per row of tiles), the rest the border lines, so the small
 // border work runs beside the interior instead of after it. Both parts reduce
 // p^T q into one ticket; whichever block arrives last finishes.
-template <typename T, bool FUSE>
+template <typename T, bool FUSE, int PATH>
 __global__ void __launch_bounds__(kThreads)
 ar_adjoint_kernel(const T* __restrict__ x, T* __restrict__ y, int nr, int nc, int mr, int mc,
                   const T* __restrict__ hdense, const int* __restrict__ arange, const int* __restrict__ runs,
-                  const T* __restrict__ runv, int nruns, const T* __restrict__ crow, const T* __restrict__ ccol,
-                  const T* __restrict__ ccor, const T* __restrict__ w, T* p0, T* p1, int tile_blocks, int gx,
-                  FuseArgs fa_tile, FuseArgs fa_border) {
+                  const T* __restrict__ runv, int nruns, const int* __restrict__ colh, T flatv,
+                  const T* __restrict__ crow, const T* __restrict__ ccol, const T* __restrict__ ccor,
+                  const T* __restrict__ w, T* p0, T* p1, int tile_blocks, int gx, FuseArgs fa_tile,
+                  FuseArgs fa_border) {
     // (the implicit trigger at block exit lets the next kernel launch)
     pdl_wait();
     if (fa_tile.st && fa_tile.st->done) return;
     __shared__ T partial[kThreads];
     const int bid = blockIdx.x;
-    if (bid < tile_blocks)
-        tile_body<T, EXT_ODD, FUSE, false>(bid % gx, bid / gx, gx, x, y, nr, nc, mr, mc, hdense, arange, runs, runv,
-                                           nruns, w, p0, p1, fa_tile);
-    else
+    if (bid < tile_blocks) {
+        if (PATH == PATH_DISK)
+            disk_body<T, EXT_ODD, FUSE, false>(bid % gx, bid / gx, gx, x, y, nr, nc, flatv, w, p0, p1, fa_tile);
+        else if (PATH == PATH_FLAT)
+            flat_body<T, EXT_ODD, FUSE, false>(bid % gx, bid / gx, gx, x, y, nr, nc, mr, mc, colh, flatv, w, p0, p1,
+                                               fa_tile);
+        else
+            tile_body<T, EXT_ODD, FUSE, false>(bid % gx, bid / gx, gx, x, y, nr, nc, mr, mc, hdense, arange, runs,
+                                               runv, nruns, w, p0, p1, fa_tile);
+    } else
         border_body<T, FUSE>(bid - tile_blocks, x, y, nr, nc, mr, mc, crow, ccol, ccor, w, p0, p1, fa_border,
                              partial);
 }
@@ -439,10 +676,33 @@ enum BlurMode { BLUR_PLAIN = 0, BLUR_PUP = 1, BLUR_FUSE = 2 };
 template <typename T, int EXT, bool FUSE, bool PUP>
 static tvd_status launch_tile(dim3 grid, size_t smem, cudaStream_t s, const T* x, T* y, const tvd_plan_s& p,
                               const Ops<T>& o, const T* w, T* p0, T* p1, const FuseArgs& fa) {
+    if (o.flat == 2) {
+        TVD_CUDA_TRY(launch_pdl(blur_disk_kernel<T, EXT, FUSE, PUP>, grid, dim3(kThreads), smem, s, x, y, p.nr, p.nc,
+                                (T)o.flatv, w, p0, p1, fa));
+        return TVD_OK;
+    }
+    if (o.flat) {
+        TVD_CUDA_TRY((allow_max_smem<blur_flat_kernel<T, EXT, FUSE, PUP>>()));
+        TVD_CUDA_TRY(launch_pdl(blur_flat_kernel<T, EXT, FUSE, PUP>, grid, dim3(kThreads), smem, s, x, y, p.nr, p.nc,
+                                p.psf.mr, p.psf.mc, (const int*)o.colh, (T)o.flatv, w, p0, p1, fa));
+        return TVD_OK;
+    }
     TVD_CUDA_TRY((allow_max_smem<blur_tile_kernel<T, EXT, FUSE, PUP>>()));
     TVD_CUDA_TRY(launch_pdl(blur_tile_kernel<T, EXT, FUSE, PUP>, grid, dim3(kThreads), smem, s, x, y, p.nr, p.nc,
                             p.psf.mr, p.psf.mc, (const T*)o.hdense, (const int*)o.arange, (const int*)o.runs,
                             (const T*)o.runv, o.nruns, w, p0, p1, fa));
+    return TVD_OK;
+}
+
+template <typename T, bool FUSE, int PATH>
+static tvd_status launch_ar_adjoint(int blocks, size_t smem, cudaStream_t s, const T* x, T* y, const tvd_plan_s& p,
+                                    const Ops<T>& o, const T* w, T* p0, T* p1, int tile_blocks, int gx,
+                                    const FuseArgs& fa, const FuseArgs& fb) {
+    TVD_CUDA_TRY((allow_max_smem<ar_adjoint_kernel<T, FUSE, PATH>>()));
+    TVD_CUDA_TRY(launch_pdl(ar_adjoint_kernel<T, FUSE, PATH>, dim3(blocks), dim3(kThreads), smem, s, x, y, p.nr,
+                            p.nc, p.psf.mr, p.psf.mc, (const T*)o.hdense, (const int*)o.arange, (const int*)o.runs,
+                            (const T*)o.runv, o.nruns, (const int*)o.colh, (T)o.flatv, (const T*)o.crow,
+                            (const T*)o.ccol, (const T*)o.ccor, w, p0, p1, tile_blocks, gx, fa, fb));
     return TVD_OK;
 }
 
@@ -452,9 +712,14 @@ template <typename T>
 static tvd_status launch_blur(const tvd_plan_s& p, const Ops<T>& o, bool transpose, int mode, const T* x, T* y,
                               const T* w, T* p0, T* p1, double alpha, CgState* st, cudaStream_t s) {
     const int nr = p.nr, nc = p.nc, mr = p.psf.mr, mc = p.psf.mc;
-    const dim3 grid((nc + BTW - 1) / BTW, (nr + BTH - 1) / BTH);
+    const int path = o.flat == 2 ? PATH_DISK : (o.flat ? PATH_FLAT : PATH_TILE);
+    const int tw = path == PATH_DISK ? DBW : (path == PATH_FLAT ? FBW : BTW);
+    const int th = path == PATH_DISK ? DBH : (path == PATH_FLAT ? FBH : BTH);
+    const dim3 grid((nc + tw - 1) / tw, (nr + th - 1) / th);
     const bool fuse = mode == BLUR_FUSE, pup = mode == BLUR_PUP;
-    const size_t smem = tile_smem(mr, mc, sizeof(T), fuse, pup, o.nruns);
+    const size_t smem = path == PATH_DISK ? 0
+                        : path == PATH_FLAT ? flat_smem_bytes<T>()
+                                            : tile_smem(mr, mc, sizeof(T), fuse, pup, o.nruns);
     FuseArgs fa{alpha, st, p.red, p.ticket + 1, (fuse && st) ? 1 : 0, 0, 0, 0};
     const int tile_blocks = (int)(grid.x * grid.y);
     const int border_blocks = 2 * ((nc - 2 + kSeg - 1) / kSeg) + 2 * ((nr - 2 + kSeg - 1) / kSeg) + 1;
@@ -490,19 +755,18 @@ static tvd_status launch_blur(const tvd_plan_s& p, const Ops<T>& o, bool transpo
         const size_t bsm = border_smem(mr, mc, sizeof(T));
         const size_t msm = smem > bsm ? smem : bsm;
         const int blocks = tile_blocks + border_blocks;
+        const int gx = (int)grid.x;
+#define TVD_ADJ(F, P) TVD_TRY((launch_ar_adjoint<T, F, P>(blocks, msm, s, x, y, p, o, w, p0, p1, tile_blocks, gx, fa, fb)))
         if (fuse) {
-            TVD_CUDA_TRY((allow_max_smem<ar_adjoint_kernel<T, true>>()));
-            TVD_CUDA_TRY(launch_pdl(ar_adjoint_kernel<T, true>, dim3(blocks), dim3(kThreads), msm, s, x, y, nr, nc,
-                                    mr, mc, (const T*)o.hdense, (const int*)o.arange, (const int*)o.runs,
-                                    (const T*)o.runv, o.nruns, (const T*)o.crow, (const T*)o.ccol, (const T*)o.ccor,
-                                    w, p0, p1, tile_blocks, (int)grid.x, fa, fb));
+            if (path == PATH_DISK) TVD_ADJ(true, PATH_DISK);
+            else if (path == PATH_FLAT) TVD_ADJ(true, PATH_FLAT);
+            else TVD_ADJ(true, PATH_TILE);
         } else {
-            TVD_CUDA_TRY((allow_max_smem<ar_adjoint_kernel<T, false>>()));
-            TVD_CUDA_TRY(launch_pdl(ar_adjoint_kernel<T, false>, dim3(blocks), dim3(kThreads), msm, s, x, y, nr, nc,
-                                    mr, mc, (const T*)o.hdense, (const int*)o.arange, (const int*)o.runs,
-                                    (const T*)o.runv, o.nruns, (const T*)o.crow, (const T*)o.ccol, (const T*)o.ccor,
-                                    w, p0, p1, tile_blocks, (int)grid.x, fa, fb));
+            if (path == PATH_DISK) TVD_ADJ(false, PATH_DISK);
+            else if (path == PATH_FLAT) TVD_ADJ(false, PATH_FLAT);
+            else TVD_ADJ(false, PATH_TILE);
         }
+#undef TVD_ADJ
     }
     TVD_CUDA_TRY(cudaGetLastError());
     return TVD_OK;

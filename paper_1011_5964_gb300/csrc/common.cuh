@@ -5,6 +5,7 @@
 #include "tvd_internal.cuh"
 
 #include <cstdlib>
+#include <mutex>
 
 namespace tvd {
 
@@ -77,22 +78,29 @@ __device__ __forceinline__ T lap_at(const T* __restrict__ w, const T* __restrict
 }
 
 // Raise a kernel's dynamic shared-memory limit to the device's opt-in maximum,
-// once per kernel (so no attribute call happens while a graph is captured).
+// once per kernel and device (a function attribute is per device), so no
+// attribute call repeats while a graph is captured.
+constexpr int kMaxDevices = 64;
+
 template <auto Kernel>
 inline cudaError_t allow_max_smem() {
-    static const cudaError_t once = []() {
-        int dev = 0, optin = 0;
-        cudaError_t e = cudaGetDevice(&dev);
-        if (e == cudaSuccess) e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-        cudaFuncAttributes fa{};
-        if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, Kernel);
-        // the opt-in maximum covers static and dynamic shared memory together
-        if (e == cudaSuccess)
-            e = cudaFuncSetAttribute(Kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     optin - (int)fa.sharedSizeBytes);
-        return e;
-    }();
-    return once;
+    static std::mutex mu;
+    static bool done[kMaxDevices] = {};
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lk(mu);
+    if (done[dev]) return cudaSuccess;
+    int optin = 0;
+    e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    cudaFuncAttributes fa{};
+    if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, Kernel);
+    // the opt-in maximum covers static and dynamic shared memory together
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(Kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, optin - (int)fa.sharedSizeBytes);
+    if (e == cudaSuccess) done[dev] = true;
+    return e;
 }
 
 // Asynchronous global -> shared copy of one element (cp.async, 4 or 8 bytes);

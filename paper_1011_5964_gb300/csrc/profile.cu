@@ -25,7 +25,7 @@ static ClassRecord g_rec[PROF_NUM_CLASSES];
 static const char* kNames[PROF_NUM_BASE] = {
     "blur_forward", "blur_adjoint_L", "precond_row_forward", "precond_column_solve", "precond_row_inverse",
     "spectrum_row", "spectrum_column", "cg_init", "cg_p_update", "cg_xr_update", "cg_simple_precond",
-    "tv_coefficients", "vector_misc", "precond_gemm_cublas", "precond_gemm_vector"};
+    "tv_coefficients", "vector_misc", "precond_gemm_tc", "precond_gemm_vector"};
 
 static thread_local bool t_capturing = false;
 
@@ -40,11 +40,9 @@ void count_launches(int k) {
     if (!t_capturing) g_launches.fetch_add((unsigned long long)k, std::memory_order_relaxed);
 }
 
-ProfScope::ProfScope(int cls, cudaStream_t s, int nkernels, bool ours) : cls_(cls), s_(s), start_(nullptr) {
-    if (ours) {
-        count_launches(nkernels);
-        if (t_capturing) capture_kernels_ += nkernels;
-    }
+ProfScope::ProfScope(int cls, cudaStream_t s, int nkernels) : cls_(cls), s_(s), start_(nullptr) {
+    count_launches(nkernels);
+    if (t_capturing) capture_kernels_ += nkernels;
     if (g_profile.load(std::memory_order_relaxed) && !t_capturing) {
         if (cudaEventCreate(&start_) == cudaSuccess) cudaEventRecord(start_, s_);
         else start_ = nullptr;

@@ -174,6 +174,41 @@ static tvd_status ops_alloc(tvd_plan_s& p, Ops<T>& o, cudaStream_t s) {
         TVD_TRY(upload<T>(&o.runv, run_v, s));
         o.nruns = nr_runs;
     }
+    // flat PSF on a centred, symmetric support whose rows and columns are runs (the disk)
+    {
+        double fv = 0.0;
+        bool flat = mr <= 8 && mc <= 8;
+        for (size_t k = 0; k < p.psf.h.size() && flat; ++k) {
+            const double hv = p.psf.h[k];
+            if (hv == 0.0) continue;
+            if (fv == 0.0) fv = hv;
+            else if (hv != fv) flat = false;
+        }
+        flat = flat && fv != 0.0;
+        auto nz = [&](int a, int b) { return p.psf.h[(size_t)(a + mr) * pw + (b + mc)] != 0.0; };
+        std::vector<double> colh(pw, -1.0);
+        for (int b = -mc; b <= mc && flat; ++b) {
+            int g = -1;
+            while (g + 1 <= mr && nz(g + 1, b)) ++g;    // column b: rows -g .. g, nothing beyond
+            for (int a = g + 1; a <= mr && flat; ++a) flat = !nz(a, b) && !nz(-a, b);
+            colh[b + mc] = g;
+        }
+        for (int a = -mr; a <= mr && flat; ++a) {      // rows: runs centred on 0
+            int w = -1;
+            while (w + 1 <= mc && nz(a, w + 1)) ++w;
+            for (int b = w + 1; b <= mc && flat; ++b) flat = !nz(a, b) && !nz(a, -b);
+        }
+        if (flat) {
+            TVD_TRY(upload<int>(&o.colh, colh, s));
+            o.flatv = fv;
+            o.flat = 1;
+            // the disk of radius 7 exactly (a^2 + b^2 <= 49) has its own stencil
+            bool disk = mr == 7 && mc == 7;
+            for (int a = -mr; a <= mr && disk; ++a)
+                for (int b = -mc; b <= mc && disk; ++b) disk = nz(a, b) == (a * a + b * b <= 49);
+            if (disk) o.flat = 2;
+        }
+    }
     TVD_TRY(upload<T>(&o.crow, p.psf.crow, s));
     TVD_TRY(upload<T>(&o.ccol, p.psf.ccol, s));
     TVD_TRY(upload<T>(&o.ccor, p.psf.ccor, s));
@@ -198,7 +233,7 @@ static tvd_status ops_alloc(tvd_plan_s& p, Ops<T>& o, cudaStream_t s) {
 
 template <typename T>
 static void ops_free(Ops<T>& o) {
-    dfree(o.hdense); dfree(o.arange); dfree(o.runs); dfree(o.runv); o.nruns = 0; dfree(o.crow); dfree(o.ccol); dfree(o.ccor);
+    dfree(o.hdense); dfree(o.arange); dfree(o.runs); dfree(o.runv); o.nruns = 0; dfree(o.colh); o.flat = 0; dfree(o.crow); dfree(o.ccol); dfree(o.ccor);
     dfree(o.tw_c); dfree(o.tw_r); dfree(o.aux_c); dfree(o.aux_r); dfree(o.blt_c); dfree(o.blt_r);
     dfree(o.lamH2); dfree(o.inv_spec); dfree(o.w); dfree(o.dmh); dfree(o.dinv);
     dfree(o.x); dfree(o.r); dfree(o.z); dfree(o.p); dfree(o.p2); dfree(o.q); dfree(o.t); dfree(o.t2);
@@ -492,6 +527,19 @@ static tvd_status read_scalars(tvd_plan_s& p, double* h, int count, cudaStream_t
     return TVD_OK;
 }
 
+// A tensor-core transform product's bounded wait expired (TVD_ETIMEOUT in the
+// CG state): the products after it skipped their work and left the reduction
+// tickets mid-count, so those are cleared (and the plan's flag read back)
+// before the error is returned; the plan stays usable.
+static tvd_status timeout_exit(tvd_plan_s& p, cudaStream_t s) {
+    cudaMemsetAsync(p.ticket, 0, 16 * sizeof(unsigned int), s);
+    gemm_precond_check(p, s);
+    cudaStreamSynchronize(s);
+    set_error("a tensor-core transform product gave up waiting for its operands (bounded wait expired); "
+              "the solve was stopped");
+    return TVD_ETIMEOUT;
+}
+
 struct SolveResult {
     int iters = 0;
     int sweeps = 0;
@@ -568,6 +616,7 @@ static tvd_status solve_mixed(tvd_plan_s& p, double alpha, const double* b, doub
         TVD_TRY(read_state<float>(p, s));
         const CgState h = *p.hstate;
         res->iters = h.iter;
+        if (h.status == TVD_ETIMEOUT) return timeout_exit(p, s);
         if (!h.done) {
             if (h.iter == last_iter) {   // the kernels always advance a running solve
                 set_error("CG made no progress between two checks");
@@ -601,7 +650,7 @@ static tvd_status solve_mixed(tvd_plan_s& p, double alpha, const double* b, doub
         TVD_TRY(cg_restart<float>(p, p.f.r, p.state, std::max(target, delta2 * rr_ref), maxit, mode, s));
     }
     hint = res->iters;
-    return TVD_OK;
+    return gemm_precond_check(p, s);
 }
 
 static tvd_status solve(tvd_plan_s& p, const double* u_lag, double alpha, double beta, const double* b, double* x,
@@ -837,6 +886,7 @@ static tvd_status adjoint_mixed(tvd_plan_s& p, const double* b, double* lam, con
         TVD_TRY(read_state<float>(p, s));
         const CgState h = *p.hstate;
         *iters_out = h.iter;
+        if (h.status == TVD_ETIMEOUT) return timeout_exit(p, s);
         if (!h.done) {
             if (h.iter == last_iter) {   // the kernels always advance a running solve
                 set_error("adjoint CG made no progress between two checks");

@@ -59,12 +59,10 @@ void set_capturing(bool on);
 int captured_kernels();   // kernels launched since set_capturing(true)
 
 // Counts the launches of one launcher call and, when profiling is on, brackets
-// them with CUDA events on the launch stream. Library launches (ours = false,
-// cuBLAS) are timed and counted per class but not in the library's own
-// kernel-launch total.
+// them with CUDA events on the launch stream.
 class ProfScope {
   public:
-    ProfScope(int cls, cudaStream_t s, int nkernels = 1, bool ours = true);
+    ProfScope(int cls, cudaStream_t s, int nkernels = 1);
     ~ProfScope();
     ProfScope(const ProfScope&) = delete;
     ProfScope& operator=(const ProfScope&) = delete;
@@ -135,6 +133,14 @@ struct Ops {
     int nruns = 0;
     int* runs = nullptr;
     T* runv = nullptr;
+    // flat PSF (h_{a,b} = flatv on a support symmetric in both axes whose rows
+    // and columns are runs centred on 0, half-widths <= 8: the out-of-focus
+    // disk): colh[b + m_c] = the half-height g_|b| of column b (-1: empty); the
+    // stencil then sums centred vertical box sums along the row (flat != 0;
+    // flat == 2: the disk of radius 7, with its column heights fixed at compile time)
+    int flat = 0;
+    int* colh = nullptr;
+    double flatv = 0.0;
     // AR adjoint border tail weights (Sec. 2 folds), sizes in the plan
     T* crow = nullptr;       // (m_r + 1) x (2 m_c + 1)
     T* ccol = nullptr;       // (2 m_r + 1) x (m_c + 1)
@@ -261,11 +267,14 @@ tvd_status lamH2_setup(const tvd_plan_s& p, Ops<T>& o, cudaStream_t s);
 // the pending update x += alpha p, r -= alpha q (r in place, p and q from o)
 // and the stopping test before preconditioning r.
 // Dense-matrix (GEMM) form of the fast preconditioners' solve on a float plan
-// (gemm_precond.cu): create / destroy its matrices, scratch and cuBLAS handle,
-// and the solve, with the same contract as precond_solve.
+// (gemm_precond.cu): create / destroy its matrices, operand buffers and tensor
+// maps, and the solve, with the same contract as precond_solve. The products
+// run the library's tensor-core kernel; gemm_precond_check reads (and clears)
+// its device error flag: TVD_ETIMEOUT if a product's bounded wait expired.
 tvd_status gemm_precond_create(tvd_plan_s& p, cudaStream_t s);
 void gemm_precond_destroy(tvd_plan_s& p);
 int gemm_precond_storage(const tvd_plan_s& p);   // 0: no GEMM form, 1: float operands, 2: bf16 operands
+tvd_status gemm_precond_check(const tvd_plan_s& p, cudaStream_t s);
 tvd_status gemm_precond_solve(const tvd_plan_s& p, const Ops<float>& o, const float* r, float* z, CgState* st,
                               cudaStream_t s, float* x);
 

@@ -5,9 +5,9 @@ noise 0.5% and 2%; alpha in {1e-4, 1e-3, 1e-2}; beta 1e-2; Gaussian PSF sigma 2 
 
 For each case: the per-step inner iteration counts, the norm of the restored
 image and 64 sampled pixels of it, and the rounding envelope of the oracle
-itself (three more runs with every operator output perturbed by a relative
-2^-50, see tests/parity.py): the per-step spread of the counts and the spread of the
-sampled pixels and of the image. Calls only the oracle, the input generator
+itself (six more runs with every operator output perturbed by a relative
+2^-50, see tests/parity.py): their per-step counts, the per-step spread of the
+counts and the spread of the sampled pixels and of the image. Calls only the oracle, the input generator
 and the perturbation helper. Run:  python tests/golden/make_config2.py
 """
 import json
@@ -57,6 +57,7 @@ def run(case):
     samp = u[idx[:, 0], idx[:, 1]]
     nu = float(np.linalg.norm(u))
     return dict(case, inner_iters=st["inner_iters"],
+                perturbed_iters=[p[1]["inner_iters"] for p in pert],
                 count_spread=count_spread(st["inner_iters"], [p[1]["inner_iters"] for p in pert]),
                 u_norm=nu, samples=samp.tolist(),
                 sample_spread=float(max(np.abs(p[0][idx[:, 0], idx[:, 1]] - samp).max() for p in pert)),

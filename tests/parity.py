@@ -4,19 +4,25 @@ CG residual trajectories are sensitive to rounding: the FP64 oracle itself,
 run on x86 and on Arm numpy builds, gives relative residuals that differ by a
 few percent after ~50 iterations, and stopping decisions near the tolerance
 can go either way. The plain FP64 GPU path is therefore held to the oracle's
-own rounding envelope: the oracle is re-run with every product with A and
-every preconditioner output multiplied by (1 + 2^-50 xi), xi standard normal
-(a few units in the last place, fresh noise each time: a model of rounding
-that differs from numpy's in every operation), and the GPU result must lie as
-close to the unperturbed oracle run as those runs do: iteration counts within
-their largest per-step spread plus one, images within ten times their spread. Where the
-perturbed runs agree exactly this is identical counts and images within
-1e-12 relative (plus rounding).
+own rounding envelope: the oracle is re-run six times with every product with
+A and every preconditioner output multiplied by (1 + 2^-50 xi), xi standard
+normal (a few units in the last place, fresh noise each time: a model of
+rounding that differs from numpy's in every operation), and the GPU result
+must lie as close to the unperturbed oracle run as those runs do:
+
+* iteration counts: every FP step within B of the oracle's count, where B is
+  the run's largest per-step spread of the perturbed runs plus one, and B = 0
+  (identical counts) when the perturbed runs agree with the oracle at every
+  step. Measured on the 256 x 256 sweep (24 cases, each of the six perturbed
+  runs held out in turn against the other five): this rule rejects none of the
+  144 held-out runs, all 102 held-out runs with a zero envelope match exactly,
+  while a step's own spread without slack would reject 10 of them;
+* images within ten times the perturbed runs' spread (at least 1e-12 relative).
 """
 import numpy as np
 
 EPS = 2.0 ** -50
-N_PERTURBED = 3
+N_PERTURBED = 6
 
 
 def noise(j):
@@ -35,18 +41,18 @@ def count_spread(ref, perturbed):
     return [max(abs(p[k] - ref[k]) for p in perturbed) for k in range(len(ref))]
 
 
-def check_counts(gpu, ref, spread, slack=1):
-    """Every step's count within the run's largest per-step spread plus slack.
+def count_bound(spread):
+    """The run's largest per-step spread plus one, or 0 where every step's spread is 0."""
+    m = max(spread) if len(spread) else 0
+    return m + 1 if m > 0 else 0
 
-    Three perturbed runs estimate the spread of each step poorly (a step can
-    show 0 where its neighbours show 2); the operator, and so the sensitivity
-    of the counts to rounding, is the same in every step of a run, so the
-    largest spread over the steps bounds each of them.
-    """
-    assert len(gpu) == len(ref), (gpu, ref)
-    bound = max(spread) + slack
+
+def check_counts(gpu, ref, spread):
+    """Every step's count within count_bound(spread) of the oracle's."""
+    assert len(gpu) == len(ref) == len(spread), (gpu, ref, spread)
+    bound = count_bound(spread)
     for k in range(len(ref)):
-        assert abs(gpu[k] - ref[k]) <= bound, (k, gpu, ref, spread)
+        assert abs(gpu[k] - ref[k]) <= bound, (k, gpu, ref, spread, bound)
 
 
 def image_bound(ref, perturbed_images, floor=1e-12):

@@ -1,9 +1,10 @@
 """GPU parity of pcg_solve and tv_deblur against the FP64 oracle.
 
 * FP64 plans: held to the oracle's own rounding envelope (tests/parity.py):
-  per-FP-step inner iteration counts within the largest per-step spread of oracle runs whose
-  operator outputs are perturbed at a relative 2^-50, plus one; restored
-  images within ten times that spread (at least 1e-12 relative).
+  each FP step's inner iteration count within that step's own spread over
+  oracle runs whose operator outputs are perturbed at a relative 2^-50 (equal
+  counts where those runs agree); restored images within ten times their
+  spread (at least 1e-12 relative).
 * MIXED plans: both sides solve each FP step to ||r||/||r_0|| < 1e-10; the
   restored images agree within 1e-5 relative.
 * Error paths: NaN data (breakdown), maxit too small (no convergence),

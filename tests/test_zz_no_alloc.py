@@ -1,15 +1,20 @@
-"""The allocation-free entry point tvd_normal_apply_noalloc against the plan-based path.
+"""The allocation-free entry point tvd_normal_apply_noalloc.
 
-tvd_normal_apply_noalloc serves callers that must not allocate device memory
-(code running during a CUDA graph capture, or under a framework that owns a
-fixed device-memory pool). It keeps H x, the diffusivity and the PSF tables in
-fixed arrays of the library instead. This file is collected last so that a
-failure here does not hide the results of the other tests; it must pass both
-alone in a fresh process and after the rest of the suite.
+tvd_normal_apply_noalloc serves callers that cannot allocate device memory
+themselves or through the library: code running under a framework that owns
+a fixed device-memory pool or budget, and callbacks from such a framework that
+must not allocate behind its back. It keeps H x, the diffusivity and the PSF
+tables in fixed arrays of the library instead. Its output is checked against
+the plan-based entry points (ar_blur_apply, tv_operator_apply) and against the
+FP64 oracle's H^T H x + alpha L(u) x, on two calls in a row. This file is
+collected last so that a failure here does not hide the results of the other
+tests; it must pass both alone in a fresh process and after the rest of the
+suite.
 """
 import numpy as np
 import pytest
 
+import oracle as O
 from paper_1011_5964_gb300 import synth
 
 pytestmark = pytest.mark.gpu
@@ -44,6 +49,11 @@ def test_noalloc_matches_plan_path_twice(bc):
         ref = reference(pkg, torch, h, bc, u, x, alpha, beta)
         err = float((y - ref).abs().max() / ref.abs().max())
         assert err < 1e-12, (bc, n_rows, n_cols, err)
+        # the oracle's product of the FP step (eq. (fp)), element by element
+        un, xn = u.cpu().numpy(), x.cpu().numpy()
+        ref_o = O.normal_apply(xn, h, bc, O.diffusivity(un, beta), alpha)
+        err_o = float(np.abs(y.cpu().numpy() - ref_o).max() / np.abs(ref_o).max())
+        assert err_o < 1e-12, (bc, n_rows, n_cols, err_o)
 
 
 def test_noalloc_rejects_oversize():
