@@ -419,13 +419,17 @@ def spectrum_scaled(w: np.ndarray, d: np.ndarray, bc: str):
 # Preconditioners, Sec. 3
 # --------------------------------------------------------------------------
 
-def precond_setup(u_lag, h, bc, alpha, beta, kind):
+def precond_setup(u_lag, h, bc, alpha, beta, kind, method="fp"):
     """Everything the preconditioner solve needs for the FP step at u_lag.
 
     Returns a dict with the diffusivity ``w``, ``D`` = 1 + alpha diag(L) (eq. (D)),
     and ``spec`` = Lambda_H^2 + alpha Lambda_L, the eigenvalues of R (eq. (R2)) or
     M (2D form of eq. (M)); D_R / D_M scale these by D^1/2 on both sides.
+    With method = METHOD_REBLUR (eq. (fpp), AR BCs) the fast kinds are the
+    reblurring preconditioners P, D_P, P_D of Sec. 3 (see reblur_setup).
     """
+    if method == METHOD_REBLUR:
+        return reblur_setup(u_lag, h, bc, alpha, beta, kind)
     w = diffusivity(u_lag, beta)
     nr, nc = w.shape
     D = 1.0 + alpha * tv_diag(w)
@@ -460,6 +464,12 @@ def precond_apply(r: np.ndarray, P) -> np.ndarray:
         return r / P["D"]
     scaled = kind in (PC_DFAST, PC_FASTD)
     t = r / np.sqrt(P["D"]) if scaled else r.copy()
+    if "Tr" in P:
+        # reblurring preconditioners: (T_r (x) T_c) diag(spec) (T_r (x) T_c)^{-1}
+        t = P["Tinv_r"] @ t @ P["Tinv_c"].T
+        t = t / P["spec"]
+        t = P["Tr"] @ t @ P["Tc"].T
+        return t / np.sqrt(P["D"]) if scaled else t
     t = transform_fwd(transform_fwd(t, bc, 1), bc, 0)
     t = t / P["spec"]
     t = transform_inv(transform_inv(t, bc, 0), bc, 1)
@@ -530,30 +540,36 @@ def pcg(apply_A, apply_M, b, x0, tol, maxit, hist=None, noise=None):
     return x, k, relres, False
 
 
-def fp_step(u, b, h, bc, alpha, beta, kind, tol, maxit, hist=None, noise=None):
-    """One lagged-diffusivity step: solve (H^T H + alpha L(u)) x = H^T v from x0 = u."""
-    P = precond_setup(u, h, bc, alpha, beta, kind)
+def fp_step(u, b, h, bc, alpha, beta, kind, tol, maxit, hist=None, noise=None, method="fp"):
+    """One lagged-diffusivity step from x0 = u: solve (H^T H + alpha L(u)) x = H^T v by PCG
+    (eq. (fp)), or with method = METHOD_REBLUR (H' H + alpha L(u)) x = H' v by PBiCGstab
+    (eq. (fpp)); b is the right-hand side."""
+    P = precond_setup(u, h, bc, alpha, beta, kind, method)
     w = P["w"]
+    if method == METHOD_REBLUR:
+        return bicgstab(lambda y: reblur_apply(y, h, bc, w, alpha),
+                        lambda r: precond_apply(r, P), b, u, tol, maxit, hist, noise)
     return pcg(lambda y: normal_apply(y, h, bc, w, alpha),
                lambda r: precond_apply(r, P), b, u, tol, maxit, hist, noise)
 
 
 def tv_deblur(v, h, bc, alpha, beta, outer=10, tol=1e-6, maxit=1000,
-              kind=PC_DFAST, outer_tol=0.0, noise=None):
+              kind=PC_DFAST, outer_tol=0.0, noise=None, method="fp"):
     """Lagged-diffusivity FP iteration with PCG inner solves, u^0 = v (Sec. 5).
 
     Runs ``outer`` FP steps, or stops earlier when ||u^k - u^{k-1}|| / ||u^k||
     < outer_tol (if outer_tol > 0). Returns (u, stats) where stats holds the
     per-step inner iteration counts, residuals, relative changes and the
-    relative residuals of the last two inner iterations of each step.
+    relative residuals of the last two inner iterations of each step. With
+    method = METHOD_REBLUR each step solves eq. (fpp) by PBiCGstab (Sec. 5).
     """
     v = np.asarray(v, dtype=np.float64)
-    b = blur_adjoint(v, h, bc)
+    b = reblur_rhs(v, h, bc) if method == METHOD_REBLUR else blur_adjoint(v, h, bc)
     u = v.copy()
     stats = {"inner_iters": [], "relres": [], "rel_change": [], "converged": [], "relres_tail": []}
     for _ in range(outer):
         hist = []
-        x, k, rr, ok = fp_step(u, b, h, bc, alpha, beta, kind, tol, maxit, hist, noise)
+        x, k, rr, ok = fp_step(u, b, h, bc, alpha, beta, kind, tol, maxit, hist, noise, method)
         stats["relres_tail"].append(hist[-2:])
         change = float(np.linalg.norm(x - u) / max(np.linalg.norm(x), 1e-300))
         stats["inner_iters"].append(k)
@@ -564,6 +580,221 @@ def tv_deblur(v, h, bc, alpha, beta, outer=10, tol=1e-6, maxit=1000,
         if outer_tol > 0.0 and change < outer_tol:
             break
     return u, stats
+
+
+# --------------------------------------------------------------------------
+# Reblurring, eq. (fpp): (H' H + alpha L(u^k)) u^{k+1} = H' v with H' the AR
+# blur of the PSF rotated by 180 degrees, solved by PBiCGstab; the AR algebra
+# of eq. (ARalg), the projection AR(.) and the preconditioners P, D_P, P_D
+# (Sec. 3.1 after eq. (fpp), the Remark on T_n, eq. (scalereb); 2D forms in
+# Sec. 3.2)
+# --------------------------------------------------------------------------
+
+METHOD_FP = "fp"
+METHOD_REBLUR = "reblur"
+
+
+def rotated_psf(h: np.ndarray) -> np.ndarray:
+    """The PSF rotated by 180 degrees (h'_{a,b} = h_{-a,-b})."""
+    return np.asarray(h, dtype=np.float64)[::-1, ::-1].copy()
+
+
+def reblur_apply(x, h, bc, w, alpha) -> np.ndarray:
+    """A' x = H' H x + alpha L(w) x, the matrix of eq. (fpp)."""
+    return blur(blur(x, h, bc), rotated_psf(h), bc) + alpha * tv_apply(w, x)
+
+
+def reblur_rhs(v, h, bc) -> np.ndarray:
+    """H' v, the right-hand side of eq. (fpp)."""
+    return blur(v, rotated_psf(h), bc)
+
+
+def _sine(m: int) -> np.ndarray:
+    """S_m of eq. (lambda) (the orthonormal DST-I, symmetric)."""
+    return sfft.dst(np.eye(m), type=1, norm="ortho", axis=0)
+
+
+def transform_T(n: int):
+    """(T_n, T_n^{-1}) from the Remark after AR(A): T_n = hat-S_n (I + U), T_n^{-1} = (I - U) hat-S_n,
+    U = [0 0 0; S p 0 S J p; 0 0 0] with p_j = 1 - j/(n-1), j = 1..n-2 (the interior of the sampled 1 - x)."""
+    Sh = transform_matrix(n, AR)
+    U = np.zeros((n, n))
+    if n > 2:
+        S = _sine(n - 2)
+        p = 1.0 - np.arange(1, n - 1) / (n - 1)
+        U[1:-1, 0] = S @ p
+        U[1:-1, -1] = S @ p[::-1]
+    I = np.eye(n)
+    return Sh @ (I + U), (I - U) @ Sh
+
+
+def _tau_generator(first_col: np.ndarray) -> np.ndarray:
+    """z of a tau matrix T(z) - H(sigma^2 z, J sigma^2 z) from its first column c_k = z_k - z_{k+2}."""
+    m = first_col.shape[0]
+    z = np.zeros(m)
+    for k in range(m - 1, -1, -1):
+        z[k] = first_col[k] + (z[k + 2] if k + 2 < m else 0.0)
+    return z
+
+
+def ar_projection(A: np.ndarray) -> np.ndarray:
+    """AR(A) of Sec. 3.1 for an n x n matrix A: interior block s(A(2:n-1, 2:n-1)) (the optimal sine
+    projection s(B) = S diag(S B S) S), first column z_{i} + 2 sum_{k > i} z_k (1-based, rows 1..n-1)
+    with z the Toeplitz generator of that interior block, last column its flip, first and last rows
+    zero but for the corners."""
+    A = np.asarray(A, dtype=np.float64)
+    n = A.shape[0]
+    m = n - 2
+    S = _sine(m)
+    inner = A[1:-1, 1:-1]
+    s_in = S @ np.diag(np.diag(S @ inner @ S)) @ S
+    z = np.concatenate([_tau_generator(s_in[:, 0]), [0.0, 0.0]])
+    out = np.zeros((n, n))
+    out[1:-1, 1:-1] = s_in
+    for i in range(n):
+        out[i, 0] = z[i] + 2.0 * z[i + 1:].sum()
+    out[:, -1] = out[::-1, 0]
+    return out
+
+
+def _swap_levels(A: np.ndarray, nr: int, nc: int) -> np.ndarray:
+    """Q^T A Q of Sec. 3.2: the (i, j) entry of block (k, l) becomes the (k, l) entry of block (i, j)."""
+    return A.reshape(nr, nc, nr, nc).transpose(1, 0, 3, 2).reshape(nr * nc, nr * nc)
+
+
+def ar2_projection(A: np.ndarray, nr: int, nc: int) -> np.ndarray:
+    """AR_2(A) = Q AR_1(Q^T AR_1(A) Q) Q^T (Sec. 3.2) for an (nr nc) x (nr nc) matrix; AR_1 applies
+    AR(.) to every block."""
+    def ar1(B, nb, bs):
+        out = np.empty_like(B)
+        for a in range(nb):
+            for b in range(nb):
+                out[a * bs:(a + 1) * bs, b * bs:(b + 1) * bs] = ar_projection(B[a * bs:(a + 1) * bs,
+                                                                                b * bs:(b + 1) * bs])
+        return out
+    A1 = ar1(np.asarray(A, dtype=np.float64), nr, nc)
+    A2 = ar1(_swap_levels(A1, nr, nc), nc, nr)
+    return _swap_levels(A2, nc, nr)
+
+
+def ar_extension(m: int) -> np.ndarray:
+    """c with h_hat_z(0) = c . lam: the border eigenvalue of AR(A) from the eigenvalues lam of its
+    interior sine projection (lam -> tau first column S diag(lam) S e_1 -> z -> z_1 + 2 sum z_k)."""
+    S = _sine(m)
+    cols = S * S[0][None, :]                   # column i: S diag(e_i) S e_1
+    Z = np.stack([_tau_generator(cols[:, i]) for i in range(m)], axis=1)
+    wts = np.full(m, 2.0)
+    wts[0] = 1.0
+    return wts @ Z
+
+
+def ar_extend2(lam: np.ndarray) -> np.ndarray:
+    """Eigenvalues of AR_2 from the interior ones: border rows / columns are the c-weighted sums of
+    the interior along that dimension (AR(.) per level), corners along both."""
+    nr, nc = lam.shape
+    cr, cc = ar_extension(nr - 2), ar_extension(nc - 2)
+    inner = lam[1:-1, 1:-1]
+    out = np.empty_like(lam)
+    out[1:-1, 1:-1] = inner
+    out[0, 1:-1] = out[-1, 1:-1] = cr @ inner
+    out[1:-1, 0] = out[1:-1, -1] = inner @ cc
+    out[0, 0] = out[0, -1] = out[-1, 0] = out[-1, -1] = cr @ inner @ cc
+    return out
+
+
+def reblur_setup(u_lag, h, bc, alpha, beta, kind):
+    """Preconditioner of eq. (fpp) (AR BCs): P = H' H + alpha AR_2(L) (eigenvalues Lambda_H^2 +
+    alpha Lambda_AR2(L) in the T_n (x) T_n basis: H' = H for a symmetric PSF and H is in the AR
+    algebra), D_P = D^1/2 P D^1/2, or P_D = H^' H^ + alpha AR_2(L~), H^ = H AR_2(D^-1/2), applied as
+    D^1/2 P_D D^1/2 (eigenvalues Lambda_H^2 Lambda_D^2 + alpha Lambda_L~)."""
+    if bc != AR:
+        raise ValueError("the reblurring preconditioners are defined for anti-reflective BCs")
+    w = diffusivity(u_lag, beta)
+    nr, nc = w.shape
+    D = 1.0 + alpha * tv_diag(w)
+    P = {"kind": kind, "bc": bc, "w": w, "D": D, "alpha": alpha, "method": METHOD_REBLUR}
+    if kind in (PC_FAST, PC_DFAST, PC_FASTD):
+        lam_h = spectrum_H(h, nr, nc, AR)
+        if kind == PC_FASTD:
+            lam_d, lam_lt = spectrum_scaled(w, 1.0 / np.sqrt(D), AR)
+            spec = lam_h * lam_h * ar_extend2(lam_d) ** 2 + alpha * ar_extend2(lam_lt)
+        else:
+            spec = lam_h * lam_h + alpha * ar_extend2(spectrum_L(w, AR))
+        if np.min(spec) <= 1e-300:
+            raise ValueError("preconditioner spectrum is not positive")
+        P["spec"] = spec
+        P["Tr"], P["Tinv_r"] = transform_T(nr)
+        P["Tc"], P["Tinv_c"] = transform_T(nc)
+    return P
+
+
+def bicgstab(apply_A, apply_M, b, x0, tol, maxit, hist=None, noise=None):
+    """Preconditioned BiCGstab (van der Vorst 1992, cited as [V92]) on A x = b from x0, with the
+    preconditioned directions p^ = M^-1 p and s^ = M^-1 s and the shadow residual r^ = r_0.
+
+    Stops when ||r_k||_2 / ||r_0||_2 < tol (Sec. 5), tested on the half-step residual s and on
+    r after each iteration, or after ``maxit`` iterations (one iteration = two products with A).
+    Returns (x, iterations, relres, converged); ``hist`` and ``noise`` as for pcg.
+    """
+    if noise is not None:
+        rng, eps = noise
+        A0, M0 = apply_A, apply_M
+
+        def apply_A(y):
+            q = A0(y)
+            return q * (1.0 + eps * rng.standard_normal(q.shape))
+
+        def apply_M(r):
+            z = M0(r)
+            return z * (1.0 + eps * rng.standard_normal(z.shape))
+    x = np.array(x0, dtype=np.float64, copy=True)
+    r = b - apply_A(x)
+    r0 = float(np.sqrt((r * r).sum()))
+    if r0 == 0.0:
+        return x, 0, 0.0, True
+    rhat = r.copy()
+    rho_old = alpha = omega = 1.0
+    v = np.zeros_like(r)
+    p = np.zeros_like(r)
+    k = 0
+    relres = 1.0
+    while k < maxit:
+        k += 1
+        rho = float((rhat * r).sum())
+        if rho == 0.0:
+            return x, k, relres, False
+        if k == 1:
+            p = r.copy()
+        else:
+            beta = (rho / rho_old) * (alpha / omega)
+            p = r + beta * (p - omega * v)
+        phat = apply_M(p)
+        v = apply_A(phat)
+        alpha = rho / float((rhat * v).sum())
+        s = r - alpha * v
+        relres = float(np.sqrt((s * s).sum())) / r0
+        if relres < tol:
+            x = x + alpha * phat
+            if hist is not None:
+                hist.append(relres)
+            return x, k, relres, True
+        shat = apply_M(s)
+        t = apply_A(shat)
+        tt = float((t * t).sum())
+        if tt == 0.0:
+            return x, k, relres, False
+        omega = float((t * s).sum()) / tt
+        x = x + alpha * phat + omega * shat
+        r = s - omega * t
+        relres = float(np.sqrt((r * r).sum())) / r0
+        if hist is not None:
+            hist.append(relres)
+        if relres < tol:
+            return x, k, relres, True
+        if omega == 0.0:
+            return x, k, relres, False
+        rho_old = rho
+    return x, k, relres, False
 
 
 # --------------------------------------------------------------------------
