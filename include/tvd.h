@@ -225,7 +225,8 @@ tvd_status pcg_solve(tvd_plan plan, const void* u_lag, double alpha, double beta
 
 /*
  * tv_deblur -- the FP iteration u^{k+1} = A(u^k)^{-1} H^T v from u^0 = v
- * (Sec. 5), each step solved by pcg_solve warm-started at u^k. Runs max_outer
+ * (Sec. 5), each step solved by pcg_solve warm-started at u^k (on a REBLUR
+ * plan: u^{k+1} = A'(u^k)^{-1} H' v, each step solved by pbicgstab_solve). Runs max_outer
  * steps, or stops earlier when ||u^k - u^{k-1}|| / ||u^k|| < outer_tol
  * (outer_tol <= 0: fixed count). v and u_out: DOUBLE device arrays; u_out may
  * equal v. stats may be NULL. Inner non-convergence of a step is recorded in
@@ -235,6 +236,61 @@ tvd_status pcg_solve(tvd_plan plan, const void* u_lag, double alpha, double beta
 tvd_status tv_deblur(tvd_plan plan, const void* v, double alpha, double beta,
                      int max_outer, double outer_tol, double inner_tol, int inner_maxit,
                      void* u_out, tvd_stats* stats, void* stream);
+
+/*
+ * Reblurring (Sec. 3, eq. (fpp)): each FP step solves
+ *     A' u^{k+1} = H' v,   A' = H' H + alpha L(u^k),
+ * with H' the blur of the PSF rotated by 180 degrees under the same
+ * anti-reflective BCs (H' = H for the quadrantally symmetric PSFs every plan
+ * requires), by preconditioned BiCGstab, since A' is not symmetric. On a
+ * reblurring plan the fast preconditioner kinds are the reblurring
+ * preconditioners of Sec. 3 in their 2D form (Sec. 3.2):
+ *   TVD_PC_FAST  = P   = H' H + alpha AR_2(L(u^k)),
+ *   TVD_PC_DFAST = D_P = D^1/2 P D^1/2,
+ *   TVD_PC_FASTD = P_D = H^' H^ + alpha AR_2(L~), H^ = H AR_2(D^-1/2) (the
+ *                  preconditioner of the scaled system eq. (scalereb)),
+ *                  applied as D^1/2 P_D D^1/2,
+ * all diagonalised by T_n (x) T_n of eq. (Tn), T_n = hat-S (I + U) (the
+ * Remark on AR(A)); their eigenvalues are those of the sine projections at
+ * interior frequencies, extended to the border ones as AR(.) prescribes.
+ * TVD_PC_NONE and TVD_PC_DIAG keep their meaning.
+ */
+typedef enum {
+    TVD_METHOD_FP = 0,      /* eq. (fp), PCG (default) */
+    TVD_METHOD_REBLUR = 1   /* eq. (fpp), PBiCGstab (anti-reflective BCs only) */
+} tvd_method;
+
+/*
+ * tvd_plan_set_method -- switch the plan between eq. (fp) with PCG and
+ * eq. (fpp) with PBiCGstab (method: a tvd_method value). REBLUR needs
+ * anti-reflective BCs (else TVD_EINVAL). Any earlier tau_precond_setup is
+ * discarded; a plan in the GEMM transform form rebuilds its matrices (T_n^-1
+ * forward, T_n inverse, per side). tau_precond_setup / tau_precond_solve,
+ * tv_deblur and pbicgstab_solve follow the method; pcg_solve on a REBLUR plan
+ * and pbicgstab_solve on an FP plan return TVD_EINVAL. Synchronises stream.
+ */
+tvd_status tvd_plan_set_method(tvd_plan plan, int method, void* stream);
+
+/* tvd_plan_method -- the plan's tvd_method (TVD_METHOD_FP for NULL). */
+int tvd_plan_method(tvd_plan plan);
+
+/*
+ * pbicgstab_solve -- solve (H' H + alpha L(u_lag)) x = b (eq. (fpp)) on a
+ * REBLUR plan by preconditioned BiCGstab (van der Vorst's method, cited in
+ * Sec. 3) from the initial guess in x_inout, stopping when
+ * ||r_k||_2 / ||r_0||_2 < tol (Sec. 5), tested on the half-step residual and
+ * on r after each iteration, or after maxit iterations (one iteration: two
+ * products with A', two preconditioner solves). u_lag, b, x_inout: DOUBLE
+ * device arrays. In MIXED mode BiCGstab runs in float with double scalars
+ * inside a double iterative refinement: each float solve, from a fresh shadow
+ * residual, reduces the double residual b - A' x (recomputed in double after
+ * it) by 1e-4 or to the target. *iters receives the BiCGstab iterations (all
+ * float solves together), *relres the final double relative residual; both may
+ * be NULL. Returns TVD_ENOCONV if tol was not reached within maxit iterations,
+ * TVD_EBREAKDOWN on a zero rho, r^T v or t^T t. Synchronises stream.
+ */
+tvd_status pbicgstab_solve(tvd_plan plan, const void* u_lag, double alpha, double beta, const void* b,
+                           void* x_inout, double tol, int maxit, int* iters, double* relres, void* stream);
 
 /*
  * tv_deblur_batched -- tv_deblur of many independent problems at once (the

@@ -33,8 +33,10 @@ STATUS_NAMES = ["TVD_OK", "TVD_EINVAL", "TVD_EPSF_ASYM", "TVD_EPSF_SIZE", "TVD_E
 
 # Function names of the C ABI, in include/tvd.h order.
 TRANSFORM = {"fft": 0, "gemm": 1}
+METHOD = {"fp": 0, "reblur": 1}
 ABI_FUNCTIONS = ["tvd_plan_create", "tvd_plan_destroy", "ar_blur_apply", "tv_operator_apply",
                  "tau_precond_setup", "tau_precond_solve", "pcg_solve", "tv_deblur",
+                 "tvd_plan_set_method", "tvd_plan_method", "pbicgstab_solve",
                  "tv_deblur_batched", "tv_hessian_apply", "tv_deblur_adjoint", "tvd_plan_psf_size",
                  "tvd_normal_apply_noalloc", "tvd_plan_set_transform", "tvd_plan_transform", "tvd_plan_gemm_storage",
                  "tvd_last_error", "tvd_version", "tvd_kernel_launches",
@@ -91,6 +93,9 @@ def load_library(path: str | None = None) -> ctypes.CDLL:
                                       ctypes.POINTER(d), ctypes.POINTER(i), ctypes.POINTER(d), vp]
     lib.tvd_plan_psf_size.argtypes = [vp, ctypes.POINTER(i), ctypes.POINTER(i)]
     lib.tvd_plan_set_transform.argtypes = [vp, i, vp]
+    lib.tvd_plan_set_method.argtypes = [vp, i, vp]
+    lib.tvd_plan_method.argtypes = [vp]
+    lib.pbicgstab_solve.argtypes = [vp, vp, d, d, vp, vp, d, i, ctypes.POINTER(i), ctypes.POINTER(d), vp]
     lib.tvd_plan_transform.argtypes = [vp]
     lib.tvd_plan_gemm_storage.argtypes = [vp]
     lib.tvd_last_error.restype = ctypes.c_char_p
@@ -136,13 +141,15 @@ class Plan:
 
     ``psf`` is a (2 m_r + 1, 2 m_c + 1) float64 array, centred and quadrantally
     symmetric. ``bc``: 'ar' (anti-reflective) or 'r' (reflective). ``pc``:
-    'none', 'diag', 'fast' (R / M) or 'dfast' (D_R / D_M). ``mode``: 'fp64' or
-    'mixed'. Operator calls take float64 tensors in fp64 mode and float32 in
-    mixed mode; solver calls always take float64 tensors.
+    'none', 'diag', 'fast' (R / M), 'dfast' (D_R / D_M) or 'fastd' (R_D / M_D).
+    ``mode``: 'fp64' or 'mixed'. ``method``: 'fp' (eq. (fp), PCG) or 'reblur'
+    (eq. (fpp), PBiCGstab; the fast kinds are then P, D_P, P_D). Operator calls
+    take float64 tensors in fp64 mode and float32 in mixed mode; solver calls
+    always take float64 tensors.
     """
 
     def __init__(self, n_rows: int, n_cols: int, psf, bc: str = "ar", pc: str = "dfast", mode: str = "fp64",
-                 transform: str | None = None):
+                 transform: str | None = None, method: str = "fp"):
         import torch
         self.lib = load_library()
         self.shape = (int(n_rows), int(n_cols))
@@ -155,8 +162,18 @@ class Plan:
                                         h.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), h.shape[0], h.shape[1],
                                         BC[bc], PC[pc], MODE[mode], _stream()))
         self.handle = handle
+        if method != "fp":
+            self.set_method(method)
         if transform is not None:
             self.set_transform(transform)
+
+    def set_method(self, method: str):
+        """'fp' (eq. (fp), PCG) or 'reblur' (eq. (fpp), PBiCGstab; anti-reflective BCs)."""
+        _check(self.lib.tvd_plan_set_method(self.handle, METHOD[method], _stream()))
+
+    @property
+    def method(self) -> str:
+        return "reblur" if self.lib.tvd_plan_method(self.handle) == METHOD["reblur"] else "fp"
 
     def set_transform(self, kind: str):
         """Transform form of the fast preconditioners on a mixed plan: 'fft' or 'gemm'."""
@@ -223,6 +240,18 @@ class Plan:
         st = self.lib.pcg_solve(self.handle, _ptr(u_lag, torch.float64, self.n), float(alpha), float(beta),
                                 _ptr(b, torch.float64, self.n), _ptr(x, torch.float64, self.n), float(tol), int(maxit),
                                 ctypes.byref(it), ctypes.byref(rr), _stream())
+        _check(st, allow=(TVD_ENOCONV,))
+        return it.value, rr.value, st
+
+    def pbicgstab_solve(self, u_lag, alpha: float, beta: float, b, x, tol: float = 1e-6, maxit: int = 1000):
+        """Solve (H' H + alpha L(u_lag)) x = b (eq. (fpp)) in place on a reblurring plan.
+        Returns (iterations, relres, status)."""
+        import torch
+        it = ctypes.c_int(0)
+        rr = ctypes.c_double(0.0)
+        st = self.lib.pbicgstab_solve(self.handle, _ptr(u_lag, torch.float64, self.n), float(alpha), float(beta),
+                                      _ptr(b, torch.float64, self.n), _ptr(x, torch.float64, self.n), float(tol),
+                                      int(maxit), ctypes.byref(it), ctypes.byref(rr), _stream())
         _check(st, allow=(TVD_ENOCONV,))
         return it.value, rr.value, st
 
@@ -374,6 +403,14 @@ def tau_precond_solve(plan: Plan, r, z=None):
 
 def pcg_solve(plan: Plan, u_lag, alpha, beta, b, x, tol=1e-6, maxit=1000):
     return plan.pcg_solve(u_lag, alpha, beta, b, x, tol, maxit)
+
+
+def pbicgstab_solve(plan: Plan, u_lag, alpha, beta, b, x, tol=1e-6, maxit=1000):
+    return plan.pbicgstab_solve(u_lag, alpha, beta, b, x, tol, maxit)
+
+
+def tvd_plan_set_method(plan: Plan, method: str):
+    return plan.set_method(method)
 
 
 def tv_deblur(plan: Plan, v, alpha, beta, max_outer=10, outer_tol=0.0, inner_tol=1e-6, inner_maxit=1000, u=None):

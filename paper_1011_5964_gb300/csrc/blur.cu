@@ -443,10 +443,12 @@ __device__ __forceinline__ void disk_body(int bx, int by, int gx, const T* __res
         for (int t = 0; t < DROWS + 2 * DR; ++t) win[t] = ext_at<T, EXT>(src, i0 - DR + t, J, nr, nc);
     }
     T part = T(0);
+    const size_t o0 = (size_t)i0 * nc + J;           // (i0, J); row t at o0 + t nc
 #pragma unroll
     for (int t = 0; t < DROWS; ++t) {
         const int i = i0 + t;
-        if (PUP && out_lane && i < nr) pnew[(size_t)i * nc + J] = win[t + DR];
+        const size_t oi = o0 + (size_t)t * nc;
+        if (PUP && out_lane && i < nr) pnew[oi] = win[t + DR];
         // centred vertical sums of this lane's column at row i
         T c[DR + 1];
         c[0] = win[t + DR];
@@ -455,8 +457,9 @@ __device__ __forceinline__ void disk_body(int bx, int by, int gx, const T* __res
         T acc = c[disk_height(0)];
 #pragma unroll
         for (int b = 1; b <= DR; ++b) {
+            // lane +- b (immediate offsets; lanes near the warp's ends read their own value: not outputs)
             const T cg = c[disk_height(b)];
-            acc += __shfl_sync(0xffffffffu, cg, lane - b) + __shfl_sync(0xffffffffu, cg, lane + b);
+            acc += __shfl_up_sync(0xffffffffu, cg, b) + __shfl_down_sync(0xffffffffu, cg, b);
         }
         if (!out_lane || i >= nr) continue;
         if (EXT == EXT_ODD && (i == 0 || i == nr - 1 || J == 0 || J == nc - 1)) continue;
@@ -464,9 +467,9 @@ __device__ __forceinline__ void disk_body(int bx, int by, int gx, const T* __res
         if (FUSE) {
             // alpha L(w) p (5-point stencil, zero Neumann), read through the L1 cache
             out += T(fa.alpha) * lap_at(w, pv, i, J, nr, nc);
-            part += __ldg(pv + (size_t)i * nc + J) * out;
+            part += __ldg(pv + oi) * out;
         }
-        y[(size_t)i * nc + J] = out;
+        y[oi] = out;
     }
     if (FUSE && fa.reduce) {
         const int slot = fa.slot0 + by * gx + bx;
@@ -732,7 +735,12 @@ static tvd_status launch_blur(const tvd_plan_s& p, const Ops<T>& o, bool transpo
             return TVD_EINVAL;
         }
     }
-    if (!transpose) {
+    if (!transpose && fuse) {
+        // H t + alpha L(w) p (the reblurring product H' H p + alpha L p with t = H p)
+        fa.finish_here = 1;
+        if (p.bc == TVD_BC_ANTIREFLECTIVE) TVD_TRY((launch_tile<T, EXT_AR, true, false>(grid, smem, s, x, y, p, o, w, p0, p1, fa)));
+        else TVD_TRY((launch_tile<T, EXT_R, true, false>(grid, smem, s, x, y, p, o, w, p0, p1, fa)));
+    } else if (!transpose) {
         if (p.bc == TVD_BC_ANTIREFLECTIVE) {
             if (pup) TVD_TRY((launch_tile<T, EXT_AR, false, true>(grid, smem, s, x, y, p, o, w, p0, p1, fa)));
             else TVD_TRY((launch_tile<T, EXT_AR, false, false>(grid, smem, s, x, y, p, o, w, p0, p1, fa)));
@@ -788,6 +796,12 @@ template <typename T>
 tvd_status normal_finish(const tvd_plan_s& p, const Ops<T>& o, const T* t, const T* p0, const T* p1, double alpha,
                          T* q, CgState* st, cudaStream_t s) {
     return launch_blur<T>(p, o, true, BLUR_FUSE, t, q, o.w, const_cast<T*>(p0), const_cast<T*>(p1), alpha, st, s);
+}
+
+template <typename T>
+tvd_status forward_fuse(const tvd_plan_s& p, const Ops<T>& o, const T* t, const T* x, double alpha, T* y,
+                        cudaStream_t s) {
+    return launch_blur<T>(p, o, false, BLUR_FUSE, t, y, o.w, const_cast<T*>(x), const_cast<T*>(x), alpha, nullptr, s);
 }
 
 // ---------------------------------------------------------------- allocation-free normal-equations product
@@ -915,7 +929,9 @@ namespace tvd {
     template tvd_status blur_pupdate<T>(const tvd_plan_s&, const Ops<T>&, const T*, T*, T*, T*, CgState*,       \
                                         cudaStream_t);                                                           \
     template tvd_status normal_finish<T>(const tvd_plan_s&, const Ops<T>&, const T*, const T*, const T*, double, \
-                                         T*, CgState*, cudaStream_t);
+                                         T*, CgState*, cudaStream_t);                                            \
+    template tvd_status forward_fuse<T>(const tvd_plan_s&, const Ops<T>&, const T*, const T*, double, T*,       \
+                                        cudaStream_t);
 INST(float)
 INST(double)
 

@@ -57,10 +57,38 @@ static int pad8(int n) { return (n + 7) / 8 * 8; }
 // Row-major n x n matrix of the 1D transform (row k = basis vector k): AR hat-S_n,
 // R the DCT-II C_n (frequency by space); transposed on request. Arguments are
 // reduced modulo the period in integers; rows padded to ld.
-static void transform_matrix(int n, int ld, tvd_bc bc, bool transpose, std::vector<double>& out) {
+// For the reblurring method (AR): the forward matrix is T_n^-1 =
+// [1 0 0; -S p S -S J p; 0 0 1] and the inverse one T_n = [1 0 0; p S J p; 0 0 1]
+// (eq. (Tn) in the block form of Sec. 2, p_i = 1 - i / (n - 1)).
+static void transform_matrix(int n, int ld, tvd_bc bc, bool transpose, std::vector<double>& out,
+                             bool reblur = false) {
     out.assign((size_t)n * ld, 0.0);
     const double pi = 3.14159265358979323846;
     auto at = [&](int k, int j) -> double& { return transpose ? out[(size_t)j * ld + k] : out[(size_t)k * ld + j]; };
+    if (reblur) {
+        const int m = n - 2, M = n - 1;
+        const double sc = std::sqrt(2.0 / M);
+        auto S = [&](int k, int l) { return sc * std::sin(pi * (double)(((long long)k * l) % (2LL * M)) / M); };
+        out[0] = 1.0;
+        out[(size_t)(n - 1) * ld + n - 1] = 1.0;
+        for (int k = 1; k <= m; ++k) {
+            double sp = 0.0, sjp = 0.0;
+            for (int l = 1; l <= m; ++l) {
+                const double skl = S(k, l);
+                out[(size_t)k * ld + l] = skl;
+                sp += skl * (1.0 - (double)l / M);
+                sjp += skl * ((double)l / M);
+            }
+            if (transpose) {   // T_n
+                out[(size_t)k * ld] = 1.0 - (double)k / M;
+                out[(size_t)k * ld + n - 1] = (double)k / M;
+            } else {           // T_n^-1
+                out[(size_t)k * ld] = -sp;
+                out[(size_t)k * ld + n - 1] = -sjp;
+            }
+        }
+        return;
+    }
     if (bc == TVD_BC_ANTIREFLECTIVE) {
         const int M = n - 1;   // S_{n-2}: sqrt(2/M) sin(k l pi / M), k, l = 1..n-2
         const double sc = std::sqrt(2.0 / M);
@@ -145,7 +173,8 @@ tvd_status gemm_precond_create(tvd_plan_s& p, cudaStream_t s) {
         g->owned.push_back(*ptr);
         return true;
     };
-    const bool sym = p.bc == TVD_BC_ANTIREFLECTIVE;   // hat-S = hat-S^T
+    const bool reblur = p.method == TVD_METHOD_REBLUR;
+    const bool sym = p.bc == TVD_BC_ANTIREFLECTIVE && !reblur;   // hat-S = hat-S^T (T_n is not symmetric)
     if (!alloc(&g->Br, (size_t)p.nr * g->ldr * esz)) return fail(TVD_ENOMEM);
     g->BrT = g->Br;
     if (!sym && !alloc(&g->BrT, (size_t)p.nr * g->ldr * esz)) return fail(TVD_ENOMEM);
@@ -175,7 +204,7 @@ tvd_status gemm_precond_create(tvd_plan_s& p, cudaStream_t s) {
     }
     auto upload = [&](int side, int ld, bool transpose, void* dst) -> bool {
         std::vector<double> B;
-        transform_matrix(side, ld, p.bc, transpose, B);
+        transform_matrix(side, ld, p.bc, transpose, B, reblur);
         cudaError_t e;
         if (g->bf) {
             std::vector<bf16> Bh(B.size());

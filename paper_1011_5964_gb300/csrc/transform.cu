@@ -57,6 +57,11 @@ struct LineArgs {
     const T* scale;      // D^{-1/2} (optional), applied on load (ROW_FWD) or store (ROW_INV)
     const T* spec;       // inv_spec (COL_SOLVE) / lamH2 (COL_EG)
     T* inv_out;          // COL_EG: inv_spec output
+    T* lam_out;          // COL_EG: when set, Lambda_L itself instead of inv_out
+    // reblurring (AR): the rank-2 corrections of T_n = hat-S (I + U), T_n^-1 =
+    // (I - U) hat-S along each line: ucorr[k - 1] = (S p)_k, ucorr[n - 2 + k - 1]
+    // = (S J p)_k for the interior k = 1..n-2 (nullptr: hat-S alone)
+    const T* ucorr;
     const T* rvec;       // ROW_INV: r for r^T z
     const cplx<T>* tw;   // twiddles, length L
     const cplx<T>* blt;  // Bluestein tables (fp.bl): chirp exp(-i pi j^2 / L) (L) | filter spectrum / M2 (M2) | M2 twiddles
@@ -699,6 +704,10 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? TVD_LINE_MINB : 1) 
                 const int g = gline(2 * pp);
                 if (g < 0) continue;
                 const T lamL = go[(size_t)(2 * pp) * ns + idx] + eo[(size_t)(2 * pp + 1) * ns + idx];
+                if (a.lam_out) {
+                    a.lam_out[(size_t)idx * a.nc + g] = lamL;
+                    continue;
+                }
                 const double sp = (double)lam[pp * ns + idx] + a.alpha * (double)lamL;
                 if (!(sp > 1e-300) || !isfinite(sp)) atomicOr(a.bad, 1);
                 a.inv_out[(size_t)idx * a.nc + g] = T(1.0 / sp);
@@ -707,8 +716,22 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? TVD_LINE_MINB : 1) 
         return;
     }
 
+    // reblurring: y -/+= y_0 (S p) + y_{n-1} (S J p) on every line's interior (the
+    // endpoints, which hat-S passes through, are read but not written)
+    auto ucorrect = [&](T sign) {
+        __syncthreads();
+        for (Walk w(n); w.hi < lines; w.next(n)) {
+            const int l = w.hi, idx = w.lo;
+            if (idx == 0 || idx == n - 1 || gline(l) < 0) continue;
+            const int b0 = l * ns;
+            raw[b0 + idx] += sign * (raw[b0] * a.ucorr[idx - 1] + raw[b0 + n - 1] * a.ucorr[n - 2 + idx - 1]);
+        }
+        __syncthreads();
+    };
+    if (BC == BCK_AR && OP == OP_ROW_INV && a.ucorr) ucorrect(T(1));    // T_n = hat-S (I + U): (I + U) first
     if (BC == BCK_AR) dst1_lines<T>(raw, bufA, bufB, a, tw);
     else dct_lines<T>(raw, bufA, bufB, a, tw, OP == OP_ROW_INV);
+    if (BC == BCK_AR && (OP == OP_ROW_FWD || OP == OP_COL_SOLVE) && a.ucorr) ucorrect(T(-1));   // T_n^-1 = (I - U) hat-S
 
     if (OP == OP_COL_SOLVE) {
         for (Walk w(n); w.hi < lines; w.next(n)) {
@@ -716,6 +739,7 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? TVD_LINE_MINB : 1) 
             if (gline(l) >= 0) raw[si] *= ex[si];
         }
         __syncthreads();
+        if (BC == BCK_AR && a.ucorr) ucorrect(T(1));
         if (BC == BCK_AR) dst1_lines<T>(raw, bufA, bufB, a, tw);
         else dct_lines<T>(raw, bufA, bufB, a, tw, true);
         for (int e = threadIdx.x; e < ln; e += kThreads) {
@@ -871,6 +895,7 @@ static LineArgs<T> base_args(const tvd_plan_s& p, const Ops<T>& o, bool cols) {
     a.aux = cols ? o.aux_r : o.aux_c;
     a.red = p.red;
     a.ticket = p.ticket + 2;
+    a.ucorr = p.method == TVD_METHOD_REBLUR ? (cols ? o.ucorr_r : o.ucorr_c) : nullptr;
     return a;
 }
 
@@ -988,8 +1013,131 @@ static tvd_status scaled_spectrum_setup(const tvd_plan_s& p, Ops<T>& o, double a
     return TVD_OK;
 }
 
+// ---------------------------------------------------------------- reblurring spectrum
+//
+// Eigenvalues of the level-2 projection AR_2(X) (Sec. 3.2) from the interior
+// ones, which equal those of the sine projection of X's interior block: along
+// each dimension the two border eigenvalues are the symbol at 0 of the tau
+// matrix with those interior eigenvalues, a fixed linear functional c of them
+// (c from the host). Border columns first (interior rows), then border rows
+// over all columns (so the corners get both functionals).
+template <typename T>
+__global__ void __launch_bounds__(kThreads)
+ar_ext_cols_kernel(T* __restrict__ X, int nr, int nc, const double* __restrict__ cc) {
+    const int lane = threadIdx.x & 31;
+    const int warps = (gridDim.x * blockDim.x) >> 5;
+    for (int i = 1 + ((blockIdx.x * blockDim.x + threadIdx.x) >> 5); i <= nr - 2; i += warps) {
+        const T* row = X + (size_t)i * nc;
+        double acc = 0.0;
+        for (int j = 1 + lane; j <= nc - 2; j += 32) acc += cc[j - 1] * (double)row[j];
+        acc = warp_sum(acc);
+        if (lane == 0) X[(size_t)i * nc] = X[(size_t)i * nc + nc - 1] = T(acc);
+    }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kThreads)
+ar_ext_rows_kernel(T* __restrict__ X, int nr, int nc, const double* __restrict__ cr) {
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < nc; j += gridDim.x * blockDim.x) {
+        double acc = 0.0;
+        for (int i = 1; i <= nr - 2; ++i) acc += cr[i - 1] * (double)X[(size_t)i * nc + j];
+        X[j] = X[(size_t)(nr - 1) * nc + j] = T(acc);
+    }
+}
+
+// lamLt = U1 - 2 U2 - 2 U3 (the scaled-system Lambda_L~ before the extension)
+template <typename T>
+__global__ void __launch_bounds__(kThreads)
+combine_lt_kernel(const T* __restrict__ U1, const T* __restrict__ U2, const T* __restrict__ U3, T* __restrict__ out,
+                  size_t n) {
+    for (size_t o = blockIdx.x * (size_t)blockDim.x + threadIdx.x; o < n; o += (size_t)gridDim.x * blockDim.x)
+        out[o] = T((double)U1[o] - 2.0 * (double)U2[o] - 2.0 * (double)U3[o]);
+}
+
+// 1 / (Lambda_H^2 [Lambda_D^2] + alpha Lambda_L)
+template <typename T>
+__global__ void __launch_bounds__(kThreads)
+reblur_spec_kernel(const T* __restrict__ lamH2, const T* __restrict__ lamL, const T* __restrict__ lamD,
+                   double alpha, T* __restrict__ inv_out, int* bad, size_t n) {
+    for (size_t o = blockIdx.x * (size_t)blockDim.x + threadIdx.x; o < n; o += (size_t)gridDim.x * blockDim.x) {
+        double h2 = (double)lamH2[o];
+        if (lamD) h2 *= (double)lamD[o] * (double)lamD[o];
+        const double sp = h2 + alpha * (double)lamL[o];
+        if (!(sp > 1e-300) || !isfinite(sp)) atomicOr(bad, 1);
+        inv_out[o] = T(1.0 / sp);
+    }
+}
+
+template <typename T>
+static tvd_status ar_extend(const tvd_plan_s& p, const Ops<T>& o, T* X, cudaStream_t s) {
+    const int blocks = num_sms() * 4;
+    ar_ext_cols_kernel<T><<<blocks, kThreads, 0, s>>>(X, p.nr, p.nc, o.extc_c);
+    TVD_CUDA_TRY(cudaGetLastError());
+    ar_ext_rows_kernel<T><<<(p.nc + kThreads - 1) / kThreads, kThreads, 0, s>>>(X, p.nr, p.nc, o.extc_r);
+    TVD_CUDA_TRY(cudaGetLastError());
+    return TVD_OK;
+}
+
+// P / D_P: Lambda_H^2 + alpha Lambda_AR2(L); P_D: Lambda_H^2 Lambda_D^2 + alpha Lambda_L~ with both
+// projections extended (uses o.z, o.p, o.p2, o.q, o.r, o.x, o.t, o.t2 as scratch).
+template <typename T>
+static tvd_status reblur_spectrum_setup(const tvd_plan_s& p, Ops<T>& o, double alpha, int* bad_flag,
+                                        cudaStream_t s) {
+    const size_t n = (size_t)p.nr * p.nc;
+    const int blocks = num_sms() * 4;
+    if (p.pc == TVD_PC_FASTD) {
+        {
+            ProfScope prof(prof_class<T>(PROF_TV), s);
+            scaled_weights_kernel<T><<<blocks, kThreads, 0, s>>>(o.w, o.dmh, o.z, o.p, o.p2, o.q, p.nr, p.nc);
+            TVD_CUDA_TRY(cudaGetLastError());
+        }
+        auto pass = [&](bool cols, const T* in0, const T* in1, T* out0, T* out1, int xa, int xb) -> tvd_status {
+            LineArgs<T> a = base_args<T>(p, o, cols);
+            a.in0 = in0;
+            a.in1 = in1;
+            a.out0 = out0;
+            a.out1 = out1;
+            a.xa = xa;
+            a.xb = xb;
+            return cols ? launch_line<T, BCK_AR, OP_COL_X>(a, s) : launch_line<T, BCK_AR, OP_ROW_X>(a, s);
+        };
+        TVD_TRY(pass(false, o.z, o.p, o.t, o.t2, 0, 0));
+        TVD_TRY(pass(false, o.p2, o.q, o.r, o.x, 1, 0));
+        TVD_TRY(pass(true, o.t, o.t2, o.z, o.p, 0, 1));
+        TVD_TRY(pass(true, o.r, o.x, o.p2, o.q, 0, 0));
+        ProfScope prof(prof_class<T>(PROF_EG_COL), s, 4);
+        combine_lt_kernel<T><<<blocks, kThreads, 0, s>>>(o.z, o.p, o.p2, o.t, n);
+        TVD_CUDA_TRY(cudaGetLastError());
+        TVD_TRY(ar_extend<T>(p, o, o.t, s));     // Lambda_L~
+        TVD_TRY(ar_extend<T>(p, o, o.q, s));     // Lambda_D
+        reblur_spec_kernel<T><<<blocks, kThreads, 0, s>>>(o.lamH2, o.t, o.q, alpha, o.inv_spec, bad_flag, n);
+        TVD_CUDA_TRY(cudaGetLastError());
+        return TVD_OK;
+    }
+    LineArgs<T> a = base_args<T>(p, o, false);
+    a.in0 = o.w;
+    a.out0 = o.t;
+    a.out1 = o.t2;
+    LineArgs<T> c = base_args<T>(p, o, true);
+    c.in0 = o.t;
+    c.in1 = o.t2;
+    c.spec = o.lamH2;
+    c.lam_out = o.z;
+    c.alpha = alpha;
+    c.bad = bad_flag;
+    TVD_TRY((launch_line<T, BCK_AR, OP_ROW_EG>(a, s)));
+    TVD_TRY((launch_line<T, BCK_AR, OP_COL_EG>(c, s)));
+    ProfScope prof(prof_class<T>(PROF_EG_COL), s, 3);
+    TVD_TRY(ar_extend<T>(p, o, o.z, s));
+    reblur_spec_kernel<T><<<blocks, kThreads, 0, s>>>(o.lamH2, o.z, (const T*)nullptr, alpha, o.inv_spec, bad_flag,
+                                                       n);
+    TVD_CUDA_TRY(cudaGetLastError());
+    return TVD_OK;
+}
+
 template <typename T>
 tvd_status spectrum_setup(const tvd_plan_s& p, Ops<T>& o, double alpha, int* bad_flag, cudaStream_t s) {
+    if (p.method == TVD_METHOD_REBLUR) return reblur_spectrum_setup<T>(p, o, alpha, bad_flag, s);
     if (p.pc == TVD_PC_FASTD) return scaled_spectrum_setup<T>(p, o, alpha, bad_flag, s);
     LineArgs<T> a = base_args<T>(p, o, false);
     a.in0 = o.w;

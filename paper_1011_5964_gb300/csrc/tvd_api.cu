@@ -248,6 +248,7 @@ static void plan_free(tvd_plan_s* p) {
     if (p->cap_stream) cudaStreamDestroy(p->cap_stream);
     p->cap_stream = nullptr;
     gemm_precond_destroy(*p);
+    reblur_free(*p);
     ops_free(p->d);
     ops_free(p->f);
     dfree(p->state); dfree(p->red); dfree(p->ticket); dfree(p->scal);
@@ -655,6 +656,13 @@ static tvd_status solve_mixed(tvd_plan_s& p, double alpha, const double* b, doub
 
 static tvd_status solve(tvd_plan_s& p, const double* u_lag, double alpha, double beta, const double* b, double* x,
                         double tol, int maxit, SolveResult* res, cudaStream_t s, bool cached_hx = false) {
+    if (p.method == TVD_METHOD_REBLUR) {
+        // eq. (fpp): the preconditioner of the reblurring method, then PBiCGstab
+        if (p.mode == TVD_MODE_FP64) TVD_TRY(setup_precond<double>(p, p.d, u_lag, alpha, beta, s));
+        else TVD_TRY(setup_mixed(p, u_lag, alpha, beta, s));
+        TVD_TRY(reblur_solve(p, alpha, b, x, tol, maxit, &res->iters, &res->sweeps, &res->relres, &res->status, s));
+        return p.mode == TVD_MODE_MIXED ? gemm_precond_check(p, s) : TVD_OK;
+    }
     if (p.mode == TVD_MODE_FP64) {
         TVD_TRY(setup_precond<double>(p, p.d, u_lag, alpha, beta, s));
         CgState cs;
@@ -1073,10 +1081,66 @@ tvd_status tau_precond_solve(tvd_plan plan, const void* r, void* z, void* stream
     return precond_solve<float>(*plan, o, (const float*)r, (float*)z, nullptr, s);
 }
 
+tvd_status tvd_plan_set_method(tvd_plan plan, int method, void* stream) {
+    if (!plan || (method != TVD_METHOD_FP && method != TVD_METHOD_REBLUR)) {
+        set_error("tvd_plan_set_method: invalid argument");
+        return TVD_EINVAL;
+    }
+    if (method == TVD_METHOD_REBLUR && plan->bc != TVD_BC_ANTIREFLECTIVE) {
+        set_error("tvd_plan_set_method: the reblurring method needs anti-reflective BCs (Sec. 3)");
+        return TVD_EINVAL;
+    }
+    if (plan->method == method) return TVD_OK;
+    cudaStream_t s = (cudaStream_t)stream;
+    TVD_CUDA_TRY(cudaStreamSynchronize(s));
+    if (method == TVD_METHOD_REBLUR) TVD_TRY(reblur_tables(*plan, s));
+    plan->method = method;
+    plan->precond_ready = false;
+    if (plan->gemm) {
+        // the transform matrices follow the method: rebuild them
+        TVD_CUDA_TRY(cudaDeviceSynchronize());
+        gemm_precond_destroy(*plan);
+        for (auto& g : plan->graph)
+            if (g.exec) {
+                cudaGraphExecDestroy(g.exec);
+                g.exec = nullptr;
+            }
+        TVD_TRY(gemm_precond_create(*plan, s));
+    }
+    return TVD_OK;
+}
+
+int tvd_plan_method(tvd_plan plan) { return plan ? plan->method : TVD_METHOD_FP; }
+
+tvd_status pbicgstab_solve(tvd_plan plan, const void* u_lag, double alpha, double beta, const void* b,
+                           void* x_inout, double tol, int maxit, int* iters, double* relres, void* stream) {
+    if (!plan || !u_lag || !b || !x_inout || !(alpha >= 0.0) || !(beta > 0.0) || !(tol > 0.0) || maxit < 0) {
+        set_error("pbicgstab_solve: invalid argument");
+        return TVD_EINVAL;
+    }
+    if (plan->method != TVD_METHOD_REBLUR) {
+        set_error("pbicgstab_solve: the plan solves eq. (fp); call tvd_plan_set_method(plan, TVD_METHOD_REBLUR)");
+        return TVD_EINVAL;
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    SolveResult r;
+    TVD_TRY(solve(*plan, (const double*)u_lag, alpha, beta, (const double*)b, (double*)x_inout, tol, maxit, &r, s));
+    if (iters) *iters = r.iters;
+    if (relres) *relres = r.relres;
+    if (r.status != TVD_OK)
+        set_error(r.status == TVD_ENOCONV ? "pbicgstab_solve: tolerance not reached within maxit"
+                                          : "pbicgstab_solve: BiCGstab breakdown (zero rho, r^T v or t^T t)");
+    return r.status;
+}
+
 tvd_status pcg_solve(tvd_plan plan, const void* u_lag, double alpha, double beta, const void* b, void* x_inout,
                      double tol, int maxit, int* iters, double* relres, void* stream) {
     if (!plan || !u_lag || !b || !x_inout || !(alpha >= 0.0) || !(beta > 0.0) || !(tol > 0.0) || maxit < 0) {
         set_error("pcg_solve: invalid argument");
+        return TVD_EINVAL;
+    }
+    if (plan->method == TVD_METHOD_REBLUR) {
+        set_error("pcg_solve: the plan solves eq. (fpp) (not symmetric); use pbicgstab_solve");
         return TVD_EINVAL;
     }
     cudaStream_t s = (cudaStream_t)stream;
@@ -1103,8 +1167,9 @@ tvd_status tv_deblur(tvd_plan plan, const void* v, double alpha, double beta, in
     const size_t n = (size_t)p.nr * p.nc;
     double* u = (double*)u_out;
     p.hx_for = nullptr;
-    // b = H^T v (into p.xd), u^0 = v
-    TVD_TRY(blur_apply<double>(p, p.d, true, (const double*)v, p.xd, s));
+    // b = H^T v (eq. (fp)) or H' v = H v (eq. (fpp), symmetric PSF) into p.xd; u^0 = v
+    const bool reblur = p.method == TVD_METHOD_REBLUR;
+    TVD_TRY(blur_apply<double>(p, p.d, !reblur, (const double*)v, p.xd, s));
     if (u != (const double*)v) TVD_CUDA_TRY(cudaMemcpyAsync(u, v, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
     if (stats) {
         stats->outer_iters = 0;
@@ -1120,7 +1185,7 @@ tvd_status tv_deblur(tvd_plan plan, const void* v, double alpha, double beta, in
         SolveResult r;
         // u_lag = u^k (kept in p.tmp), x starts at u^k and becomes u^{k+1} in place
         // from the second step on, H^T H u^k is known from the previous step's last residual check
-        TVD_TRY(solve(p, p.tmp, alpha, beta, p.xd, u, inner_tol, inner_maxit, &r, s, k > 0));
+        TVD_TRY(solve(p, p.tmp, alpha, beta, p.xd, u, inner_tol, inner_maxit, &r, s, k > 0 && !reblur));
         double h2[2];
         TVD_TRY(diffnorm2_d(p, u, p.tmp, p.scal + 2, s));
         TVD_TRY(norm2_d(p, u, p.scal + 3, s));

@@ -153,6 +153,13 @@ struct Ops {
     cplx<T>* blt_r = nullptr;
     T* aux_c = nullptr;      // see transform.cu: per-length auxiliary factors
     T* aux_r = nullptr;
+    // reblurring (AR, eq. (fpp)): per line length the rank-2 correction vectors
+    // S p | S J p of T_n = hat-S (I + U) (2 (n - 2) each), and the weights c of
+    // the border eigenvalues of AR(.) (n - 2 doubles each)
+    T* ucorr_r = nullptr;    // lines along columns (length n_rows)
+    T* ucorr_c = nullptr;    // lines along rows (length n_cols)
+    double* extc_r = nullptr;
+    double* extc_c = nullptr;
     // preconditioner data
     T* lamH2 = nullptr;      // Lambda_H^2
     T* inv_spec = nullptr;   // 1 / (Lambda_H^2 + alpha Lambda_L)
@@ -182,6 +189,7 @@ struct Psf {
 
 struct tvd_plan_s {
     int nr = 0, nc = 0;
+    int method = 0;                     // tvd_method: TVD_METHOD_FP (eq. (fp), PCG) or TVD_METHOD_REBLUR
     tvd_bc bc = TVD_BC_ANTIREFLECTIVE;
     tvd_precond pc = TVD_PC_DFAST;
     tvd_mode mode = TVD_MODE_FP64;
@@ -217,6 +225,8 @@ struct tvd_plan_s {
     // dense-matrix (GEMM) form of the preconditioner transforms, MIXED plans
     // with a fast preconditioner only (gemm_precond.cu); nullptr: FFT form
     void* gemm = nullptr;
+    // BiCGstab state and vectors of the reblurring method (reblur.cu)
+    void* bicg = nullptr;
 };
 
 namespace tvd {
@@ -247,6 +257,24 @@ tvd_status tv_apply(const tvd_plan_s& p, const T* w, const T* x, T* y, cudaStrea
 template <typename T>
 tvd_status normal_finish(const tvd_plan_s& p, const Ops<T>& o, const T* t, const T* p0, const T* p1, double alpha,
                          T* q, CgState* st, cudaStream_t s);
+
+// y = H t + alpha L(w) x (forward blur of t fused with the TV operator of x):
+// with t = H x, the product H' H x + alpha L x of eq. (fpp).
+template <typename T>
+tvd_status forward_fuse(const tvd_plan_s& p, const Ops<T>& o, const T* t, const T* x, double alpha, T* y,
+                        cudaStream_t s);
+
+// Reblurring, eq. (fpp) (reblur.cu): the plan's correction and extension
+// tables, y = H' H x + alpha L x (hx: scratch), one FP step's PBiCGstab solve
+// (FP64, or float BiCGstab inside double refinement for MIXED plans) with the
+// preconditioner already set up, and the release of its resources.
+tvd_status reblur_tables(tvd_plan_s& p, cudaStream_t s);
+template <typename T>
+tvd_status reblur_matvec(const tvd_plan_s& p, const Ops<T>& o, const T* x, T* hx, T* y, double alpha,
+                         cudaStream_t s);
+tvd_status reblur_solve(tvd_plan_s& p, double alpha, const double* b, double* x, double tol, int maxit, int* iters,
+                        int* sweeps, double* relres, tvd_status* status, cudaStream_t s);
+void reblur_free(tvd_plan_s& p);
 
 // CG direction update fused with the forward blur: p_new = z (fresh) or
 // z + beta p_old, with p_old / p_new the two direction buffers chosen by

@@ -76,3 +76,14 @@ def test_batched_argument_checks_without_gpu(lib):
     assert lib.tv_deblur_batched(items, 1, 10, 1e-6, 100, 0, None) == pkg.TVD_EINVAL   # null plan
     assert lib.tv_deblur_batched(items, 1, 10, 0.0, 100, 0, None) == pkg.TVD_EINVAL    # tol <= 0
     assert lib.tv_deblur_batched(items, 1, 10, 1e-6, 100, 65, None) == pkg.TVD_EINVAL  # workers > 64
+
+
+def test_reblur_entry_points_validate_without_gpu(lib):
+    """The reblurring entry points refuse a NULL plan or an unknown method before any CUDA call."""
+    import ctypes
+    import paper_1011_5964_gb300 as pkg
+    assert lib.tvd_plan_set_method(None, 1, None) == pkg.TVD_EINVAL
+    assert lib.tvd_plan_method(None) == pkg.METHOD["fp"]
+    it, rr = ctypes.c_int(), ctypes.c_double()
+    assert lib.pbicgstab_solve(None, None, 1e-3, 1e-2, None, None, 1e-6, 10, ctypes.byref(it), ctypes.byref(rr),
+                               None) == pkg.TVD_EINVAL
