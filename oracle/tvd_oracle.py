@@ -18,7 +18,7 @@ deblurring with anti-reflective boundary conditions"):
 * PCG: Golub & Van Loan, Algorithm 10.3.1, as cited in Sec. 1, with the stopping
   rule ||r_k|| / ||r_0|| < tol of Sec. 5.
 
-Readings where the paper is silent or garbled (each also listed in the design doc):
+Readings where the paper is silent or garbled:
 
 * L(u) is discretised as D_r^T W D_r + D_c^T W D_c with forward differences that
   vanish on the last row / column (zero Neumann, eq. (el)), W = diag(psi^-1),
@@ -825,13 +825,65 @@ def jacobian_apply(u, h, bc, alpha, beta, x):
     return blur_adjoint(blur(x, h, bc), h, bc) + alpha * tv_hessian_apply(u, beta, x)
 
 
-def adjoint_solve(u, h, bc, alpha, beta, rhs, tol=1e-12, maxit=20000):
-    """lambda with J(u) lambda = rhs, by the PCG of Algorithm 10.3.1 (no preconditioner), from 0.
+def adjoint_solve(u, h, bc, alpha, beta, rhs, tol=1e-12, maxit=20000, kind=PC_NONE):
+    """lambda with J(u) lambda = rhs, by the PCG of Algorithm 10.3.1, from 0.
 
+    ``kind`` picks the preconditioner: the FP step's one at u (``precond_setup``,
+    built for H^T H + alpha L(u), which bounds J from above); PC_NONE by default.
     Returns (lambda, iterations, ||r|| / ||r_0||, converged).
     """
     rhs = np.asarray(rhs, dtype=np.float64)
-    return pcg(lambda y: jacobian_apply(u, h, bc, alpha, beta, y), lambda r: r, rhs, np.zeros_like(rhs), tol, maxit)
+    P = precond_setup(u, h, bc, alpha, beta, kind)
+    return pcg(lambda y: jacobian_apply(u, h, bc, alpha, beta, y), lambda r: precond_apply(r, P), rhs,
+               np.zeros_like(rhs), tol, maxit)
+
+
+def newton_polish(u, v, h, bc, alpha, beta, tol=1e-10, max_steps=30, cg_tol=1e-12, maxit=20000,
+                  kind=PC_DFAST):
+    """Finish the fixed point of eq. (fp) by Newton's method on g(u) = 0, eq. (el).
+
+    Not a step of the paper: the lagged-diffusivity iteration converges only
+    linearly, and the adjoint needs u* to a tolerance it reaches slowly. From an
+    FP iterate u each step solves J(u) d = g(u) (``adjoint_solve`` with the FP
+    step's preconditioner at u, to ||r|| / ||r_0|| < cg_tol) and moves to
+    u - t d, where t = 1, halved while ||g(u - t d)|| >= ||g(u)|| (at most 10
+    times; a step that never lowers ||g|| ends the loop, unconverged). The loop
+    stops after the step with ||t d|| / ||u - t d|| < tol (converged), or after
+    max_steps. Returns (u, stats): per step the relative change, ||g|| before the
+    step, the step length t and the CG iterations; ``converged``; and ``g_norm``
+    of the returned u.
+    """
+    u = np.array(u, dtype=np.float64, copy=True)
+    v = np.asarray(v, dtype=np.float64)
+    g = euler_lagrange(u, v, h, bc, alpha, beta)
+    gn = float(np.linalg.norm(g))
+    stats = {"rel_change": [], "g_norm": [], "t": [], "cg_iters": [], "converged": False}
+    for _ in range(max_steps):
+        if gn == 0.0:
+            stats["converged"] = True
+            break
+        d, k, _, _ = adjoint_solve(u, h, bc, alpha, beta, g, cg_tol, maxit, kind)
+        t = 1.0
+        for _ in range(11):
+            u_new = u - t * d
+            g_new = euler_lagrange(u_new, v, h, bc, alpha, beta)
+            gn_new = float(np.linalg.norm(g_new))
+            if gn_new < gn:
+                break
+            t *= 0.5
+        else:
+            break
+        change = t * float(np.linalg.norm(d)) / max(float(np.linalg.norm(u_new)), 1e-300)
+        stats["rel_change"].append(change)
+        stats["g_norm"].append(gn)
+        stats["t"].append(t)
+        stats["cg_iters"].append(k)
+        u, g, gn = u_new, g_new, gn_new
+        if change < tol:
+            stats["converged"] = True
+            break
+    stats["g_norm_final"] = gn
+    return u, stats
 
 
 def unit_psf(h, a, b):
