@@ -326,6 +326,8 @@ def symbol_grid(n: int, bc: str) -> np.ndarray:
     y = k pi / (n-1). R: DCT-II frequency k takes y = k pi / n.
     """
     k = np.arange(n, dtype=np.float64)
+    if n == 1:
+        return np.zeros(1)     # a single sample (a 1D signal's row axis): the constant, y = 0
     if bc == AR:
         y = k * np.pi / (n - 1)
         y[0] = 0.0
@@ -644,6 +646,8 @@ def ar_projection(A: np.ndarray) -> np.ndarray:
     zero but for the corners."""
     A = np.asarray(A, dtype=np.float64)
     n = A.shape[0]
+    if n == 1:
+        return A.copy()        # every 1 x 1 matrix is in the algebra (T_1 = 1)
     m = n - 2
     S = _sine(m)
     inner = A[1:-1, 1:-1]
@@ -690,15 +694,16 @@ def ar_extension(m: int) -> np.ndarray:
 
 def ar_extend2(lam: np.ndarray) -> np.ndarray:
     """Eigenvalues of AR_2 from the interior ones: border rows / columns are the c-weighted sums of
-    the interior along that dimension (AR(.) per level), corners along both."""
+    the interior along that dimension (AR(.) per level), corners along both. A dimension of length
+    1 (a 1D signal's row axis) has no border to extend: there the projection is the identity."""
     nr, nc = lam.shape
-    cr, cc = ar_extension(nr - 2), ar_extension(nc - 2)
-    inner = lam[1:-1, 1:-1]
-    out = np.empty_like(lam)
-    out[1:-1, 1:-1] = inner
-    out[0, 1:-1] = out[-1, 1:-1] = cr @ inner
-    out[1:-1, 0] = out[1:-1, -1] = inner @ cc
-    out[0, 0] = out[0, -1] = out[-1, 0] = out[-1, -1] = cr @ inner @ cc
+    out = np.array(lam, dtype=np.float64, copy=True)
+    rows = slice(1, nr - 1) if nr > 1 else slice(0, 1)
+    cc = ar_extension(nc - 2)
+    out[rows, 0] = out[rows, -1] = out[rows, 1:-1] @ cc
+    if nr > 1:
+        cr = ar_extension(nr - 2)
+        out[0, :] = out[-1, :] = cr @ out[1:-1, :]
     return out
 
 
@@ -847,11 +852,13 @@ def newton_polish(u, v, h, bc, alpha, beta, tol=1e-10, max_steps=30, cg_tol=1e-1
     FP iterate u each step solves J(u) d = g(u) (``adjoint_solve`` with the FP
     step's preconditioner at u, to ||r|| / ||r_0|| < cg_tol) and moves to
     u - t d, where t = 1, halved while ||g(u - t d)|| >= ||g(u)|| (at most 10
-    times; a step that never lowers ||g|| ends the loop, unconverged). The loop
-    stops after the step with ||t d|| / ||u - t d|| < tol (converged), or after
-    max_steps. Returns (u, stats): per step the relative change, ||g|| before the
-    step, the step length t and the CG iterations; ``converged``; and ``g_norm``
-    of the returned u.
+    times; a step that never lowers ||g|| ends the loop, unconverged). A full
+    step with ||d|| / ||u - d|| < tol is taken as it is: there ||g|| sits at
+    its rounding floor and need not fall. The loop stops after the step with
+    ||t d|| / ||u - t d|| < tol (converged), or after max_steps. Returns
+    (u, stats): per step the relative change, ||g|| before the step, the step
+    length t and the CG iterations; ``converged``; and ``g_norm_final`` of the
+    returned u.
     """
     u = np.array(u, dtype=np.float64, copy=True)
     v = np.asarray(v, dtype=np.float64)
@@ -864,11 +871,12 @@ def newton_polish(u, v, h, bc, alpha, beta, tol=1e-10, max_steps=30, cg_tol=1e-1
             break
         d, k, _, _ = adjoint_solve(u, h, bc, alpha, beta, g, cg_tol, maxit, kind)
         t = 1.0
-        for _ in range(11):
+        for k in range(11):
             u_new = u - t * d
             g_new = euler_lagrange(u_new, v, h, bc, alpha, beta)
             gn_new = float(np.linalg.norm(g_new))
-            if gn_new < gn:
+            tiny = k == 0 and float(np.linalg.norm(d)) < tol * float(np.linalg.norm(u_new))
+            if gn_new < gn or tiny:
                 break
             t *= 0.5
         else:

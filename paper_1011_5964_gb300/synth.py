@@ -119,3 +119,44 @@ def batch_items(count: int = 96, seed: int = 1000,
         items.append({"n": n, "sigma": sigma, "alpha": alpha, "beta": 1e-2,
                       "noise": 0.01, "seed": seed + i})
     return items
+
+
+def piecewise_constant_signal(n: int, seed: int, margin: float = 0.125, n_jumps: int = 9) -> tuple[np.ndarray, slice]:
+    """1D piecewise-constant signal on a support wider than the field of view.
+
+    The paper's 1D experiment (Sec. 5.1) restores a signal on [0, 1] observed in
+    the field of view [0.1, 0.9], the parts outside being left to the boundary
+    conditions; its true signal is only shown in a figure, so the jumps are
+    drawn at random. Returns (u_wide, fov): u_wide has n + 2 k samples, k =
+    round(margin n), with ``n_jumps`` jump positions uniform over the support
+    and levels U[0, 1] between them; fov = slice(k, k + n) selects the n
+    samples of the field of view. Blur u_wide, then keep ``[fov]``: the
+    observation then depends on the signal outside the field of view as a
+    physical blur does, not on a boundary model (this needs the PSF half-width
+    to be at most k).
+    """
+    k = int(round(margin * n))
+    N = n + 2 * k
+    rng = np.random.default_rng(seed)
+    cuts = np.sort(rng.integers(1, N, size=n_jumps))
+    levels = rng.uniform(0.0, 1.0, size=n_jumps + 1)
+    u = np.empty(N)
+    edges = np.concatenate([[0], cuts, [N]])
+    for q in range(n_jumps + 1):
+        u[edges[q]:edges[q + 1]] = levels[q]
+    return u, slice(k, k + n)
+
+
+def out_of_focus_psf_1d(m: int) -> np.ndarray:
+    """The 1D out-of-focus PSF of eq. (of): h_i = c for |i| < m, else 0, sum 1,
+    as a (1, 2m - 1) array (a PSF of one row for the 2D plans)."""
+    if m < 1:
+        raise ValueError("m must be at least 1")
+    return np.full((1, 2 * m - 1), 1.0 / (2 * m - 1))
+
+
+def alpha_grid(lo: float = 1e-6, hi: float = 1e-1, per_decade: int = 2) -> list[float]:
+    """Log-spaced regularisation parameters from lo to hi (inclusive), ``per_decade``
+    values per decade: the abscissa of an RRE-versus-alpha sweep (Sec. 5.1)."""
+    k = int(round(math.log10(hi / lo) * per_decade))
+    return [float(lo * 10.0 ** (i / per_decade)) for i in range(k + 1)]
