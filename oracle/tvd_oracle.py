@@ -250,6 +250,54 @@ def tv_apply(w: np.ndarray, y: np.ndarray) -> np.ndarray:
     return grad_r_T(w * grad_r(y)) + grad_c_T(w * grad_c(y))
 
 
+def tv_apply_ar(w: np.ndarray, y: np.ndarray) -> np.ndarray:
+    """L_AR y: the lagged-diffusivity operator with anti-reflective BCs (the remark after
+    eq. (scalereb); the "AR L" of Tables 1-1 and 2-1).
+
+    Reading: y is extended by one pixel on every side with the rule of eq. (anti1d),
+    y_{-1} = 2 y_0 - y_1 and y_n = 2 y_{n-1} - y_{n-2} along each axis, the diffusivity
+    at a ghost pixel is that of its neighbour inside (in 1D this is exactly the AR
+    extension of u, whose difference across the border repeats the first inner one),
+    and every pixel of the image takes the full divergence-form stencil
+    (L y)_i = w_{i-1} (y_i - y_{i-1}) - w_i (y_{i+1} - y_i) along each axis. On the
+    first and last line of an axis the two differences are equal and the weights too,
+    so that axis contributes nothing there: L_AR has the interior rows of L and is not
+    symmetric.
+    """
+    w = np.asarray(w, dtype=np.float64)
+    y = np.asarray(y, dtype=np.float64)
+    nr, nc = y.shape
+    out = np.zeros_like(y)
+
+    def axis_terms(ya, wa):
+        # ya, wa: lines along axis 0 of length n; returns the divergence-form terms
+        n = ya.shape[0]
+        if n == 1:
+            return np.zeros_like(ya)
+        ye = np.concatenate([2 * ya[:1] - ya[1:2], ya, 2 * ya[-1:] - ya[-2:-1]], axis=0)   # eq. (anti1d)
+        # forward-difference weights w_k for k = -1 .. n-1 (pair (k, k+1)); ghosts copy the neighbour
+        we = np.concatenate([wa[:1], wa[:-1], wa[-2:-1]], axis=0)
+        fwd = we * (ye[1:] - ye[:-1])            # w_k (y_{k+1} - y_k), k = -1 .. n-1
+        return fwd[:-1] - fwd[1:]                # w_{i-1}(y_i - y_{i-1}) - w_i(y_{i+1} - y_i)
+
+    out += axis_terms(y, w)
+    out += axis_terms(y.T, w.T).T
+    return out
+
+
+def tv_diag_ar(w: np.ndarray) -> np.ndarray:
+    """diag(L_AR): the 5-point stencil's diagonal, each axis's pair of weights dropped on its first
+    and last line (see ``tv_apply_ar``)."""
+    w = np.asarray(w, dtype=np.float64)
+    nr, nc = w.shape
+    d = np.zeros_like(w)
+    if nr > 2:
+        d[1:-1, :] += w[1:-1, :] + w[:-2, :]
+    if nc > 2:
+        d[:, 1:-1] += w[:, 1:-1] + w[:, :-2]
+    return d
+
+
 def tv_diag(w: np.ndarray) -> np.ndarray:
     """diag(L) for the diffusivity w: the sum of the coefficients of the 5-point stencil."""
     w = np.asarray(w, dtype=np.float64)
@@ -430,8 +478,8 @@ def precond_setup(u_lag, h, bc, alpha, beta, kind, method="fp"):
     With method = METHOD_REBLUR (eq. (fpp), AR BCs) the fast kinds are the
     reblurring preconditioners P, D_P, P_D of Sec. 3 (see reblur_setup).
     """
-    if method == METHOD_REBLUR:
-        return reblur_setup(u_lag, h, bc, alpha, beta, kind)
+    if method in REBLUR_METHODS:
+        return reblur_setup(u_lag, h, bc, alpha, beta, kind, arl=method == METHOD_REBLUR_ARL)
     w = diffusivity(u_lag, beta)
     nr, nc = w.shape
     D = 1.0 + alpha * tv_diag(w)
@@ -545,11 +593,12 @@ def pcg(apply_A, apply_M, b, x0, tol, maxit, hist=None, noise=None):
 def fp_step(u, b, h, bc, alpha, beta, kind, tol, maxit, hist=None, noise=None, method="fp"):
     """One lagged-diffusivity step from x0 = u: solve (H^T H + alpha L(u)) x = H^T v by PCG
     (eq. (fp)), or with method = METHOD_REBLUR (H' H + alpha L(u)) x = H' v by PBiCGstab
-    (eq. (fpp)); b is the right-hand side."""
+    (eq. (fpp)); METHOD_REBLUR_ARL puts L_AR(u) in place of L(u). b is the right-hand side."""
     P = precond_setup(u, h, bc, alpha, beta, kind, method)
     w = P["w"]
-    if method == METHOD_REBLUR:
-        return bicgstab(lambda y: reblur_apply(y, h, bc, w, alpha),
+    if method in REBLUR_METHODS:
+        arl = method == METHOD_REBLUR_ARL
+        return bicgstab(lambda y: reblur_apply(y, h, bc, w, alpha, arl),
                         lambda r: precond_apply(r, P), b, u, tol, maxit, hist, noise)
     return pcg(lambda y: normal_apply(y, h, bc, w, alpha),
                lambda r: precond_apply(r, P), b, u, tol, maxit, hist, noise)
@@ -563,10 +612,11 @@ def tv_deblur(v, h, bc, alpha, beta, outer=10, tol=1e-6, maxit=1000,
     < outer_tol (if outer_tol > 0). Returns (u, stats) where stats holds the
     per-step inner iteration counts, residuals, relative changes and the
     relative residuals of the last two inner iterations of each step. With
-    method = METHOD_REBLUR each step solves eq. (fpp) by PBiCGstab (Sec. 5).
+    method = METHOD_REBLUR each step solves eq. (fpp) by PBiCGstab (Sec. 5); METHOD_REBLUR_ARL
+    does the same with L_AR in place of L (``tv_apply_ar``).
     """
     v = np.asarray(v, dtype=np.float64)
-    b = reblur_rhs(v, h, bc) if method == METHOD_REBLUR else blur_adjoint(v, h, bc)
+    b = reblur_rhs(v, h, bc) if method in REBLUR_METHODS else blur_adjoint(v, h, bc)
     u = v.copy()
     stats = {"inner_iters": [], "relres": [], "rel_change": [], "converged": [], "relres_tail": []}
     for _ in range(outer):
@@ -594,6 +644,8 @@ def tv_deblur(v, h, bc, alpha, beta, outer=10, tol=1e-6, maxit=1000,
 
 METHOD_FP = "fp"
 METHOD_REBLUR = "reblur"
+METHOD_REBLUR_ARL = "reblur_arl"     # eq. (fpp) with L_AR (the "AR+Reblur+AR L" columns)
+REBLUR_METHODS = (METHOD_REBLUR, METHOD_REBLUR_ARL)
 
 
 def rotated_psf(h: np.ndarray) -> np.ndarray:
@@ -601,9 +653,9 @@ def rotated_psf(h: np.ndarray) -> np.ndarray:
     return np.asarray(h, dtype=np.float64)[::-1, ::-1].copy()
 
 
-def reblur_apply(x, h, bc, w, alpha) -> np.ndarray:
-    """A' x = H' H x + alpha L(w) x, the matrix of eq. (fpp)."""
-    return blur(blur(x, h, bc), rotated_psf(h), bc) + alpha * tv_apply(w, x)
+def reblur_apply(x, h, bc, w, alpha, arl=False) -> np.ndarray:
+    """A' x = H' H x + alpha L(w) x, the matrix of eq. (fpp); with arl, L is L_AR (``tv_apply_ar``)."""
+    return blur(blur(x, h, bc), rotated_psf(h), bc) + alpha * (tv_apply_ar(w, x) if arl else tv_apply(w, x))
 
 
 def reblur_rhs(v, h, bc) -> np.ndarray:
@@ -707,17 +759,22 @@ def ar_extend2(lam: np.ndarray) -> np.ndarray:
     return out
 
 
-def reblur_setup(u_lag, h, bc, alpha, beta, kind):
+def reblur_setup(u_lag, h, bc, alpha, beta, kind, arl=False):
     """Preconditioner of eq. (fpp) (AR BCs): P = H' H + alpha AR_2(L) (eigenvalues Lambda_H^2 +
     alpha Lambda_AR2(L) in the T_n (x) T_n basis: H' = H for a symmetric PSF and H is in the AR
     algebra), D_P = D^1/2 P D^1/2, or P_D = H^' H^ + alpha AR_2(L~), H^ = H AR_2(D^-1/2), applied as
-    D^1/2 P_D D^1/2 (eigenvalues Lambda_H^2 Lambda_D^2 + alpha Lambda_L~)."""
+    D^1/2 P_D D^1/2 (eigenvalues Lambda_H^2 Lambda_D^2 + alpha Lambda_L~).
+
+    With arl (L_AR of ``tv_apply_ar`` in the system): D = I + alpha diag(L_AR), eq. (D) for that
+    L. AR_2(.) reads only the interior block of its argument, where L_AR equals L, so the
+    eigenvalues are those of the Neumann L."""
     if bc != AR:
         raise ValueError("the reblurring preconditioners are defined for anti-reflective BCs")
     w = diffusivity(u_lag, beta)
     nr, nc = w.shape
-    D = 1.0 + alpha * tv_diag(w)
-    P = {"kind": kind, "bc": bc, "w": w, "D": D, "alpha": alpha, "method": METHOD_REBLUR}
+    D = 1.0 + alpha * (tv_diag_ar(w) if arl else tv_diag(w))
+    P = {"kind": kind, "bc": bc, "w": w, "D": D, "alpha": alpha,
+         "method": METHOD_REBLUR_ARL if arl else METHOD_REBLUR}
     if kind in (PC_FAST, PC_DFAST, PC_FASTD):
         lam_h = spectrum_H(h, nr, nc, AR)
         if kind == PC_FASTD:
