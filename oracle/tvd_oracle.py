@@ -928,11 +928,11 @@ def newton_polish(u, v, h, bc, alpha, beta, tol=1e-10, max_steps=30, cg_tol=1e-1
             break
         d, k, _, _ = adjoint_solve(u, h, bc, alpha, beta, g, cg_tol, maxit, kind)
         t = 1.0
-        for k in range(11):
+        for halving in range(11):
             u_new = u - t * d
             g_new = euler_lagrange(u_new, v, h, bc, alpha, beta)
             gn_new = float(np.linalg.norm(g_new))
-            tiny = k == 0 and float(np.linalg.norm(d)) < tol * float(np.linalg.norm(u_new))
+            tiny = halving == 0 and float(np.linalg.norm(d)) < tol * float(np.linalg.norm(u_new))
             if gn_new < gn or tiny:
                 break
             t *= 0.5

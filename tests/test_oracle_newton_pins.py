@@ -111,3 +111,14 @@ def test_newton_polish_at_a_stationary_point_takes_no_step():
     u2, st = O.newton_polish(u, v, h, O.R, alpha, beta, tol=1e-9)
     assert st["converged"] and len(st["rel_change"]) <= 1
     assert np.linalg.norm(u2 - u) <= 1e-12 * np.linalg.norm(u)
+
+
+def test_newton_stats_count_the_cg_iterations():
+    """The reported CG iterations of each Newton step are those of its Jacobian solve."""
+    h, _, v = _problem(12, O.AR)
+    alpha, beta = 0.05, 0.1
+    u3, _ = O.tv_deblur(v, h, O.AR, alpha, beta, outer=3, tol=1e-10, maxit=5000)
+    _, st = O.newton_polish(u3, v, h, O.AR, alpha, beta, tol=1e-12, kind=O.PC_NONE)
+    g = O.euler_lagrange(u3, v, h, O.AR, alpha, beta)
+    _, k, _, _ = O.adjoint_solve(u3, h, O.AR, alpha, beta, g, 1e-12, 20000, O.PC_NONE)
+    assert st["cg_iters"][0] == k and k > 10
