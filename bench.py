@@ -208,10 +208,11 @@ def batched_leg(pkg, torch, dev, synth):
             "timing": "host clock around the call, inputs resident"}
 
 
-def size_leg(pkg, torch, dev, synth, n, steps=2, warmup=1, pc="dfast", transform=None):
+def size_leg(pkg, torch, dev, synth, n, steps=2, warmup=1, pc="dfast", transform=None, method="fp"):
     """The same workload at n x n (radius-7 disk on 31 x 31, AR, MIXED, 10 FP steps) with
     preconditioner pc (D_M, or M_D for 'fastd') and the plan's default transform form
-    (or `transform`): device time per deblur by CUDA events, L2 flushed before each step."""
+    (or `transform`); with method 'reblur' each FP step solves eq. (fpp) by PBiCGstab (D_P / P_D).
+    Device time per deblur by CUDA events, L2 flushed before each step."""
     h = synth.disk_psf(7.0, side=31)
     u_true = torch.tensor(synth.piecewise_constant_image(n, n, seed=SEED), dtype=torch.float64, device=dev)
     with pkg.Plan(n, n, h, bc="ar", pc="dfast", mode="fp64") as p64:
@@ -221,7 +222,7 @@ def size_leg(pkg, torch, dev, synth, n, steps=2, warmup=1, pc="dfast", transform
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream()
     ms, iters = 0.0, 0
-    with pkg.Plan(n, n, h, bc="ar", pc=pc, mode="mixed", transform=transform) as plan:
+    with pkg.Plan(n, n, h, bc="ar", pc=pc, mode="mixed", transform=transform, method=method) as plan:
         form = plan.transform
         for s_ in range(warmup + steps):
             flush.zero_()
@@ -233,9 +234,14 @@ def size_leg(pkg, torch, dev, synth, n, steps=2, warmup=1, pc="dfast", transform
             if s_ >= warmup:
                 ms += e0.elapsed_time(e1)
                 iters += st["total_inner_iters"]
-    name = "M_D" if pc == "fastd" else "D_M"
+    if method == "reblur":
+        name = "P_D" if pc == "fastd" else "D_P"
+        eq = "reblurring eq. (fpp), PBiCGstab"
+    else:
+        name = "M_D" if pc == "fastd" else "D_M"
+        eq = "eq. (fp), PCG"
     return {"workload": f"tv_deblur {n}x{n} AR disk-r7(31x31) 1% noise alpha=1e-3 beta=1e-2 10 FP steps tol=1e-6 "
-                        f"{name}, MIXED, {form} transforms", "deblurs_per_s": 1000.0 * steps / ms,
+                        f"{eq}, {name}, MIXED, {form} transforms", "deblurs_per_s": 1000.0 * steps / ms,
             "ms_per_step": ms / steps,
             "pcg_iters_per_s": iters / (ms / 1000.0), "inner_iters_per_deblur": iters / steps}
 
@@ -244,9 +250,10 @@ def adjoint_leg(pkg, torch, dev, synth):
     """Adjoint of the converged fixed point at 512 x 512: the observation blurred
     with a Gaussian sigma = 2.5, the plan's PSF sigma = 2.0 on a 17 x 17 support
     (half-width ceil(3 x 2.5)), alpha 1e-3, beta 1e-2, AR, D_M, MIXED. u* from
-    tv_deblur run to ||u^k - u^{k-1}|| / ||u^k|| < 1e-8; then one adjoint solve
-    (tol 1e-10) for l = ||u* - u_true||^2 and dl/dsigma by the chain rule through
-    the PSF taps. Device time by CUDA events."""
+    tv_deblur run to ||u^k - u^{k-1}|| / ||u^k|| < 1e-4, then Newton steps on
+    g(u) = 0 (tv_deblur_newton) to a relative change below 1e-12; then one
+    adjoint solve (tol 1e-10) for l = ||u* - u_true||^2 and dl/dsigma by the
+    chain rule through the PSF taps. Device time by CUDA events."""
     import numpy as np
     n, seed, m = 512, 77, 8
     u_true = synth.piecewise_constant_image(n, n, seed=seed)
@@ -258,20 +265,25 @@ def adjoint_leg(pkg, torch, dev, synth):
     v = torch.tensor(synth.add_noise(hu, synth.noise_direction(n, n, seed), 0.01), dtype=torch.float64, device=dev)
     stream = torch.cuda.current_stream()
     with pkg.Plan(n, n, h, bc="ar", pc="dfast", mode="mixed") as plan:
-        e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+        e0, e1, e2, e3 = (torch.cuda.Event(enable_timing=True) for _ in range(4))
         e0.record(stream)
-        u, st = plan.deblur(v, ALPHA, BETA, max_outer=200, outer_tol=1e-8, inner_tol=1e-8, inner_maxit=5000)
+        u, st = plan.deblur(v, ALPHA, BETA, max_outer=400, outer_tol=1e-4, inner_tol=1e-8, inner_maxit=5000)
         e1.record(stream)
-        lam, da, db, dh, ast = plan.adjoint(u, v, ALPHA, BETA, 2.0 * (u - ut), tol=1e-10, maxit=5000)
+        nst = plan.newton(u, v, ALPHA, BETA, tol=1e-12, cg_tol=1e-12, cg_maxit=20000)
         e2.record(stream)
-        e2.synchronize()
+        lam, da, db, dh, ast = plan.adjoint(u, v, ALPHA, BETA, 2.0 * (u - ut), tol=1e-10, maxit=5000)
+        e3.record(stream)
+        e3.synchronize()
     eps = 1e-6
     dh_dsigma = (synth.gaussian_psf(2.0 + eps, half_width=m) - synth.gaussian_psf(2.0 - eps, half_width=m)) / (2 * eps)
     return {"workload": "adjoint of the converged fixed point, 512x512 AR, plan PSF Gaussian sigma 2.0 on 17x17, "
                         "data blurred with sigma 2.5, alpha 1e-3, beta 1e-2, D_M, MIXED",
             "fixed_point_ms": e0.elapsed_time(e1), "fp_steps": st["outer_iters"],
-            "fp_inner_iters": st["total_inner_iters"], "last_rel_change": st["last_rel_change"],
-            "adjoint_ms": e1.elapsed_time(e2), "adjoint_iters": ast["iters"], "adjoint_relres": ast["relres"],
+            "fp_inner_iters": st["total_inner_iters"], "fp_last_rel_change": st["last_rel_change"],
+            "newton_ms": e1.elapsed_time(e2), "newton_steps": nst["steps"], "newton_cg_iters": nst["total_cg_iters"],
+            "newton_halvings": nst["halvings"], "last_rel_change": nst["last_rel_change"],
+            "g_norm_initial": nst["g_norm_initial"], "g_norm": nst["g_norm"], "newton_status": nst["status"],
+            "adjoint_ms": e2.elapsed_time(e3), "adjoint_iters": ast["iters"], "adjoint_relres": ast["relres"],
             "dl_dalpha": da, "dl_dbeta": db, "dl_dsigma": float(np.sum(dh * dh_dsigma))}
 
 
@@ -307,6 +319,26 @@ def bf16_peak():
         return float(json.load(open(path))["bf16_tflops_sustained"]), "measured (bf16 sustained)"
     except Exception:
         return 1700.0, "fallback (bf16 sustained 1.7 PF)"
+
+
+def path_roofline(pcg_iters_per_s, prec_bytes=4):
+    """The whole PCG iteration against HBM: the floor of the standard recurrence, 15 words per pixel
+    (matvec 3, x / r update 6, preconditioner 3, p update 3), times the iteration rate."""
+    bytes_per_iter = 15 * prec_bytes * N_SIDE * N_SIDE
+    achieved = bytes_per_iter * pcg_iters_per_s / 1e9
+    peak, src = peaks()
+    return {"bound": "hbm", "words_per_pixel": 15, "bytes_per_iteration": bytes_per_iter, "achieved": achieved,
+            "peak": peak, "unit": "GB/s", "frac": achieved / peak, "peak_source": src}
+
+
+def rooflines_of(prof, total_ms, storage):
+    """Roofline entry of every kernel class of the step with a known algorithmic work per launch."""
+    out = {}
+    for name, (kms, kl) in prof.items():
+        base = name.rsplit(".", 1)[0]
+        if kl and (base in WORDS_PER_PIXEL or base == "precond_gemm_tc"):
+            out[name] = roofline_of(name, kms, kl, total_ms, storage)
+    return out
 
 
 def roofline_of(name, kms, klaunch, total_ms, storage=None):
@@ -348,6 +380,19 @@ def cpu_sample(h, v, sample_iters: int):
     t2 = time.perf_counter()
     # pcg also applies A once to form r_0: charge it as one iteration
     return (t1 - t0) + (t2 - t1) / (sample_iters + 1), (t2 - t1) / (sample_iters + 1)
+
+
+def cpu_full_deblur(n):
+    """One complete oracle deblur of the workload at n x n (disk r7, AR, D_M, 10 FP steps, tol 1e-6),
+    wall-clock seconds and its inner iterations."""
+    import oracle as O
+    from paper_1011_5964_gb300 import synth
+    h = synth.disk_psf(7.0, side=31)
+    u_true = synth.piecewise_constant_image(n, n, seed=SEED)
+    v = synth.add_noise(O.blur(u_true, h, "ar"), synth.noise_direction(n, n, SEED), NOISE)
+    t0 = time.perf_counter()
+    _, st = O.tv_deblur(v, h, "ar", ALPHA, BETA, outer=OUTER, tol=TOL, maxit=5000, kind="dfast")
+    return time.perf_counter() - t0, int(sum(st["inner_iters"]))
 
 
 def oracle_iters_per_deblur():
@@ -499,11 +544,10 @@ def run_ours(args):
                  if v_[1]}
         print("per-kernel-class device time of one chosen-form step: " + json.dumps(table), file=sys.stderr)
     total_ms = sum(v_[0] for v_ in prof.values())
+    # every kernel is the library's own: the dominant class by device time, and all classes
     top = max(prof.items(), key=lambda kv: kv[1][0])
     roofline = roofline_of(top[0], top[1][0], top[1][1], total_ms, mixed.gemm_storage)
-    # the library's own dominant kernel (the stencils and the vector kernels are ours; cuBLAS is not)
-    own = max(((k, v_) for k, v_ in prof.items() if not k.startswith("precond_gemm_cublas")), key=lambda kv: kv[1][0])
-    roofline_own = roofline_of(own[0], own[1][0], own[1][1], total_ms)
+    rooflines = rooflines_of(prof, total_ms, mixed.gemm_storage)
 
     # end to end through the public API with pinned host buffers
     v_pin = torch.tensor(v_host, dtype=torch.float64).pin_memory()
@@ -540,7 +584,8 @@ def run_ours(args):
             "rel_err_vs_plain_fp64": rel_err,
             "gpu_launches": launches,
             "roofline": roofline,
-            "roofline_own_kernel": roofline_own,
+            "rooflines": rooflines,
+            "path_roofline": path_roofline(ws * iters_mixed / (ms_mixed / 1000.0)),
             "transform_form": mixed.transform,
             "gemm_operands": mixed.gemm_storage,
             "clocks": clocks,
@@ -553,6 +598,7 @@ def run_ours(args):
         line["size_2048"] = size_leg(pkg, torch, dev, synth, 2048)
         line["m_d_1024"] = size_leg(pkg, torch, dev, synth, 1024, steps=3, pc="fastd")
         line["fft_form_1024"] = size_leg(pkg, torch, dev, synth, 1024, steps=3, transform="fft")
+        line["reblur_1024"] = size_leg(pkg, torch, dev, synth, 1024, steps=3, method="reblur")
 
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         iters_per_deblur, src = oracle_iters_per_deblur()
@@ -560,11 +606,16 @@ def run_ours(args):
             iters_per_deblur, src = int(round(iters_plain / p_steps)), "iteration count of the FP64 GPU form"
         setup_s, it_s = cpu_sample(h, v_host, 8)
         deblur_s = OUTER * setup_s + iters_per_deblur * it_s
+        full_s, full_iters = cpu_full_deblur(256)
         line["cpu_baseline"] = {"value": 1.0 / deblur_s, "unit": "deblurs/s", "cores": os.cpu_count(),
                                 "kind": "oracle", "pcg_iters_per_s": 1.0 / it_s,
-                                "sample": f"FP-step set-up + 8 PCG iterations of the first FP step at 1024x1024 "
-                                          f"(numpy/scipy default threading); deblur time = 10 x set-up + "
-                                          f"{iters_per_deblur} iterations ({src})"}
+                                "sample": f"extrapolated: FP-step set-up + 8 PCG iterations of the first FP step at "
+                                          f"1024x1024 (numpy/scipy default threading); deblur time = 10 x set-up + "
+                                          f"{iters_per_deblur} iterations ({src})",
+                                "full_256": {"measured_s": full_s, "deblurs_per_s": 1.0 / full_s,
+                                             "inner_iters": full_iters,
+                                             "sample": "measured: one complete oracle tv_deblur of the same "
+                                                       "workload at 256x256 (wall clock)"}}
     if rank == 0:
         print(json.dumps(line))
     mixed.close()

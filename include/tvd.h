@@ -85,8 +85,12 @@ typedef enum {
                              plan stays usable */
 } tvd_status;
 
-/* Per-call statistics of tv_deblur. inner_iters is caller-owned host memory
- * with room for `cap` entries (may be NULL with cap = 0). */
+/* Per-call statistics of tv_deblur. inner_iters, g_norm and functional are
+ * caller-owned host arrays with room for `cap` entries each; any of them may be
+ * NULL (cap = 0 when all are). g_norm and functional cost one double H^T H
+ * product (and, for functional, a data-term and a TV-term reduction) per FP
+ * step; NULL skips that work. Zero-initialise the structure (fields added at
+ * the end keep older callers' layouts valid). */
 typedef struct {
     int outer_iters;         /* FP steps taken */
     int* inner_iters;        /* inner CG iterations of each FP step (first min(outer, cap)) */
@@ -96,19 +100,42 @@ typedef struct {
     double last_relres;      /* ||r|| / ||r_0|| of the last FP step (double residual) */
     double last_rel_change;  /* ||u^k - u^{k-1}|| / ||u^k|| of the last FP step */
     tvd_status last_status;  /* status of the last inner solve */
+    double* g_norm;          /* ||g(u^k)|| of the iterate FP step k starts from, k = 0, 1, ...,
+                                g(u) = H^T (H u - v) + alpha L(u) u of eq. (el); on a reblurring plan
+                                the residual norm of eq. (fpp), ||H' v - (H' H + alpha L(u^k)) u^k|| */
+    double* functional;      /* T(u^k) = 1/2 ||H u^k - v||^2 + alpha sum_pq sqrt(|D u^k|_pq^2 + beta^2),
+                                the discretised functional of eq. (mp), for the same iterates */
+    double final_g_norm;     /* the same two quantities for the returned iterate (0 when the */
+    double final_functional; /* corresponding array is NULL) */
 } tvd_stats;
+
+/* Statistics of tv_deblur_newton. */
+typedef struct {
+    int steps;               /* Newton steps taken */
+    int total_cg_iters;      /* CG iterations over all Jacobian solves */
+    int halvings;            /* step-length halvings over all steps */
+    double last_t;           /* step length of the last step (1 = full Newton step) */
+    double last_rel_change;  /* t ||d|| / ||u|| of the last step */
+    double last_cg_relres;   /* ||r|| / ||r_0|| of the last Jacobian solve */
+    double g_norm_initial;   /* ||g(u)|| of the incoming iterate */
+    double g_norm;           /* ||g(u)|| of the returned iterate */
+} tvd_newton_stats;
 
 /*
  * tvd_plan_create -- validate the problem and build the plan.
  *   out         receives the plan handle.
  *   n_rows, n_cols  image size, each in [3, 2048] for TVD_MODE_FP64 plans and
  *               in [3, 4096] for TVD_MODE_MIXED plans (each transform line is
- *               held in shared memory).
+ *               held in shared memory). n_rows = 1 makes a 1D signal of n_cols
+ *               samples (Sec. 5.1): its PSF has one row, the row axis carries
+ *               no boundary condition and no difference of L, and the 2D
+ *               transforms reduce to the 1D ones of Sec. 3.1 (the 1-point
+ *               transform is the identity). Such plans always use the FFT form.
  *   psf_host    HOST pointer to the (p_rows x p_cols) PSF, row-major doubles,
  *               centred: psf[(m_r + a) * p_cols + (m_c + b)] = h_{a,b}. Copied.
  *               p_rows, p_cols odd. All-zero outer rows/columns are trimmed (this
- *               does not change H). After trimming, m_r <= n_rows - 2 and
- *               m_c <= n_cols - 2 (else TVD_EPSF_SIZE), and h must be
+ *               does not change H). After trimming, m_r <= n_rows - 2 (m_r = 0
+ *               when n_rows = 1) and m_c <= n_cols - 2 (else TVD_EPSF_SIZE), and h must be
  *               quadrantally symmetric h_{a,b} = h_{-a,b} = h_{a,-b} to a relative
  *               tolerance of 1e-12 (else TVD_EPSF_ASYM). Normalisation sum h = 1
  *               (Sec. 2) is the caller's choice and is not enforced.
@@ -198,7 +225,8 @@ typedef enum {
  * and encodes their TMA tensor maps (cuTensorMapEncodeTiled, taken from the
  * driver); switching back frees them. Synchronises `stream` (and, when
  * freeing, the device). Errors: TVD_EINVAL for a NULL plan, an unknown kind,
- * or GEMM on an FP64 plan or with the I / D preconditioners; TVD_ENOMEM,
+ * or GEMM on an FP64 plan, a 1D plan (n_rows = 1) or with the I / D
+ * preconditioners; TVD_ENOMEM,
  * TVD_ECUDA (also when the driver offers no tensor-map encoder).
  */
 tvd_status tvd_plan_set_transform(tvd_plan plan, int kind, void* stream);
@@ -256,14 +284,32 @@ tvd_status tv_deblur(tvd_plan plan, const void* v, double alpha, double beta,
  * TVD_PC_NONE and TVD_PC_DIAG keep their meaning.
  */
 typedef enum {
-    TVD_METHOD_FP = 0,      /* eq. (fp), PCG (default) */
-    TVD_METHOD_REBLUR = 1   /* eq. (fpp), PBiCGstab (anti-reflective BCs only) */
+    TVD_METHOD_FP = 0,         /* eq. (fp), PCG (default) */
+    TVD_METHOD_REBLUR = 1,     /* eq. (fpp), PBiCGstab (anti-reflective BCs only) */
+    TVD_METHOD_REBLUR_ARL = 2  /* eq. (fpp) with anti-reflective BCs on L as well ("AR+Reblur+AR L"
+                                  of Tables 1-1 and 2-1), PBiCGstab (anti-reflective BCs only) */
 } tvd_method;
 
 /*
+ * L with anti-reflective BCs (TVD_METHOD_REBLUR_ARL; the remark after
+ * eq. (scalereb)): L_AR x applies the divergence-form stencil
+ *     w_{i-1} (x_i - x_{i-1}) - w_i (x_{i+1} - x_i)   (per axis)
+ * to the AR extension of x (eq. (anti1d)), the diffusivity of a ghost pixel
+ * taken from its inner neighbour (exact in 1D, where the AR extension of u
+ * repeats the first inner difference). On the first and last line of an axis
+ * the two differences and weights then coincide, so that axis contributes
+ * nothing there; elsewhere L_AR = L. L_AR is not symmetric; for a constant
+ * diffusivity it is the AR blur of the 5-point Laplacian. The preconditioners
+ * are those of the REBLUR method (AR_2(.) reads only the interior block, where
+ * L_AR = L), with D = I + alpha diag(L_AR) (eq. (D) for this L).
+ * tv_operator_apply on such a plan applies L_AR.
+ */
+
+/*
  * tvd_plan_set_method -- switch the plan between eq. (fp) with PCG and
- * eq. (fpp) with PBiCGstab (method: a tvd_method value). REBLUR needs
- * anti-reflective BCs (else TVD_EINVAL). Any earlier tau_precond_setup is
+ * eq. (fpp) with PBiCGstab, with L under zero Neumann or anti-reflective BCs
+ * (method: a tvd_method value). REBLUR and REBLUR_ARL need anti-reflective
+ * BCs (else TVD_EINVAL); "a REBLUR plan" below means either. Any earlier tau_precond_setup is
  * discarded; a plan in the GEMM transform form rebuilds its matrices (T_n^-1
  * forward, T_n inverse, per side). tau_precond_setup / tau_precond_solve,
  * tv_deblur and pbicgstab_solve follow the method; pcg_solve on a REBLUR plan
@@ -275,8 +321,8 @@ tvd_status tvd_plan_set_method(tvd_plan plan, int method, void* stream);
 int tvd_plan_method(tvd_plan plan);
 
 /*
- * pbicgstab_solve -- solve (H' H + alpha L(u_lag)) x = b (eq. (fpp)) on a
- * REBLUR plan by preconditioned BiCGstab (van der Vorst's method, cited in
+ * pbicgstab_solve -- solve (H' H + alpha L(u_lag)) x = b (eq. (fpp); L_AR on a
+ * REBLUR_ARL plan) on a REBLUR plan by preconditioned BiCGstab (van der Vorst's method, cited in
  * Sec. 3) from the initial guess in x_inout, stopping when
  * ||r_k||_2 / ||r_0||_2 < tol (Sec. 5), tested on the half-step residual and
  * on r after each iteration, or after maxit iterations (one iteration: two
@@ -319,6 +365,8 @@ typedef struct {
     double alpha, beta;
     int* inner_iters;     /* optional host array of max_outer entries (NULL: not reported) */
     tvd_status status;    /* out: the item's tv_deblur status */
+    double outer_tol;     /* the item's FP stopping rule, as tv_deblur's outer_tol (<= 0: max_outer steps) */
+    int outer_iters;      /* out: FP steps the item took */
 } tvd_batch_item;
 
 tvd_status tv_deblur_batched(tvd_batch_item* items, int count, int max_outer, double inner_tol,
@@ -335,6 +383,38 @@ tvd_status tv_deblur_batched(tvd_batch_item* items, int count, int max_outer, do
 tvd_status tv_hessian_apply(tvd_plan plan, const void* u, double beta, const void* x, void* y, void* stream);
 
 /*
+ * tv_deblur_newton -- finish the fixed point of eq. (fp) by Newton's method on
+ * the Euler-Lagrange equation g(u) = H^T (H u - v) + alpha L(u) u = 0 of
+ * eq. (el). Not a construction of the paper: the lagged-diffusivity iteration
+ * converges linearly, and the adjoint (tv_deblur_adjoint) wants a stationary
+ * point to a tolerance that iteration reaches slowly. From the incoming
+ * iterate (normally a tv_deblur result), each step solves
+ *     J(u) d = -g(u),   J = H^T H + alpha nabla^2 J_beta(u)   (SPD),
+ * by PCG from d = 0 to ||r|| / ||r_0|| < cg_tol (at most cg_maxit iterations),
+ * preconditioned by the plan's preconditioner of the lagged operator
+ * H^T H + alpha L(u) set up at u (MIXED plans: float PCG with double residual
+ * replacement, as in tv_deblur_adjoint), and moves to u + t d with t = 1,
+ * halved while ||g(u + t d)|| >= ||g(u)|| (at most 10 halvings; a full step
+ * with ||d|| / ||u + d|| < tol is taken as it is, since ||g|| is then at its
+ * rounding floor). It stops after the first step with t ||d|| / ||u + t d||
+ * < tol, or when g(u) = 0.
+ *   v            DOUBLE device array, the observation.
+ *   u_inout      DOUBLE device array (distinct from v): the starting iterate in,
+ *                the finished iterate out.
+ *   tol          relative-change stopping rule (> 0); max_steps >= 0 (0: only
+ *                ||g(u)|| is evaluated, into stats->g_norm_initial).
+ *   stats        may be NULL.
+ * Runs in double in both modes; allocates 6 n (MIXED: 7 n) doubles of scratch
+ * and synchronises the stream. Returns TVD_OK when the stopping rule was met;
+ * TVD_ENOCONV after max_steps steps without it, or when no halving lowered
+ * ||g|| (u_inout then holds the last accepted iterate); TVD_EBREAKDOWN,
+ * TVD_ETIMEOUT from a Jacobian solve; TVD_EINVAL for invalid arguments or a
+ * reblurring plan (its fixed point is not a stationary point of a functional).
+ */
+tvd_status tv_deblur_newton(tvd_plan plan, const void* v, double alpha, double beta, void* u_inout, double tol,
+                            int max_steps, double cg_tol, int cg_maxit, tvd_newton_stats* stats, void* stream);
+
+/*
  * tv_deblur_adjoint -- gradients of a loss l(u*) of the converged fixed point
  * u* of tv_deblur (g(u*) = H^T (H u* - v) + alpha L(u*) u* = 0, eq. (el)) with
  * respect to alpha, beta and the PSF taps, by implicit differentiation: one
@@ -349,7 +429,7 @@ tvd_status tv_hessian_apply(tvd_plan plan, const void* u, double beta, const voi
  * construction of the paper: it differentiates the paper's method. Runs in
  * double in both modes.
  *   u_star, v, dl_du   DOUBLE device arrays (u* should satisfy g(u*) ~ 0:
- *                      run tv_deblur to a small outer_tol first).
+ *                      run tv_deblur, then tv_deblur_newton to a small tol).
  *   lambda_out         DOUBLE device array, receives lambda (distinct from the inputs).
  *   tol, maxit         ||r_k|| / ||r_0|| < tol stopping rule and cap of the adjoint PCG.
  *   dl_dalpha, dl_dbeta  host doubles (may be NULL).
@@ -358,7 +438,8 @@ tvd_status tv_hessian_apply(tvd_plan plan, const void* u, double beta, const voi
  *                      outer rows / columns), row-major like the PSF; may be NULL.
  *   iters, relres      host outputs of the adjoint PCG (may be NULL).
  * Synchronises the stream. Returns TVD_ENOCONV (gradients still written) if
- * the PCG hit maxit, TVD_EBREAKDOWN if it broke down.
+ * the PCG hit maxit, TVD_EBREAKDOWN if it broke down, TVD_EINVAL on a
+ * reblurring plan (its linearisation is not symmetric).
  */
 tvd_status tv_deblur_adjoint(tvd_plan plan, const void* u_star, const void* v, double alpha, double beta,
                              const void* dl_du, void* lambda_out, double tol, int maxit, double* dl_dalpha,

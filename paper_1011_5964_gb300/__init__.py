@@ -33,11 +33,11 @@ STATUS_NAMES = ["TVD_OK", "TVD_EINVAL", "TVD_EPSF_ASYM", "TVD_EPSF_SIZE", "TVD_E
 
 # Function names of the C ABI, in include/tvd.h order.
 TRANSFORM = {"fft": 0, "gemm": 1}
-METHOD = {"fp": 0, "reblur": 1}
+METHOD = {"fp": 0, "reblur": 1, "reblur_arl": 2}
 ABI_FUNCTIONS = ["tvd_plan_create", "tvd_plan_destroy", "ar_blur_apply", "tv_operator_apply",
                  "tau_precond_setup", "tau_precond_solve", "pcg_solve", "tv_deblur",
                  "tvd_plan_set_method", "tvd_plan_method", "pbicgstab_solve",
-                 "tv_deblur_batched", "tv_hessian_apply", "tv_deblur_adjoint", "tvd_plan_psf_size",
+                 "tv_deblur_batched", "tv_hessian_apply", "tv_deblur_adjoint", "tv_deblur_newton", "tvd_plan_psf_size",
                  "tvd_normal_apply_noalloc", "tvd_plan_set_transform", "tvd_plan_transform", "tvd_plan_gemm_storage",
                  "tvd_last_error", "tvd_version", "tvd_kernel_launches",
                  "tvd_profile_enable", "tvd_profile_classes", "tvd_profile_name", "tvd_profile_read"]
@@ -56,13 +56,23 @@ class _Stats(ctypes.Structure):
     _fields_ = [("outer_iters", ctypes.c_int), ("inner_iters", ctypes.POINTER(ctypes.c_int)),
                 ("cap", ctypes.c_int), ("total_inner_iters", ctypes.c_int),
                 ("refinement_sweeps", ctypes.c_int), ("last_relres", ctypes.c_double),
-                ("last_rel_change", ctypes.c_double), ("last_status", ctypes.c_int)]
+                ("last_rel_change", ctypes.c_double), ("last_status", ctypes.c_int),
+                ("g_norm", ctypes.POINTER(ctypes.c_double)), ("functional", ctypes.POINTER(ctypes.c_double)),
+                ("final_g_norm", ctypes.c_double), ("final_functional", ctypes.c_double)]
+
+
+class _NewtonStats(ctypes.Structure):
+    _fields_ = [("steps", ctypes.c_int), ("total_cg_iters", ctypes.c_int), ("halvings", ctypes.c_int),
+                ("last_t", ctypes.c_double), ("last_rel_change", ctypes.c_double),
+                ("last_cg_relres", ctypes.c_double), ("g_norm_initial", ctypes.c_double),
+                ("g_norm", ctypes.c_double)]
 
 
 class _BatchItem(ctypes.Structure):
     _fields_ = [("plan", ctypes.c_void_p), ("v", ctypes.c_void_p), ("u_out", ctypes.c_void_p),
                 ("alpha", ctypes.c_double), ("beta", ctypes.c_double),
-                ("inner_iters", ctypes.POINTER(ctypes.c_int)), ("status", ctypes.c_int)]
+                ("inner_iters", ctypes.POINTER(ctypes.c_int)), ("status", ctypes.c_int),
+                ("outer_tol", ctypes.c_double), ("outer_iters", ctypes.c_int)]
 
 
 _lib = None
@@ -91,6 +101,7 @@ def load_library(path: str | None = None) -> ctypes.CDLL:
     lib.tv_hessian_apply.argtypes = [vp, vp, d, vp, vp, vp]
     lib.tv_deblur_adjoint.argtypes = [vp, vp, vp, d, d, vp, vp, d, i, ctypes.POINTER(d), ctypes.POINTER(d),
                                       ctypes.POINTER(d), ctypes.POINTER(i), ctypes.POINTER(d), vp]
+    lib.tv_deblur_newton.argtypes = [vp, vp, d, d, vp, d, i, d, i, ctypes.POINTER(_NewtonStats), vp]
     lib.tvd_plan_psf_size.argtypes = [vp, ctypes.POINTER(i), ctypes.POINTER(i)]
     lib.tvd_plan_set_transform.argtypes = [vp, i, vp]
     lib.tvd_plan_set_method.argtypes = [vp, i, vp]
@@ -142,7 +153,7 @@ class Plan:
     ``psf`` is a (2 m_r + 1, 2 m_c + 1) float64 array, centred and quadrantally
     symmetric. ``bc``: 'ar' (anti-reflective) or 'r' (reflective). ``pc``:
     'none', 'diag', 'fast' (R / M), 'dfast' (D_R / D_M) or 'fastd' (R_D / M_D).
-    ``mode``: 'fp64' or 'mixed'. ``method``: 'fp' (eq. (fp), PCG) or 'reblur'
+    ``mode``: 'fp64' or 'mixed'. ``method``: 'fp' (eq. (fp), PCG), 'reblur' or 'reblur_arl'
     (eq. (fpp), PBiCGstab; the fast kinds are then P, D_P, P_D). Operator calls
     take float64 tensors in fp64 mode and float32 in mixed mode; solver calls
     always take float64 tensors.
@@ -168,12 +179,14 @@ class Plan:
             self.set_transform(transform)
 
     def set_method(self, method: str):
-        """'fp' (eq. (fp), PCG) or 'reblur' (eq. (fpp), PBiCGstab; anti-reflective BCs)."""
+        """'fp' (eq. (fp), PCG), 'reblur' (eq. (fpp), PBiCGstab) or 'reblur_arl' (eq. (fpp) with
+        anti-reflective BCs on L too, PBiCGstab); both reblurring methods need anti-reflective BCs."""
         _check(self.lib.tvd_plan_set_method(self.handle, METHOD[method], _stream()))
 
     @property
     def method(self) -> str:
-        return "reblur" if self.lib.tvd_plan_method(self.handle) == METHOD["reblur"] else "fp"
+        code = self.lib.tvd_plan_method(self.handle)
+        return next(k for k, c in METHOD.items() if c == code)
 
     def set_transform(self, kind: str):
         """Transform form of the fast preconditioners on a mixed plan: 'fft' or 'gemm'."""
@@ -290,22 +303,54 @@ class Plan:
         return lam, da.value, db.value, dpsf, {"iters": it.value, "relres": rr.value, "status": st}
 
     def deblur(self, v, alpha: float, beta: float, max_outer: int = 10, outer_tol: float = 0.0,
-               inner_tol: float = 1e-6, inner_maxit: int = 1000, out=None):
-        """Lagged-diffusivity FP iteration from u^0 = v. Returns (u, stats dict)."""
+               inner_tol: float = 1e-6, inner_maxit: int = 1000, out=None, track: bool = False):
+        """Lagged-diffusivity FP iteration from u^0 = v. Returns (u, stats dict).
+
+        With track=True the stats also hold, per FP step k, ||g(u^k)|| (eq. (el)) and
+        the functional T(u^k) of the iterate the step starts from, and both for the
+        returned iterate ("final_g_norm", "final_functional").
+        """
         import torch
         u = torch.empty_like(v) if out is None else out
         cap = max(int(max_outer), 1)
         arr = (ctypes.c_int * cap)()
-        stats = _Stats(0, arr, cap, 0, 0, 0.0, 0.0, 0)
+        gn = (ctypes.c_double * cap)() if track else None
+        fn = (ctypes.c_double * cap)() if track else None
+        stats = _Stats()
+        stats.inner_iters, stats.cap = arr, cap
+        if track:
+            stats.g_norm, stats.functional = gn, fn
         st = self.lib.tv_deblur(self.handle, _ptr(v, torch.float64, self.n), float(alpha), float(beta), int(max_outer),
                                 float(outer_tol), float(inner_tol), int(inner_maxit), _ptr(u, torch.float64, self.n),
                                 ctypes.byref(stats), _stream())
         _check(st, allow=(TVD_ENOCONV,))
         k = stats.outer_iters
-        return u, {"outer_iters": k, "inner_iters": list(arr[:min(k, cap)]),
-                   "total_inner_iters": stats.total_inner_iters, "refinement_sweeps": stats.refinement_sweeps,
-                   "last_relres": stats.last_relres, "last_rel_change": stats.last_rel_change,
-                   "last_status": stats.last_status, "status": st}
+        out = {"outer_iters": k, "inner_iters": list(arr[:min(k, cap)]),
+               "total_inner_iters": stats.total_inner_iters, "refinement_sweeps": stats.refinement_sweeps,
+               "last_relres": stats.last_relres, "last_rel_change": stats.last_rel_change,
+               "last_status": stats.last_status, "status": st}
+        if track:
+            out.update({"g_norm": list(gn[:min(k, cap)]), "functional": list(fn[:min(k, cap)]),
+                        "final_g_norm": stats.final_g_norm, "final_functional": stats.final_functional})
+        return u, out
+
+    def newton(self, u, v, alpha: float, beta: float, tol: float = 1e-10, max_steps: int = 30,
+               cg_tol: float = 1e-10, cg_maxit: int = 20000):
+        """Newton finish of the fixed point in place (u: float64 CUDA tensor, distinct from v).
+
+        Steps on g(u) = 0 (eq. (el)) until the relative change falls below tol;
+        returns the stats dict (steps, CG iterations, halvings, last step length,
+        last relative change, ||g|| before and after, status).
+        """
+        import torch
+        ns = _NewtonStats()
+        st = self.lib.tv_deblur_newton(self.handle, _ptr(v, torch.float64, self.n), float(alpha), float(beta),
+                                       _ptr(u, torch.float64, self.n), float(tol), int(max_steps), float(cg_tol),
+                                       int(cg_maxit), ctypes.byref(ns), _stream())
+        _check(st, allow=(TVD_ENOCONV,))
+        return {"steps": ns.steps, "total_cg_iters": ns.total_cg_iters, "halvings": ns.halvings,
+                "last_t": ns.last_t, "last_rel_change": ns.last_rel_change, "last_cg_relres": ns.last_cg_relres,
+                "g_norm_initial": ns.g_norm_initial, "g_norm": ns.g_norm, "status": st}
 
 
 def normal_apply_noalloc(psf, u_lag, alpha: float, beta: float, x, y=None, bc: str = "ar"):
@@ -332,12 +377,13 @@ def normal_apply_noalloc(psf, u_lag, alpha: float, beta: float, x, y=None, bc: s
 
 
 def deblur_batched(plans, vs, alphas, betas, max_outer: int = 10, inner_tol: float = 1e-6,
-                   inner_maxit: int = 1000, outs=None, workers: int = 8):
+                   inner_maxit: int = 1000, outs=None, workers: int = 8, outer_tol: float = 0.0):
     """tv_deblur of independent problems at once (one Plan per item; float64 CUDA tensors).
 
     Items run on `workers` host threads with a CUDA stream each, largest
-    first; each item's result equals that of plan.deblur(v, alpha, beta, ...).
-    Returns (list of u, list of per-item dicts {"status", "inner_iters"}).
+    first; each item's result equals that of plan.deblur(v, alpha, beta, ...,
+    outer_tol=outer_tol). Returns (list of u, list of per-item dicts
+    {"status", "inner_iters", "outer_iters"}).
     """
     import torch
     lib = load_library()
@@ -356,10 +402,33 @@ def deblur_batched(plans, vs, alphas, betas, max_outer: int = 10, inner_tol: flo
         arr[i].beta = float(betas[i])
         arr[i].inner_iters = ctypes.cast(iters[i], ctypes.POINTER(ctypes.c_int))
         arr[i].status = 0
+        arr[i].outer_tol = float(outer_tol)
     st = lib.tv_deblur_batched(arr, count, int(max_outer), float(inner_tol), int(inner_maxit), int(workers),
                                _stream())
     _check(st, allow=(TVD_ENOCONV,))
-    return us, [{"status": arr[i].status, "inner_iters": list(iters[i][:max_outer])} for i in range(count)]
+    return us, [{"status": arr[i].status, "outer_iters": arr[i].outer_iters,
+                 "inner_iters": list(iters[i][:min(arr[i].outer_iters, max_outer)])} for i in range(count)]
+
+
+def alpha_sweep(v, psf, alphas, beta: float, bc: str = "ar", pc: str = "dfast", mode: str = "fp64",
+                method: str = "fp", max_outer: int = 100, outer_tol: float = 1e-3, inner_tol: float = 1e-6,
+                inner_maxit: int = 5000, workers: int = 8):
+    """Deblur one observation v (float64 CUDA tensor, an image or a 1 x n signal) once per
+    regularisation parameter in ``alphas``, as one batch of independent problems: one plan per
+    alpha (same size, PSF, BCs, preconditioner, arithmetic and method), run by tv_deblur_batched.
+
+    The FP iteration of each item stops at ||u^k - u^{k-1}|| / ||u^k|| < outer_tol (1e-3 in the
+    paper's 1D experiment, Sec. 5.1) or after max_outer steps. Returns (list of u, list of per-item
+    stats): the input of an RRE-versus-alpha curve (Fig. tvrs).
+    """
+    nr, nc = v.shape
+    plans = [Plan(nr, nc, psf, bc=bc, pc=pc, mode=mode, method=method) for _ in alphas]
+    try:
+        return deblur_batched(plans, [v] * len(alphas), list(alphas), [beta] * len(alphas), max_outer=max_outer,
+                              inner_tol=inner_tol, inner_maxit=inner_maxit, workers=workers, outer_tol=outer_tol)
+    finally:
+        for pl in plans:
+            pl.close()
 
 
 def kernel_launches() -> int:

@@ -1,7 +1,9 @@
 """torch.autograd.Function over tv_deblur and tv_deblur_adjoint.
 
-The forward pass runs the lagged-diffusivity FP iteration of libtvd to its
-fixed point u* (eq. (fp) to a small outer tolerance); the backward pass runs
+The forward pass runs the lagged-diffusivity FP iteration of libtvd (eq. (fp))
+until its relative change falls below ``newton_from``, then finishes the fixed
+point u* by Newton steps on g(u) = 0 (tv_deblur_newton) to ``outer_tol``
+(``newton_from`` = 0: the FP iteration alone to ``outer_tol``); the backward pass runs
 the adjoint of that fixed point (tv_deblur_adjoint: one preconditioned solve
 with J = H^T H + alpha nabla^2 J_beta(u*)), so no outer iterate is stored,
 only u*. Gradients flow to the observation v, alpha, beta and the width sigma
@@ -33,13 +35,16 @@ class GaussianTVFixedPoint(torch.autograd.Function):
 
     @staticmethod
     def forward(ctx, v, alpha, beta, sigma, half_width: int, bc: str, mode: str, max_outer: int, outer_tol: float,
-                inner_tol: float, adjoint_tol: float):
+                inner_tol: float, adjoint_tol: float, newton_from: float):
         a, b, s = float(alpha), float(beta), float(sigma)
         h, dh = gaussian_taps(s, half_width)
         v64 = v.detach().to(torch.float64).contiguous()
         plan = Plan(v64.shape[0], v64.shape[1], h, bc=bc, pc="dfast", mode=mode)
-        u, stats = plan.deblur(v64, a, b, max_outer=max_outer, outer_tol=outer_tol, inner_tol=inner_tol,
+        fp_tol = newton_from if newton_from > 0.0 else outer_tol
+        u, stats = plan.deblur(v64, a, b, max_outer=max_outer, outer_tol=fp_tol, inner_tol=inner_tol,
                                inner_maxit=20000)
+        if newton_from > 0.0:
+            stats["newton"] = plan.newton(u, v64, a, b, tol=outer_tol, cg_tol=inner_tol)
         ctx.plan = plan
         ctx.pdev = [x.device if torch.is_tensor(x) else v.device for x in (alpha, beta, sigma)]
         ctx.params = (a, b, dh, adjoint_tol)
@@ -65,12 +70,12 @@ class GaussianTVFixedPoint(torch.autograd.Function):
         dsigma = float(np.sum(dpsf * dh))
         scal = lambda x, k: (torch.tensor(x, dtype=torch.float64, device=ctx.pdev[k - 1])
                              if ctx.needs_input_grad[k] else None)
-        return dv, scal(da, 1), scal(db, 2), scal(dsigma, 3), None, None, None, None, None, None, None
+        return dv, scal(da, 1), scal(db, 2), scal(dsigma, 3), None, None, None, None, None, None, None, None
 
 
 def tv_fixed_point(v, alpha, beta, sigma, half_width: int, bc: str = "ar", mode: str = "fp64",
                    max_outer: int = 500, outer_tol: float = 1e-10, inner_tol: float = 1e-10,
-                   adjoint_tol: float = 1e-10):
+                   adjoint_tol: float = 1e-10, newton_from: float = 1e-4):
     """Differentiable u*(v, alpha, beta, sigma): alpha, beta, sigma are 0-dim tensors (requires_grad as needed)."""
     return GaussianTVFixedPoint.apply(v, alpha, beta, sigma, half_width, bc, mode, max_outer, outer_tol, inner_tol,
-                                      adjoint_tol)
+                                      adjoint_tol, newton_from)

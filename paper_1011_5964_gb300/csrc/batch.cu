@@ -76,8 +76,9 @@ extern "C" tvd_status tv_deblur_batched(tvd_batch_item* items, int count, int ma
                 tvd_stats stats{};
                 stats.inner_iters = it.inner_iters;
                 stats.cap = it.inner_iters ? max_outer : 0;
-                it.status = tv_deblur(it.plan, it.v, it.alpha, it.beta, max_outer, 0.0, inner_tol, inner_maxit,
-                                      it.u_out, &stats, s);
+                it.status = tv_deblur(it.plan, it.v, it.alpha, it.beta, max_outer, it.outer_tol, inner_tol,
+                                      inner_maxit, it.u_out, &stats, s);
+                it.outer_iters = stats.outer_iters;
                 if (it.status != TVD_OK) msgs[i] = tvd_last_error();
             }
         }

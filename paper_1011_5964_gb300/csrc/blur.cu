@@ -573,7 +573,8 @@ __device__ __forceinline__ void border_body(int bid, const T* __restrict__ y, T*
             const T* srow = strip + i * SW + o + mc;
             for (int b = -mc; b <= mc; ++b) acc += __ldg(crw + b + mc) * srow[b];
         }
-        if (l <= nc - 2) { oi = top ? 0 : nr - 1; oj = l; }
+        // one row (a 1D signal): the top row's sums are complete, the bottom copy writes nothing
+        if (l <= nc - 2 && (top || nr > 1)) { oi = top ? 0 : nr - 1; oj = l; }
     } else if (bid < 2 * nseg_r + 2 * nseg_c) {
         // left (0) / right (nc - 1) column, interior rows k0 .. k0 + 31
         bid -= 2 * nseg_r;
@@ -596,8 +597,9 @@ __device__ __forceinline__ void border_body(int bid, const T* __restrict__ y, T*
                 acc += __ldg(ccol + (size_t)(a + mr) * (mc + 1) + j) * strip[(o + mr + a) * (mc + 1) + j];
         if (k <= nr - 2) { oi = k; oj = left ? 0 : nc - 1; }
     } else {
-        // the four corners: output c = o (< 4); groups share the (mr + 1) rows
-        if (o < 4) {
+        // the four corners: output c = o (< 4); groups share the (mr + 1) rows (one row:
+        // only the two top corners, which are then the line's two ends)
+        if (o < 4 && ((o & 1) == 0 || nr > 1)) {
             const bool top = (o & 1) == 0, left = (o & 2) == 0;
             for (int i = grp; i <= mr; i += ngrp) {
                 const int ri = top ? i : nr - 1 - i;

@@ -77,6 +77,21 @@ __device__ __forceinline__ T lap_at(const T* __restrict__ w, const T* __restrict
     return acc;
 }
 
+// (L_AR p)_ij: the same stencil with anti-reflective BCs (L with AR BCs, the remark
+// after eq. (scalereb)): on the first and last line of an axis the AR extension
+// makes that axis's two differences and weights equal, so the axis adds nothing there.
+template <typename T>
+__device__ __forceinline__ T lap_at_ar(const T* __restrict__ w, const T* __restrict__ p, int i, int j, int nr,
+                                       int nc) {
+    const size_t o = (size_t)i * nc + j;
+    const T pc = p[o];
+    const T wc = w[o];
+    T acc = T(0);
+    if (i > 0 && i < nr - 1) acc += wc * (pc - p[o + nc]) + w[o - nc] * (pc - p[o - nc]);
+    if (j > 0 && j < nc - 1) acc += wc * (pc - p[o + 1]) + w[o - 1] * (pc - p[o - 1]);
+    return acc;
+}
+
 // Raise a kernel's dynamic shared-memory limit to the device's opt-in maximum,
 // once per kernel and device (a function attribute is per device), so no
 // attribute call repeats while a graph is captured.

@@ -173,7 +173,7 @@ tvd_status gemm_precond_create(tvd_plan_s& p, cudaStream_t s) {
         g->owned.push_back(*ptr);
         return true;
     };
-    const bool reblur = p.method == TVD_METHOD_REBLUR;
+    const bool reblur = p.reblur();
     const bool sym = p.bc == TVD_BC_ANTIREFLECTIVE && !reblur;   // hat-S = hat-S^T (T_n is not symmetric)
     if (!alloc(&g->Br, (size_t)p.nr * g->ldr * esz)) return fail(TVD_ENOMEM);
     g->BrT = g->Br;

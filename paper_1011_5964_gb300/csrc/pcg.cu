@@ -210,17 +210,18 @@ cg_restart_kernel(const T* __restrict__ r, size_t n, CgState* st, double* red, u
     }
 }
 
-// r = b - hx - alpha L(w) x and ||r||^2 (double): the FP-step residual when
+// r = b - hx - alpha L(w) x (L_AR on a REBLUR_ARL plan) and ||r||^2 (double): the FP-step residual when
 // hx = H^T H x is already known.
 __global__ void __launch_bounds__(kThreads)
 residual_lx_kernel(const double* __restrict__ b, const double* __restrict__ hx, const double* __restrict__ w,
                    const double* __restrict__ x, double alpha, double* __restrict__ r, int nr, int nc, double* out,
-                   double* red, unsigned int* ticket) {
+                   double* red, unsigned int* ticket, int arl) {
     const size_t n = (size_t)nr * nc;
     double part = 0.0;
     GRID_STRIDE(o, n) {
         const int i = (int)(o / nc), j = (int)(o - (size_t)i * nc);
-        const double v = b[o] - hx[o] - alpha * lap_at(w, x, i, j, nr, nc);
+        const double l = arl ? lap_at_ar(w, x, i, j, nr, nc) : lap_at(w, x, i, j, nr, nc);
+        const double v = b[o] - hx[o] - alpha * l;
         r[o] = v;
         part += v * v;
     }
@@ -326,11 +327,43 @@ diffnorm_kernel(const double* __restrict__ a, const double* __restrict__ b, size
     if (block_reduce_last(part, red, ticket, blockIdx.x, gridDim.x, &s) && threadIdx.x == 0) *out = s;
 }
 
-__global__ void cast_d2f_kernel(const double* __restrict__ a, float* __restrict__ b, size_t n) {
-    GRID_STRIDE(o, n) b[o] = (float)a[o];
+// sum over pixels of psi = sqrt(|D u|^2 + beta^2) (forward differences, zero
+// on the last row / column): the TV term of the functional of eq. (mp).
+__global__ void __launch_bounds__(kThreads)
+tv_sum_kernel(const double* __restrict__ u, int nr, int nc, double beta2, double* out, double* red,
+              unsigned int* ticket) {
+    const size_t n = (size_t)nr * nc;
+    double part = 0.0;
+    GRID_STRIDE(o, n) {
+        const int i = (int)(o / nc), j = (int)(o - (size_t)i * nc);
+        const double uc = u[o];
+        const double dr = i < nr - 1 ? u[o + nc] - uc : 0.0;
+        const double dc = j < nc - 1 ? u[o + 1] - uc : 0.0;
+        part += sqrt(dr * dr + dc * dc + beta2);
+    }
+    double s;
+    if (block_reduce_last(part, red, ticket, blockIdx.x, gridDim.x, &s) && threadIdx.x == 0) *out = s;
 }
-__global__ void axpy_f2d_kernel(double* __restrict__ x, const float* __restrict__ d, size_t n) {
-    GRID_STRIDE(o, n) x[o] += (double)d[o];
+
+// out = x0 + t d and ||out||^2 (double).
+__global__ void __launch_bounds__(kThreads)
+axpy_to_kernel(const double* __restrict__ x0, const double* __restrict__ d, double t, double* __restrict__ out,
+               size_t n, double* norm2, double* red, unsigned int* ticket) {
+    double part = 0.0;
+    GRID_STRIDE(o, n) {
+        const double v = x0[o] + t * d[o];
+        out[o] = v;
+        part += v * v;
+    }
+    double s;
+    if (block_reduce_last(part, red, ticket, blockIdx.x, gridDim.x, &s) && threadIdx.x == 0) *norm2 = s;
+}
+
+__global__ void cast_d2f_kernel(const double* __restrict__ a, float* __restrict__ b, size_t n, double scale) {
+    GRID_STRIDE(o, n) b[o] = (float)(a[o] * scale);
+}
+__global__ void axpy_f2d_kernel(double* __restrict__ x, const float* __restrict__ d, size_t n, double scale) {
+    GRID_STRIDE(o, n) x[o] += (double)d[o] * scale;
 }
 __global__ void copy_f_kernel(const float* __restrict__ a, float* __restrict__ b, size_t n) {
     GRID_STRIDE(o, n) b[o] = a[o];
@@ -354,7 +387,7 @@ tvd_status residual_lx(const tvd_plan_s& p, const double* b, const double* hx, c
     const size_t n = (size_t)p.nr * p.nc;
     ProfScope prof(prof_class<double>(PROF_MISC), s);
     residual_lx_kernel<<<red_blocks(n), kThreads, 0, s>>>(b, hx, w, x, alpha, r, p.nr, p.nc, out_norm2, p.red,
-                                                          p.ticket + 5);
+                                                          p.ticket + 5, p.method == TVD_METHOD_REBLUR_ARL);
     TVD_CUDA_TRY(cudaGetLastError());
     return TVD_OK;
 }
@@ -384,16 +417,33 @@ tvd_status diffnorm2_d(const tvd_plan_s& p, const double* a, const double* b, do
     return TVD_OK;
 }
 
-tvd_status cast_d2f(const double* a, float* b, size_t n, cudaStream_t s) {
-    ProfScope prof(PROF_MISC, s);
-    cast_d2f_kernel<<<red_blocks(n), kThreads, 0, s>>>(a, b, n);
+tvd_status tv_sum_d(const tvd_plan_s& p, const double* u, double beta, double* out, cudaStream_t s) {
+    const size_t n = (size_t)p.nr * p.nc;
+    ProfScope prof(prof_class<double>(PROF_MISC), s);
+    tv_sum_kernel<<<red_blocks(n), kThreads, 0, s>>>(u, p.nr, p.nc, beta * beta, out, p.red, p.ticket + 5);
     TVD_CUDA_TRY(cudaGetLastError());
     return TVD_OK;
 }
 
-tvd_status axpy_f2d(double* x, const float* d, size_t n, cudaStream_t s) {
+tvd_status axpy_to_d(const tvd_plan_s& p, const double* x0, const double* d, double t, double* out, double* norm2,
+                     cudaStream_t s) {
+    const size_t n = (size_t)p.nr * p.nc;
+    ProfScope prof(prof_class<double>(PROF_MISC), s);
+    axpy_to_kernel<<<red_blocks(n), kThreads, 0, s>>>(x0, d, t, out, n, norm2, p.red, p.ticket + 5);
+    TVD_CUDA_TRY(cudaGetLastError());
+    return TVD_OK;
+}
+
+tvd_status cast_d2f(const double* a, float* b, size_t n, cudaStream_t s, double scale) {
     ProfScope prof(PROF_MISC, s);
-    axpy_f2d_kernel<<<red_blocks(n), kThreads, 0, s>>>(x, d, n);
+    cast_d2f_kernel<<<red_blocks(n), kThreads, 0, s>>>(a, b, n, scale);
+    TVD_CUDA_TRY(cudaGetLastError());
+    return TVD_OK;
+}
+
+tvd_status axpy_f2d(double* x, const float* d, size_t n, cudaStream_t s, double scale) {
+    ProfScope prof(PROF_MISC, s);
+    axpy_f2d_kernel<<<red_blocks(n), kThreads, 0, s>>>(x, d, n, scale);
     TVD_CUDA_TRY(cudaGetLastError());
     return TVD_OK;
 }

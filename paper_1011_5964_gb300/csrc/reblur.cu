@@ -58,6 +58,7 @@ static void ucorr_vectors(int n, std::vector<double>& out) {
 static void extension_weights(int n, std::vector<double>& c) {
     const int m = n - 2;
     c.assign(std::max(m, 0), 0.0);
+    if (m <= 0) return;   // a line of one sample (a 1D signal's row axis) has no border to extend
     std::vector<double> col(m), z(m + 2);
     for (int i = 1; i <= m; ++i) {
         const double s1 = sine_entry(m, i, 1);
@@ -417,12 +418,14 @@ static int bi_blocks(size_t n) {
     return (int)(b ? b : 1);
 }
 
-// y = A' x = H' H x + alpha L(w) x (H' = H: the plan's PSF is symmetric); hx: scratch
+// y = A' x = H' H x + alpha L(w) x (H' = H: the plan's PSF is symmetric; L_AR on a
+// REBLUR_ARL plan, as the fused L product plus its border-line correction); hx: scratch
 template <typename T>
 tvd_status reblur_matvec(const tvd_plan_s& p, const Ops<T>& o, const T* x, T* hx, T* y, double alpha,
                          cudaStream_t s) {
     TVD_TRY(blur_apply<T>(p, o, false, x, hx, s));
     TVD_TRY(forward_fuse<T>(p, o, hx, x, alpha, y, s));
+    if (p.method == TVD_METHOD_REBLUR_ARL) TVD_TRY(lar_border<T>(p, o.w, x, y, alpha, s));
     return TVD_OK;
 }
 

@@ -851,9 +851,45 @@ static void pick_pairs(LineArgs<T>& a, bool cols, int op) {
     }
 }
 
+// A column pass over lines of one sample (a 1D signal stored as one row): the
+// 1-point transform is the identity, its E weights are 1 and its G (difference)
+// and F (neighbour) weights 0, so each operation reduces to an elementwise one.
+template <typename T, int OP>
+__global__ void __launch_bounds__(kThreads) col1_kernel(LineArgs<T> a) {
+    pdl_wait();
+    if (a.st && a.st->done) return;
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < a.nc; j += gridDim.x * blockDim.x) {
+        if (OP == OP_COL_SOLVE) {
+            a.out0[j] = a.in0[j] * a.spec[j];
+        } else if (OP == OP_COL_EG) {
+            // Lambda_L = G_col (E_row w) + E_col (G_row w) = G_row w
+            const T lamL = a.in1[j];
+            if (a.lam_out) {
+                a.lam_out[j] = lamL;
+                continue;
+            }
+            const double sp = (double)a.spec[j] + a.alpha * (double)lamL;
+            if (!(sp > 1e-300) || !isfinite(sp)) atomicOr(a.bad, 1);
+            a.inv_out[j] = T(1.0 / sp);
+        } else {   // OP_COL_X: out = (x ? F : E) in
+            a.out0[j] = a.xa ? T(0) : a.in0[j];
+            a.out1[j] = a.xb ? T(0) : a.in1[j];
+        }
+    }
+}
+
 template <typename T, int BC, int OP>
 static tvd_status launch_line(LineArgs<T> a, cudaStream_t s) {
     const bool cols = (OP == OP_COL_SOLVE || OP == OP_COL_EG || OP == OP_COL_X);
+    if constexpr (OP == OP_COL_SOLVE || OP == OP_COL_EG || OP == OP_COL_X) {
+        if (a.n == 1) {
+            ProfScope prof(prof_class<T>(OP == OP_COL_SOLVE ? PROF_COL_SOLVE : PROF_EG_COL), s);
+            TVD_CUDA_TRY(launch_pdl(col1_kernel<T, OP>, dim3((a.nc + kThreads - 1) / kThreads), dim3(kThreads), 0,
+                                    s, a));
+            TVD_CUDA_TRY(cudaGetLastError());
+            return TVD_OK;
+        }
+    }
     pick_pairs<T>(a, cols, OP);
     if (a.fp.bl && line_smem<T>(a, OP) > 227 * 1024) {
         a.fp.bl = 0;   // the M2-point buffers do not fit: direct sums for the large prime factors
@@ -895,7 +931,7 @@ static LineArgs<T> base_args(const tvd_plan_s& p, const Ops<T>& o, bool cols) {
     a.aux = cols ? o.aux_r : o.aux_c;
     a.red = p.red;
     a.ticket = p.ticket + 2;
-    a.ucorr = p.method == TVD_METHOD_REBLUR ? (cols ? o.ucorr_r : o.ucorr_c) : nullptr;
+    a.ucorr = p.reblur() ? (cols ? o.ucorr_r : o.ucorr_c) : nullptr;
     return a;
 }
 
@@ -1026,7 +1062,9 @@ __global__ void __launch_bounds__(kThreads)
 ar_ext_cols_kernel(T* __restrict__ X, int nr, int nc, const double* __restrict__ cc) {
     const int lane = threadIdx.x & 31;
     const int warps = (gridDim.x * blockDim.x) >> 5;
-    for (int i = 1 + ((blockIdx.x * blockDim.x + threadIdx.x) >> 5); i <= nr - 2; i += warps) {
+    // interior rows; a single row (a 1D signal) has no border row, so it is extended itself
+    const int i0 = nr == 1 ? 0 : 1, i1 = nr == 1 ? 0 : nr - 2;
+    for (int i = i0 + ((blockIdx.x * blockDim.x + threadIdx.x) >> 5); i <= i1; i += warps) {
         const T* row = X + (size_t)i * nc;
         double acc = 0.0;
         for (int j = 1 + lane; j <= nc - 2; j += 32) acc += cc[j - 1] * (double)row[j];
@@ -1073,6 +1111,7 @@ static tvd_status ar_extend(const tvd_plan_s& p, const Ops<T>& o, T* X, cudaStre
     const int blocks = num_sms() * 4;
     ar_ext_cols_kernel<T><<<blocks, kThreads, 0, s>>>(X, p.nr, p.nc, o.extc_c);
     TVD_CUDA_TRY(cudaGetLastError());
+    if (p.nr == 1) return TVD_OK;
     ar_ext_rows_kernel<T><<<(p.nc + kThreads - 1) / kThreads, kThreads, 0, s>>>(X, p.nr, p.nc, o.extc_r);
     TVD_CUDA_TRY(cudaGetLastError());
     return TVD_OK;
@@ -1137,7 +1176,7 @@ static tvd_status reblur_spectrum_setup(const tvd_plan_s& p, Ops<T>& o, double a
 
 template <typename T>
 tvd_status spectrum_setup(const tvd_plan_s& p, Ops<T>& o, double alpha, int* bad_flag, cudaStream_t s) {
-    if (p.method == TVD_METHOD_REBLUR) return reblur_spectrum_setup<T>(p, o, alpha, bad_flag, s);
+    if (p.reblur()) return reblur_spectrum_setup<T>(p, o, alpha, bad_flag, s);
     if (p.pc == TVD_PC_FASTD) return scaled_spectrum_setup<T>(p, o, alpha, bad_flag, s);
     LineArgs<T> a = base_args<T>(p, o, false);
     a.in0 = o.w;
@@ -1175,6 +1214,7 @@ __global__ void lamH2_kernel(const double* __restrict__ cr, const double* __rest
 }
 
 static std::vector<double> symbol_grid(int n, tvd_bc bc) {
+    if (n == 1) return std::vector<double>(1, 0.0);   // one sample: the constant, y = 0
     std::vector<double> y(n);
     for (int k = 0; k < n; ++k) y[k] = (bc == TVD_BC_ANTIREFLECTIVE) ? k * M_PI / (n - 1) : k * M_PI / n;
     if (bc == TVD_BC_ANTIREFLECTIVE) {

@@ -24,16 +24,22 @@ diffusivity_kernel(const T* __restrict__ u, T* __restrict__ w, int nr, int nc, T
 
 template <typename T>
 __global__ void __launch_bounds__(kThreads)
-diag_scale_kernel(const T* __restrict__ w, T* __restrict__ dmh, T* __restrict__ dinv, int nr, int nc, T alpha) {
+diag_scale_kernel(const T* __restrict__ w, T* __restrict__ dmh, T* __restrict__ dinv, int nr, int nc, T alpha,
+                  int arl) {
     const size_t n = (size_t)nr * nc;
     for (size_t o = blockIdx.x * (size_t)blockDim.x + threadIdx.x; o < n; o += (size_t)gridDim.x * blockDim.x) {
         const int i = (int)(o / nc), j = (int)(o - (size_t)i * nc);
         const T wc = w[o];
         T d = T(0);
-        if (i < nr - 1) d += wc;
-        if (j < nc - 1) d += wc;
-        if (i > 0) d += w[o - nc];
-        if (j > 0) d += w[o - 1];
+        if (arl) {   // diag(L_AR): each axis's pair dropped on its first and last line
+            if (i > 0 && i < nr - 1) d += wc + w[o - nc];
+            if (j > 0 && j < nc - 1) d += wc + w[o - 1];
+        } else {
+            if (i < nr - 1) d += wc;
+            if (j < nc - 1) d += wc;
+            if (i > 0) d += w[o - nc];
+            if (j > 0) d += w[o - 1];
+        }
         const T D = T(1) + alpha * d;
         dmh[o] = T(1) / sqrt(D);
         dinv[o] = T(1) / D;
@@ -42,11 +48,33 @@ diag_scale_kernel(const T* __restrict__ w, T* __restrict__ dmh, T* __restrict__ 
 
 template <typename T>
 __global__ void __launch_bounds__(kThreads)
-tv_apply_kernel(const T* __restrict__ w, const T* __restrict__ x, T* __restrict__ y, int nr, int nc) {
+tv_apply_kernel(const T* __restrict__ w, const T* __restrict__ x, T* __restrict__ y, int nr, int nc, int arl) {
     const size_t n = (size_t)nr * nc;
     for (size_t o = blockIdx.x * (size_t)blockDim.x + threadIdx.x; o < n; o += (size_t)gridDim.x * blockDim.x) {
         const int i = (int)(o / nc), j = (int)(o - (size_t)i * nc);
-        y[o] = lap_at(w, x, i, j, nr, nc);
+        y[o] = arl ? lap_at_ar(w, x, i, j, nr, nc) : lap_at(w, x, i, j, nr, nc);
+    }
+}
+
+// y -= alpha (L - L_AR) x on the border lines (the only pixels where they differ): turns a
+// product with L, fused elsewhere, into one with L_AR.
+template <typename T>
+__global__ void __launch_bounds__(kThreads)
+lar_border_kernel(const T* __restrict__ w, const T* __restrict__ x, T* __restrict__ y, int nr, int nc, T alpha) {
+    // border pixels in order: row 0, row nr-1 (if nr > 1), then columns 0 and nc-1 of rows 1..nr-2
+    const int nrow = nr > 1 ? 2 * nc : nc, ncol = nr > 2 ? 2 * (nr - 2) : 0;
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < nrow + ncol; k += gridDim.x * blockDim.x) {
+        int i, j;
+        if (k < nrow) {
+            i = k < nc ? 0 : nr - 1;
+            j = k < nc ? k : k - nc;
+        } else {
+            const int q = k - nrow;
+            i = 1 + (q >> 1);
+            j = (q & 1) ? nc - 1 : 0;
+        }
+        const size_t o = (size_t)i * nc + j;
+        y[o] -= alpha * (lap_at(w, x, i, j, nr, nc) - lap_at_ar(w, x, i, j, nr, nc));
     }
 }
 
@@ -69,7 +97,8 @@ template <typename T>
 tvd_status diag_scale(const tvd_plan_s& p, const T* w, double alpha, T* dmh, T* dinv, cudaStream_t s) {
     const size_t n = (size_t)p.nr * p.nc;
     ProfScope prof(prof_class<T>(PROF_TV), s);
-    diag_scale_kernel<T><<<ew_blocks(n), kThreads, 0, s>>>(w, dmh, dinv, p.nr, p.nc, T(alpha));
+    diag_scale_kernel<T><<<ew_blocks(n), kThreads, 0, s>>>(w, dmh, dinv, p.nr, p.nc, T(alpha),
+                                                           p.method == TVD_METHOD_REBLUR_ARL);
     TVD_CUDA_TRY(cudaGetLastError());
     return TVD_OK;
 }
@@ -78,7 +107,16 @@ template <typename T>
 tvd_status tv_apply(const tvd_plan_s& p, const T* w, const T* x, T* y, cudaStream_t s) {
     const size_t n = (size_t)p.nr * p.nc;
     ProfScope prof(prof_class<T>(PROF_TV), s);
-    tv_apply_kernel<T><<<ew_blocks(n), kThreads, 0, s>>>(w, x, y, p.nr, p.nc);
+    tv_apply_kernel<T><<<ew_blocks(n), kThreads, 0, s>>>(w, x, y, p.nr, p.nc, p.method == TVD_METHOD_REBLUR_ARL);
+    TVD_CUDA_TRY(cudaGetLastError());
+    return TVD_OK;
+}
+
+template <typename T>
+tvd_status lar_border(const tvd_plan_s& p, const T* w, const T* x, T* y, double alpha, cudaStream_t s) {
+    const int nb = (p.nr > 1 ? 2 * p.nc : p.nc) + (p.nr > 2 ? 2 * (p.nr - 2) : 0);
+    ProfScope prof(prof_class<T>(PROF_TV), s);
+    lar_border_kernel<T><<<(nb + kThreads - 1) / kThreads, kThreads, 0, s>>>(w, x, y, p.nr, p.nc, T(alpha));
     TVD_CUDA_TRY(cudaGetLastError());
     return TVD_OK;
 }
@@ -89,5 +127,8 @@ template tvd_status diag_scale<float>(const tvd_plan_s&, const float*, double, f
 template tvd_status diag_scale<double>(const tvd_plan_s&, const double*, double, double*, double*, cudaStream_t);
 template tvd_status tv_apply<float>(const tvd_plan_s&, const float*, const float*, float*, cudaStream_t);
 template tvd_status tv_apply<double>(const tvd_plan_s&, const double*, const double*, double*, cudaStream_t);
+template tvd_status lar_border<float>(const tvd_plan_s&, const float*, const float*, float*, double, cudaStream_t);
+template tvd_status lar_border<double>(const tvd_plan_s&, const double*, const double*, double*, double,
+                                       cudaStream_t);
 
 }  // namespace tvd

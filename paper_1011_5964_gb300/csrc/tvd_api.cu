@@ -216,7 +216,12 @@ static tvd_status ops_alloc(tvd_plan_s& p, Ops<T>& o, cudaStream_t s) {
     transform_tables(p.nc, p.bc, tw, aux);
     TVD_TRY(upload<T>((T**)&o.tw_c, tw, s));
     TVD_TRY(upload<T>(&o.aux_c, aux, s));
-    transform_tables(p.nr, p.bc, tw, aux);
+    if (p.nr > 1) {
+        transform_tables(p.nr, p.bc, tw, aux);
+    } else {
+        tw.assign(2, 0.0);
+        aux.assign(16, 0.0);
+    }
     TVD_TRY(upload<T>((T**)&o.tw_r, tw, s));
     TVD_TRY(upload<T>(&o.aux_r, aux, s));
     if (p.fft_c.bl) {
@@ -295,8 +300,9 @@ tvd_status build_psf(Psf& out, const double* h, int pr, int pc, int nr, int nc) 
     };
     while (mr > 0 && row_zero(mr) && row_zero(-mr)) --mr;
     while (mc > 0 && col_zero(mc) && col_zero(-mc)) --mc;
-    if (mr > nr - 2 || mc > nc - 2) {
-        set_error("PSF half-width exceeds n - 2 along an axis");
+    if ((nr == 1 ? mr > 0 : mr > nr - 2) || mc > nc - 2) {
+        set_error(nr == 1 ? "a 1D signal (n_rows = 1) needs a PSF of one row"
+                          : "PSF half-width exceeds n - 2 along an axis");
         return TVD_EPSF_SIZE;
     }
     if (mr > 48 || mc > 48) {
@@ -356,7 +362,7 @@ static bool fast_pc(tvd_precond pc) { return pc == TVD_PC_FAST || pc == TVD_PC_D
 // 128-512 images 74 -> 87 deblurs/s against a bound of 256), else the FFT form.
 // TVD_TRANSFORM=gemm / fft overrides the rule.
 static tvd_transform default_transform(const tvd_plan_s& p) {
-    if (p.mode != TVD_MODE_MIXED || !fast_pc(p.pc)) return TVD_TRANSFORM_FFT;
+    if (p.mode != TVD_MODE_MIXED || !fast_pc(p.pc) || p.nr == 1) return TVD_TRANSFORM_FFT;
     const char* v = std::getenv("TVD_TRANSFORM");
     if (v && !std::strcmp(v, "gemm")) return TVD_TRANSFORM_GEMM;
     if (v && !std::strcmp(v, "fft")) return TVD_TRANSFORM_FFT;
@@ -656,7 +662,7 @@ static tvd_status solve_mixed(tvd_plan_s& p, double alpha, const double* b, doub
 
 static tvd_status solve(tvd_plan_s& p, const double* u_lag, double alpha, double beta, const double* b, double* x,
                         double tol, int maxit, SolveResult* res, cudaStream_t s, bool cached_hx = false) {
-    if (p.method == TVD_METHOD_REBLUR) {
+    if (p.reblur()) {
         // eq. (fpp): the preconditioner of the reblurring method, then PBiCGstab
         if (p.mode == TVD_MODE_FP64) TVD_TRY(setup_precond<double>(p, p.d, u_lag, alpha, beta, s));
         else TVD_TRY(setup_mixed(p, u_lag, alpha, beta, s));
@@ -692,8 +698,8 @@ tvd_status tvd_plan_set_transform(tvd_plan plan, int kind, void* stream) {
         set_error("tvd_plan_set_transform: NULL plan or unknown transform kind");
         return TVD_EINVAL;
     }
-    if (kind == TVD_TRANSFORM_GEMM && (plan->mode != TVD_MODE_MIXED || !fast_pc(plan->pc))) {
-        set_error("tvd_plan_set_transform: the GEMM form needs a MIXED plan with a fast preconditioner");
+    if (kind == TVD_TRANSFORM_GEMM && (plan->mode != TVD_MODE_MIXED || !fast_pc(plan->pc) || plan->nr == 1)) {
+        set_error("tvd_plan_set_transform: the GEMM form needs a MIXED 2D plan with a fast preconditioner");
         return TVD_EINVAL;
     }
     if ((kind == TVD_TRANSFORM_GEMM) == (plan->gemm != nullptr)) return TVD_OK;
@@ -729,10 +735,12 @@ tvd_status tvd_plan_create(tvd_plan* out, int n_rows, int n_cols, const double* 
         return TVD_EINVAL;
     }
     *out = nullptr;
-    // line transforms keep two lines (float: up to 4096) or one line pair in shared memory
+    // line transforms keep two lines (float: up to 4096) or one line pair in shared memory;
+    // n_rows = 1 is a 1D signal of n_cols samples (Sec. 5.1)
     const int max_side = (mode == TVD_MODE_FP64) ? 2048 : 4096;
-    if (n_rows < 3 || n_cols < 3 || n_rows > max_side || n_cols > max_side) {
-        set_error("image sides must be in [3, 2048] (FP64 plans) or [3, 4096] (MIXED plans)");
+    if ((n_rows < 3 && n_rows != 1) || n_cols < 3 || n_rows > max_side || n_cols > max_side) {
+        set_error("image sides must be in [3, 2048] (FP64 plans) or [3, 4096] (MIXED plans); n_rows may be 1 "
+                  "(a 1D signal)");
         return TVD_EINVAL;
     }
     if ((bc != TVD_BC_REFLECTIVE && bc != TVD_BC_ANTIREFLECTIVE) || pc < TVD_PC_NONE || pc > TVD_PC_FASTD ||
@@ -754,7 +762,8 @@ tvd_status tvd_plan_create(tvd_plan* out, int n_rows, int n_cols, const double* 
     }
     const int Lr = bc == TVD_BC_ANTIREFLECTIVE ? n_rows - 1 : n_rows;
     const int Lc = bc == TVD_BC_ANTIREFLECTIVE ? n_cols - 1 : n_cols;
-    p->fft_r = make_fft_plan(Lr);
+    // one row: the column passes are elementwise (the 1-point transform is the identity)
+    if (n_rows > 1) p->fft_r = make_fft_plan(Lr);
     p->fft_c = make_fft_plan(Lc);
     const size_t n = (size_t)n_rows * n_cols;
     auto fail = [&](tvd_status e) {
@@ -868,17 +877,23 @@ static tvd_status adjoint_mixed(tvd_plan_s& p, const double* b, double* lam, con
     *iters_out = 0;
     *relres_out = 0.0;
     if (!std::isfinite(rr0)) {
-        set_error("tv_deblur_adjoint: non-finite right-hand side");
+        set_error("Jacobian solve: non-finite right-hand side");
         return TVD_EBREAKDOWN;
     }
     if (rr0 == 0.0) return TVD_OK;
     const double target = tol * tol * rr0, delta2 = 1e-8;
     const bool transform_pc = (p.pc == TVD_PC_FAST || p.pc == TVD_PC_DFAST || p.pc == TVD_PC_FASTD);
     double rr_ref = rr0;
-    int sweeps = 0, last_iter = -1;
-    TVD_TRY(cast_d2f(b, f.r, n, s));
+    int sweeps = 0, last_iter = -1, stalled = 0;
+    // The float CG runs on the residual times sc, a power of two that brings its norm
+    // to [1, 2) (exact in float): a tiny right-hand side, as in the last Newton steps,
+    // would otherwise reach the float denormal range, where products flush to zero.
+    // sc is renewed (with a fresh search direction) once the scaled residual fell below 2^-40.
+    auto pow2_scale = [](double rr) { return std::ldexp(1.0, -std::ilogb(std::sqrt(rr))); };
+    double sc = pow2_scale(rr0);
+    TVD_TRY(cast_d2f(b, f.r, n, s, sc));
     TVD_TRY(fill_zero_f(f.x, n, s));
-    TVD_TRY(cg_restart<float>(p, f.r, st, std::max(target, delta2 * rr_ref), maxit, 0, s));
+    TVD_TRY(cg_restart<float>(p, f.r, st, std::max(target, delta2 * rr_ref) * sc * sc, maxit, 0, s));
     for (;;) {
         for (int k = 0; k < 2 * kChunk; ++k) {
             switch (p.pc) {
@@ -897,14 +912,14 @@ static tvd_status adjoint_mixed(tvd_plan_s& p, const double* b, double* lam, con
         if (h.status == TVD_ETIMEOUT) return timeout_exit(p, s);
         if (!h.done) {
             if (h.iter == last_iter) {   // the kernels always advance a running solve
-                set_error("adjoint CG made no progress between two checks");
+                set_error("Jacobian CG made no progress between two checks");
                 return TVD_ECUDA;
             }
             last_iter = h.iter;
             continue;
         }
         last_iter = -1;
-        TVD_TRY(axpy_f2d(lam, f.x, n, s));
+        TVD_TRY(axpy_f2d(lam, f.x, n, s, 1.0 / sc));
         TVD_TRY(fill_zero_f(f.x, n, s));
         TVD_TRY(blur_apply<double>(p, p.d, false, lam, p.d.t, s));
         TVD_TRY(blur_apply<double>(p, p.d, true, p.d.t, p.d.q, s));
@@ -914,20 +929,111 @@ static tvd_status adjoint_mixed(tvd_plan_s& p, const double* b, double* lam, con
         TVD_CUDA_TRY(cudaStreamSynchronize(s));
         ++sweeps;
         if (!std::isfinite(rr) || h.status == TVD_EBREAKDOWN) {
-            set_error("tv_deblur_adjoint: the adjoint CG broke down");
+            set_error("Jacobian solve: the CG broke down");
             return TVD_EBREAKDOWN;
         }
         *relres_out = std::sqrt(rr / rr0);
-        if (rr < target) return TVD_OK;
-        if (h.iter >= maxit || sweeps > 200) {
-            set_error("tv_deblur_adjoint: the adjoint CG did not reach its tolerance");
+        if (rr < target) return gemm_precond_check(p, s);
+        // each float sweep lowers the residual by about 1e4; three sweeps in a row that
+        // do not halve the double residual mean it sits at its rounding floor
+        stalled = rr > 0.25 * rr_ref ? stalled + 1 : 0;
+        if (h.iter >= maxit || sweeps > 200 || stalled >= 3) {
+            set_error(stalled >= 3 ? "Jacobian solve: the double residual stagnated above the tolerance"
+                                   : "Jacobian solve: the CG did not reach its tolerance");
             return TVD_ENOCONV;
         }
-        const int mode = (rr < 4.0 * h.rr) ? 1 : 2;
+        int mode = (rr * sc * sc < 4.0 * h.rr) ? 1 : 2;
+        if (rr * sc * sc < 0x1p-80) {
+            sc = pow2_scale(rr);
+            mode = 2;
+        }
         rr_ref = rr;
-        TVD_TRY(cast_d2f(p.res, f.r, n, s));
-        TVD_TRY(cg_restart<float>(p, f.r, st, std::max(target, delta2 * rr_ref), maxit, mode, s));
+        TVD_TRY(cast_d2f(p.res, f.r, n, s, sc));
+        TVD_TRY(cg_restart<float>(p, f.r, st, std::max(target, delta2 * rr_ref) * sc * sc, maxit, mode, s));
     }
+}
+
+// lam = J(u)^-1 b from lam = 0, J = H^T H + alpha nabla^2 J_beta(u) (SPD), by PCG
+// preconditioned with the plan's preconditioner of the lagged operator at u,
+// which the caller has set up (setup_precond / setup_mixed at u: o.w holds
+// w(u)), with the Hessian coefficients gr, gc of hess_coef at u (and their
+// float copies grf, gcf on MIXED plans). FP64 plans run one double PCG; MIXED
+// plans the float PCG with double residual replacement of adjoint_mixed.
+// Returns TVD_OK, TVD_ENOCONV (lam holds the last iterate), TVD_EBREAKDOWN,
+// TVD_ETIMEOUT or a CUDA error, with *iters and *relres.
+static tvd_status jacobian_solve(tvd_plan_s& p, const double* b, double* lam, const double* gr, const double* gc,
+                                 const float* grf, const float* gcf, double alpha, double tol, int maxit, int* iters,
+                                 double* relres, cudaStream_t s) {
+    *iters = 0;
+    *relres = 0.0;
+    if (p.mode == TVD_MODE_MIXED) return adjoint_mixed(p, b, lam, gr, gc, grf, gcf, alpha, tol, maxit, iters, relres, s);
+    const size_t n = (size_t)p.nr * p.nc;
+    Ops<double>& o = p.d;
+    TVD_CUDA_TRY(cudaMemsetAsync(lam, 0, n * sizeof(double), s));
+    TVD_CUDA_TRY(cudaMemsetAsync(o.q, 0, n * sizeof(double), s));
+    CgState* st = p.state;
+    TVD_TRY(cg_init<double>(p, b, o.q, o.r, st, tol, maxit, s));
+    const bool fused_xr = (p.pc == TVD_PC_FAST || p.pc == TVD_PC_DFAST || p.pc == TVD_PC_FASTD);
+    int done_iters = 0;
+    for (;;) {
+        for (int k = 0; k < 2 * kChunk; ++k) {
+            switch (p.pc) {
+                case TVD_PC_NONE: TVD_TRY(cg_simple_precond<double>(p, o.r, nullptr, o.z, st, s)); break;
+                case TVD_PC_DIAG: TVD_TRY(cg_simple_precond<double>(p, o.r, o.dinv, o.z, st, s)); break;
+                default: TVD_TRY(precond_solve<double>(p, o, o.r, o.z, st, s, lam)); break;
+            }
+            TVD_TRY(blur_pupdate<double>(p, o, o.z, o.p, o.p2, o.t, st, s));
+            TVD_TRY(blur_apply<double>(p, o, true, o.t, o.q, s, st));
+            TVD_TRY(hess_add(p, o.q, o.p, o.p2, o.w, gr, gc, alpha, st, s));
+            if (!fused_xr) TVD_TRY(cg_xrupdate<double>(p, lam, o.r, o.p, o.p2, o.q, st, s));
+        }
+        done_iters += 2 * kChunk;
+        TVD_TRY(read_state<double>(p, s));
+        if (p.hstate->done) break;
+        if (done_iters > maxit + 4 * kChunk) {
+            set_error("Jacobian CG state did not reach done after maxit iterations");
+            return TVD_ECUDA;
+        }
+    }
+    const CgState h = *p.hstate;
+    *iters = h.iter;
+    *relres = h.rr0 > 0.0 ? std::sqrt(h.rr / h.rr0) : 0.0;
+    if (h.status == TVD_EBREAKDOWN) {
+        set_error("Jacobian solve: the CG broke down");
+        return TVD_EBREAKDOWN;
+    }
+    if (h.status == TVD_ENOCONV) {
+        set_error("Jacobian solve: the CG did not reach its tolerance");
+        return TVD_ENOCONV;
+    }
+    return TVD_OK;
+}
+
+// g(x) = H^T (H x - v) + alpha L(x) x of eq. (el), returned as r = -g(x) = b - H^T H x - alpha L(w(x)) x
+// with b = H^T v (double, any mode), and ||g||^2 on the host. w(x) goes to p.d.w, H x to p.d.t,
+// H^T H x to p.hx (for x, recorded in p.hx_for). On a reblurring plan, with b = H' v, the same call
+// gives the residual of eq. (fpp), b - H' H x - alpha L(w(x)) x (H' = H for the plans' PSFs).
+// With data_out non-NULL, also ||H x - v||^2 and sum psi(x) (the two terms of the functional).
+static tvd_status el_residual(tvd_plan_s& p, const double* x, const double* v, const double* b, double alpha,
+                              double beta, double* r, double* g2, double* data_out, cudaStream_t s) {
+    TVD_TRY(diffusivity<double>(p, x, beta, p.d.w, s));
+    TVD_TRY(blur_apply<double>(p, p.d, false, x, p.d.t, s));
+    if (data_out) {
+        TVD_TRY(diffnorm2_d(p, p.d.t, v, p.scal + 13, s));
+        TVD_TRY(tv_sum_d(p, x, beta, p.scal + 14, s));
+    }
+    TVD_TRY(blur_apply<double>(p, p.d, !p.reblur(), p.d.t, p.hx, s));
+    TVD_TRY(residual_lx(p, b, p.hx, p.d.w, x, alpha, r, p.scal + 12, s));
+    p.hx_for = x;
+    double h3[3] = {0.0, 0.0, 0.0};
+    TVD_CUDA_TRY(cudaMemcpyAsync(h3, p.scal + 12, 3 * sizeof(double), cudaMemcpyDeviceToHost, s));
+    TVD_CUDA_TRY(cudaStreamSynchronize(s));
+    *g2 = h3[0];
+    if (data_out) {
+        data_out[0] = h3[1];
+        data_out[1] = h3[2];
+    }
+    return TVD_OK;
 }
 
 extern "C" {
@@ -938,6 +1044,11 @@ tvd_status tv_deblur_adjoint(tvd_plan plan, const void* u_star, const void* v, d
     if (!plan || !u_star || !v || !dl_du || !lambda_out || lambda_out == dl_du || lambda_out == u_star ||
         lambda_out == v || !(alpha >= 0.0) || !(beta > 0.0) || !(tol > 0.0) || maxit < 0) {
         set_error("tv_deblur_adjoint: invalid argument");
+        return TVD_EINVAL;
+    }
+    if (plan->reblur()) {
+        set_error("tv_deblur_adjoint: differentiates the fixed point of eq. (fp); a reblurring plan's "
+                  "linearisation is not symmetric");
         return TVD_EINVAL;
     }
     tvd_plan_s& p = *plan;
@@ -964,58 +1075,14 @@ tvd_status tv_deblur_adjoint(tvd_plan plan, const void* u_star, const void* v, d
         if (mixed) {
             TVD_TRY(cast_d2f(gr, gf, n, s));
             TVD_TRY(cast_d2f(gc, gf + n, n, s));
-            int it = 0;
-            double rel = 0.0;
-            const tvd_status cg = adjoint_mixed(p, (const double*)dl_du, lam, gr, gc, gf, gf + n, alpha, tol, maxit,
-                                                &it, &rel, s);
-            if (iters) *iters = it;
-            if (relres) *relres = rel;
-            if (cg != TVD_OK && cg != TVD_ENOCONV) return cg;   // gradients still written after ENOCONV
-            TVD_TRY(adjoint_gradients(p, o, lam, u, (const double*)v, alpha, beta, ext, dl_dpsf ? taps : nullptr,
-                                      out2, s));
-            double h2[2] = {0.0, 0.0};
-            TVD_CUDA_TRY(cudaMemcpyAsync(h2, out2, sizeof(h2), cudaMemcpyDeviceToHost, s));
-            if (dl_dpsf)
-                TVD_CUDA_TRY(cudaMemcpyAsync(dl_dpsf, taps, ntap * sizeof(double), cudaMemcpyDeviceToHost, s));
-            TVD_CUDA_TRY(cudaStreamSynchronize(s));
-            if (dl_dalpha) *dl_dalpha = -h2[0];
-            if (dl_dbeta) *dl_dbeta = alpha * beta * h2[1];
-            if (cg == TVD_ENOCONV) set_error("tv_deblur_adjoint: the adjoint CG did not reach its tolerance");
-            return cg;
         }
-        TVD_CUDA_TRY(cudaMemsetAsync(lam, 0, n * sizeof(double), s));
-        TVD_CUDA_TRY(cudaMemsetAsync(o.q, 0, n * sizeof(double), s));
-        CgState* st = p.state;
-        TVD_TRY(cg_init<double>(p, (const double*)dl_du, o.q, o.r, st, tol, maxit, s));
-        const bool fused_xr = (p.pc == TVD_PC_FAST || p.pc == TVD_PC_DFAST || p.pc == TVD_PC_FASTD);
-        int done_iters = 0;
-        for (;;) {
-            for (int k = 0; k < 2 * kChunk; ++k) {
-                switch (p.pc) {
-                    case TVD_PC_NONE: TVD_TRY(cg_simple_precond<double>(p, o.r, nullptr, o.z, st, s)); break;
-                    case TVD_PC_DIAG: TVD_TRY(cg_simple_precond<double>(p, o.r, o.dinv, o.z, st, s)); break;
-                    default: TVD_TRY(precond_solve<double>(p, o, o.r, o.z, st, s, lam)); break;
-                }
-                TVD_TRY(blur_pupdate<double>(p, o, o.z, o.p, o.p2, o.t, st, s));
-                TVD_TRY(blur_apply<double>(p, o, true, o.t, o.q, s, st));
-                TVD_TRY(hess_add(p, o.q, o.p, o.p2, o.w, gr, gc, alpha, st, s));
-                if (!fused_xr) TVD_TRY(cg_xrupdate<double>(p, lam, o.r, o.p, o.p2, o.q, st, s));
-            }
-            done_iters += 2 * kChunk;
-            TVD_TRY(read_state<double>(p, s));
-            if (p.hstate->done) break;
-            if (done_iters > maxit + 4 * kChunk) {
-                set_error("adjoint CG state did not reach done after maxit iterations");
-                return TVD_ECUDA;
-            }
-        }
-        const CgState h = *p.hstate;
-        if (iters) *iters = h.iter;
-        if (relres) *relres = h.rr0 > 0.0 ? std::sqrt(h.rr / h.rr0) : 0.0;
-        if (h.status == TVD_EBREAKDOWN) {
-            set_error("tv_deblur_adjoint: the adjoint CG broke down");
-            return TVD_EBREAKDOWN;
-        }
+        int it = 0;
+        double rel = 0.0;
+        const tvd_status cg = jacobian_solve(p, (const double*)dl_du, lam, gr, gc, gf, mixed ? gf + n : nullptr, alpha,
+                                             tol, maxit, &it, &rel, s);
+        if (iters) *iters = it;
+        if (relres) *relres = rel;
+        if (cg != TVD_OK && cg != TVD_ENOCONV) return cg;   // gradients still written after ENOCONV
         TVD_TRY(adjoint_gradients(p, o, lam, u, (const double*)v, alpha, beta, ext, dl_dpsf ? taps : nullptr, out2,
                                   s));
         double h2[2] = {0.0, 0.0};
@@ -1024,11 +1091,8 @@ tvd_status tv_deblur_adjoint(tvd_plan plan, const void* u_star, const void* v, d
         TVD_CUDA_TRY(cudaStreamSynchronize(s));
         if (dl_dalpha) *dl_dalpha = -h2[0];
         if (dl_dbeta) *dl_dbeta = alpha * beta * h2[1];
-        if (h.status == TVD_ENOCONV) {
-            set_error("tv_deblur_adjoint: the adjoint CG did not reach its tolerance");
-            return TVD_ENOCONV;
-        }
-        return TVD_OK;
+        if (cg == TVD_ENOCONV) set_error("tv_deblur_adjoint: the adjoint CG did not reach its tolerance");
+        return cg;
     };
     const tvd_status st = run();
     cudaStreamSynchronize(s);
@@ -1082,21 +1146,22 @@ tvd_status tau_precond_solve(tvd_plan plan, const void* r, void* z, void* stream
 }
 
 tvd_status tvd_plan_set_method(tvd_plan plan, int method, void* stream) {
-    if (!plan || (method != TVD_METHOD_FP && method != TVD_METHOD_REBLUR)) {
+    if (!plan || (method != TVD_METHOD_FP && method != TVD_METHOD_REBLUR && method != TVD_METHOD_REBLUR_ARL)) {
         set_error("tvd_plan_set_method: invalid argument");
         return TVD_EINVAL;
     }
-    if (method == TVD_METHOD_REBLUR && plan->bc != TVD_BC_ANTIREFLECTIVE) {
+    if (method != TVD_METHOD_FP && plan->bc != TVD_BC_ANTIREFLECTIVE) {
         set_error("tvd_plan_set_method: the reblurring method needs anti-reflective BCs (Sec. 3)");
         return TVD_EINVAL;
     }
     if (plan->method == method) return TVD_OK;
     cudaStream_t s = (cudaStream_t)stream;
     TVD_CUDA_TRY(cudaStreamSynchronize(s));
-    if (method == TVD_METHOD_REBLUR) TVD_TRY(reblur_tables(*plan, s));
+    if (method != TVD_METHOD_FP) TVD_TRY(reblur_tables(*plan, s));
+    const bool same_transforms = (method != TVD_METHOD_FP) == plan->reblur();
     plan->method = method;
     plan->precond_ready = false;
-    if (plan->gemm) {
+    if (plan->gemm && !same_transforms) {
         // the transform matrices follow the method: rebuild them
         TVD_CUDA_TRY(cudaDeviceSynchronize());
         gemm_precond_destroy(*plan);
@@ -1118,7 +1183,7 @@ tvd_status pbicgstab_solve(tvd_plan plan, const void* u_lag, double alpha, doubl
         set_error("pbicgstab_solve: invalid argument");
         return TVD_EINVAL;
     }
-    if (plan->method != TVD_METHOD_REBLUR) {
+    if (!plan->reblur()) {
         set_error("pbicgstab_solve: the plan solves eq. (fp); call tvd_plan_set_method(plan, TVD_METHOD_REBLUR)");
         return TVD_EINVAL;
     }
@@ -1139,7 +1204,7 @@ tvd_status pcg_solve(tvd_plan plan, const void* u_lag, double alpha, double beta
         set_error("pcg_solve: invalid argument");
         return TVD_EINVAL;
     }
-    if (plan->method == TVD_METHOD_REBLUR) {
+    if (plan->reblur()) {
         set_error("pcg_solve: the plan solves eq. (fpp) (not symmetric); use pbicgstab_solve");
         return TVD_EINVAL;
     }
@@ -1168,7 +1233,7 @@ tvd_status tv_deblur(tvd_plan plan, const void* v, double alpha, double beta, in
     double* u = (double*)u_out;
     p.hx_for = nullptr;
     // b = H^T v (eq. (fp)) or H' v = H v (eq. (fpp), symmetric PSF) into p.xd; u^0 = v
-    const bool reblur = p.method == TVD_METHOD_REBLUR;
+    const bool reblur = p.reblur();
     TVD_TRY(blur_apply<double>(p, p.d, !reblur, (const double*)v, p.xd, s));
     if (u != (const double*)v) TVD_CUDA_TRY(cudaMemcpyAsync(u, v, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
     if (stats) {
@@ -1178,9 +1243,27 @@ tvd_status tv_deblur(tvd_plan plan, const void* v, double alpha, double beta, in
         stats->last_relres = 0.0;
         stats->last_rel_change = 0.0;
         stats->last_status = TVD_OK;
+        stats->final_g_norm = 0.0;
+        stats->final_functional = 0.0;
     }
     tvd_status overall = TVD_OK;
+    const bool track_g = stats && stats->g_norm, track_f = stats && stats->functional;
+    // ||g(x)|| and T(x) of an iterate x (eq. (el), eq. (mp)), on request; w(x) and H^T H x land
+    // in p.d.w / p.hx, where the next FP step's set-up and first residual take them anyway
+    auto track = [&](const double* x, double* gn, double* fn) -> tvd_status {
+        double g2 = 0.0, parts[2] = {0.0, 0.0};
+        TVD_TRY(el_residual(p, x, (const double*)v, p.xd, alpha, beta, p.res, &g2, track_f ? parts : nullptr, s));
+        if (track_g) *gn = std::sqrt(g2);
+        if (track_f) *fn = 0.5 * parts[0] + alpha * parts[1];
+        return TVD_OK;
+    };
     for (int k = 0; k < max_outer; ++k) {
+        if ((track_g || track_f) && k < stats->cap) {
+            double gn = 0.0, fn = 0.0;
+            TVD_TRY(track(u, &gn, &fn));
+            if (track_g) stats->g_norm[k] = gn;
+            if (track_f) stats->functional[k] = fn;
+        }
         TVD_CUDA_TRY(cudaMemcpyAsync(p.tmp, u, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
         SolveResult r;
         // u_lag = u^k (kept in p.tmp), x starts at u^k and becomes u^{k+1} in place
@@ -1205,10 +1288,116 @@ tvd_status tv_deblur(tvd_plan plan, const void* v, double alpha, double beta, in
         if (r.status == TVD_EBREAKDOWN) break;
         if (outer_tol > 0.0 && change < outer_tol) break;
     }
+    if (track_g || track_f) {
+        double gn = 0.0, fn = 0.0;
+        TVD_TRY(track(u, &gn, &fn));
+        stats->final_g_norm = gn;
+        stats->final_functional = fn;
+    }
     if (overall != TVD_OK)
         set_error(overall == TVD_ENOCONV ? "tv_deblur: an inner solve did not reach its tolerance"
                                          : "tv_deblur: an inner solve broke down");
     return overall;
+}
+
+tvd_status tv_deblur_newton(tvd_plan plan, const void* v, double alpha, double beta, void* u_inout, double tol,
+                            int max_steps, double cg_tol, int cg_maxit, tvd_newton_stats* stats, void* stream) {
+    if (!plan || !v || !u_inout || u_inout == v || !(alpha >= 0.0) || !(beta > 0.0) || !(tol > 0.0) ||
+        max_steps < 0 || !(cg_tol > 0.0) || cg_maxit < 0) {
+        set_error("tv_deblur_newton: invalid argument");
+        return TVD_EINVAL;
+    }
+    if (plan->reblur()) {
+        set_error("tv_deblur_newton: finishes the fixed point of eq. (fp) (a stationary point of the functional); "
+                  "a reblurring plan has no such functional");
+        return TVD_EINVAL;
+    }
+    tvd_plan_s& p = *plan;
+    cudaStream_t s = (cudaStream_t)stream;
+    const size_t n = (size_t)p.nr * p.nc;
+    const bool mixed = p.mode == TVD_MODE_MIXED;
+    double* u = (double*)u_inout;
+    tvd_newton_stats local{};
+    tvd_newton_stats& ns = stats ? *stats : local;
+    ns = tvd_newton_stats{};
+    p.hx_for = nullptr;
+    double* scratch = nullptr;
+    // b = H^T v, r = -g, d (the step), u0 (the iterate the step starts from), g_r, g_c, float g_r, g_c
+    TVD_TRY(dalloc(&scratch, 6 * n + (mixed ? n : 0)));
+    double *b = scratch, *r = b + n, *d = r + n, *u0 = d + n, *gr = u0 + n, *gc = gr + n;
+    float* gf = mixed ? reinterpret_cast<float*>(gc + n) : nullptr;
+    auto run = [&]() -> tvd_status {
+        TVD_TRY(blur_apply<double>(p, p.d, true, (const double*)v, b, s));
+        double g2 = 0.0;
+        TVD_TRY(el_residual(p, u, (const double*)v, b, alpha, beta, r, &g2, nullptr, s));
+        ns.g_norm_initial = std::sqrt(g2);
+        ns.g_norm = ns.g_norm_initial;
+        for (int k = 0; k < max_steps; ++k) {
+            if (g2 == 0.0) return TVD_OK;
+            if (!std::isfinite(g2)) {
+                set_error("tv_deblur_newton: non-finite gradient");
+                return TVD_EBREAKDOWN;
+            }
+            // J(u) d = -g(u) with the FP step's preconditioner at u
+            if (mixed) TVD_TRY(setup_mixed(p, u, alpha, beta, s));
+            else TVD_TRY(setup_precond<double>(p, p.d, u, alpha, beta, s));
+            TVD_TRY(hess_coef(p, u, p.d.w, gr, gc, s));
+            if (mixed) {
+                TVD_TRY(cast_d2f(gr, gf, n, s));
+                TVD_TRY(cast_d2f(gc, gf + n, n, s));
+            }
+            int it = 0;
+            double rel = 0.0;
+            const tvd_status cg = jacobian_solve(p, r, d, gr, gc, gf, mixed ? gf + n : nullptr, alpha, cg_tol,
+                                                 cg_maxit, &it, &rel, s);
+            ns.total_cg_iters += it;
+            if (cg != TVD_OK && cg != TVD_ENOCONV) return cg;   // an inexact direction is still taken
+            TVD_TRY(norm2_d(p, d, p.scal + 11, s));
+            double d2 = 0.0;
+            TVD_CUDA_TRY(cudaMemcpyAsync(&d2, p.scal + 11, sizeof(double), cudaMemcpyDeviceToHost, s));
+            TVD_CUDA_TRY(cudaMemcpyAsync(u0, u, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+            // u = u0 + t d, t = 1 halved while ||g|| does not fall (at most 10 halvings); a full
+            // step whose relative change is already below tol is taken as it is (near the
+            // solution ||g|| is at its rounding floor and need not fall)
+            double t = 1.0, g2_new = 0.0, u2 = 0.0;
+            bool accepted = false;
+            for (int h = 0; h <= 10; ++h) {
+                TVD_TRY(axpy_to_d(p, u0, d, t, u, p.scal + 11, s));
+                TVD_TRY(el_residual(p, u, (const double*)v, b, alpha, beta, r, &g2_new, nullptr, s));
+                TVD_CUDA_TRY(cudaMemcpyAsync(&u2, p.scal + 11, sizeof(double), cudaMemcpyDeviceToHost, s));
+                TVD_CUDA_TRY(cudaStreamSynchronize(s));
+                const bool tiny = h == 0 && std::sqrt(d2) < tol * std::sqrt(u2);
+                if (g2_new < g2 || tiny) {
+                    accepted = true;
+                    break;
+                }
+                t *= 0.5;
+                ++ns.halvings;
+            }
+            if (!accepted) {
+                TVD_CUDA_TRY(cudaMemcpyAsync(u, u0, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+                TVD_CUDA_TRY(cudaStreamSynchronize(s));
+                p.hx_for = nullptr;
+                set_error("tv_deblur_newton: no step along the Newton direction lowered ||g||");
+                return TVD_ENOCONV;
+            }
+            g2 = g2_new;
+            ns.steps = k + 1;
+            ns.last_t = t;
+            ns.last_cg_relres = rel;
+            ns.last_rel_change = t * std::sqrt(d2) / std::max(std::sqrt(u2), 1e-300);
+            ns.g_norm = std::sqrt(g2);
+            if (ns.last_rel_change < tol) return TVD_OK;
+        }
+        if (max_steps == 0 || g2 == 0.0) return TVD_OK;
+        set_error("tv_deblur_newton: max_steps reached before the relative change fell below tol");
+        return TVD_ENOCONV;
+    };
+    const tvd_status st = run();
+    cudaStreamSynchronize(s);
+    p.hx_for = nullptr;
+    dfree(scratch);
+    return st;
 }
 
 }  // extern "C"

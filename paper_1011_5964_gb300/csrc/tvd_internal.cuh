@@ -189,7 +189,8 @@ struct Psf {
 
 struct tvd_plan_s {
     int nr = 0, nc = 0;
-    int method = 0;                     // tvd_method: TVD_METHOD_FP (eq. (fp), PCG) or TVD_METHOD_REBLUR
+    int method = 0;                     // tvd_method: TVD_METHOD_FP (eq. (fp), PCG), TVD_METHOD_REBLUR or
+                                        // TVD_METHOD_REBLUR_ARL (eq. (fpp), PBiCGstab; L or L_AR)
     tvd_bc bc = TVD_BC_ANTIREFLECTIVE;
     tvd_precond pc = TVD_PC_DFAST;
     tvd_mode mode = TVD_MODE_FP64;
@@ -227,6 +228,8 @@ struct tvd_plan_s {
     void* gemm = nullptr;
     // BiCGstab state and vectors of the reblurring method (reblur.cu)
     void* bicg = nullptr;
+    // eq. (fpp), with L or L_AR
+    bool reblur() const { return method == TVD_METHOD_REBLUR || method == TVD_METHOD_REBLUR_ARL; }
 };
 
 namespace tvd {
@@ -250,6 +253,9 @@ tvd_status diag_scale(const tvd_plan_s& p, const T* w, double alpha, T* dmh, T* 
 
 template <typename T>
 tvd_status tv_apply(const tvd_plan_s& p, const T* w, const T* x, T* y, cudaStream_t s);
+// y -= alpha (L - L_AR) x on the border lines (after a fused product with L)
+template <typename T>
+tvd_status lar_border(const tvd_plan_s& p, const T* w, const T* x, T* y, double alpha, cudaStream_t s);
 
 // q = H^T t + alpha L(w) p; with st, p is the direction buffer the current
 // iteration wrote (p0 / p1 by st->pbuf), and p^T q -> st->pq, alpha = rho / pq;
@@ -359,9 +365,15 @@ tvd_status residual_d(const tvd_plan_s& p, const double* b, const double* ax, do
                       cudaStream_t s);
 tvd_status norm2_d(const tvd_plan_s& p, const double* a, double* out, cudaStream_t s);
 tvd_status diffnorm2_d(const tvd_plan_s& p, const double* a, const double* b, double* out, cudaStream_t s);
-tvd_status cast_d2f(const double* a, float* b, size_t n, cudaStream_t s);
+// b = (float)(a * scale); x += (double)d * scale
+tvd_status cast_d2f(const double* a, float* b, size_t n, cudaStream_t s, double scale = 1.0);
+// sum_pq sqrt(|D u|_pq^2 + beta^2) into *out (device), the TV term of eq. (mp)
+tvd_status tv_sum_d(const tvd_plan_s& p, const double* u, double beta, double* out, cudaStream_t s);
+// out = x0 + t d, ||out||^2 into *norm2 (device)
+tvd_status axpy_to_d(const tvd_plan_s& p, const double* x0, const double* d, double t, double* out, double* norm2,
+                     cudaStream_t s);
 tvd_status copy_f(const float* a, float* b, size_t n, cudaStream_t s);
-tvd_status axpy_f2d(double* x, const float* d, size_t n, cudaStream_t s);
+tvd_status axpy_f2d(double* x, const float* d, size_t n, cudaStream_t s, double scale = 1.0);
 tvd_status fill_zero_f(float* a, size_t n, cudaStream_t s);
 
 int num_sms();

@@ -87,3 +87,28 @@ def test_reblur_entry_points_validate_without_gpu(lib):
     it, rr = ctypes.c_int(), ctypes.c_double()
     assert lib.pbicgstab_solve(None, None, 1e-3, 1e-2, None, None, 1e-6, 10, ctypes.byref(it), ctypes.byref(rr),
                                None) == pkg.TVD_EINVAL
+
+
+def test_newton_entry_point_validates_without_gpu(lib):
+    import ctypes
+    import paper_1011_5964_gb300 as pkg
+    ns = pkg._NewtonStats()
+    assert lib.tv_deblur_newton(None, None, 1e-3, 1e-2, None, 1e-10, 10, 1e-10, 100, ctypes.byref(ns),
+                                None) == pkg.TVD_EINVAL
+    assert b"tv_deblur_newton" in lib.tvd_last_error()
+
+
+def test_stats_structures_match_the_header():
+    """The ctypes mirrors of tvd_stats / tvd_newton_stats list the header's fields in order."""
+    import re
+    import paper_1011_5964_gb300 as pkg
+    hdr = open(os.path.join(ROOT, "include", "tvd.h")).read()
+    for cname, py in (("tvd_stats", pkg._Stats), ("tvd_newton_stats", pkg._NewtonStats),
+                      ("tvd_batch_item", pkg._BatchItem)):
+        flat = re.sub(r"/\*.*?\*/", "", hdr, flags=re.S)
+        body = re.search(r"typedef struct \{([^{}]*)\} " + cname + ";", flat).group(1)
+        names = []
+        for stmt in filter(str.strip, body.split(";")):
+            parts = stmt.split(",")          # "double alpha, beta" declares two fields
+            names += [re.findall(r"\w+", parts[0])[-1]] + [re.findall(r"\w+", q)[-1] for q in parts[1:]]
+        assert names == [f[0] for f in py._fields_], (cname, names)
