@@ -234,9 +234,9 @@ def size_leg(pkg, torch, dev, synth, n, steps=2, warmup=1, pc="dfast", transform
             if s_ >= warmup:
                 ms += e0.elapsed_time(e1)
                 iters += st["total_inner_iters"]
-    if method == "reblur":
+    if method in ("reblur", "reblur_arl"):
         name = "P_D" if pc == "fastd" else "D_P"
-        eq = "reblurring eq. (fpp), PBiCGstab"
+        eq = "reblurring eq. (fpp), PBiCGstab" + (", AR BCs on L" if method == "reblur_arl" else "")
     else:
         name = "M_D" if pc == "fastd" else "D_M"
         eq = "eq. (fp), PCG"
@@ -244,6 +244,39 @@ def size_leg(pkg, torch, dev, synth, n, steps=2, warmup=1, pc="dfast", transform
                         f"{eq}, {name}, MIXED, {form} transforms", "deblurs_per_s": 1000.0 * steps / ms,
             "ms_per_step": ms / steps,
             "pcg_iters_per_s": iters / (ms / 1000.0), "inner_iters_per_deblur": iters / steps}
+
+
+def signal_leg(pkg, torch, dev, synth):
+    """The 1D experiment (Sec. 5.1): a 203-sample signal in the field of view of a wider support,
+    out-of-focus PSF (21 taps), 1% noise, beta 0.1, FP stop 1e-3, PCG tol 1e-6, D_M / D_R, FP64;
+    the RRE-versus-alpha sweep over 11 alphas (1e-6 .. 1e-1) for AR and R BCs, each sweep one batch
+    of plans. The observation is blurred on the wider support with the library's own FP64 H (no BC
+    reaches the field of view). Host clock around each sweep (plan set-up included)."""
+    import numpy as np
+    n, m, seed = 203, 11, 4
+    h = synth.out_of_focus_psf_1d(m)
+    uw, fov = synth.piecewise_constant_signal(n, seed)
+    with pkg.Plan(1, uw.size, h, bc="r", pc="dfast", mode="fp64") as pw:
+        hv = pw.blur(torch.tensor(uw[None, :], device=dev)).cpu().numpy()[:, fov]
+    v = torch.tensor(synth.add_noise(hv, synth.noise_direction(1, n, seed), 0.01), device=dev)
+    ut = uw[fov][None, :]
+    alphas = synth.alpha_grid()
+    out = {"workload": "1D signal n=203 (field of view of 253 samples), out-of-focus PSF 21 taps, 1% noise, "
+                       "beta 0.1, FP stop 1e-3, PCG tol 1e-6, D_M (AR) / D_R (R), FP64, alpha sweep 1e-6..1e-1",
+           "alphas": alphas}
+    for bc in ("ar", "r"):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        us, stats = pkg.alpha_sweep(v, h, alphas, 0.1, bc=bc, pc="dfast", mode="fp64", outer_tol=1e-3,
+                                    inner_tol=1e-6)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        rre = [float(np.linalg.norm(u.cpu().numpy() - ut) / np.linalg.norm(ut)) for u in us]
+        k = int(np.argmin(rre))
+        out[bc] = {"sweep_s": dt, "rre": rre, "best_alpha": alphas[k], "best_rre": rre[k],
+                   "fp_steps": [st["outer_iters"] for st in stats],
+                   "inner_per_step": [float(np.mean(st["inner_iters"])) for st in stats]}
+    return out
 
 
 def adjoint_leg(pkg, torch, dev, synth):
@@ -599,6 +632,8 @@ def run_ours(args):
         line["m_d_1024"] = size_leg(pkg, torch, dev, synth, 1024, steps=3, pc="fastd")
         line["fft_form_1024"] = size_leg(pkg, torch, dev, synth, 1024, steps=3, transform="fft")
         line["reblur_1024"] = size_leg(pkg, torch, dev, synth, 1024, steps=3, method="reblur")
+        line["reblur_arl_1024"] = size_leg(pkg, torch, dev, synth, 1024, steps=3, method="reblur_arl")
+        line["signal_1d"] = signal_leg(pkg, torch, dev, synth)
 
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         iters_per_deblur, src = oracle_iters_per_deblur()
