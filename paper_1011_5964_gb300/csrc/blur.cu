@@ -390,17 +390,21 @@ __device__ __forceinline__ void flat_body(int bx, int by, int gx, const T* __res
 // The flat disk of radius R (h_{a,b} = v where a^2 + b^2 <= R^2, the
 // out-of-focus PSF of Sec. 5) has column heights g_b = floor(sqrt(R^2 - b^2))
 // known at compile time, so
-//   y_ij = v sum_{|b| <= R} C_{g_b}(i, j - b),   C_g(i, c) = sum_{|a| <= g} x~_{i-a, c},
-// runs with no shared memory and no block barrier: each warp owns a strip of
-// 32 consecutive columns (18 outputs and R halo columns on each side) and 16
-// rows; a lane keeps its column's 16 + 2R extended values in registers, forms
-// the vertical sums C_g of each row by nested pair additions, and takes the 15
-// horizontal terms from its neighbours with warp shuffles.
+//   y_ij = v sum_{|b| <= R} C_{g_b}(i, j - b),   C_g(i, c) = sum_{|a| <= g} x~_{i-a, c}.
+// A block is two groups of 128 threads; each thread owns one column of a
+// 128-column window (114 outputs and R halo columns on each side) and DROWS
+// rows of one group. It keeps its column's DROWS + 2R extended values in
+// registers and forms the vertical sums C_g of each row by nested pair
+// additions; the sums other columns need (the distinct heights below g_0) go to
+// a double-buffered shared row, one barrier per row, and each output thread adds
+// its 14 neighbours' terms from there.
 constexpr int DR = 7;                            // disk radius of the specialised path
-constexpr int DOUT = 32 - 2 * DR;                // output columns per warp strip
-constexpr int DROWS = 16;                        // output rows per warp strip
-constexpr int DWX = 4, DWY = kThreads / 32 / DWX;   // warps per block across / down
-constexpr int DBW = DWX * DOUT, DBH = DWY * DROWS;  // block tile: 72 x 32 outputs
+constexpr int DCOLS = 128;                       // window columns of a row group
+constexpr int DOUT = DCOLS - 2 * DR;             // output columns per block
+constexpr int DROWS = 16;                        // output rows per row group
+constexpr int DGROUPS = kThreads / DCOLS;        // row groups per block
+constexpr int DBW = DOUT, DBH = DGROUPS * DROWS; // block tile: 114 x 32 outputs
+constexpr int DNG = 5;                           // shared heights g_b, b = 1..R: 6 (b <= 3), 5, 4, 3, 0
 
 __host__ __device__ constexpr int disk_height(int b) {
     int g = 0;
@@ -408,9 +412,14 @@ __host__ __device__ constexpr int disk_height(int b) {
     return g;
 }
 
-// x~ at (I, J) for a warp whose lanes straddle the image border: the extension
-// of Sec. 2 (AR: reflection through the boundary value; R: mirror; ODD: the
-// odd extension used by the AR transpose), from at most four image values.
+// slot of the shared row that holds C_{g_b} (b = 1..R)
+__host__ __device__ constexpr int disk_slot(int b) {
+    return b <= 3 ? 0 : b - 3;
+}
+
+// x~ at (I, J) near the image border: the extension of Sec. 2 (AR: reflection
+// through the boundary value; R: mirror; ODD: the odd extension used by the AR
+// transpose), from at most four image values.
 template <typename T, int EXT, typename S>
 __device__ __forceinline__ T ext_at(const S& x, int I, int J, int nr, int nc) {
     return ext_value<T, EXT>(x, I, J, nr, nc, DR, DR);
@@ -419,20 +428,23 @@ __device__ __forceinline__ T ext_at(const S& x, int I, int J, int nr, int nc) {
 template <typename T, int EXT, bool FUSE, bool PUP>
 __device__ __forceinline__ void disk_body(int bx, int by, int gx, const T* __restrict__ x, T* __restrict__ y, int nr,
                                           int nc, T v, const T* __restrict__ w, T* p0, T* p1, const FuseArgs& fa) {
+    static_assert(disk_height(1) == 6 && disk_height(3) == 6 && disk_height(4) == 5 && disk_height(5) == 4 &&
+                      disk_height(6) == 3 && disk_height(7) == 0,
+                  "the shared-row slots assume the heights of the radius-7 disk");
+    __shared__ T crow_buf[2][DGROUPS][DNG][DCOLS];
     const int pb = fa.st ? fa.st->pbuf : 0;
     const T* pv = fa.st ? (pb ? p0 : p1) : p0;
     const T* pold = pb ? p1 : p0;
     T* pnew = pb ? p0 : p1;
     const Src<T, PUP> src{x, pold, PUP ? T(fa.st->beta) : T(0), PUP ? fa.st->fresh != 0 : true};
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    const int jo = bx * DBW + (wid % DWX) * DOUT;   // first output column of the strip
-    const int i0 = by * DBH + (wid / DWX) * DROWS;   // first output row of the strip
-    const int J = jo - DR + lane;                    // this lane's column
-    const bool out_lane = lane >= DR && lane < DR + DOUT && J < nc;
+    const int col = threadIdx.x % DCOLS, grp = threadIdx.x / DCOLS;
+    const int jo = bx * DBW;                          // first output column of the block
+    const int i0 = by * DBH + grp * DROWS;            // first output row of the group
+    const int J = jo - DR + col;                      // this thread's column
+    const bool out_col = col >= DR && col < DR + DOUT && J < nc;
     // the window rows i0 - DR .. i0 + DROWS - 1 + DR of column J
-    const bool inside = (EXT == EXT_ODD)
-                            ? (i0 - DR >= 1 && i0 + DROWS + DR <= nr - 1 && jo - DR >= 1 && jo - DR + 31 <= nc - 2)
-                            : (i0 - DR >= 0 && i0 + DROWS + DR <= nr && jo - DR >= 0 && jo - DR + 31 < nc);
+    const bool inside = (EXT == EXT_ODD) ? (i0 - DR >= 1 && i0 + DROWS + DR <= nr - 1 && J >= 1 && J <= nc - 2)
+                                         : (i0 - DR >= 0 && i0 + DROWS + DR <= nr && J >= 0 && J < nc);
     T win[DROWS + 2 * DR];
     if (inside) {
         const size_t o = (size_t)(i0 - DR) * nc + J;
@@ -443,26 +455,30 @@ __device__ __forceinline__ void disk_body(int bx, int by, int gx, const T* __res
         for (int t = 0; t < DROWS + 2 * DR; ++t) win[t] = ext_at<T, EXT>(src, i0 - DR + t, J, nr, nc);
     }
     T part = T(0);
-    const size_t o0 = (size_t)i0 * nc + J;           // (i0, J); row t at o0 + t nc
+    const size_t o0 = (size_t)i0 * nc + J;            // (i0, J); row t at o0 + t nc
 #pragma unroll
     for (int t = 0; t < DROWS; ++t) {
         const int i = i0 + t;
         const size_t oi = o0 + (size_t)t * nc;
-        if (PUP && out_lane && i < nr) pnew[oi] = win[t + DR];
-        // centred vertical sums of this lane's column at row i
+        if (PUP && out_col && i < nr) pnew[oi] = win[t + DR];
+        // centred vertical sums of this column at row i
         T c[DR + 1];
         c[0] = win[t + DR];
 #pragma unroll
         for (int g = 1; g <= DR; ++g) c[g] = c[g - 1] + (win[t + DR - g] + win[t + DR + g]);
+        T(*row)[DCOLS] = crow_buf[t & 1][grp];
+        row[0][col] = c[6];
+        row[1][col] = c[5];
+        row[2][col] = c[4];
+        row[3][col] = c[3];
+        row[4][col] = c[0];
+        // every thread passes every barrier (no early exit before the last row)
+        __syncthreads();
+        if (!out_col || i >= nr) continue;
+        if (EXT == EXT_ODD && (i == 0 || i == nr - 1 || J == 0 || J == nc - 1)) continue;
         T acc = c[disk_height(0)];
 #pragma unroll
-        for (int b = 1; b <= DR; ++b) {
-            // lane +- b (immediate offsets; lanes near the warp's ends read their own value: not outputs)
-            const T cg = c[disk_height(b)];
-            acc += __shfl_up_sync(0xffffffffu, cg, b) + __shfl_down_sync(0xffffffffu, cg, b);
-        }
-        if (!out_lane || i >= nr) continue;
-        if (EXT == EXT_ODD && (i == 0 || i == nr - 1 || J == 0 || J == nc - 1)) continue;
+        for (int b = 1; b <= DR; ++b) acc += row[disk_slot(b)][col - b] + row[disk_slot(b)][col + b];
         T out = v * acc;
         if (FUSE) {
             // alpha L(w) p (5-point stencil, zero Neumann), read through the L1 cache
