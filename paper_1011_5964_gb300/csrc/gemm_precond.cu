@@ -48,7 +48,6 @@ struct GemmPrecond {
     void* bufC = nullptr;         // n_c x ldr: X1^T, then W^T
     int* err = nullptr;           // device flag: TVD_ETIMEOUT when a product's wait gave up
     int bn = 64;                  // tile width of the products
-    int cx = 1;                   // CTAs per cluster sharing the transform-matrix tile (1 or 4)
     CUtensorMap mBr, mBc, mBrT, mBcT, mR, mC;
     std::vector<void*> owned;     // distinct device allocations
 };
@@ -124,24 +123,19 @@ int gemm_precond_storage(const tvd_plan_s& p) {
     return g ? (g->bf ? 2 : 1) : 0;
 }
 
-template <typename OpT, int CX>
-static tvd_status prepare_kernels_cx(int bn) {
+template <typename OpT>
+static tvd_status prepare_kernels(int bn) {
     using namespace tc;
     if (bn == 128) {
-        TVD_CUDA_TRY((tc_gemm_prepare<OpT, 128, kStagesBn128, EPI_STORE, CX>()));
-        TVD_CUDA_TRY((tc_gemm_prepare<OpT, 128, kStagesBn128, EPI_SCALE, CX>()));
-        TVD_CUDA_TRY((tc_gemm_prepare<OpT, 128, kStagesBn128, EPI_POST, CX>()));
+        TVD_CUDA_TRY((tc_gemm_prepare<OpT, 128, kStagesBn128, EPI_STORE>()));
+        TVD_CUDA_TRY((tc_gemm_prepare<OpT, 128, kStagesBn128, EPI_SCALE>()));
+        TVD_CUDA_TRY((tc_gemm_prepare<OpT, 128, kStagesBn128, EPI_POST>()));
     } else {
-        TVD_CUDA_TRY((tc_gemm_prepare<OpT, 64, kStagesBn64, EPI_STORE, CX>()));
-        TVD_CUDA_TRY((tc_gemm_prepare<OpT, 64, kStagesBn64, EPI_SCALE, CX>()));
-        TVD_CUDA_TRY((tc_gemm_prepare<OpT, 64, kStagesBn64, EPI_POST, CX>()));
+        TVD_CUDA_TRY((tc_gemm_prepare<OpT, 64, kStagesBn64, EPI_STORE>()));
+        TVD_CUDA_TRY((tc_gemm_prepare<OpT, 64, kStagesBn64, EPI_SCALE>()));
+        TVD_CUDA_TRY((tc_gemm_prepare<OpT, 64, kStagesBn64, EPI_POST>()));
     }
     return TVD_OK;
-}
-
-template <typename OpT>
-static tvd_status prepare_kernels(int bn, int cx) {
-    return cx == 4 ? prepare_kernels_cx<OpT, 4>(bn) : prepare_kernels_cx<OpT, 1>(bn);
 }
 
 tvd_status gemm_precond_create(tvd_plan_s& p, cudaStream_t s) {
@@ -170,12 +164,6 @@ tvd_status gemm_precond_create(tvd_plan_s& p, cudaStream_t s) {
     g->bn = tiles128 >= num_sms() ? 128 : 64;
     const char* bv = std::getenv("TVD_GEMM_BN");
     if (bv && (std::atoi(bv) == 64 || std::atoi(bv) == 128)) g->bn = std::atoi(bv);
-    // one CTA per tile; TVD_GEMM_CLUSTER=4 runs clusters of 4 CTAs along N that multicast each
-    // transform-matrix tile (a quarter of the A operand's L2 reads; measured slower at 1024^2:
-    // 13.6 against 14.4 deblurs/s, the cluster's CTAs waiting on each other's stages)
-    g->cx = 1;
-    const char* cv = std::getenv("TVD_GEMM_CLUSTER");
-    if (cv && std::atoi(cv) == 4 && std::min((p.nr + g->bn - 1) / g->bn, (p.nc + g->bn - 1) / g->bn) >= 4) g->cx = 4;
     auto alloc = [&](void** ptr, size_t bytes) -> bool {
         if (cudaMalloc(ptr, bytes) != cudaSuccess) {
             cudaGetLastError();
@@ -238,12 +226,10 @@ tvd_status gemm_precond_create(tvd_plan_s& p, cudaStream_t s) {
         if (g->BcT != g->Bc && !upload(p.nc, g->ldc, true, g->BcT)) return fail(TVD_ECUDA);
     }
     const int eb = (int)esz;
-    // each CTA of a cluster loads BM / cx rows of the shared transform-matrix tile
-    const int abox = tc::BM / g->cx;
-    const bool maps = tc::make_tc_map(&g->mBr, g->Br, eb, p.nr, p.nr, g->ldr, abox) &&
-                      tc::make_tc_map(&g->mBrT, g->BrT, eb, p.nr, p.nr, g->ldr, abox) &&
-                      tc::make_tc_map(&g->mBc, g->Bc, eb, p.nc, p.nc, g->ldc, abox) &&
-                      tc::make_tc_map(&g->mBcT, g->BcT, eb, p.nc, p.nc, g->ldc, abox) &&
+    const bool maps = tc::make_tc_map(&g->mBr, g->Br, eb, p.nr, p.nr, g->ldr, tc::BM) &&
+                      tc::make_tc_map(&g->mBrT, g->BrT, eb, p.nr, p.nr, g->ldr, tc::BM) &&
+                      tc::make_tc_map(&g->mBc, g->Bc, eb, p.nc, p.nc, g->ldc, tc::BM) &&
+                      tc::make_tc_map(&g->mBcT, g->BcT, eb, p.nc, p.nc, g->ldc, tc::BM) &&
                       tc::make_tc_map(&g->mR, g->bufR, eb, p.nc, p.nr, g->ldc, g->bn) &&
                       tc::make_tc_map(&g->mC, g->bufC, eb, p.nr, p.nc, g->ldr, g->bn);
     if (!maps) {
@@ -251,7 +237,7 @@ tvd_status gemm_precond_create(tvd_plan_s& p, cudaStream_t s) {
         return fail(TVD_ECUDA);
     }
     // shared-memory opt-in of the product kernels now, outside any stream capture
-    const tvd_status ps = g->bf ? prepare_kernels<bf16>(g->bn, g->cx) : prepare_kernels<float>(g->bn, g->cx);
+    const tvd_status ps = g->bf ? prepare_kernels<bf16>(g->bn) : prepare_kernels<float>(g->bn);
     if (ps != TVD_OK) return fail(ps);
     return TVD_OK;
 }
@@ -373,13 +359,8 @@ static tvd_status run_products(const tvd_plan_s& p, const GemmPrecond& g, const 
     auto launch = [&](auto kernel_tag, const CUtensorMap& A, const CUtensorMap& B, int M, int N, int K) -> tvd_status {
         constexpr int EPI = decltype(kernel_tag)::value;
         cudaError_t ce;
-        if (g.cx == 4) {
-            if (g.bn == 128) ce = launch_tc_gemm<OpT, 128, kStagesBn128, EPI, 4>(A, B, M, N, K, e, s);
-            else ce = launch_tc_gemm<OpT, 64, kStagesBn64, EPI, 4>(A, B, M, N, K, e, s);
-        } else {
-            if (g.bn == 128) ce = launch_tc_gemm<OpT, 128, kStagesBn128, EPI, 1>(A, B, M, N, K, e, s);
-            else ce = launch_tc_gemm<OpT, 64, kStagesBn64, EPI, 1>(A, B, M, N, K, e, s);
-        }
+        if (g.bn == 128) ce = launch_tc_gemm<OpT, 128, kStagesBn128, EPI>(A, B, M, N, K, e, s);
+        else ce = launch_tc_gemm<OpT, 64, kStagesBn64, EPI>(A, B, M, N, K, e, s);
         TVD_CUDA_TRY(ce);
         return TVD_OK;
     };
@@ -421,8 +402,7 @@ tvd_status gemm_precond_solve(const tvd_plan_s& p, const Ops<float>& o, const fl
         set_error("GEMM preconditioner: vectors must be 16-byte aligned");
         return TVD_EINVAL;
     }
-    const long long nt = ((p.nc + g->bn - 1) / g->bn + g->cx - 1) / g->cx * g->cx;   // whole clusters
-    if (st && (long long)((p.nr + tc::BM - 1) / tc::BM) * nt > kMaxRedBlocks) {
+    if (st && (long long)((p.nr + tc::BM - 1) / tc::BM) * ((p.nc + g->bn - 1) / g->bn) > kMaxRedBlocks) {
         set_error("image too large for the reduction buffer");
         return TVD_EINVAL;
     }

@@ -99,29 +99,6 @@ __device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, u
         : "memory");
 }
 
-// The same load multicast to the CTAs of the cluster named in `mask`: the box
-// lands at the same shared-memory offset in each, completing `bytes` on the
-// mbarrier at the same offset in each.
-__device__ __forceinline__ void tma_load_2d_mc(void* dst, const CUtensorMap* map, uint64_t* bar, int c0, int c1,
-                                               uint16_t mask) {
-    asm volatile(
-        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes.multicast::cluster"
-        " [%0], [%1, {%3, %4}], [%2], %5;" ::"r"(smem_u32(dst)),
-        "l"(map), "r"(smem_u32(bar)), "r"(c0), "r"(c1), "h"(mask)
-        : "memory");
-}
-
-__device__ __forceinline__ uint32_t cluster_rank() {
-    uint32_t r;
-    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
-    return r;
-}
-
-// All threads of all CTAs of the cluster (release / acquire).
-__device__ __forceinline__ void cluster_sync() {
-    asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
-}
-
 __device__ __forceinline__ void tma_prefetch_map(const CUtensorMap* map) {
     asm volatile("prefetch.tensormap [%0];" ::"l"(map) : "memory");
 }
@@ -167,15 +144,6 @@ __device__ __forceinline__ void umma_commit(uint64_t* bar) {
     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
                      smem_u32(bar))
                  : "memory");
-}
-
-// The same arrival on the mbarrier at this offset in every CTA of `mask`.
-__device__ __forceinline__ void umma_commit_mc(uint64_t* bar, uint16_t mask) {
-    asm volatile(
-        "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;" ::"r"(
-            smem_u32(bar)),
-        "h"(mask)
-        : "memory");
 }
 
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
@@ -259,19 +227,11 @@ __device__ __forceinline__ void load_row32(const float* p, float (&v)[32]) {
     }
 }
 
-// CX > 1: the kernel runs in clusters of CX CTAs along N, which share their A
-// tile (the same 128 rows of the transform matrix): each CTA loads BM / CX of
-// its rows (mapA's box) and multicasts them to the whole cluster, so the A
-// operand leaves L2 once per cluster instead of once per CTA. A stage may then
-// only be refilled once every CTA of the cluster has consumed it: each MMA
-// issuer's release arrives on that stage's "empty" mbarrier in every CTA.
-template <typename OpT, int BN, int STAGES, int EPI, int CX>
+template <typename OpT, int BN, int STAGES, int EPI>
 __global__ void __launch_bounds__(kTcThreads, 1)
 tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB, int M, int N,
                int K, TcEpi ea) {
     static_assert(BN % 32 == 0 && BN >= 32 && BN <= 256, "BN");
-    static_assert(CX == 1 || CX == 2 || CX == 4, "CX");
-    constexpr uint16_t kMask = (uint16_t)((1u << CX) - 1u);
     using L = TcSmem<BN, STAGES>;
     extern __shared__ __align__(1024) unsigned char tc_smem_raw[];
     unsigned char* base = reinterpret_cast<unsigned char*>(((uintptr_t)tc_smem_raw + 1023) & ~(uintptr_t)1023);
@@ -290,7 +250,7 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__
     if (threadIdx.x == 0) {
         for (int s = 0; s < STAGES; ++s) {
             mbar_init(&full[s], 1);
-            mbar_init(&empty[s], CX);
+            mbar_init(&empty[s], 1);
         }
         mbar_init(done, 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -305,10 +265,8 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
-    // the peers' barriers are initialised before any multicast reaches them
-    if (CX > 1) cluster_sync();
     const uint32_t tmem = *tmem_slot;
-    const bool skip = flags[0] != 0;   // the same in every CTA of the cluster (one CG state)
+    const bool skip = flags[0] != 0;
 
     if (!skip && warp == 0 && lane == 0) {
         // loader
@@ -322,13 +280,7 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__
             }
             unsigned char* sa = base + s * L::kStageBytes;
             mbar_expect_tx(&full[s], (uint32_t)L::kStageBytes);
-            if (CX == 1) {
-                tma_load_2d(sa, &mapA, &full[s], kb * BK, m0);
-            } else {
-                const int rk = (int)cluster_rank();
-                tma_load_2d_mc(sa + rk * (BM / CX) * kRowBytes, &mapA, &full[s], kb * BK, m0 + rk * (BM / CX),
-                               kMask);
-            }
+            tma_load_2d(sa, &mapA, &full[s], kb * BK, m0);
             tma_load_2d(sa + L::kABytes, &mapB, &full[s], kb * BK, n0);
             issued = kb + 1;
         }
@@ -355,8 +307,7 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__
 #pragma unroll
             for (int kk = 0; kk < kRowBytes / 32; ++kk)   // 32 bytes of K = 2 descriptor units per step
                 umma<OpT>(tmem, da + 2 * kk, db + 2 * kk, idesc, (kb | kk) != 0 ? 1u : 0u);
-            if (CX == 1) umma_commit(&empty[s]);
-            else umma_commit_mc(&empty[s], kMask);
+            umma_commit(&empty[s]);
         }
         if (ok) umma_commit(done);
         // no MMA may still be running when the tensor memory is released
@@ -479,8 +430,6 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__
         tc_fence_after();
         tmem_dealloc(tmem, tmem_cols<BN>());
     }
-    // no CTA leaves while a peer may still multicast into it or arrive on its barriers
-    if (CX > 1) cluster_sync();
 }
 
 // ---------------------------------------------------------------- host side
@@ -522,7 +471,7 @@ inline bool make_tc_map(CUtensorMap* map, const void* ptr, int elem_bytes, int i
 // Raise the kernel's dynamic shared-memory limit (once per device; plans call
 // this at set-up, before any stream capture), then launch with programmatic
 // stream serialisation.
-template <typename OpT, int BN, int STAGES, int EPI, int CX>
+template <typename OpT, int BN, int STAGES, int EPI>
 inline cudaError_t tc_gemm_prepare() {
     static std::mutex mu;
     static bool done[kMaxDevices] = {};
@@ -532,44 +481,20 @@ inline cudaError_t tc_gemm_prepare() {
     if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
     std::lock_guard<std::mutex> lk(mu);
     if (done[dev]) return cudaSuccess;
-    e = cudaFuncSetAttribute(tc_gemm_kernel<OpT, BN, STAGES, EPI, CX>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    e = cudaFuncSetAttribute(tc_gemm_kernel<OpT, BN, STAGES, EPI>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              TcSmem<BN, STAGES>::kBytes);
     if (e == cudaSuccess) done[dev] = true;
     return e;
 }
 
-// Grid of a product: N tiles rounded up to whole clusters (the extra tiles lie
-// beyond N: their B rows read as zeros and the epilogue writes nothing).
-template <int BN, int CX>
-inline dim3 tc_grid(int M, int N) {
-    const int nt = (N + BN - 1) / BN;
-    return dim3((unsigned)(((nt + CX - 1) / CX) * CX), (unsigned)((M + BM - 1) / BM));
-}
-
-template <typename OpT, int BN, int STAGES, int EPI, int CX>
+template <typename OpT, int BN, int STAGES, int EPI>
 inline cudaError_t launch_tc_gemm(const CUtensorMap& mapA, const CUtensorMap& mapB, int M, int N, int K,
                                   const TcEpi& ea, cudaStream_t s) {
-    const cudaError_t attr = tc_gemm_prepare<OpT, BN, STAGES, EPI, CX>();
+    const cudaError_t attr = tc_gemm_prepare<OpT, BN, STAGES, EPI>();
     if (attr != cudaSuccess) return attr;
-    const dim3 grid = tc_grid<BN, CX>(M, N);
-    if (CX == 1)
-        return launch_pdl(tc_gemm_kernel<OpT, BN, STAGES, EPI, CX>, grid, dim3(kTcThreads),
-                          (size_t)TcSmem<BN, STAGES>::kBytes, s, mapA, mapB, M, N, K, ea);
-    cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = grid;
-    cfg.blockDim = dim3(kTcThreads);
-    cfg.dynamicSmemBytes = (size_t)TcSmem<BN, STAGES>::kBytes;
-    cfg.stream = s;
-    cudaLaunchAttribute at[2];
-    at[0].id = cudaLaunchAttributeClusterDimension;
-    at[0].val.clusterDim.x = CX;
-    at[0].val.clusterDim.y = 1;
-    at[0].val.clusterDim.z = 1;
-    at[1].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-    at[1].val.programmaticStreamSerializationAllowed = 1;
-    cfg.attrs = at;
-    cfg.numAttrs = 2;
-    return cudaLaunchKernelEx(&cfg, tc_gemm_kernel<OpT, BN, STAGES, EPI, CX>, mapA, mapB, M, N, K, ea);
+    const dim3 grid((N + BN - 1) / BN, (M + BM - 1) / BM);
+    return launch_pdl(tc_gemm_kernel<OpT, BN, STAGES, EPI>, grid, dim3(kTcThreads),
+                      (size_t)TcSmem<BN, STAGES>::kBytes, s, mapA, mapB, M, N, K, ea);
 }
 
 }  // namespace tc

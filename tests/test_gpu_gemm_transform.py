@@ -201,19 +201,3 @@ def test_batched_gemm_plans_equal_individual_calls(tdev):
     finally:
         for p in plans:
             p.close()
-
-
-@pytest.mark.parametrize("nr,nc,bc", [(512, 512, "ar"), (300, 520, "r"), (1024, 1024, "ar")])
-@pytest.mark.parametrize("storage", ["bf16", "f32"])
-def test_clustered_products_equal_single_cta_products(tdev, nr, nc, bc, storage):
-    """Clusters of 4 CTAs that multicast the transform-matrix tile compute the same
-    products as single CTAs (same accumulation order): the solves agree bit for bit,
-    and the clustered one matches the oracle like any GEMM-form solve."""
-    torch, dev = tdev
-    zs = []
-    for cx in ("1", "4"):
-        with _env(TVD_GEMM_CLUSTER=cx):
-            z, ref = _solve(torch, dev, nr, nc, bc, "dfast", "gemm", storage=storage)
-        zs.append(z)
-    assert np.array_equal(zs[0], zs[1])
-    assert maxrel(zs[1], ref) < TOL[storage]
