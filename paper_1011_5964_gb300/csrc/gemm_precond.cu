@@ -36,6 +36,16 @@ using bf16 = __nv_bfloat16;
 // Tile widths and pipeline depths of the products (about 192 KB of stages).
 constexpr int kStagesBn64 = 8;
 constexpr int kStagesBn128 = 6;
+// 64-column products whose epilogue stages f (spectral divide) or d and r (last product) in
+// shared memory keep fewer stages so that both fit
+template <int BN, int EPI>
+constexpr int stages_of() {
+    return BN == 128 ? kStagesBn128 : (EPI == tc::EPI_POST ? 5 : (EPI == tc::EPI_SCALE ? 7 : kStagesBn64));
+}
+static_assert(tc::TcSmem<64, stages_of<64, tc::EPI_POST>(), tc::EPI_POST>::kBytes <= 227 * 1024, "smem");
+static_assert(tc::TcSmem<64, stages_of<64, tc::EPI_SCALE>(), tc::EPI_SCALE>::kBytes <= 227 * 1024, "smem");
+static_assert(tc::TcSmem<64, stages_of<64, tc::EPI_STORE>(), tc::EPI_STORE>::kBytes <= 227 * 1024, "smem");
+static_assert(tc::TcSmem<128, stages_of<128, tc::EPI_POST>(), tc::EPI_POST>::kBytes <= 227 * 1024, "smem");
 
 struct GemmPrecond {
     bool bf = false;              // operands: bf16 (kind::f16) or float (kind::tf32)
@@ -127,13 +137,13 @@ template <typename OpT>
 static tvd_status prepare_kernels(int bn) {
     using namespace tc;
     if (bn == 128) {
-        TVD_CUDA_TRY((tc_gemm_prepare<OpT, 128, kStagesBn128, EPI_STORE>()));
-        TVD_CUDA_TRY((tc_gemm_prepare<OpT, 128, kStagesBn128, EPI_SCALE>()));
-        TVD_CUDA_TRY((tc_gemm_prepare<OpT, 128, kStagesBn128, EPI_POST>()));
+        TVD_CUDA_TRY((tc_gemm_prepare<OpT, 128, stages_of<128, EPI_STORE>(), EPI_STORE>()));
+        TVD_CUDA_TRY((tc_gemm_prepare<OpT, 128, stages_of<128, EPI_SCALE>(), EPI_SCALE>()));
+        TVD_CUDA_TRY((tc_gemm_prepare<OpT, 128, stages_of<128, EPI_POST>(), EPI_POST>()));
     } else {
-        TVD_CUDA_TRY((tc_gemm_prepare<OpT, 64, kStagesBn64, EPI_STORE>()));
-        TVD_CUDA_TRY((tc_gemm_prepare<OpT, 64, kStagesBn64, EPI_SCALE>()));
-        TVD_CUDA_TRY((tc_gemm_prepare<OpT, 64, kStagesBn64, EPI_POST>()));
+        TVD_CUDA_TRY((tc_gemm_prepare<OpT, 64, stages_of<64, EPI_STORE>(), EPI_STORE>()));
+        TVD_CUDA_TRY((tc_gemm_prepare<OpT, 64, stages_of<64, EPI_SCALE>(), EPI_SCALE>()));
+        TVD_CUDA_TRY((tc_gemm_prepare<OpT, 64, stages_of<64, EPI_POST>(), EPI_POST>()));
     }
     return TVD_OK;
 }
@@ -359,8 +369,8 @@ static tvd_status run_products(const tvd_plan_s& p, const GemmPrecond& g, const 
     auto launch = [&](auto kernel_tag, const CUtensorMap& A, const CUtensorMap& B, int M, int N, int K) -> tvd_status {
         constexpr int EPI = decltype(kernel_tag)::value;
         cudaError_t ce;
-        if (g.bn == 128) ce = launch_tc_gemm<OpT, 128, kStagesBn128, EPI>(A, B, M, N, K, e, s);
-        else ce = launch_tc_gemm<OpT, 64, kStagesBn64, EPI>(A, B, M, N, K, e, s);
+        if (g.bn == 128) ce = launch_tc_gemm<OpT, 128, stages_of<128, EPI>(), EPI>(A, B, M, N, K, e, s);
+        else ce = launch_tc_gemm<OpT, 64, stages_of<64, EPI>(), EPI>(A, B, M, N, K, e, s);
         TVD_CUDA_TRY(ce);
         return TVD_OK;
     };

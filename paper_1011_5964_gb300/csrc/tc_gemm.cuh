@@ -185,12 +185,25 @@ __device__ __forceinline__ uint32_t pack_bf16(float a, float b) {
     return *reinterpret_cast<uint32_t*>(&v);
 }
 
-template <int BN, int STAGES>
+// Arrays of float the epilogue needs, staged in shared memory by the epilogue
+// warps while the main loop runs (64-column tiles only): EPI_SCALE the
+// multiplier f, EPI_POST the scaling d and the residual r. Rows of BN + 1
+// floats, so that the 32 threads of a warp (32 rows) reading one column hit 32
+// banks.
+template <int BN, int EPI>
+__host__ __device__ constexpr int pre_arrays() {
+    return BN != 64 ? 0 : (EPI == EPI_POST ? 2 : (EPI == EPI_SCALE ? 1 : 0));
+}
+
+template <int BN, int STAGES, int EPI = EPI_STORE>
 struct TcSmem {
     static constexpr int kABytes = BM * kRowBytes;
     static constexpr int kBBytes = BN * kRowBytes;
     static constexpr int kStageBytes = kABytes + kBBytes;
-    static constexpr int kBarOffset = STAGES * kStageBytes;
+    static constexpr int kPreStride = BN + 1;                       // floats per staged row
+    static constexpr int kPreBytes = pre_arrays<BN, EPI>() * BM * kPreStride * 4;
+    static constexpr int kPreOffset = STAGES * kStageBytes;
+    static constexpr int kBarOffset = kPreOffset + kPreBytes;
     static constexpr int kBytes = 1024 /* alignment slack */ + kBarOffset + (2 * STAGES + 1) * 8 + 64;
 };
 
@@ -232,7 +245,8 @@ __global__ void __launch_bounds__(kTcThreads, 1)
 tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB, int M, int N,
                int K, TcEpi ea) {
     static_assert(BN % 32 == 0 && BN >= 32 && BN <= 256, "BN");
-    using L = TcSmem<BN, STAGES>;
+    using L = TcSmem<BN, STAGES, EPI>;
+    constexpr int NPRE = pre_arrays<BN, EPI>();
     extern __shared__ __align__(1024) unsigned char tc_smem_raw[];
     unsigned char* base = reinterpret_cast<unsigned char*>(((uintptr_t)tc_smem_raw + 1023) & ~(uintptr_t)1023);
     uint64_t* full = reinterpret_cast<uint64_t*>(base + L::kBarOffset);
@@ -320,6 +334,25 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__
         // epilogue: thread = row m0 + 32 q + lane of the tile, q = warp % 4 (its TMEM lane quarter)
         const int q = warp & 3;
         const int m = m0 + 32 * q + lane;
+        float* pre = reinterpret_cast<float*>(base + L::kPreOffset);   // NPRE arrays of BM x kPreStride
+        if (NPRE > 0) {
+            // while the main loop runs: this warp stages its 32 rows of f (SCALE) or d and r
+            // (POST), one row at a time with coalesced reads; zeros outside the matrix
+            const float* src0 = EPI == EPI_SCALE ? ea.f : ea.d;
+            for (int rr = 0; rr < 32; ++rr) {
+                const int row = 32 * q + rr, gm = m0 + row;
+#pragma unroll
+                for (int h = 0; h < BN / 32; ++h) {
+                    const int c = lane + 32 * h, gn = n0 + c;
+                    const bool in = gm < M && gn < N;
+                    const size_t off = (size_t)gm * N + gn;
+                    pre[row * L::kPreStride + c] = (in && src0) ? __ldg(src0 + off) : (src0 ? 0.0f : 1.0f);
+                    if (NPRE > 1)
+                        pre[BM * L::kPreStride + row * L::kPreStride + c] = (in && ea.r) ? __ldg(ea.r + off) : 0.0f;
+                }
+            }
+            __syncwarp();
+        }
         const bool ok = mbar_wait(done, 0);
         if (!ok) flags[1] = 1;
         tc_fence_after();
@@ -335,9 +368,13 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__
                 // start on 16 bytes move as float4; the rest element by element
                 const bool full_cols = n + 32 <= N;
                 const bool vec = full_cols && (N % 4) == 0;
+                const float* prow = pre + (32 * q + lane) * L::kPreStride + c0;   // staged row (NPRE > 0)
                 if (EPI == EPI_STORE || EPI == EPI_SCALE) {
                     OpT* o = reinterpret_cast<OpT*>(ea.out) + (size_t)m * ea.ldo + n;
-                    if (EPI == EPI_SCALE) {
+                    if (EPI == EPI_SCALE && NPRE > 0) {
+#pragma unroll
+                        for (int i = 0; i < 32; ++i) v[i] *= prow[i];
+                    } else if (EPI == EPI_SCALE) {
                         const float* f = ea.f + (size_t)m * N + n;
                         if (vec) {
                             float fv[32];
@@ -362,7 +399,23 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__
                     const float* d = ea.d ? ea.d + (size_t)m * N + n : nullptr;
                     const float* r = ea.r + (size_t)m * N + n;
                     float acc = 0.0f;
-                    if (vec && (ea.ldo % 4) == 0) {
+                    if (NPRE > 1) {
+                        // d (1 where there is none) and r from the staged rows
+                        const float* rrow = prow + BM * L::kPreStride;
+#pragma unroll
+                        for (int i = 0; i < 32; ++i) v[i] *= prow[i];
+                        if (full_cols && (ea.ldo % 4) == 0 && ((uintptr_t)o & 15u) == 0) {
+                            store_row32(o, v);
+                        } else {
+#pragma unroll
+                            for (int i = 0; i < 32; ++i)
+                                if (n + i < N) o[i] = v[i];
+                        }
+                        if (ea.st) {
+#pragma unroll
+                            for (int i = 0; i < 32; ++i) acc += rrow[i] * v[i];
+                        }
+                    } else if (vec && (ea.ldo % 4) == 0) {
                         if (d) {
                             float dv[32];
                             load_row32(d, dv);
@@ -482,7 +535,7 @@ inline cudaError_t tc_gemm_prepare() {
     std::lock_guard<std::mutex> lk(mu);
     if (done[dev]) return cudaSuccess;
     e = cudaFuncSetAttribute(tc_gemm_kernel<OpT, BN, STAGES, EPI>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             TcSmem<BN, STAGES>::kBytes);
+                             TcSmem<BN, STAGES, EPI>::kBytes);
     if (e == cudaSuccess) done[dev] = true;
     return e;
 }
@@ -494,7 +547,7 @@ inline cudaError_t launch_tc_gemm(const CUtensorMap& mapA, const CUtensorMap& ma
     if (attr != cudaSuccess) return attr;
     const dim3 grid((N + BN - 1) / BN, (M + BM - 1) / BM);
     return launch_pdl(tc_gemm_kernel<OpT, BN, STAGES, EPI>, grid, dim3(kTcThreads),
-                      (size_t)TcSmem<BN, STAGES>::kBytes, s, mapA, mapB, M, N, K, ea);
+                      (size_t)TcSmem<BN, STAGES, EPI>::kBytes, s, mapA, mapB, M, N, K, ea);
 }
 
 }  // namespace tc
