@@ -59,10 +59,44 @@ struct GemmPrecond {
     int* err = nullptr;           // device flag: TVD_ETIMEOUT when a product's wait gave up
     int bn = 64;                  // tile width of the products
     CUtensorMap mBr, mBc, mBrT, mBcT, mR, mC;
+    // folded products (AR, eq. (fp), sides multiples of 256): n x n/2 matrices of the two
+    // half-length transforms, columns indexed by natural (An) or grouped-pair (Ag) slots
+    bool fold = false;
+    void *An_r = nullptr, *Ag_r = nullptr, *An_c = nullptr, *Ag_c = nullptr;
+    CUtensorMap mAn_r, mAg_r, mAn_c, mAg_c, mR32, mC32;
     std::vector<void*> owned;     // distinct device allocations
 };
 
 static int pad8(int n) { return (n + 7) / 8 * 8; }
+
+// Position p of the grouped order -> natural index (the host twin of tc::nat_of).
+static int nat_host(int p, int n) {
+    const int h = n / 2;
+    if (p < h) return p == 0 ? 0 : 2 * p - 1;
+    const int a = p - h;
+    return a == 0 ? n - 1 : n - 2 * a;
+}
+
+// n x n/2 matrix of the folded hat-S (n even): row p = output nat_host(p, n); column
+// a = input slot a of its half (slot 0: the raw endpoint). grouped_cols: slot a >= 1
+// holds the pair (2a - 1, n - 2a) (inputs in grouped order), else (a, n - 1 - a).
+static void folded_matrix(int n, bool grouped_cols, std::vector<double>& out) {
+    const int h = n / 2, M = n - 1;
+    const double pi = 3.14159265358979323846, sc = std::sqrt(2.0 / M);
+    out.assign((size_t)n * h, 0.0);
+    for (int p = 0; p < n; ++p) {
+        const int q = nat_host(p, n);
+        if (q == 0 || q == n - 1) {
+            out[(size_t)p * h] = 1.0;
+            continue;
+        }
+        for (int a = 1; a < h; ++a) {
+            const int l = grouped_cols ? 2 * a - 1 : a;
+            const long long t = ((long long)q * l) % (2LL * M);
+            out[(size_t)p * h + a] = sc * std::sin(pi * (double)t / M);
+        }
+    }
+}
 
 // Row-major n x n matrix of the 1D transform (row k = basis vector k): AR hat-S_n,
 // R the DCT-II C_n (frequency by space); transposed on request. Arguments are
@@ -134,8 +168,15 @@ int gemm_precond_storage(const tvd_plan_s& p) {
 }
 
 template <typename OpT>
-static tvd_status prepare_kernels(int bn) {
+static tvd_status prepare_kernels(int bn, bool fold) {
     using namespace tc;
+    if (fold) {
+        TVD_CUDA_TRY((tc_gemm_prepare<OpT, 64, stages_of<64, EPI_STORE>(), EPI_STORE, 1>()));
+        TVD_CUDA_TRY((tc_gemm_prepare<OpT, 64, stages_of<64, EPI_SCALE>(), EPI_SCALE, 2>()));
+        TVD_CUDA_TRY((tc_gemm_prepare<OpT, 64, stages_of<64, EPI_STORE>(), EPI_STORE, 3>()));
+        TVD_CUDA_TRY((tc_gemm_prepare<OpT, 64, stages_of<64, EPI_POST>(), EPI_POST, 4>()));
+        return TVD_OK;
+    }
     if (bn == 128) {
         TVD_CUDA_TRY((tc_gemm_prepare<OpT, 128, stages_of<128, EPI_STORE>(), EPI_STORE>()));
         TVD_CUDA_TRY((tc_gemm_prepare<OpT, 128, stages_of<128, EPI_SCALE>(), EPI_SCALE>()));
@@ -174,6 +215,12 @@ tvd_status gemm_precond_create(tvd_plan_s& p, cudaStream_t s) {
     g->bn = tiles128 >= num_sms() ? 128 : 64;
     const char* bv = std::getenv("TVD_GEMM_BN");
     if (bv && (std::atoi(bv) == 64 || std::atoi(bv) == 128)) g->bn = std::atoi(bv);
+    // folded products (half the K of each product) for AR plans of eq. (fp) whose sides are
+    // multiples of 256; TVD_GEMM_FOLD=0 keeps the full products
+    const char* fv = std::getenv("TVD_GEMM_FOLD");
+    g->fold = p.bc == TVD_BC_ANTIREFLECTIVE && !p.reblur() && p.nr % 256 == 0 && p.nc % 256 == 0 &&
+              !(fv && fv[0] == '0');
+    if (g->fold) g->bn = 64;
     auto alloc = [&](void** ptr, size_t bytes) -> bool {
         if (cudaMalloc(ptr, bytes) != cudaSuccess) {
             cudaGetLastError();
@@ -246,8 +293,46 @@ tvd_status gemm_precond_create(tvd_plan_s& p, cudaStream_t s) {
         set_error("cuTensorMapEncodeTiled failed for the GEMM transform operands");
         return fail(TVD_ECUDA);
     }
+    if (g->fold) {
+        auto upload_fold = [&](int side, bool grouped, void** dst) -> bool {
+            std::vector<double> B;
+            folded_matrix(side, grouped, B);
+            if (!alloc(dst, B.size() * esz)) return false;
+            cudaError_t e;
+            if (g->bf) {
+                std::vector<bf16> Bh(B.size());
+                for (size_t i = 0; i < B.size(); ++i) Bh[i] = __double2bfloat16(B[i]);
+                e = cudaMemcpyAsync(*dst, Bh.data(), Bh.size() * esz, cudaMemcpyHostToDevice, s);
+                if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+            } else {
+                std::vector<float> Bf(B.begin(), B.end());
+                e = cudaMemcpyAsync(*dst, Bf.data(), Bf.size() * esz, cudaMemcpyHostToDevice, s);
+                if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+            }
+            if (e != cudaSuccess) set_error("upload of the folded transform matrix failed");
+            return e == cudaSuccess;
+        };
+        if (!upload_fold(p.nr, false, &g->An_r) || !upload_fold(p.nr, true, &g->Ag_r)) return fail(TVD_ECUDA);
+        if (p.nc == p.nr) {
+            g->An_c = g->An_r;
+            g->Ag_c = g->Ag_r;
+        } else if (!upload_fold(p.nc, false, &g->An_c) || !upload_fold(p.nc, true, &g->Ag_c)) {
+            return fail(TVD_ECUDA);
+        }
+        const int hr = p.nr / 2, hc = p.nc / 2;
+        const bool fmaps = tc::make_tc_map(&g->mAn_r, g->An_r, eb, hr, p.nr, hr, tc::BM) &&
+                           tc::make_tc_map(&g->mAg_r, g->Ag_r, eb, hr, p.nr, hr, tc::BM) &&
+                           tc::make_tc_map(&g->mAn_c, g->An_c, eb, hc, p.nc, hc, tc::BM) &&
+                           tc::make_tc_map(&g->mAg_c, g->Ag_c, eb, hc, p.nc, hc, tc::BM) &&
+                           tc::make_tc_map(&g->mR32, g->bufR, eb, p.nc, p.nr, g->ldc, 32) &&
+                           tc::make_tc_map(&g->mC32, g->bufC, eb, p.nr, p.nc, g->ldr, 32);
+        if (!fmaps) {
+            set_error("cuTensorMapEncodeTiled failed for the folded transform operands");
+            return fail(TVD_ECUDA);
+        }
+    }
     // shared-memory opt-in of the product kernels now, outside any stream capture
-    const tvd_status ps = g->bf ? prepare_kernels<bf16>(g->bn) : prepare_kernels<float>(g->bn);
+    const tvd_status ps = g->bf ? prepare_kernels<bf16>(g->bn, g->fold) : prepare_kernels<float>(g->bn, g->fold);
     if (ps != TVD_OK) return fail(ps);
     return TVD_OK;
 }
@@ -338,6 +423,66 @@ gemm_pre_kernel(float* __restrict__ r, float* __restrict__ x, const float* __res
         finish_xr(st, sum);
 }
 
+// The folded form's vector pass: the same pending update and stopping test, then
+// S = D^-1/2 r folded along each row for the first folded product: slot a of the
+// first half s_a = S_a + S_{nc-1-a}, of the second half S_a - S_{nc-1-a}, a = 1 ..
+// nc/2 - 1, slot 0 of each half the raw S_0 and S_{nc-1}. A thread takes a quad of
+// columns of the first half and its mirror quad (nc a multiple of 8).
+template <typename OutT>
+__global__ void __launch_bounds__(kThreads)
+gemm_fold_pre_kernel(float* __restrict__ r, float* __restrict__ x, const float* __restrict__ q, const float* p0,
+                     const float* p1, const float* __restrict__ d, OutT* __restrict__ s, int nr, int nc,
+                     CgState* st, double* red, unsigned int* ticket) {
+    pdl_wait();
+    if (st && st->done) return;
+    const bool upd = x && st && st->pending;
+    const float al = upd ? (float)st->alpha : 0.0f;
+    const float* __restrict__ pv = (st && st->pbuf) ? p0 : p1;
+    const int hq = nc / 8;                     // quads in the first half of a row
+    const size_t units = (size_t)nr * hq;
+    float part = 0.0f;
+    for (size_t u = blockIdx.x * (size_t)blockDim.x + threadIdx.x; u < units; u += (size_t)gridDim.x * blockDim.x) {
+        const size_t row = u / hq;
+        const int qd = (int)(u - row * hq);
+        const size_t il = (row * nc + 4 * (size_t)qd) / 4;              // float4 index of the low quad
+        const size_t ih = (row * nc + (size_t)(nc - 4 - 4 * qd)) / 4;   // and of its mirror quad
+        float4 rl = reinterpret_cast<const float4*>(r)[il], rh = reinterpret_cast<const float4*>(r)[ih];
+        if (upd) {
+            const float4 ql = reinterpret_cast<const float4*>(q)[il], qh = reinterpret_cast<const float4*>(q)[ih];
+            const float4 pl = reinterpret_cast<const float4*>(pv)[il], ph = reinterpret_cast<const float4*>(pv)[ih];
+            float4 xl = reinterpret_cast<const float4*>(x)[il], xh = reinterpret_cast<const float4*>(x)[ih];
+            rl.x -= al * ql.x; rl.y -= al * ql.y; rl.z -= al * ql.z; rl.w -= al * ql.w;
+            rh.x -= al * qh.x; rh.y -= al * qh.y; rh.z -= al * qh.z; rh.w -= al * qh.w;
+            xl.x += al * pl.x; xl.y += al * pl.y; xl.z += al * pl.z; xl.w += al * pl.w;
+            xh.x += al * ph.x; xh.y += al * ph.y; xh.z += al * ph.z; xh.w += al * ph.w;
+            reinterpret_cast<float4*>(r)[il] = rl;
+            reinterpret_cast<float4*>(r)[ih] = rh;
+            reinterpret_cast<float4*>(x)[il] = xl;
+            reinterpret_cast<float4*>(x)[ih] = xh;
+            part += rl.x * rl.x + rl.y * rl.y + rl.z * rl.z + rl.w * rl.w;
+            part += rh.x * rh.x + rh.y * rh.y + rh.z * rh.z + rh.w * rh.w;
+        }
+        if (d) {
+            const float4 dl = reinterpret_cast<const float4*>(d)[il], dh = reinterpret_cast<const float4*>(d)[ih];
+            rl.x *= dl.x; rl.y *= dl.y; rl.z *= dl.z; rl.w *= dl.w;
+            rh.x *= dh.x; rh.y *= dh.y; rh.z *= dh.z; rh.w *= dh.w;
+        }
+        // element e of the low quad (column 4 qd + e) pairs with element 3 - e of the mirror quad
+        float4 sv = make_float4(rl.x + rh.w, rl.y + rh.z, rl.z + rh.y, rl.w + rh.x);
+        float4 dv = make_float4(rl.x - rh.w, rl.y - rh.z, rl.z - rh.y, rl.w - rh.x);
+        if (qd == 0) {
+            sv.x = rl.x;   // the raw endpoints S_0 and S_{nc-1}
+            dv.x = rh.w;
+        }
+        store4(s, (row * nc + 4 * (size_t)qd) / 4, sv);
+        store4(s, (row * nc + nc / 2 + 4 * (size_t)qd) / 4, dv);
+    }
+    if (!upd) return;
+    double sum;
+    if (block_reduce_last((double)part, red, ticket, blockIdx.x, gridDim.x, &sum) && threadIdx.x == 0)
+        finish_xr(st, sum);
+}
+
 // Grid of the vector kernel: at most TVD_EW_BLOCKS_PER_SM (default 2) blocks
 // per SM, each thread walking several float4 by the grid-stride loops. With
 // one float4 per thread the block reductions dominated (ncu: barrier and
@@ -377,6 +522,34 @@ static tvd_status run_products(const tvd_plan_s& p, const GemmPrecond& g, const 
     using Store = std::integral_constant<int, EPI_STORE>;
     using Scale = std::integral_constant<int, EPI_SCALE>;
     using Post = std::integral_constant<int, EPI_POST>;
+    if (g.fold) {
+        // folded products (tc_gemm.cuh): each runs K/2 per tile and folds its N direction for the next
+        constexpr int S64 = stages_of<64, EPI_STORE>(), C64 = stages_of<64, EPI_SCALE>(),
+                      P64 = stages_of<64, EPI_POST>();
+        // 1. over the row halves of S (folded by the vector pass): rows k_c grouped, N = image rows
+        e.out = g.bufC;
+        e.ldo = g.ldr;
+        TVD_CUDA_TRY((launch_tc_gemm<OpT, 64, S64, EPI_STORE, 1>(g.mAn_c, g.mR32, nc, nr, nc, e, s)));
+        // 2. spectral divide (f gathered at natural indices), rows k_r grouped, N = k_c grouped
+        e.out = g.bufR;
+        e.ldo = g.ldc;
+        e.f = o.inv_spec;
+        TVD_CUDA_TRY((launch_tc_gemm<OpT, 64, C64, EPI_SCALE, 2>(g.mAn_r, g.mC32, nr, nc, nr, e, s)));
+        // 3. inverse along k_c: rows j (written at their natural index), N = k_r grouped
+        e.out = g.bufC;
+        e.ldo = g.ldr;
+        e.f = nullptr;
+        TVD_CUDA_TRY((launch_tc_gemm<OpT, 64, S64, EPI_STORE, 3>(g.mAg_c, g.mR32, nc, nr, nc, e, s)));
+        // 4. inverse along k_r: z = d o (.), r^T z, rows i at their natural index, N = j natural
+        e.out = z;
+        e.ldo = nc;
+        e.d = d;
+        e.r = r;
+        e.red = p.red;
+        e.ticket = p.ticket + 2;
+        TVD_CUDA_TRY((launch_tc_gemm<OpT, 64, P64, EPI_POST, 4>(g.mAg_r, g.mC, nr, nc, nr, e, s)));
+        return TVD_OK;
+    }
     // 1. X1^T = B_c S^T  (M = n_c, N = n_r, K = n_c)
     e.out = g.bufC;
     e.ldo = g.ldr;
@@ -419,7 +592,15 @@ tvd_status gemm_precond_solve(const tvd_plan_s& p, const Ops<float>& o, const fl
     const int blocks = ew_blocks(n);
     {
         ProfScope prof(PROF_GEMM_EW, s);
-        if (g->bf)
+        if (g->fold && g->bf)
+            TVD_CUDA_TRY(launch_pdl(gemm_fold_pre_kernel<bf16>, dim3(blocks), dim3(kThreads), 0, s,
+                                    const_cast<float*>(r), x, o.q, o.p, o.p2, d, (bf16*)g->bufR, p.nr, p.nc, st,
+                                    p.red, p.ticket + 7));
+        else if (g->fold)
+            TVD_CUDA_TRY(launch_pdl(gemm_fold_pre_kernel<float>, dim3(blocks), dim3(kThreads), 0, s,
+                                    const_cast<float*>(r), x, o.q, o.p, o.p2, d, (float*)g->bufR, p.nr, p.nc, st,
+                                    p.red, p.ticket + 7));
+        else if (g->bf)
             TVD_CUDA_TRY(launch_pdl(gemm_pre_kernel<bf16>, dim3(blocks), dim3(kThreads), 0, s, const_cast<float*>(r),
                                     x, o.q, o.p, o.p2, d, (bf16*)g->bufR, p.nr, p.nc, g->ldc, st, p.red,
                                     p.ticket + 7));

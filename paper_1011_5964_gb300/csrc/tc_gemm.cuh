@@ -240,11 +240,40 @@ __device__ __forceinline__ void load_row32(const float* p, float (&v)[32]) {
     }
 }
 
-template <typename OpT, int BN, int STAGES, int EPI>
+// Folded products (anti-reflective plans, sides multiples of 256). hat-S is
+// symmetric and hat-S[k][n-1-j] = (-1)^(k+1) hat-S[k][j] on the interior, so a
+// transform of a line splits into two half-length ones: rows k odd (and the
+// endpoint 0) take the sums x_a + x_{n-1-a}, rows k even (and the endpoint
+// n-1) the differences, a = 1 .. n/2 - 1 (slot 0 of each half holds the raw
+// endpoint value). Outputs are kept in the "grouped" order [0, 1, 3, 5, .. |
+// n-1, n-2, n-4, ..] (position p -> index nat_of(p, n)), in which output p of
+// the first half and output p of the second half are mirror images. Each
+// product then runs K/2 per tile (its rows lie in one half), and its epilogue
+// folds its N direction for the next product:
+//   FOLD 1: N in natural order; the CTA takes the 32-column tile at a and its
+//           mirror tile N - 32 - a (reversed), writes sums / differences;
+//   FOLD 2: N grouped; tiles at a and N/2 + a; multiplies by f (gathered at
+//           the natural indices), then writes sums / differences;
+//   FOLD 3: as 2 without f; rows written to their natural index;
+//   FOLD 4: N natural (one 64-column tile); rows written to their natural index
+//           (the last product: z = d o C, r^T z).
+__device__ __forceinline__ int nat_of(int p, int n) {
+    const int h = n >> 1;
+    if (p < h) return p == 0 ? 0 : 2 * p - 1;
+    const int a = p - h;
+    return a == 0 ? n - 1 : n - 2 * a;
+}
+
+template <typename OpT, int BN, int STAGES, int EPI, int FOLD = 0>
 __global__ void __launch_bounds__(kTcThreads, 1)
 tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB, int M, int N,
                int K, TcEpi ea) {
     static_assert(BN % 32 == 0 && BN >= 32 && BN <= 256, "BN");
+    static_assert(FOLD == 0 || BN == 64, "folded products use 64-column tiles");
+    static_assert(FOLD != 4 || EPI == EPI_POST, "FOLD 4 is the last product");
+    static_assert(FOLD != 2 || EPI == EPI_SCALE, "FOLD 2 carries the spectral divide");
+    static_assert((FOLD != 1 && FOLD != 3) || EPI == EPI_STORE, "FOLD 1 and 3 store");
+    constexpr bool kPaired = FOLD >= 1 && FOLD <= 3;
     using L = TcSmem<BN, STAGES, EPI>;
     constexpr int NPRE = pre_arrays<BN, EPI>();
     extern __shared__ __align__(1024) unsigned char tc_smem_raw[];
@@ -259,7 +288,13 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     constexpr int BK = kRowBytes / (int)sizeof(OpT);   // K elements per stage
     const int n0 = blockIdx.x * BN, m0 = blockIdx.y * BM;
-    const int nk = (K + BK - 1) / BK;
+    // folded: half the K range, the second half for tiles in the second half of M
+    const int kh = FOLD ? K / 2 : K;
+    const int kofs = (FOLD && m0 >= M / 2) ? kh : 0;
+    const int nk = (kh + BK - 1) / BK;
+    // paired tiles: the 32 B rows at na and the 32 at nb (FOLD 1: mirror, reversed; 2, 3: N/2 + na)
+    const int na = kPaired ? blockIdx.x * 32 : n0;
+    const int nb = FOLD == 1 ? N - 32 - na : N / 2 + na;
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < STAGES; ++s) {
@@ -295,7 +330,12 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__
             unsigned char* sa = base + s * L::kStageBytes;
             mbar_expect_tx(&full[s], (uint32_t)L::kStageBytes);
             tma_load_2d(sa, &mapA, &full[s], kb * BK, m0);
-            tma_load_2d(sa + L::kABytes, &mapB, &full[s], kb * BK, n0);
+            if (kPaired) {   // mapB's box is 32 rows
+                tma_load_2d(sa + L::kABytes, &mapB, &full[s], kofs + kb * BK, na);
+                tma_load_2d(sa + L::kABytes + 32 * kRowBytes, &mapB, &full[s], kofs + kb * BK, nb);
+            } else {
+                tma_load_2d(sa + L::kABytes, &mapB, &full[s], kofs + kb * BK, n0);
+            }
             issued = kb + 1;
         }
         // no copy may still be landing in shared memory when the CTA exits
@@ -340,10 +380,13 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__
             // (POST), one row at a time with coalesced reads; zeros outside the matrix
             const float* src0 = EPI == EPI_SCALE ? ea.f : ea.d;
             for (int rr = 0; rr < 32; ++rr) {
-                const int row = 32 * q + rr, gm = m0 + row;
+                const int row = 32 * q + rr;
+                // folded products read f, d, r at the natural row and (FOLD 2) natural columns
+                const int gm = FOLD ? nat_of(m0 + row, M) : m0 + row;
 #pragma unroll
                 for (int h = 0; h < BN / 32; ++h) {
-                    const int c = lane + 32 * h, gn = n0 + c;
+                    const int c = lane + 32 * h;
+                    const int gn = FOLD == 2 ? nat_of(h == 0 ? na + lane : nb + lane, N) : n0 + c;
                     const bool in = gm < M && gn < N;
                     const size_t off = (size_t)gm * N + gn;
                     pre[row * L::kPreStride + c] = (in && src0) ? __ldg(src0 + off) : (src0 ? 0.0f : 1.0f);
@@ -357,7 +400,35 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__
         if (!ok) flags[1] = 1;
         tc_fence_after();
         double part = 0.0;
-        if (ok) {
+        if (ok && kPaired) {
+            // both 32-column halves of the accumulator, then sums / differences of mirror pairs
+            float va[32], vb[32];
+            tmem_ld32(tmem + ((uint32_t)(32 * q) << 16), va);
+            tmem_ld32(tmem + ((uint32_t)(32 * q) << 16) + 32u, vb);
+            if (FOLD == 2) {
+                const float* prow = pre + (32 * q + lane) * L::kPreStride;
+#pragma unroll
+                for (int i = 0; i < 32; ++i) {
+                    va[i] *= prow[i];
+                    vb[i] *= prow[32 + i];
+                }
+            }
+            float sv[32], dv[32];
+#pragma unroll
+            for (int i = 0; i < 32; ++i) {
+                const float b = FOLD == 1 ? vb[31 - i] : vb[i];   // the mirror of column na + i
+                sv[i] = va[i] + b;
+                dv[i] = va[i] - b;
+            }
+            if (na == 0) {   // slot 0 of each half: the raw endpoint values
+                sv[0] = va[0];
+                dv[0] = FOLD == 1 ? vb[31] : vb[0];
+            }
+            const int row = FOLD == 3 ? nat_of(m, M) : m;
+            OpT* o = reinterpret_cast<OpT*>(ea.out) + (size_t)row * ea.ldo;
+            store_row32(o + na, sv);
+            store_row32(o + N / 2 + na, dv);
+        } else if (ok) {
 #pragma unroll 1
             for (int c0 = 0; c0 < BN; c0 += 32) {
                 float v[32];
@@ -395,7 +466,7 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__
                             if (n + i < N) store_one(o + i, v[i]);
                     }
                 } else {
-                    float* o = reinterpret_cast<float*>(ea.out) + (size_t)m * ea.ldo + n;
+                    float* o = reinterpret_cast<float*>(ea.out) + (size_t)(FOLD == 4 ? nat_of(m, M) : m) * ea.ldo + n;
                     const float* d = ea.d ? ea.d + (size_t)m * N + n : nullptr;
                     const float* r = ea.r + (size_t)m * N + n;
                     float acc = 0.0f;
@@ -524,7 +595,7 @@ inline bool make_tc_map(CUtensorMap* map, const void* ptr, int elem_bytes, int i
 // Raise the kernel's dynamic shared-memory limit (once per device; plans call
 // this at set-up, before any stream capture), then launch with programmatic
 // stream serialisation.
-template <typename OpT, int BN, int STAGES, int EPI>
+template <typename OpT, int BN, int STAGES, int EPI, int FOLD = 0>
 inline cudaError_t tc_gemm_prepare() {
     static std::mutex mu;
     static bool done[kMaxDevices] = {};
@@ -534,19 +605,19 @@ inline cudaError_t tc_gemm_prepare() {
     if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
     std::lock_guard<std::mutex> lk(mu);
     if (done[dev]) return cudaSuccess;
-    e = cudaFuncSetAttribute(tc_gemm_kernel<OpT, BN, STAGES, EPI>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    e = cudaFuncSetAttribute(tc_gemm_kernel<OpT, BN, STAGES, EPI, FOLD>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              TcSmem<BN, STAGES, EPI>::kBytes);
     if (e == cudaSuccess) done[dev] = true;
     return e;
 }
 
-template <typename OpT, int BN, int STAGES, int EPI>
+template <typename OpT, int BN, int STAGES, int EPI, int FOLD = 0>
 inline cudaError_t launch_tc_gemm(const CUtensorMap& mapA, const CUtensorMap& mapB, int M, int N, int K,
                                   const TcEpi& ea, cudaStream_t s) {
-    const cudaError_t attr = tc_gemm_prepare<OpT, BN, STAGES, EPI>();
+    const cudaError_t attr = tc_gemm_prepare<OpT, BN, STAGES, EPI, FOLD>();
     if (attr != cudaSuccess) return attr;
     const dim3 grid((N + BN - 1) / BN, (M + BM - 1) / BM);
-    return launch_pdl(tc_gemm_kernel<OpT, BN, STAGES, EPI>, grid, dim3(kTcThreads),
+    return launch_pdl(tc_gemm_kernel<OpT, BN, STAGES, EPI, FOLD>, grid, dim3(kTcThreads),
                       (size_t)TcSmem<BN, STAGES, EPI>::kBytes, s, mapA, mapB, M, N, K, ea);
 }
 

@@ -201,3 +201,37 @@ def test_batched_gemm_plans_equal_individual_calls(tdev):
     finally:
         for p in plans:
             p.close()
+
+
+@pytest.mark.parametrize("nr,nc", [(256, 256), (512, 256), (256, 768)])
+@pytest.mark.parametrize("kind", ["dfast", "fast", "fastd"])
+@pytest.mark.parametrize("storage", ["f32", "bf16"])
+def test_folded_products_match_the_oracle(tdev, nr, nc, kind, storage):
+    """Anti-reflective plans with sides multiples of 256 run the folded products (each
+    transform split into its sum and difference halves, half the K per product): the solve
+    matches the oracle like the full products do, and the two forms agree."""
+    torch, dev = tdev
+    z, ref = _solve(torch, dev, nr, nc, "ar", kind, "gemm", storage=storage)
+    assert maxrel(z, ref) < TOL[storage]
+    with _env(TVD_GEMM_FOLD="0"):
+        z0, _ = _solve(torch, dev, nr, nc, "ar", kind, "gemm", storage=storage)
+    assert maxrel(z0, ref) < TOL[storage]
+    assert maxrel(z, z0) < TOL[storage]
+
+
+@pytest.mark.parametrize("storage", ["f32", "bf16"])
+@pytest.mark.parametrize("kind", ["dfast", "fastd"])
+def test_folded_mixed_deblur_within_1e5_of_oracle(tdev, kind, storage):
+    torch, dev = tdev
+    import paper_1011_5964_gb300 as pkg
+    n = 256
+    h = synth.gaussian_psf(2.0, half_width=7)
+    v = observe(n, n, h, "ar", 0.01, 78)
+    u_ref, _ = O.tv_deblur(v, h, "ar", 1e-3, 1e-2, outer=3, tol=1e-10, maxit=5000, kind=kind)
+    with _env(TVD_GEMM_STORAGE=storage), pkg.Plan(n, n, h, bc="ar", pc=kind, mode="mixed", transform="gemm") as plan:
+        u, st = plan.deblur(torch.tensor(v, dtype=torch.float64, device=dev), 1e-3, 1e-2, max_outer=3,
+                            inner_tol=1e-10, inner_maxit=5000)
+        u = u.cpu().numpy()
+    assert st["status"] == pkg.TVD_OK
+    err = np.linalg.norm(u - u_ref) / np.linalg.norm(u_ref)
+    assert err < 1e-5, err
