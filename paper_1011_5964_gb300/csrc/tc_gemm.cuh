@@ -379,6 +379,8 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__
             // while the main loop runs: this warp stages its 32 rows of f (SCALE) or d and r
             // (POST), one row at a time with coalesced reads; zeros outside the matrix
             const float* src0 = EPI == EPI_SCALE ? ea.f : ea.d;
+            // unrolled so that the loads of several rows are in flight together
+#pragma unroll 8
             for (int rr = 0; rr < 32; ++rr) {
                 const int row = 32 * q + rr;
                 // folded products read f, d, r at the natural row and (FOLD 2) natural columns
