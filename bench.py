@@ -67,7 +67,12 @@ WORDS_PER_PIXEL = {
 # workload, each with the SHA-256 (first 16 hex digits) of the source file of
 # its kernel at capture time: an entry is used only while that file is
 # unchanged, so a stale figure is reported as null.
-NCU_TRAFFIC = {}
+NCU_TRAFFIC = {
+    # the four folded products of one CG iteration, averaged (3.16, 7.36, 3.16, 11.57 MB)
+    "precond_gemm_tc.f32": {"source": "tc_gemm.cuh", "sha16": "0e21a148903b6e71", "bytes": 6312384},
+    "blur_forward.f32": {"source": "blur.cu", "sha16": "613b0e8572161374", "bytes": 8476928},
+    "blur_adjoint_L.f32": {"source": "blur.cu", "sha16": "613b0e8572161374", "bytes": 12658944},
+}
 
 
 def traffic_of(name):
@@ -188,23 +193,41 @@ def batched_leg(pkg, torch, dev, synth):
     betas = [it["beta"] for it in items]
     outs = [torch.empty_like(v) for v in vs]
     res = {}
-    for workers in (1, BATCH_WORKERS):
+
+    def timed(key, workers):
         pkg.deblur_batched(plans, vs, alphas, betas, OUTER, TOL, 5000, outs, workers)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         _, stats = pkg.deblur_batched(plans, vs, alphas, betas, OUTER, TOL, 5000, outs, workers)
         torch.cuda.synchronize()
-        res[workers] = (reduce_over_ranks(time.perf_counter() - t0, "max", dev),
-                        reduce_over_ranks(sum(sum(st["inner_iters"]) for st in stats), "sum", dev))
+        res[key] = (reduce_over_ranks(time.perf_counter() - t0, "max", dev),
+                    reduce_over_ranks(sum(sum(st["inner_iters"]) for st in stats), "sum", dev))
+
+    timed("default_1", 1)
+    timed("default", BATCH_WORKERS)
+    # the library's autotuner picks each plan's preconditioner form (FFT, 64- or
+    # 128-column product tiles, folded products) by timing them
+    t0 = time.perf_counter()
+    forms = {}
+    for p in plans:
+        rep = p.tune()
+        c = rep["candidates"][rep["chosen"]]
+        key = "fft" if c["transform"] == "fft" else f"gemm{c['tile_n']}" + ("_folded" if c["folded"] else "")
+        forms[key] = forms.get(key, 0) + 1
+    torch.cuda.synchronize()
+    tune_s = time.perf_counter() - t0
+    timed("tuned", BATCH_WORKERS)
     for p in plans:
         p.close()
     pixels = sum(it["n"] * it["n"] for it in every)
     return {"workload": f"{BATCH} independent tv_deblur, sides from {{128,192,256,384,512}} "
                         f"({pixels / 1e6:.2f} Mpixel in all), Gaussian sigma U[1,3], alpha log-U[1e-4,1e-2], "
                         f"beta 1e-2, 1% noise, AR, D_M, MIXED, 10 FP steps, tol 1e-6",
-            "deblurs_per_s": BATCH / res[BATCH_WORKERS][0], "workers": BATCH_WORKERS,
-            "pcg_iters_per_s": res[BATCH_WORKERS][1] / res[BATCH_WORKERS][0],
-            "one_stream_deblurs_per_s": BATCH / res[1][0], "plan_setup_s": setup_s,
+            "deblurs_per_s": BATCH / res["tuned"][0], "workers": BATCH_WORKERS,
+            "pcg_iters_per_s": res["tuned"][1] / res["tuned"][0],
+            "untuned_deblurs_per_s": BATCH / res["default"][0],
+            "one_stream_deblurs_per_s": BATCH / res["default_1"][0], "plan_setup_s": setup_s,
+            "tune_s": tune_s, "tuned_forms": forms,
             "timing": "host clock around the call, inputs resident"}
 
 
@@ -364,28 +387,30 @@ def path_roofline(pcg_iters_per_s, prec_bytes=4):
             "peak": peak, "unit": "GB/s", "frac": achieved / peak, "peak_source": src}
 
 
-def rooflines_of(prof, total_ms, storage):
+def rooflines_of(prof, total_ms, storage, folded=False):
     """Roofline entry of every kernel class of the step with a known algorithmic work per launch."""
     out = {}
     for name, (kms, kl) in prof.items():
         base = name.rsplit(".", 1)[0]
         if kl and (base in WORDS_PER_PIXEL or base == "precond_gemm_tc"):
-            out[name] = roofline_of(name, kms, kl, total_ms, storage)
+            out[name] = roofline_of(name, kms, kl, total_ms, storage, folded)
     return out
 
 
-def roofline_of(name, kms, klaunch, total_ms, storage=None):
+def roofline_of(name, kms, klaunch, total_ms, storage=None, folded=False):
     """Roofline entry of one kernel class from its summed device time and launch count."""
     base, prec = name.rsplit(".", 1)
     avg_s = kms / 1000.0 / max(klaunch, 1)
     share = kms / max(total_ms, 1e-12)
     if base == "precond_gemm_tc":
         # one n x n x n product of the transform form (the library's tcgen05 kernel): 2 n^3 flops
-        # (bf16 or tf32 operands, float accumulation)
-        flops = 2.0 * N_SIDE ** 3
+        # (bf16 or tf32 operands, float accumulation); n^3 for the folded products (two half-length
+        # transforms of n lines each)
+        flops = (1.0 if folded else 2.0) * N_SIDE ** 3
         peak, src = bf16_peak() if storage == "bf16" else tf32_peak()
         achieved = flops / avg_s / 1e12
-        return {"bound": "tensor", "kernel": f"{name} ({storage} transform product, tcgen05)", "achieved": achieved,
+        kind = "folded transform product" if folded else "transform product"
+        return {"bound": "tensor", "kernel": f"{name} ({storage} {kind}, tcgen05)", "achieved": achieved,
                 "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
                 "traffic": traffic_of(name), "peak_source": src,
                 "flops_per_launch": flops, "avg_launch_us": avg_s * 1e6, "launches": klaunch, "share": share}
@@ -579,8 +604,8 @@ def run_ours(args):
     total_ms = sum(v_[0] for v_ in prof.values())
     # every kernel is the library's own: the dominant class by device time, and all classes
     top = max(prof.items(), key=lambda kv: kv[1][0])
-    roofline = roofline_of(top[0], top[1][0], top[1][1], total_ms, mixed.gemm_storage)
-    rooflines = rooflines_of(prof, total_ms, mixed.gemm_storage)
+    roofline = roofline_of(top[0], top[1][0], top[1][1], total_ms, mixed.gemm_storage, mixed.gemm_folded)
+    rooflines = rooflines_of(prof, total_ms, mixed.gemm_storage, mixed.gemm_folded)
 
     # end to end through the public API with pinned host buffers
     v_pin = torch.tensor(v_host, dtype=torch.float64).pin_memory()
@@ -620,7 +645,7 @@ def run_ours(args):
             "rooflines": rooflines,
             "path_roofline": path_roofline(ws * iters_mixed / (ms_mixed / 1000.0)),
             "transform_form": mixed.transform,
-            "gemm_operands": mixed.gemm_storage,
+            "gemm_operands": mixed.gemm_storage, "gemm_folded": mixed.gemm_folded,
             "clocks": clocks,
             "e2e": {"value": ws * 1000.0 * args.steps / e2e_ms, "unit": "deblurs/s",
                     "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes}}

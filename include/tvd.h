@@ -238,6 +238,53 @@ int tvd_plan_transform(tvd_plan plan);
  * (FFT form or NULL plan), 1 float operands (tf32 products), 2 bf16 operands. */
 int tvd_plan_gemm_storage(tvd_plan plan);
 
+/* tvd_plan_gemm_folded -- 1 when the plan's GEMM form runs the folded products
+ * (anti-reflective eq. (fp) plans whose sides are multiples of 256: hat-S's
+ * symmetry splits each transform into two half-length ones on the sums and
+ * differences of mirror-image entries, so each product does n^3 instead of
+ * 2 n^3 flops; TVD_GEMM_FOLD=0 at plan set-up keeps the full products), else 0. */
+int tvd_plan_gemm_folded(tvd_plan plan);
+
+/* tvd_plan_gemm_tile -- output tile width of the plan's transform products
+ * (64 or 128 columns per 128-row tile), 0 in the FFT form or for NULL. */
+int tvd_plan_gemm_tile(tvd_plan plan);
+
+/*
+ * tvd_plan_tune -- the library's autotuner of the preconditioner's tile
+ * shapes. Times every form of the preconditioner solve that a MIXED 2D plan
+ * with a fast preconditioner admits -- the FFT-form line passes, the
+ * transform products with 128 x 64 and with 128 x 128 output tiles, and the
+ * folded products where the plan allows them (tvd_plan_gemm_folded) -- and
+ * leaves the plan in the fastest. The preconditioner solve is the only part of
+ * a CG or BiCGstab iteration the forms change (the stencils and vector passes
+ * are common); each form is set up for u_lag = 0, alpha = 1e-3, beta = 1e-2,
+ * TVD_TUNE_SOLVES solves of one seeded residual are captured in one CUDA graph
+ * (direct launches while per-kernel profiling is on), and the graph is
+ * replayed `reps` times (0: 3) after one warm-up replay, the fastest replay
+ * counting. The choice outlasts later tvd_plan_set_method calls; a later
+ * tvd_plan_set_transform to GEMM keeps its tile width and fold choice.
+ * Afterwards the plan needs tau_precond_setup again before tau_precond_solve
+ * (tv_deblur and the solvers set themselves up). Allocates and frees three
+ * image-sized scratch vectors; synchronises `stream` and the device.
+ * report (caller-owned, may be NULL) receives every candidate and the index
+ * of the chosen one. Errors: TVD_EINVAL (NULL plan, reps < 0, an FP64 or 1D
+ * plan, I / D preconditioners), TVD_ENOMEM, TVD_ECUDA, TVD_ETIMEOUT (a
+ * product's bounded wait gave up); after an error the plan may be left in
+ * the FFT form.
+ */
+#define TVD_TUNE_MAX 4
+#define TVD_TUNE_SOLVES 16
+typedef struct {
+    int count;                          /* candidates timed */
+    int chosen;                         /* index of the form the plan now runs */
+    int transform[TVD_TUNE_MAX];        /* tvd_transform of candidate k */
+    int tile_n[TVD_TUNE_MAX];           /* product tile width, 0 for the FFT form */
+    int folded[TVD_TUNE_MAX];           /* 1 for the folded products */
+    double us_per_solve[TVD_TUNE_MAX];  /* fastest replay / TVD_TUNE_SOLVES, microseconds */
+} tvd_tune_report;
+
+tvd_status tvd_plan_tune(tvd_plan plan, int reps, tvd_tune_report* report, void* stream);
+
 /*
  * pcg_solve -- solve (H^T H + alpha L(u_lag)) x = b by preconditioned CG from
  * the initial guess in x_inout, stopping when ||r_k||_2 / ||r_0||_2 < tol

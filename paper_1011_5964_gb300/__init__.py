@@ -38,7 +38,8 @@ ABI_FUNCTIONS = ["tvd_plan_create", "tvd_plan_destroy", "ar_blur_apply", "tv_ope
                  "tau_precond_setup", "tau_precond_solve", "pcg_solve", "tv_deblur",
                  "tvd_plan_set_method", "tvd_plan_method", "pbicgstab_solve",
                  "tv_deblur_batched", "tv_hessian_apply", "tv_deblur_adjoint", "tv_deblur_newton", "tvd_plan_psf_size",
-                 "tvd_normal_apply_noalloc", "tvd_plan_set_transform", "tvd_plan_transform", "tvd_plan_gemm_storage",
+                 "tvd_normal_apply_noalloc", "tvd_plan_set_transform", "tvd_plan_transform", "tvd_plan_gemm_storage", "tvd_plan_gemm_folded",
+                 "tvd_plan_gemm_tile", "tvd_plan_tune",
                  "tvd_last_error", "tvd_version", "tvd_kernel_launches",
                  "tvd_profile_enable", "tvd_profile_classes", "tvd_profile_name", "tvd_profile_read"]
 
@@ -59,6 +60,16 @@ class _Stats(ctypes.Structure):
                 ("last_rel_change", ctypes.c_double), ("last_status", ctypes.c_int),
                 ("g_norm", ctypes.POINTER(ctypes.c_double)), ("functional", ctypes.POINTER(ctypes.c_double)),
                 ("final_g_norm", ctypes.c_double), ("final_functional", ctypes.c_double)]
+
+
+TUNE_MAX = 4      # TVD_TUNE_MAX
+TUNE_SOLVES = 16  # TVD_TUNE_SOLVES
+
+
+class _TuneReport(ctypes.Structure):
+    _fields_ = [("count", ctypes.c_int), ("chosen", ctypes.c_int), ("transform", ctypes.c_int * TUNE_MAX),
+                ("tile_n", ctypes.c_int * TUNE_MAX), ("folded", ctypes.c_int * TUNE_MAX),
+                ("us_per_solve", ctypes.c_double * TUNE_MAX)]
 
 
 class _NewtonStats(ctypes.Structure):
@@ -109,6 +120,9 @@ def load_library(path: str | None = None) -> ctypes.CDLL:
     lib.pbicgstab_solve.argtypes = [vp, vp, d, d, vp, vp, d, i, ctypes.POINTER(i), ctypes.POINTER(d), vp]
     lib.tvd_plan_transform.argtypes = [vp]
     lib.tvd_plan_gemm_storage.argtypes = [vp]
+    lib.tvd_plan_gemm_folded.argtypes = [vp]
+    lib.tvd_plan_gemm_tile.argtypes = [vp]
+    lib.tvd_plan_tune.argtypes = [vp, i, ctypes.POINTER(_TuneReport), vp]
     lib.tvd_last_error.restype = ctypes.c_char_p
     lib.tvd_version.restype = ctypes.c_char_p
     lib.tvd_kernel_launches.restype = ctypes.c_ulonglong
@@ -195,6 +209,28 @@ class Plan:
     @property
     def transform(self) -> str:
         return "gemm" if self.lib.tvd_plan_transform(self.handle) == TRANSFORM["gemm"] else "fft"
+
+    @property
+    def gemm_folded(self) -> bool:
+        """True when the GEMM form runs the folded (half-K) products."""
+        return bool(self.lib.tvd_plan_gemm_folded(self.handle))
+
+    @property
+    def gemm_tile(self) -> int:
+        """Output tile width of the transform products (64 / 128), 0 in the FFT form."""
+        return int(self.lib.tvd_plan_gemm_tile(self.handle))
+
+    def tune(self, reps: int = 3) -> dict:
+        """Time every preconditioner form the plan admits and keep the fastest (tvd_plan_tune).
+
+        Returns {"chosen": k, "candidates": [{"transform", "tile_n", "folded", "us_per_solve"}, ...]}.
+        """
+        rep = _TuneReport()
+        _check(self.lib.tvd_plan_tune(self.handle, int(reps), ctypes.byref(rep), _stream()))
+        cands = [{"transform": "gemm" if rep.transform[k] == TRANSFORM["gemm"] else "fft",
+                  "tile_n": int(rep.tile_n[k]), "folded": bool(rep.folded[k]),
+                  "us_per_solve": float(rep.us_per_solve[k])} for k in range(rep.count)]
+        return {"chosen": int(rep.chosen), "candidates": cands}
 
     @property
     def gemm_storage(self):

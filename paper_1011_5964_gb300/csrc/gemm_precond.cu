@@ -162,6 +162,20 @@ void gemm_precond_destroy(tvd_plan_s& p) {
     p.gemm = nullptr;
 }
 
+bool gemm_fold_allowed(const tvd_plan_s& p) {
+    return p.bc == TVD_BC_ANTIREFLECTIVE && !p.reblur() && p.nr % 256 == 0 && p.nc % 256 == 0;
+}
+
+int gemm_precond_folded(const tvd_plan_s& p) {
+    const auto* g = static_cast<const GemmPrecond*>(p.gemm);
+    return g && g->fold ? 1 : 0;
+}
+
+int gemm_precond_tile(const tvd_plan_s& p) {
+    const auto* g = static_cast<const GemmPrecond*>(p.gemm);
+    return g ? g->bn : 0;
+}
+
 int gemm_precond_storage(const tvd_plan_s& p) {
     const auto* g = static_cast<const GemmPrecond*>(p.gemm);
     return g ? (g->bf ? 2 : 1) : 0;
@@ -216,10 +230,11 @@ tvd_status gemm_precond_create(tvd_plan_s& p, cudaStream_t s) {
     const char* bv = std::getenv("TVD_GEMM_BN");
     if (bv && (std::atoi(bv) == 64 || std::atoi(bv) == 128)) g->bn = std::atoi(bv);
     // folded products (half the K of each product) for AR plans of eq. (fp) whose sides are
-    // multiples of 256; TVD_GEMM_FOLD=0 keeps the full products
+    // multiples of 256; TVD_GEMM_FOLD=0 keeps the full products. The autotuner's choice
+    // (tvd_plan_tune) comes before both rules.
     const char* fv = std::getenv("TVD_GEMM_FOLD");
-    g->fold = p.bc == TVD_BC_ANTIREFLECTIVE && !p.reblur() && p.nr % 256 == 0 && p.nc % 256 == 0 &&
-              !(fv && fv[0] == '0');
+    g->fold = gemm_fold_allowed(p) && (p.gemm_fold >= 0 ? p.gemm_fold == 1 : !(fv && fv[0] == '0'));
+    if (p.gemm_bn == 64 || p.gemm_bn == 128) g->bn = p.gemm_bn;
     if (g->fold) g->bn = 64;
     auto alloc = [&](void** ptr, size_t bytes) -> bool {
         if (cudaMalloc(ptr, bytes) != cudaSuccess) {

@@ -725,6 +725,161 @@ int tvd_plan_transform(tvd_plan plan) { return plan && plan->gemm ? TVD_TRANSFOR
 
 int tvd_plan_gemm_storage(tvd_plan plan) { return plan ? gemm_precond_storage(*plan) : 0; }
 
+int tvd_plan_gemm_folded(tvd_plan plan) { return plan ? gemm_precond_folded(*plan) : 0; }
+
+int tvd_plan_gemm_tile(tvd_plan plan) { return plan ? gemm_precond_tile(*plan) : 0; }
+
+}  // extern "C"
+
+namespace tvd {
+
+// Put the plan in one preconditioner form: FFT, or the products with tile width
+// bn (64 / 128) and the folded products on or off.
+static tvd_status tune_apply(tvd_plan_s& p, int transform, int bn, int fold, cudaStream_t s) {
+    TVD_CUDA_TRY(cudaStreamSynchronize(s));
+    if (p.graph[0].exec) {
+        cudaGraphExecDestroy(p.graph[0].exec);
+        p.graph[0].exec = nullptr;
+    }
+    TVD_CUDA_TRY(cudaDeviceSynchronize());
+    gemm_precond_destroy(p);
+    p.gemm_bn = bn;
+    p.gemm_fold = fold;
+    return transform == TVD_TRANSFORM_GEMM ? gemm_precond_create(p, s) : TVD_OK;
+}
+
+// Average time of one preconditioner solve r -> z in the plan's current form:
+// TVD_TUNE_SOLVES solves per graph replay, the fastest of `reps` replays after
+// one warm-up.
+static tvd_status tune_time(tvd_plan_s& p, const float* r, float* z, int reps, double* us, cudaStream_t s) {
+    const bool use_graph = !profiling_enabled();
+    cudaGraphExec_t exec = nullptr;
+    int kernels = 0;
+    if (use_graph) {
+        if (!p.cap_stream) TVD_CUDA_TRY(cudaStreamCreateWithFlags(&p.cap_stream, cudaStreamNonBlocking));
+        TVD_CUDA_TRY(cudaStreamBeginCapture(p.cap_stream, cudaStreamCaptureModeThreadLocal));
+        set_capturing(true);
+        tvd_status st = TVD_OK;
+        for (int k = 0; k < TVD_TUNE_SOLVES && st == TVD_OK; ++k)
+            st = precond_solve<float>(p, p.f, r, z, nullptr, p.cap_stream);
+        kernels = captured_kernels();
+        set_capturing(false);
+        cudaGraph_t graph = nullptr;
+        const cudaError_t e = cudaStreamEndCapture(p.cap_stream, &graph);
+        if (st != TVD_OK) {
+            if (graph) cudaGraphDestroy(graph);
+            return st;
+        }
+        TVD_CUDA_TRY(e);
+        const cudaError_t ei = cudaGraphInstantiate(&exec, graph, 0);
+        cudaGraphDestroy(graph);
+        TVD_CUDA_TRY(ei);
+    }
+    auto run = [&]() -> tvd_status {
+        if (use_graph) {
+            TVD_CUDA_TRY(cudaGraphLaunch(exec, s));
+            count_launches(kernels);
+            return TVD_OK;
+        }
+        for (int k = 0; k < TVD_TUNE_SOLVES; ++k) TVD_TRY(precond_solve<float>(p, p.f, r, z, nullptr, s));
+        return TVD_OK;
+    };
+    cudaEvent_t ev[2] = {nullptr, nullptr};
+    tvd_status st = TVD_OK;
+    double best = 1e300;
+    if (cudaEventCreate(&ev[0]) != cudaSuccess || cudaEventCreate(&ev[1]) != cudaSuccess) {
+        set_error("cudaEventCreate failed");
+        st = TVD_ECUDA;
+    }
+    for (int k = 0; k <= reps && st == TVD_OK; ++k) {   // k = 0: warm-up
+        if (cudaEventRecord(ev[0], s) != cudaSuccess) st = TVD_ECUDA;
+        if (st == TVD_OK) st = run();
+        if (st == TVD_OK && (cudaEventRecord(ev[1], s) != cudaSuccess || cudaEventSynchronize(ev[1]) != cudaSuccess))
+            st = TVD_ECUDA;
+        float ms = 0.0f;
+        if (st == TVD_OK && cudaEventElapsedTime(&ms, ev[0], ev[1]) != cudaSuccess) st = TVD_ECUDA;
+        if (st == TVD_OK && k > 0) best = std::min(best, 1e3 * (double)ms / TVD_TUNE_SOLVES);
+    }
+    if (st == TVD_ECUDA) set_error("timing a preconditioner form failed");
+    for (cudaEvent_t e : ev)
+        if (e) cudaEventDestroy(e);
+    if (exec) cudaGraphExecDestroy(exec);
+    if (st == TVD_OK && p.gemm) st = gemm_precond_check(p, s);
+    *us = best;
+    return st;
+}
+
+}  // namespace tvd
+
+extern "C" {
+
+tvd_status tvd_plan_tune(tvd_plan plan, int reps, tvd_tune_report* report, void* stream) {
+    if (!plan || reps < 0) {
+        set_error("tvd_plan_tune: NULL plan or reps < 0");
+        return TVD_EINVAL;
+    }
+    if (plan->mode != TVD_MODE_MIXED || !fast_pc(plan->pc) || plan->nr == 1) {
+        set_error("tvd_plan_tune: only MIXED 2D plans with a fast preconditioner have forms to choose from");
+        return TVD_EINVAL;
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    if (reps == 0) reps = 3;
+    tvd_tune_report rep{};
+    const int cand[TVD_TUNE_MAX][3] = {{TVD_TRANSFORM_FFT, 0, 0},
+                                       {TVD_TRANSFORM_GEMM, 64, 0},
+                                       {TVD_TRANSFORM_GEMM, 128, 0},
+                                       {TVD_TRANSFORM_GEMM, 64, 1}};
+    const int count = gemm_fold_allowed(*plan) ? 4 : 3;
+    const size_t n = (size_t)plan->nr * plan->nc;
+    // scratch: u_lag = 0 (double), a seeded residual r in [-1, 1) and z (float)
+    double* u0 = nullptr;
+    float *r = nullptr, *z = nullptr;
+    tvd_status st = dalloc(&u0, n);
+    if (st == TVD_OK) st = dalloc(&r, n);
+    if (st == TVD_OK) st = dalloc(&z, n);
+    if (st == TVD_OK) {
+        std::vector<float> hr(n);
+        unsigned long long x = 0x9E3779B97F4A7C15ull;   // splitmix64 stream
+        for (size_t i = 0; i < n; ++i) {
+            x += 0x9E3779B97F4A7C15ull;
+            unsigned long long y = x;
+            y = (y ^ (y >> 30)) * 0xBF58476D1CE4E5B9ull;
+            y = (y ^ (y >> 27)) * 0x94D049BB133111EBull;
+            y ^= y >> 31;
+            hr[i] = (float)((double)(y >> 11) * 0x1.0p-52 - 1.0);
+        }
+        if (cudaMemsetAsync(u0, 0, n * sizeof(double), s) != cudaSuccess ||
+            cudaMemcpyAsync(r, hr.data(), n * sizeof(float), cudaMemcpyHostToDevice, s) != cudaSuccess ||
+            cudaStreamSynchronize(s) != cudaSuccess) {
+            set_error("tvd_plan_tune: scratch set-up failed");
+            st = TVD_ECUDA;
+        }
+    }
+    for (int k = 0; k < count && st == TVD_OK; ++k) {
+        st = tune_apply(*plan, cand[k][0], cand[k][1], cand[k][2], s);
+        if (st == TVD_OK) st = setup_mixed(*plan, u0, 1e-3, 1e-2, s);
+        double us = 0.0;
+        if (st == TVD_OK) st = tune_time(*plan, r, z, reps, &us, s);
+        rep.transform[k] = cand[k][0];
+        rep.tile_n[k] = cand[k][1];
+        rep.folded[k] = cand[k][2];
+        rep.us_per_solve[k] = us;
+        rep.count = k + 1;
+        if (st == TVD_OK && us < rep.us_per_solve[rep.chosen]) rep.chosen = k;
+    }
+    if (st == TVD_OK) {
+        const int c = rep.chosen;
+        st = tune_apply(*plan, cand[c][0], cand[c][1], cand[c][2], s);
+    }
+    plan->precond_ready = false;
+    cudaStreamSynchronize(s);
+    dfree(u0);
+    dfree(r);
+    dfree(z);
+    if (report) *report = rep;
+    return st;
+}
+
 const char* tvd_version(void) { return "tvd-gb300 0.1"; }
 
 tvd_status tvd_plan_create(tvd_plan* out, int n_rows, int n_cols, const double* psf_host, int p_rows, int p_cols,

@@ -226,6 +226,8 @@ struct tvd_plan_s {
     // dense-matrix (GEMM) form of the preconditioner transforms, MIXED plans
     // with a fast preconditioner only (gemm_precond.cu); nullptr: FFT form
     void* gemm = nullptr;
+    int gemm_bn = 0;                    // tile width chosen by tvd_plan_tune (0: the default rule)
+    int gemm_fold = -1;                 // folded products chosen by tvd_plan_tune (-1: the default rule)
     // BiCGstab state and vectors of the reblurring method (reblur.cu)
     void* bicg = nullptr;
     // eq. (fpp), with L or L_AR
@@ -307,7 +309,10 @@ tvd_status lamH2_setup(const tvd_plan_s& p, Ops<T>& o, cudaStream_t s);
 // its device error flag: TVD_ETIMEOUT if a product's bounded wait expired.
 tvd_status gemm_precond_create(tvd_plan_s& p, cudaStream_t s);
 void gemm_precond_destroy(tvd_plan_s& p);
-int gemm_precond_storage(const tvd_plan_s& p);   // 0: no GEMM form, 1: float operands, 2: bf16 operands
+int gemm_precond_storage(const tvd_plan_s& p);  // 0: no GEMM form, 1: float operands, 2: bf16 operands
+int gemm_precond_folded(const tvd_plan_s& p);   // 1: the folded (half-K) products
+int gemm_precond_tile(const tvd_plan_s& p);     // product tile width, 0: no GEMM form
+bool gemm_fold_allowed(const tvd_plan_s& p);    // the plan admits the folded products
 tvd_status gemm_precond_check(const tvd_plan_s& p, cudaStream_t s);
 tvd_status gemm_precond_solve(const tvd_plan_s& p, const Ops<float>& o, const float* r, float* z, CgState* st,
                               cudaStream_t s, float* x);

@@ -104,11 +104,24 @@ def test_stats_structures_match_the_header():
     import paper_1011_5964_gb300 as pkg
     hdr = open(os.path.join(ROOT, "include", "tvd.h")).read()
     for cname, py in (("tvd_stats", pkg._Stats), ("tvd_newton_stats", pkg._NewtonStats),
-                      ("tvd_batch_item", pkg._BatchItem)):
-        flat = re.sub(r"/\*.*?\*/", "", hdr, flags=re.S)
+                      ("tvd_batch_item", pkg._BatchItem), ("tvd_tune_report", pkg._TuneReport)):
+        flat = re.sub(r"\[[^\]]*\]", "", re.sub(r"/\*.*?\*/", "", hdr, flags=re.S))
         body = re.search(r"typedef struct \{([^{}]*)\} " + cname + ";", flat).group(1)
         names = []
         for stmt in filter(str.strip, body.split(";")):
             parts = stmt.split(",")          # "double alpha, beta" declares two fields
             names += [re.findall(r"\w+", parts[0])[-1]] + [re.findall(r"\w+", q)[-1] for q in parts[1:]]
         assert names == [f[0] for f in py._fields_], (cname, names)
+
+
+def test_tune_validation_and_constants(lib):
+    """tvd_plan_tune refuses a NULL plan before touching the GPU; the binding's constants are the header's."""
+    import ctypes
+    import paper_1011_5964_gb300 as pkg
+    rep = pkg._TuneReport()
+    assert lib.tvd_plan_tune(None, 3, ctypes.byref(rep), None) == pkg.TVD_EINVAL
+    assert b"tvd_plan_tune" in lib.tvd_last_error()
+    assert lib.tvd_plan_gemm_tile(None) == 0
+    hdr = open(HEADER).read()
+    assert int(re.search(r"#define TVD_TUNE_MAX (\d+)", hdr).group(1)) == pkg.TUNE_MAX
+    assert int(re.search(r"#define TVD_TUNE_SOLVES (\d+)", hdr).group(1)) == pkg.TUNE_SOLVES

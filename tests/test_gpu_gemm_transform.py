@@ -235,3 +235,18 @@ def test_folded_mixed_deblur_within_1e5_of_oracle(tdev, kind, storage):
     assert st["status"] == pkg.TVD_OK
     err = np.linalg.norm(u - u_ref) / np.linalg.norm(u_ref)
     assert err < 1e-5, err
+
+
+def test_folded_form_is_reported(tdev):
+    torch, dev = tdev
+    import paper_1011_5964_gb300 as pkg
+    h = synth.gaussian_psf(1.0, half_width=2)
+    cases = [((256, 512), "ar", "fp", True), ((300, 256), "ar", "fp", False), ((256, 256), "r", "fp", False),
+             ((256, 256), "ar", "reblur", False)]
+    for (nr, nc), bc, method, folded in cases:
+        with pkg.Plan(nr, nc, h, bc=bc, pc="dfast", mode="mixed", transform="gemm", method=method) as plan:
+            assert plan.gemm_folded == folded, (nr, nc, bc, method)
+    with _env(TVD_GEMM_FOLD="0"), pkg.Plan(256, 256, h, bc="ar", pc="dfast", mode="mixed", transform="gemm") as plan:
+        assert not plan.gemm_folded
+    with pkg.Plan(256, 256, h, bc="ar", pc="dfast", mode="mixed", transform="fft") as plan:
+        assert not plan.gemm_folded
