@@ -382,6 +382,33 @@ tvd_status cg_restart(const tvd_plan_s& p, const T* r, CgState* st, double tol2,
     return TVD_OK;
 }
 
+__global__ void cg_loop_arm_kernel(CgState* st, int budget) {
+    st->loops = 0;
+    st->loop_budget = budget;
+}
+
+// One thread, launched after the chunk's last kernel has completed (plain
+// stream order, no programmatic overlap), so it reads the final state.
+__global__ void cg_loop_cond_kernel(cudaGraphConditionalHandle h, CgState* st) {
+    const int k = st->loops + 1;
+    st->loops = k;
+    cudaGraphSetConditional(h, (!st->done && k < st->loop_budget) ? 1u : 0u);
+}
+
+tvd_status cg_loop_arm(CgState* st, int budget, cudaStream_t s) {
+    ProfScope prof(PROF_MISC, s);
+    cg_loop_arm_kernel<<<1, 1, 0, s>>>(st, budget);
+    TVD_CUDA_TRY(cudaGetLastError());
+    return TVD_OK;
+}
+
+tvd_status cg_loop_cond(cudaGraphConditionalHandle h, CgState* st, cudaStream_t s) {
+    ProfScope prof(PROF_MISC, s);
+    cg_loop_cond_kernel<<<1, 1, 0, s>>>(h, st);
+    TVD_CUDA_TRY(cudaGetLastError());
+    return TVD_OK;
+}
+
 tvd_status residual_lx(const tvd_plan_s& p, const double* b, const double* hx, const double* w, const double* x,
                        double alpha, double* r, double* out_norm2, cudaStream_t s) {
     const size_t n = (size_t)p.nr * p.nc;

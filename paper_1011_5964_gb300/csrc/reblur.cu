@@ -124,6 +124,7 @@ struct BiState {
     double rho, rho_old, alpha, omega, beta;
     double rv, ss, ts, tt, rr, rr0, tol2;
     int iter, maxit, done, status, half, first;
+    int loops, loop_budget;   // device-driven loop: chunks run since armed, and the most it may run
 };
 
 template <typename T>
@@ -138,6 +139,19 @@ struct BiResources {
     BiVecs<float> f;
     BiVecs<double> d;
     bool have_f = false, have_d = false;
+    // captured chunk of iterations in a while node, per arithmetic (float / double),
+    // valid for one (x, r, alpha)
+    struct Loop {
+        cudaGraphExec_t exec = nullptr;
+        const void* x = nullptr;
+        const void* r = nullptr;
+        double alpha = -1.0;
+        int kernels = 0;
+        void reset() {
+            if (exec) cudaGraphExecDestroy(exec);
+            exec = nullptr;
+        }
+    } loop[2];
 };
 
 template <typename T>
@@ -153,12 +167,19 @@ void reblur_free(tvd_plan_s& p) {
     free_tables(p.f);
     auto* r = static_cast<BiResources*>(p.bicg);
     if (!r) return;
+    for (auto& l : r->loop) l.reset();
     if (r->st) cudaFree(r->st);
     if (r->hst) cudaFreeHost(r->hst);
     free_vecs(r->f);
     free_vecs(r->d);
     delete r;
     p.bicg = nullptr;
+}
+
+void reblur_graphs_reset(tvd_plan_s& p) {
+    auto* r = static_cast<BiResources*>(p.bicg);
+    if (r)
+        for (auto& l : r->loop) l.reset();
 }
 
 template <typename T>
@@ -438,7 +459,21 @@ static tvd_status precond(tvd_plan_s& p, Ops<T>& o, const T* r, T* z, cudaStream
     }
 }
 
-constexpr int kBiChunk = 4;   // iterations enqueued between host checks
+constexpr int kBiChunk = 4;   // iterations per chunk (between host checks, or per pass of the device loop)
+
+__global__ void bi_loop_arm_kernel(BiState* st, int budget) {
+    st->loops = 0;
+    st->loop_budget = budget;
+}
+
+// Last kernel of a chunk inside the while node (plain stream order: it reads
+// the state the chunk's last kernel left): count the chunk, go on while the
+// solve is not done and the budget lasts.
+__global__ void bi_loop_cond_kernel(cudaGraphConditionalHandle h, BiState* st) {
+    const int k = st->loops + 1;
+    st->loops = k;
+    cudaGraphSetConditional(h, (!st->done && k < st->loop_budget) ? 1u : 0u);
+}
 
 // BiCGstab on A' x = b (type T) from the x given; stops when ||r||^2 <=
 // max(tol2_rel ||r_0||^2, tol2_abs), or after maxit iterations.
@@ -456,33 +491,75 @@ static tvd_status bicg_run(tvd_plan_s& p, Ops<T>& o, BiVecs<T>& bv, BiResources&
         bi_init_kernel<T><<<blocks, kThreads, 0, s>>>(b, bv.t, r, bv.rhat, n, tol2_rel, tol2_abs, maxit, st, red, tk);
         TVD_CUDA_TRY(cudaGetLastError());
     }
-    int last_iter = -1;
-    for (int chunk = 0;; ++chunk) {
+    // one chunk: kBiChunk iterations on stream q (kernels of a finished solve return at once)
+    auto chunk = [&](cudaStream_t q) -> tvd_status {
         for (int it = 0; it < kBiChunk; ++it) {
             {
-                ProfScope prof(prof_class<T>(PROF_CG_SIMPLE), s, 2);
-                bi_rho_kernel<T><<<blocks, kThreads, 0, s>>>(bv.rhat, r, n, st, red, tk);
-                bi_p_kernel<T><<<blocks, kThreads, 0, s>>>(r, bv.v, bv.p, n, st);
+                ProfScope prof(prof_class<T>(PROF_CG_SIMPLE), q, 2);
+                bi_rho_kernel<T><<<blocks, kThreads, 0, q>>>(bv.rhat, r, n, st, red, tk);
+                bi_p_kernel<T><<<blocks, kThreads, 0, q>>>(r, bv.v, bv.p, n, st);
                 TVD_CUDA_TRY(cudaGetLastError());
             }
-            TVD_TRY(precond<T>(p, o, bv.p, bv.phat, s));
-            TVD_TRY(reblur_matvec<T>(p, o, bv.phat, bv.hx, bv.v, alpha, s));
+            TVD_TRY(precond<T>(p, o, bv.p, bv.phat, q));
+            TVD_TRY(reblur_matvec<T>(p, o, bv.phat, bv.hx, bv.v, alpha, q));
             {
-                ProfScope prof(prof_class<T>(PROF_CG_SIMPLE), s, 3);
-                bi_alpha_kernel<T><<<blocks, kThreads, 0, s>>>(bv.rhat, bv.v, n, st, red, tk);
-                bi_s_kernel<T><<<blocks, kThreads, 0, s>>>(r, bv.v, bv.s, n, st, red, tk);
-                bi_half_kernel<T><<<blocks, kThreads, 0, s>>>(x, bv.phat, n, st, tk);
+                ProfScope prof(prof_class<T>(PROF_CG_SIMPLE), q, 3);
+                bi_alpha_kernel<T><<<blocks, kThreads, 0, q>>>(bv.rhat, bv.v, n, st, red, tk);
+                bi_s_kernel<T><<<blocks, kThreads, 0, q>>>(r, bv.v, bv.s, n, st, red, tk);
+                bi_half_kernel<T><<<blocks, kThreads, 0, q>>>(x, bv.phat, n, st, tk);
                 TVD_CUDA_TRY(cudaGetLastError());
             }
-            TVD_TRY(precond<T>(p, o, bv.s, bv.shat, s));
-            TVD_TRY(reblur_matvec<T>(p, o, bv.shat, bv.hx, bv.t, alpha, s));
+            TVD_TRY(precond<T>(p, o, bv.s, bv.shat, q));
+            TVD_TRY(reblur_matvec<T>(p, o, bv.shat, bv.hx, bv.t, alpha, q));
             {
-                ProfScope prof(prof_class<T>(PROF_CG_XR), s, 2);
-                bi_omega_kernel<T><<<blocks, kThreads, 0, s>>>(bv.t, bv.s, n, st, red, tk);
-                bi_xr_kernel<T><<<blocks, kThreads, 0, s>>>(x, r, bv.phat, bv.shat, bv.s, bv.t, n, st, red, tk);
+                ProfScope prof(prof_class<T>(PROF_CG_XR), q, 2);
+                bi_omega_kernel<T><<<blocks, kThreads, 0, q>>>(bv.t, bv.s, n, st, red, tk);
+                bi_xr_kernel<T><<<blocks, kThreads, 0, q>>>(x, r, bv.phat, bv.shat, bv.s, bv.t, n, st, red, tk);
                 TVD_CUDA_TRY(cudaGetLastError());
             }
         }
+        return TVD_OK;
+    };
+    // device-driven loop: the chunk in a while node, one launch per solve
+    auto& L = res.loop[sizeof(T) == 8 ? 1 : 0];
+    if (!profiling_enabled() && device_loop_enabled()) {
+        if (!(L.exec && L.x == x && L.r == r && L.alpha == alpha)) {
+            L.reset();
+            const bool built = build_while_graph(
+                p,
+                [&](cudaStream_t q, cudaGraphConditionalHandle h) -> tvd_status {
+                    TVD_TRY(chunk(q));
+                    ProfScope prof(PROF_MISC, q);
+                    bi_loop_cond_kernel<<<1, 1, 0, q>>>(h, st);
+                    TVD_CUDA_TRY(cudaGetLastError());
+                    return TVD_OK;
+                },
+                &L.exec, &L.kernels);
+            L.x = x;
+            L.r = r;
+            L.alpha = built ? alpha : -1.0;
+        }
+        if (L.exec) {
+            {
+                ProfScope prof(PROF_MISC, s);
+                bi_loop_arm_kernel<<<1, 1, 0, s>>>(st, maxit / kBiChunk + 3);
+                TVD_CUDA_TRY(cudaGetLastError());
+            }
+            TVD_CUDA_TRY(cudaGraphLaunch(L.exec, s));
+            TVD_CUDA_TRY(cudaMemcpyAsync(res.hst, st, sizeof(BiState), cudaMemcpyDeviceToHost, s));
+            TVD_CUDA_TRY(cudaStreamSynchronize(s));
+            count_launches(res.hst->loops * L.kernels);
+            if (!res.hst->done) {   // the state stops at maxit, within the chunk budget
+                set_error("BiCGstab state did not reach done within its chunk budget");
+                return TVD_ECUDA;
+            }
+            *out = *res.hst;
+            return TVD_OK;
+        }
+    }
+    int last_iter = -1;
+    for (;;) {
+        TVD_TRY(chunk(s));
         TVD_CUDA_TRY(cudaMemcpyAsync(res.hst, st, sizeof(BiState), cudaMemcpyDeviceToHost, s));
         TVD_CUDA_TRY(cudaStreamSynchronize(s));
         if (res.hst->done) break;

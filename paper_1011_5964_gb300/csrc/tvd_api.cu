@@ -245,11 +245,14 @@ static void ops_free(Ops<T>& o) {
     o.allocated = false;
 }
 
+// Drop every captured solver chunk: they hold the current preconditioner form's launches.
+static void reset_graphs(tvd_plan_s& p) {
+    for (auto& g : p.graph) g.reset();
+    reblur_graphs_reset(p);
+}
+
 static void plan_free(tvd_plan_s* p) {
-    for (auto& g : p->graph) {
-        if (g.exec) cudaGraphExecDestroy(g.exec);
-        g.exec = nullptr;
-    }
+    for (auto& g : p->graph) g.reset();
     if (p->cap_stream) cudaStreamDestroy(p->cap_stream);
     p->cap_stream = nullptr;
     gemm_precond_destroy(*p);
@@ -403,14 +406,74 @@ constexpr int kChunk = 4;   // CG iterations per graph replay
 
 // Capture kChunk iterations into a CUDA graph for this (x, b, alpha). The
 // capture runs on a plan-owned stream; the graph is replayed on the caller's.
+// The device-driven loop (a while node around the chunk; TVD_CG_DEVICE_LOOP=0
+// at graph capture turns it off): one launch runs chunks until the solver state
+// is done, so the host neither polls after each chunk nor launches chunks past
+// convergence.
+bool device_loop_enabled() {
+    const char* v = std::getenv("TVD_CG_DEVICE_LOOP");
+    return !(v && v[0] == '0');
+}
+
+bool build_while_graph(tvd_plan_s& p, const std::function<tvd_status(cudaStream_t, cudaGraphConditionalHandle)>& body,
+                       cudaGraphExec_t* out, int* kernels) {
+    *out = nullptr;
+    if (!p.cap_stream && cudaStreamCreateWithFlags(&p.cap_stream, cudaStreamNonBlocking) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    cudaGraph_t graph = nullptr;
+    cudaGraphConditionalHandle h;
+    bool ok = cudaGraphCreate(&graph, 0) == cudaSuccess &&
+              cudaGraphConditionalHandleCreate(&h, graph, 1, cudaGraphCondAssignDefault) == cudaSuccess;
+    cudaGraph_t bg = nullptr;
+    if (ok) {
+        cudaGraphNodeParams np = {};
+        np.type = cudaGraphNodeTypeConditional;
+        np.conditional.handle = h;
+        np.conditional.type = cudaGraphCondTypeWhile;
+        np.conditional.size = 1;
+        cudaGraphNode_t node;
+        ok = cudaGraphAddNode(&node, graph, nullptr, nullptr, 0, &np) == cudaSuccess;
+        if (ok) bg = np.conditional.phGraph_out[0];
+    }
+    if (ok) ok = cudaStreamBeginCaptureToGraph(p.cap_stream, bg, nullptr, nullptr, 0,
+                                               cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+    if (ok) {
+        set_capturing(true);
+        const tvd_status st = body(p.cap_stream, h);
+        *kernels = captured_kernels();
+        set_capturing(false);
+        cudaGraph_t captured = nullptr;
+        const cudaError_t e = cudaStreamEndCapture(p.cap_stream, &captured);
+        ok = st == TVD_OK && e == cudaSuccess;
+    }
+    if (ok) ok = cudaGraphInstantiate(out, graph, 0) == cudaSuccess;
+    if (graph) cudaGraphDestroy(graph);
+    if (!ok) {
+        *out = nullptr;
+        cudaGetLastError();
+    }
+    return ok;
+}
+
+// g.loop: kChunk CG iterations and the condition kernel in a while node.
+template <typename T>
+static bool build_loop_graph(tvd_plan_s& p, Ops<T>& o, double alpha, T* x, tvd_plan_s::CgGraph& g) {
+    return build_while_graph(
+        p,
+        [&](cudaStream_t q, cudaGraphConditionalHandle h) -> tvd_status {
+            for (int c = 0; c < kChunk; ++c) TVD_TRY(enqueue_iteration<T>(p, o, alpha, x, p.state, q));
+            return cg_loop_cond(h, p.state, q);
+        },
+        &g.loop, &g.loop_kernels);
+}
+
 template <typename T>
 static tvd_status ensure_graph(tvd_plan_s& p, Ops<T>& o, double alpha, const T* b, T* x) {
     auto& g = p.graph[sizeof(T) == 8 ? 1 : 0];
     if (g.exec && g.x == x && g.b == b && g.alpha == alpha) return TVD_OK;
-    if (g.exec) {
-        cudaGraphExecDestroy(g.exec);
-        g.exec = nullptr;
-    }
+    g.reset();
     if (!p.cap_stream) TVD_CUDA_TRY(cudaStreamCreateWithFlags(&p.cap_stream, cudaStreamNonBlocking));
     TVD_CUDA_TRY(cudaStreamBeginCapture(p.cap_stream, cudaStreamCaptureModeThreadLocal));
     set_capturing(true);
@@ -432,6 +495,19 @@ static tvd_status ensure_graph(tvd_plan_s& p, Ops<T>& o, double alpha, const T* 
     g.b = b;
     g.alpha = alpha;
     g.kernels = kernels;
+    if (device_loop_enabled()) build_loop_graph<T>(p, o, alpha, x, g);
+    return TVD_OK;
+}
+
+// Run the device-driven loop: arm it with a budget of chunks, launch it once,
+// read the state. The budget (enough chunks for maxit iterations from the
+// start, plus slack) ends the loop even if the state never reported done.
+static tvd_status run_device_loop(tvd_plan_s& p, const tvd_plan_s::CgGraph& g, int maxit, cudaStream_t s) {
+    TVD_TRY(cg_loop_arm(p.state, maxit / kChunk + 3, s));
+    TVD_CUDA_TRY(cudaGraphLaunch(g.loop, s));
+    TVD_CUDA_TRY(cudaMemcpyAsync(p.hstate, p.state, sizeof(CgState), cudaMemcpyDeviceToHost, s));
+    TVD_CUDA_TRY(cudaStreamSynchronize(s));
+    count_launches(p.hstate->loops * g.loop_kernels);
     return TVD_OK;
 }
 
@@ -454,7 +530,14 @@ static tvd_status cg_run(tvd_plan_s& p, Ops<T>& o, double alpha, const T* b, T* 
     int& hint = p.last_iters[sizeof(T) == 8 ? 1 : 0];
     int first = std::max(1, (std::min(hint, maxit) - 2) / kChunk);
     int done_iters = 0;
-    for (;;) {
+    if (use_graph && g.loop) {
+        TVD_TRY(run_device_loop(p, g, maxit, s));
+        if (!p.hstate->done) {
+            set_error("CG state did not reach done after maxit iterations");
+            return TVD_ECUDA;
+        }
+    }
+    while (!(use_graph && g.loop)) {
         for (int c = 0; c < first; ++c) {
             if (use_graph) {
                 TVD_CUDA_TRY(cudaGraphLaunch(g.exec, s));
@@ -611,16 +694,21 @@ static tvd_status solve_mixed(tvd_plan_s& p, double alpha, const double* b, doub
     int batch = std::max(1, (std::min(hint, maxit) - 2) / kChunk);
     int last_iter = -1;
     for (;;) {
-        for (int c = 0; c < batch; ++c) {
-            if (use_graph) {
-                TVD_CUDA_TRY(cudaGraphLaunch(g.exec, s));
-                count_launches(g.kernels);
-            } else {
-                for (int i = 0; i < kChunk; ++i) TVD_TRY(enqueue_iteration<float>(p, p.f, alpha, p.f.x, p.state, s));
+        if (use_graph && g.loop) {
+            TVD_TRY(run_device_loop(p, g, maxit, s));
+        } else {
+            for (int c = 0; c < batch; ++c) {
+                if (use_graph) {
+                    TVD_CUDA_TRY(cudaGraphLaunch(g.exec, s));
+                    count_launches(g.kernels);
+                } else {
+                    for (int i = 0; i < kChunk; ++i)
+                        TVD_TRY(enqueue_iteration<float>(p, p.f, alpha, p.f.x, p.state, s));
+                }
             }
+            batch = 1;
+            TVD_TRY(read_state<float>(p, s));
         }
-        batch = 1;
-        TVD_TRY(read_state<float>(p, s));
         const CgState h = *p.hstate;
         res->iters = h.iter;
         if (h.status == TVD_ETIMEOUT) return timeout_exit(p, s);
@@ -709,10 +797,7 @@ tvd_status tvd_plan_set_transform(tvd_plan plan, int kind, void* stream) {
         return TVD_ECUDA;
     }
     // the captured float CG iterations hold the previous form's launches
-    if (plan->graph[0].exec) {
-        cudaGraphExecDestroy(plan->graph[0].exec);
-        plan->graph[0].exec = nullptr;
-    }
+    reset_graphs(*plan);
     if (kind == TVD_TRANSFORM_FFT) {
         cudaDeviceSynchronize();
         gemm_precond_destroy(*plan);
@@ -737,10 +822,7 @@ namespace tvd {
 // bn (64 / 128) and the folded products on or off.
 static tvd_status tune_apply(tvd_plan_s& p, int transform, int bn, int fold, cudaStream_t s) {
     TVD_CUDA_TRY(cudaStreamSynchronize(s));
-    if (p.graph[0].exec) {
-        cudaGraphExecDestroy(p.graph[0].exec);
-        p.graph[0].exec = nullptr;
-    }
+    reset_graphs(p);
     TVD_CUDA_TRY(cudaDeviceSynchronize());
     gemm_precond_destroy(p);
     p.gemm_bn = bn;
@@ -1316,15 +1398,11 @@ tvd_status tvd_plan_set_method(tvd_plan plan, int method, void* stream) {
     const bool same_transforms = (method != TVD_METHOD_FP) == plan->reblur();
     plan->method = method;
     plan->precond_ready = false;
+    reset_graphs(*plan);   // captured chunks hold the previous method's operator
     if (plan->gemm && !same_transforms) {
         // the transform matrices follow the method: rebuild them
         TVD_CUDA_TRY(cudaDeviceSynchronize());
         gemm_precond_destroy(*plan);
-        for (auto& g : plan->graph)
-            if (g.exec) {
-                cudaGraphExecDestroy(g.exec);
-                g.exec = nullptr;
-            }
         TVD_TRY(gemm_precond_create(*plan, s));
     }
     return TVD_OK;

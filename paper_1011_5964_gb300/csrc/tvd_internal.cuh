@@ -8,6 +8,7 @@
 
 #include <cuda_runtime.h>
 #include <cstdint>
+#include <functional>
 #include <string>
 #include <vector>
 
@@ -114,6 +115,8 @@ struct CgState {
     int fresh;         // 1: the next search direction is p = z (start or restart)
     int pbuf;          // which of the two direction buffers holds the current p
     int pending;       // 1: alpha is known and x += alpha p, r -= alpha q is still to be applied
+    int loops;         // chunks run by the device-driven loop since it was armed
+    int loop_budget;   // chunks the device-driven loop may run at most
 };
 
 // Reduction slots: each reduction writes one double per block, then the last
@@ -211,13 +214,23 @@ struct tvd_plan_s {
     double* xd = nullptr;               // double iterate
     double* tmp = nullptr;              // double scratch
     // CUDA graph of a chunk of CG iterations, per arithmetic (float / double);
-    // valid for one (x, b, alpha) operand set
+    // valid for one (x, b, alpha) operand set. `loop` is the same chunk inside a
+    // while node whose condition a kernel sets after each chunk (the device runs
+    // chunks until the CG state is done); nullptr where it could not be built.
     struct CgGraph {
         cudaGraphExec_t exec = nullptr;
+        cudaGraphExec_t loop = nullptr;
         const void* x = nullptr;
         const void* b = nullptr;
         double alpha = -1.0;
         int kernels = 0;
+        int loop_kernels = 0;   // kernels per chunk of `loop`, with its condition kernel
+        void reset() {
+            if (exec) cudaGraphExecDestroy(exec);
+            if (loop) cudaGraphExecDestroy(loop);
+            exec = nullptr;
+            loop = nullptr;
+        }
     } graph[2];
     cudaStream_t cap_stream = nullptr;  // plan-owned stream used only to capture graphs
     int last_iters[2] = {0, 0};         // iterations of the previous solve (chunking hint)
@@ -283,6 +296,17 @@ tvd_status reblur_matvec(const tvd_plan_s& p, const Ops<T>& o, const T* x, T* hx
 tvd_status reblur_solve(tvd_plan_s& p, double alpha, const double* b, double* x, double tol, int maxit, int* iters,
                         int* sweeps, double* relres, tvd_status* status, cudaStream_t s);
 void reblur_free(tvd_plan_s& p);
+void reblur_graphs_reset(tvd_plan_s& p);   // drop captured BiCGstab chunks (the preconditioner form changed)
+
+// Device-driven solver loops (tvd_api.cu). device_loop_enabled: the
+// TVD_CG_DEVICE_LOOP switch (default on). build_while_graph: a graph holding
+// one while node (condition 1 at each launch) whose body is captured from
+// `body(stream, handle)` on p.cap_stream; the body's last kernel must set the
+// condition. Returns false, with the CUDA error state cleared, where the
+// driver cannot build it; *kernels = kernels captured in the body.
+bool device_loop_enabled();
+bool build_while_graph(tvd_plan_s& p, const std::function<tvd_status(cudaStream_t, cudaGraphConditionalHandle)>& body,
+                       cudaGraphExec_t* out, int* kernels);
 
 // CG direction update fused with the forward blur: p_new = z (fresh) or
 // z + beta p_old, with p_old / p_new the two direction buffers chosen by
@@ -364,6 +388,12 @@ tvd_status cg_restart(const tvd_plan_s& p, const T* r, CgState* st, double tol2,
                       cudaStream_t s);
 tvd_status residual_lx(const tvd_plan_s& p, const double* b, const double* hx, const double* w, const double* x,
                        double alpha, double* r, double* out_norm2, cudaStream_t s);
+// Device-driven CG loop: cg_loop_arm sets the chunk budget and clears the
+// chunk count; cg_loop_cond, the last kernel of each chunk inside the while
+// node, counts the chunk and keeps the loop going while the state is not done
+// and the budget is not spent.
+tvd_status cg_loop_arm(CgState* st, int budget, cudaStream_t s);
+tvd_status cg_loop_cond(cudaGraphConditionalHandle h, CgState* st, cudaStream_t s);
 
 // elementwise helpers
 tvd_status residual_d(const tvd_plan_s& p, const double* b, const double* ax, double* r, double* out_norm2,
