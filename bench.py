@@ -377,6 +377,34 @@ def bf16_peak():
         return 1700.0, "fallback (bf16 sustained 1.7 PF)"
 
 
+def setup_ms_of(plan, u_lag, stream, reps=20):
+    """Average device time (ms) of one FP step's set-up (tau_precond_setup: diffusivity, D and
+    the preconditioner spectrum) at u_lag, or None if it cannot be taken."""
+    import torch
+    try:
+        for _ in range(3):
+            plan.precond_setup(u_lag, ALPHA, BETA)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            plan.precond_setup(u_lag, ALPHA, BETA)
+        e1.record(stream)
+        e1.synchronize()
+        return e0.elapsed_time(e1) / reps
+    except Exception as exc:   # a failed side measurement leaves the headline intact
+        print(f"set-up timing skipped: {exc}", file=sys.stderr)
+        return None
+
+
+def steady_rate(iters, ms, deblurs, setup_ms):
+    """Inner PCG iterations per second with the per-FP-step set-up taken out of the deblur time."""
+    if setup_ms is None:
+        return None
+    loop_ms = ms - deblurs * OUTER * setup_ms
+    return iters / (loop_ms / 1000.0) if loop_ms > 0 else None
+
+
 def path_roofline(pcg_iters_per_s, prec_bytes=4):
     """The whole PCG iteration against HBM: the floor of the standard recurrence, 15 words per pixel
     (matvec 3, x / r update 6, preconditioner 3, p update 3), times the iteration rate."""
@@ -589,6 +617,11 @@ def run_ours(args):
     ms_plain = max_over_ranks(ms_plain)
     iters_plain = sum(s["total_inner_iters"] for s in st_plain)
     rel_err = float(torch.linalg.norm(u_mixed - u64) / torch.linalg.norm(u64))
+    # the per-FP-step set-up alone, so the inner loop's steady rate can be reported without it
+    setup_mixed = setup_ms_of(mixed, u_mixed.float(), stream)
+    setup_plain = setup_ms_of(plain, u64, stream)
+    steady_mixed = steady_rate(iters_mixed, ms_mixed, args.steps, setup_mixed)
+    steady_plain = steady_rate(iters_plain, ms_plain, p_steps, setup_plain)
 
     # per-kernel device time of one more chosen-form step (CUDA events around every launch)
     pkg.profile_enable(True)
@@ -636,8 +669,12 @@ def run_ours(args):
                        "l2": "flushed between steps (512 MiB write)", "parallelism": f"replicas x{ws}"},
             "pcg_iters_per_s": ws * iters_mixed / (ms_mixed / 1000.0),
             "inner_iters_per_deblur": iters_mixed / args.steps,
+            "setup_ms_per_fp_step": setup_mixed,
+            "pcg_iters_per_s_steady": None if steady_mixed is None else ws * steady_mixed,
             "plain_fp64": {"deblurs_per_s": ws * 1000.0 * p_steps / ms_plain,
                            "pcg_iters_per_s": ws * iters_plain / (ms_plain / 1000.0),
+                           "setup_ms_per_fp_step": setup_plain,
+                           "pcg_iters_per_s_steady": None if steady_plain is None else ws * steady_plain,
                            "inner_iters_per_deblur": iters_plain / p_steps, "ms_per_step": ms_plain / p_steps},
             "rel_err_vs_plain_fp64": rel_err,
             "gpu_launches": launches,
