@@ -1131,19 +1131,48 @@ static tvd_status adjoint_mixed(tvd_plan_s& p, const double* b, double* lam, con
     TVD_TRY(cast_d2f(b, f.r, n, s, sc));
     TVD_TRY(fill_zero_f(f.x, n, s));
     TVD_TRY(cg_restart<float>(p, f.r, st, std::max(target, delta2 * rr_ref) * sc * sc, maxit, 0, s));
-    for (;;) {
+    // one chunk: 2 kChunk iterations of the Jacobian CG on stream q
+    auto chunk = [&](cudaStream_t q) -> tvd_status {
         for (int k = 0; k < 2 * kChunk; ++k) {
             switch (p.pc) {
-                case TVD_PC_NONE: TVD_TRY(cg_simple_precond<float>(p, f.r, nullptr, f.z, st, s)); break;
-                case TVD_PC_DIAG: TVD_TRY(cg_simple_precond<float>(p, f.r, f.dinv, f.z, st, s)); break;
-                default: TVD_TRY(precond_solve<float>(p, f, f.r, f.z, st, s, f.x)); break;
+                case TVD_PC_NONE: TVD_TRY(cg_simple_precond<float>(p, f.r, nullptr, f.z, st, q)); break;
+                case TVD_PC_DIAG: TVD_TRY(cg_simple_precond<float>(p, f.r, f.dinv, f.z, st, q)); break;
+                default: TVD_TRY(precond_solve<float>(p, f, f.r, f.z, st, q, f.x)); break;
             }
-            TVD_TRY(blur_pupdate<float>(p, f, f.z, f.p, f.p2, f.t, st, s));
-            TVD_TRY(blur_apply<float>(p, f, true, f.t, f.q, s, st));
-            TVD_TRY(hess_add<float>(p, f.q, f.p, f.p2, f.w, grf, gcf, alpha, st, s));
-            if (!transform_pc) TVD_TRY(cg_xrupdate<float>(p, f.x, f.r, f.p, f.p2, f.q, st, s));
+            TVD_TRY(blur_pupdate<float>(p, f, f.z, f.p, f.p2, f.t, st, q));
+            TVD_TRY(blur_apply<float>(p, f, true, f.t, f.q, q, st));
+            TVD_TRY(hess_add<float>(p, f.q, f.p, f.p2, f.w, grf, gcf, alpha, st, q));
+            if (!transform_pc) TVD_TRY(cg_xrupdate<float>(p, f.x, f.r, f.p, f.p2, f.q, st, q));
         }
-        TVD_TRY(read_state<float>(p, s));
+        return TVD_OK;
+    };
+    // the device-driven loop, as for the FP step's CG: the chunk in a while node, built for
+    // this solve (its operands grf, gcf and alpha belong to the call) and released on return
+    struct LoopGraph {
+        cudaGraphExec_t exec = nullptr;
+        int kernels = 0;
+        ~LoopGraph() {
+            if (exec) cudaGraphExecDestroy(exec);
+        }
+    } loop;
+    if (!profiling_enabled() && device_loop_enabled())
+        build_while_graph(
+            p,
+            [&](cudaStream_t q, cudaGraphConditionalHandle hc) -> tvd_status {
+                TVD_TRY(chunk(q));
+                return cg_loop_cond(hc, st, q);
+            },
+            &loop.exec, &loop.kernels);
+    for (;;) {
+        if (loop.exec) {
+            TVD_TRY(cg_loop_arm(st, maxit / (2 * kChunk) + 3, s));
+            TVD_CUDA_TRY(cudaGraphLaunch(loop.exec, s));
+            TVD_TRY(read_state<float>(p, s));
+            count_launches(p.hstate->loops * loop.kernels);
+        } else {
+            TVD_TRY(chunk(s));
+            TVD_TRY(read_state<float>(p, s));
+        }
         const CgState h = *p.hstate;
         *iters_out = h.iter;
         if (h.status == TVD_ETIMEOUT) return timeout_exit(p, s);

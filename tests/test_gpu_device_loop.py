@@ -100,3 +100,24 @@ def test_method_change_drops_captured_chunks(tdev):
         u, st = plan.deblur(vt, 1e-3, 1e-2, **kw)
     assert list(st["inner_iters"]) == list(st_ref["inner_iters"])
     assert float((u - u_ref).norm()) <= 1e-12 * float(u_ref.norm())
+
+
+def test_adjoint_device_loop_equals_host_polled_loop(tdev):
+    """The MIXED Jacobian CG of the adjoint (and of the Newton steps) runs through the same loop."""
+    torch, pkg, dev = tdev
+    h, v = _observation(96, 33)
+    vt = torch.tensor(v, device=dev)
+    out = []
+    for loop in (False, True):
+        os.environ["TVD_CG_DEVICE_LOOP"] = "1" if loop else "0"
+        try:
+            with pkg.Plan(96, 96, h, bc="ar", pc="dfast", mode="mixed") as plan:
+                u, _ = plan.deblur(vt, 1e-3, 1e-2, max_outer=6, inner_tol=1e-8, inner_maxit=5000)
+                lam, da, db, dh, ast = plan.adjoint(u, vt, 1e-3, 1e-2, 2.0 * (u - vt), tol=1e-10, maxit=5000)
+                out.append((lam.clone(), da, db, np.array(dh), ast))
+        finally:
+            os.environ.pop("TVD_CG_DEVICE_LOOP", None)
+    (l0, a0, b0, h0, s0), (l1, a1, b1, h1, s1) = out
+    assert s0["status"] == s1["status"] and s0["iters"] == s1["iters"] > 0
+    assert torch.equal(l0, l1)
+    assert (a0, b0) == (a1, b1) and np.array_equal(h0, h1)
