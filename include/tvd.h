@@ -292,6 +292,11 @@ tvd_status tvd_plan_tune(tvd_plan plan, int reps, tvd_tune_report* report, void*
  * *iters receives the CG iterations (products with A) and *relres the final
  * relative residual; both may be NULL. In MIXED mode the residual used for the
  * stopping test is recomputed in double after each float CG sweep.
+ * Synchronises `stream`. The iterations run as a captured chunk of four CG
+ * iterations inside a CUDA-graph while node whose condition the device sets
+ * from the solver state, so the host reads the state once per solve (once
+ * per float sweep in MIXED mode); with TVD_CG_DEVICE_LOOP=0 when the chunk is
+ * captured, the host instead relaunches the chunk and polls after each one.
  * Returns TVD_ENOCONV if tol was not reached within maxit iterations.
  */
 tvd_status pcg_solve(tvd_plan plan, const void* u_lag, double alpha, double beta,
