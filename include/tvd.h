@@ -262,7 +262,8 @@ int tvd_plan_gemm_tile(tvd_plan plan);
  * (direct launches while per-kernel profiling is on), and the graph is
  * replayed `reps` times (0: 3) after one warm-up replay, the fastest replay
  * counting. The choice outlasts later tvd_plan_set_method calls; a later
- * tvd_plan_set_transform to GEMM keeps its tile width and fold choice.
+ * tvd_plan_set_transform to GEMM keeps the chosen tile width and fold choice
+ * (after the FFT form won, the default rules of the GEMM form apply).
  * Afterwards the plan needs tau_precond_setup again before tau_precond_solve
  * (tv_deblur and the solvers set themselves up). Allocates and frees three
  * image-sized scratch vectors; synchronises `stream` and the device.

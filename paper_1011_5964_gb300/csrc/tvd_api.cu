@@ -907,7 +907,8 @@ tvd_status tvd_plan_tune(tvd_plan plan, int reps, tvd_tune_report* report, void*
     cudaStream_t s = (cudaStream_t)stream;
     if (reps == 0) reps = 3;
     tvd_tune_report rep{};
-    const int cand[TVD_TUNE_MAX][3] = {{TVD_TRANSFORM_FFT, 0, 0},
+    // {transform, tile width, fold}; the FFT form leaves the product rules at their defaults
+    const int cand[TVD_TUNE_MAX][3] = {{TVD_TRANSFORM_FFT, 0, -1},
                                        {TVD_TRANSFORM_GEMM, 64, 0},
                                        {TVD_TRANSFORM_GEMM, 128, 0},
                                        {TVD_TRANSFORM_GEMM, 64, 1}};
@@ -944,7 +945,7 @@ tvd_status tvd_plan_tune(tvd_plan plan, int reps, tvd_tune_report* report, void*
         if (st == TVD_OK) st = tune_time(*plan, r, z, reps, &us, s);
         rep.transform[k] = cand[k][0];
         rep.tile_n[k] = cand[k][1];
-        rep.folded[k] = cand[k][2];
+        rep.folded[k] = cand[k][2] == 1 ? 1 : 0;
         rep.us_per_solve[k] = us;
         rep.count = k + 1;
         if (st == TVD_OK && us < rep.us_per_solve[rep.chosen]) rep.chosen = k;
